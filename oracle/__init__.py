@@ -1,0 +1,9 @@
+"""Plain FP64 CPU oracle of the local-f_NL shell round trip (test infrastructure).
+
+This package is test infrastructure, not part of the product: only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and reference legs
+may import it.  It shares no code with the CUDA library and never imports it.
+
+Parity status of each function is stated in ``oracle/fnl_oracle.py``.
+"""
+from .fnl_oracle import *  # noqa: F401,F403

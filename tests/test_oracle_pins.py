@@ -1,0 +1,455 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a library routine (numpy, scipy,
+mpmath), a closed form (Gaunt integrals from Racah's 3j formula, Parseval,
+the addition theorem), an exact symmetry of the method, or a seeded ensemble
+statistic.  The mutation tests at the end plant mistakes in the oracle (on the
+CPU) and check that at least one pin catches each of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.wigner import gaunt, wigner3j
+
+# ---------------------------------------------------------------------------
+# Grid and Legendre functions
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 25, 49, 100, 385, 769])
+def test_gauss_legendre_matches_numpy_and_integrates_polynomials(n):
+    x, w = O.gauss_legendre(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.all(np.diff(x) < 0)  # north to south
+    assert np.max(np.abs(x - xr[::-1])) < 1e-14
+    # numpy's own weights are only good to ~1e-9 at n ~ 1000; the moment test below is the sharp pin
+    assert np.max(np.abs(w - wr[::-1]) / wr[::-1]) < 5e-9
+    for k in range(0, 2 * n, max(1, (2 * n) // 12)):
+        exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+        assert abs(np.dot(w, x ** k) - exact) < 1e-13
+
+
+def test_lambda_matches_scipy_spherical_harmonics_low_l():
+    sp = pytest.importorskip("scipy.special")
+    L = 40
+    x, _ = O.gauss_legendre(31)
+    theta = np.arccos(x)
+    tab = O.lambda_table(L, x)
+    for m in range(L + 1):
+        for l in range(m, L + 1):
+            ref = sp.sph_harm_y(l, m, theta, 0.0).real  # includes the Condon-Shortley phase
+            assert np.max(np.abs(tab[m][l - m] - ref)) < 1e-13, (l, m)
+
+
+def test_lambda_high_l_matches_mpmath():
+    # arbitrary-precision associated Legendre function (hypergeometric series) at l up to 1024
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    L = 1024
+    cases = [(1024, 0, 0.7), (1024, 0, 0.9999), (1024, 7, 0.1), (1024, 300, 0.7), (1024, 900, 0.1),
+             (662, 300, 0.7), (1000, 1000, 0.1), (1024, 1000, 0.1), (700, 650, 0.5)]
+    for l, m, x in cases:
+        col = O.lambda_column(m, L, np.array([x]))
+        ref = mp.sqrt((2 * l + 1) / (4 * mp.pi) * mp.factorial(l - m) / mp.factorial(l + m)) \
+            * mp.legenp(l, m, x, maxprec=200000)  # legenp includes the Condon-Shortley phase
+        ref = float(ref)
+        assert abs(col[l - m, 0] - ref) <= 1e-12 * max(abs(ref), 1e-3), (l, m, x)
+
+
+@pytest.mark.parametrize("m", [0, 1, 64, 511, 900, 1024])
+def test_lambda_orthonormal_on_gl_grid_lmax1024(m):
+    # 2 pi sum_j w_j lambda_lm lambda_l'm = delta_ll' for n_theta >= l_max + 1
+    L = 1024
+    x, w = O.gauss_legendre(1537)
+    lam = O.lambda_column(m, L, x)
+    M = 2.0 * math.pi * (lam * w) @ lam.T
+    assert np.max(np.abs(M - np.eye(M.shape[0]))) < 2e-13
+
+
+def test_addition_theorem_on_grid():
+    # lambda_l0^2 + 2 sum_{m>0} lambda_lm^2 = (2l+1)/(4 pi) at every ring
+    L = 96
+    g = O.Grid(L, 145, 290)
+    for l in (0, 1, 17, 96):
+        s = g.lam(0)[l] ** 2 + 2.0 * sum(g.lam(m)[l - m] ** 2 for m in range(1, l + 1))
+        assert np.max(np.abs(s - (2 * l + 1) / (4 * math.pi))) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Spherical harmonic transforms
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("lmax,nt,nph", [(8, 9, 17), (32, 49, 100), (64, 65, 130)])
+def test_analysis_of_synthesis_is_identity(lmax, nt, nph):
+    g = O.Grid(lmax, nt, nph)
+    a = W.random_alm(lmax, 3, seed=lmax)
+    b = O.analysis(O.synthesis(a, g), g)
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a)) * 10
+
+
+def test_synthesis_matches_direct_sum_of_spherical_harmonics():
+    sp = pytest.importorskip("scipy.special")
+    L, nt, nph = 6, 7, 13
+    g = O.Grid(L, nt, nph)
+    a = W.random_alm(L, 1, seed=3)[:, 0]
+    f = O.synthesis(a, g)[0]
+    theta = np.arccos(g.x)[:, None]
+    phi = 2 * math.pi * np.arange(nph)[None, :] / nph
+    ref = np.zeros((nt, nph))
+    for l in range(L + 1):
+        for m in range(-l, l + 1):
+            alm = a[W.alm_index(l, abs(m), L)]
+            if m < 0:
+                alm = (-1) ** m * np.conj(alm)
+            ref += (alm * sp.sph_harm_y(l, m, theta, phi)).real
+    assert np.max(np.abs(f - ref)) < 1e-13
+
+
+def _gaunt_square(a, L, mu):
+    """int (f^2 - mu) Y*_lm dOmega for f = sum a_lm Y_lm, by Gaunt sums (Eq. 22 prefactor)."""
+    def A(l, m):
+        v = a[W.alm_index(l, abs(m), L)]
+        return v if m >= 0 else (-1) ** m * np.conj(v)
+    out = np.zeros(W.n_alm(L), dtype=complex)
+    for l in range(L + 1):
+        for m in range(l + 1):
+            s = 0j
+            for l1 in range(L + 1):
+                for l2 in range(abs(l - l1), min(L, l + l1) + 1):
+                    if (l1 + l2 + l) % 2:
+                        continue
+                    for m1 in range(-l1, l1 + 1):
+                        m2 = m - m1
+                        if abs(m2) > l2:
+                            continue
+                        s += A(l1, m1) * A(l2, m2) * (-1) ** m * gaunt(l1, l2, l, m1, m2, -m)
+            if l == 0:
+                s -= math.sqrt(4 * math.pi) * mu
+            out[W.alm_index(l, m, L)] = s
+    return out
+
+
+def _oracle_square(a, L, mu):
+    nt, nph = W.grid_for_lmax(L)
+    g = O.Grid(L, nt, nph)
+    return O.phi_nonlinear(a[:, None], np.array([mu]), g)[:, 0]
+
+
+@pytest.mark.parametrize("L,seed", [(2, 1), (5, 2), (8, 3)])
+def test_square_matches_gaunt_brute_force(L, seed):
+    a = W.random_alm(L, 1, seed=seed)[:, 0]
+    mu = 0.37
+    got = _oracle_square(a, L, mu)
+    ref = _gaunt_square(a, L, mu)
+    assert np.max(np.abs(got - ref)) < 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_wigner3j_against_sympy_and_orthogonality():
+    # sum_{l3, m3} (2 l3 + 1) (l1 l2 l3; m1 m2 m3)^2 = 1
+    for l1, l2, m1, m2 in [(3, 4, 1, -2), (5, 5, 0, 0), (7, 2, -3, 1)]:
+        s = sum((2 * l3 + 1) * wigner3j(l1, l2, l3, m1, m2, -m1 - m2) ** 2
+                for l3 in range(abs(l1 - l2), l1 + l2 + 1))
+        assert abs(s - 1.0) < 1e-14
+    wig = pytest.importorskip("sympy.physics.wigner")
+    for args in [(2, 3, 4, 1, -1, 0), (6, 4, 4, -3, 2, 1), (8, 8, 6, 0, 0, 0), (5, 6, 7, 2, 3, -5)]:
+        assert abs(wigner3j(*args) - float(wig.wigner_3j(*args))) < 1e-15
+
+
+def test_parseval_monopole_identity():
+    # Phi_NL,00 = (sum_l [|a_l0|^2 + 2 sum_{m>0} |a_lm|^2] - 4 pi mu) / sqrt(4 pi)
+    L = 48
+    nt, nph = W.grid_for_lmax(L)
+    g = O.Grid(L, nt, nph)
+    a = W.random_alm(L, 4, seed=9)
+    mu = np.array([0.0, 0.5, 1.3, 2.0])
+    out = O.phi_nonlinear(a, mu, g)
+    l, m = W.alm_lm(L)
+    wgt = np.where(m == 0, 1.0, 2.0)[:, None]
+    power = (wgt * np.abs(a) ** 2).sum(axis=0)
+    ref = (power - 4 * math.pi * mu) / math.sqrt(4 * math.pi)
+    assert np.max(np.abs(out[0] - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_single_monopole_mode():
+    L = 16
+    nt, nph = W.grid_for_lmax(L)
+    g = O.Grid(L, nt, nph)
+    a = np.zeros((W.n_alm(L), 1), dtype=complex)
+    c, mu = 1.7, 0.05
+    a[0, 0] = c
+    out = O.phi_nonlinear(a, np.array([mu]), g)[:, 0]
+    assert abs(out[0] - (c * c / math.sqrt(4 * math.pi) - math.sqrt(4 * math.pi) * mu)) < 1e-14
+    assert np.max(np.abs(out[1:])) < 1e-14
+
+
+def test_z_rotation_equivariance():
+    L = 24
+    nt, nph = W.grid_for_lmax(L)
+    g = O.Grid(L, nt, nph)
+    a = W.random_alm(L, 2, seed=11)
+    _, m = W.alm_lm(L)
+    psi = 0.7371  # not a grid angle: equivariance holds because the projection is exact
+    rot = np.exp(-1j * m * psi)[:, None]
+    mu = np.array([0.2, 0.1])
+    out = O.phi_nonlinear(a, mu, g)
+    out_r = O.phi_nonlinear(a * rot, mu, g)
+    assert np.max(np.abs(out_r - out * rot)) < 1e-12 * np.max(np.abs(out))
+
+
+def test_parity_equivariance():
+    L = 24
+    nt, nph = W.grid_for_lmax(L)
+    g = O.Grid(L, nt, nph)
+    a = W.random_alm(L, 2, seed=12)
+    l, m = W.alm_lm(L)
+    par = ((-1.0) ** (l + m))[:, None]
+    mu = np.array([0.2, 0.1])
+    out = O.phi_nonlinear(a, mu, g)
+    out_p = O.phi_nonlinear(a * par, mu, g)
+    assert np.max(np.abs(out_p - out * par)) < 1e-12 * np.max(np.abs(out))
+
+
+# ---------------------------------------------------------------------------
+# Radial statistics
+# ---------------------------------------------------------------------------
+
+
+def test_spherical_jn_matches_scipy():
+    sp = pytest.importorskip("scipy.special")
+    xs = np.concatenate([np.linspace(1.3, 40, 60), np.linspace(40, 1200, 80), np.linspace(1200, 4500, 40)])
+    J = O.spherical_jn_table(1024, xs)
+    for l in (0, 1, 2, 7, 50, 333, 800, 1024):
+        ref = sp.spherical_jn(l, xs)
+        scale = np.maximum(np.abs(ref), 1e-6 * np.max(np.abs(ref)))
+        ok = np.abs(ref) > 1e-250
+        assert np.max(np.abs(J[l][ok] - ref[ok]) / scale[ok]) < 5e-12, l
+        assert np.all(np.abs(J[l][~ok]) < 1e-240)
+
+
+def test_covariance_matches_scipy_brute_force():
+    sp = pytest.importorskip("scipy.special")
+    L, nr = 6, 4
+    r, _ = W.radial_grid(nr)
+    cp = W.COV
+    C = O.covariance(L, r, cp.A, cp.ns, cp.kmin, cp.kmax, cp.nk)
+    k = np.linspace(cp.kmin, cp.kmax, cp.nk)
+    h = k[1] - k[0]
+    wk = np.full(cp.nk, h)
+    wk[[0, -1]] = h / 2
+    for l in range(L + 1):
+        J = sp.spherical_jn(l, k[:, None] * r[None, :])
+        ref = (2 / math.pi) * np.einsum("k,ki,kj->ij", wk * k ** 2 * cp.A * k ** (cp.ns - 4), J, J)
+        assert np.max(np.abs(C[l] - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_filters_are_cholesky_factors():
+    L, nr = 12, 16
+    r, _ = W.radial_grid(nr)
+    cp = W.COV
+    C = O.covariance(L, r, cp.A, cp.ns, cp.kmin, cp.kmax, cp.nk)
+    K = O.filters(C, cp.jitter_rel)
+    for l in range(L + 1):
+        assert np.allclose(np.triu(K[l], 1), 0.0)
+        assert np.all(np.diag(K[l]) > 0)
+        eps = cp.jitter_rel * np.mean(np.diag(C[l]))
+        assert np.max(np.abs(K[l] @ K[l].T - C[l] - eps * np.eye(nr))) < 1e-12 * np.max(np.abs(C[l]))
+
+
+def test_mu_is_pixel_variance_of_the_ensemble():
+    # mu_i = <Phi_L^2(r_i, n)>: compare with the sample mean of f^2 over pixels and draws
+    L, nr, nreal = 12, 3, 96
+    K = W.random_lower_filters(L, nr, seed=5, scale=1.0)
+    mu = O.mu_ensemble(K)
+    nt, nph = W.grid_for_lmax(L)
+    g = O.Grid(L, nt, nph)
+    acc = np.zeros(nr)
+    samples = []
+    for s in range(nreal):
+        phi = O.phi_linear(K, W.gaussian_noise(L, nr, seed=1000 + s))
+        f = O.synthesis(phi, g)
+        # area-weighted sky mean of f^2 for each shell
+        v = np.einsum("sjk,j->s", f * f, g.w) * (2 * math.pi / nph) / (4 * math.pi)
+        samples.append(v)
+    samples = np.array(samples)
+    mean = samples.mean(axis=0)
+    err = samples.std(axis=0, ddof=1) / math.sqrt(nreal)
+    assert np.all(np.abs(mean - mu) < 5 * err)
+
+
+# ---------------------------------------------------------------------------
+# Noise generator
+# ---------------------------------------------------------------------------
+
+
+def test_philox_matches_numpy_bit_generator():
+    rng = np.random.default_rng(77)
+    for _ in range(8):
+        ctr = [int(v) for v in rng.integers(0, 2 ** 63, size=4, dtype=np.int64)]
+        key = [int(v) for v in rng.integers(0, 2 ** 63, size=2, dtype=np.int64)]
+        # numpy's Philox increments its counter before producing each 4-word block
+        bg = np.random.Philox(counter=[ctr[0] - 1, ctr[1], ctr[2], ctr[3]], key=key)
+        ref = bg.random_raw(4)
+        got = O.philox4x64(*[np.uint64(c) for c in ctr], np.uint64(key[0]), np.uint64(key[1]))
+        assert [int(v) for v in got] == [int(v) for v in ref]
+
+
+def test_philox_noise_statistics():
+    st = pytest.importorskip("scipy.stats")
+    L, nr = 64, 16
+    n = O.philox_noise(L, nr, seed=1, realisation=0)
+    _, m = W.alm_lm(L)
+    m0 = n[:, m == 0]
+    mp = n[:, m > 0]
+    assert np.all(m0.imag == 0)
+    assert st.kstest(m0.real.ravel(), "norm").pvalue > 1e-3
+    assert st.kstest(math.sqrt(2) * mp.real.ravel(), "norm").pvalue > 1e-3
+    assert st.kstest(math.sqrt(2) * mp.imag.ravel(), "norm").pvalue > 1e-3
+    assert abs(np.mean(np.abs(mp) ** 2) - 1.0) < 0.02
+    # distinct shells, seeds and realisations draw distinct numbers
+    n2 = O.philox_noise(L, nr, seed=1, realisation=1)
+    n3 = O.philox_noise(L, nr, seed=2, realisation=0)
+    assert abs(np.corrcoef(n.real.ravel(), n2.real.ravel())[0, 1]) < 0.02
+    assert abs(np.corrcoef(n.real.ravel(), n3.real.ravel())[0, 1]) < 0.02
+    assert abs(np.corrcoef(n[0].real, n[1].real)[0, 1]) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Whole generator
+# ---------------------------------------------------------------------------
+
+
+def _small_setup(L=12, nr=6, seed=3):
+    r, w = W.radial_grid(nr)
+    aT, aE = W.transfer_kernels(L, r)
+    cp = W.COV
+    K = O.filters(O.covariance(L, r, cp.A, cp.ns, cp.kmin, cp.kmax, cp.nk), cp.jitter_rel)
+    nt, nph = W.grid_for_lmax(L)
+    return r, w, aT, aE, K, O.Grid(L, nt, nph)
+
+
+def test_linearity_in_fnl():
+    r, w, aT, aE, K, g = _small_setup()
+    n = O.philox_noise(12, 6, seed=1, realisation=0)
+    a0 = O.generate(K, n, g, r, w, aT, aE, 0.0)
+    a1 = O.generate(K, n, g, r, w, aT, aE, 37.5)
+    for X in ("T", "E"):
+        d = a1["a" + X] - a0["a" + X]
+        assert np.max(np.abs(d - 37.5 * a0["aNL" + X])) < 1e-12 * np.max(np.abs(d))
+
+
+def test_fnl0_power_spectrum_matches_closed_form():
+    # Cov(a^X_L,lm, a^Y_L,lm) = q^X_l^T K_l K_l^T q^Y_l (Eq. 5 with Eq. 9); chi^2 over l
+    L, nr, nreal = 12, 6, 64
+    r, w, aT, aE, K, g = _small_setup(L, nr)
+    qT = O.quadrature_weights(r, w, aT)
+    qE = O.quadrature_weights(r, w, aE)
+    l, m = W.alm_lm(L)
+    est = {"TT": np.zeros(L + 1), "EE": np.zeros(L + 1)}
+    for s in range(nreal):
+        n = O.philox_noise(L, nr, seed=100 + s, realisation=0)
+        phiL = O.phi_linear(K, n)
+        for X, q in (("T", qT), ("E", qE)):
+            a = O.radial_quadrature(phiL, q)
+            p = np.abs(a) ** 2 * np.where(m == 0, 1.0, 2.0)
+            est[X + X] += np.bincount(l, weights=p, minlength=L + 1) / (2 * l_range(L) + 1)
+    chi2, dof = 0.0, 0
+    for X, q in (("T", qT), ("E", qE)):
+        th = np.einsum("li,lij,lkj,lk->l", q, K, K, q)
+        for ll in range(1 if X == "E" else 0, L + 1):
+            mean = est[X + X][ll] / nreal
+            var = 2 * th[ll] ** 2 / ((2 * ll + 1) * nreal)  # chi^2 with (2l+1) dof per draw
+            chi2 += (mean - th[ll]) ** 2 / var
+            dof += 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof)
+
+
+def l_range(L):
+    return np.arange(L + 1, dtype=float)
+
+
+def test_fnl0_linear_part_is_the_filtered_noise_projection():
+    # a^X_L = v^X . n with v^X_l = K_l^T q^X_l: the quadrature of Eq. 5 applied to Eq. 9
+    r, w, aT, aE, K, g = _small_setup()
+    n = O.philox_noise(12, 6, seed=5, realisation=2)
+    out = O.generate(K, n, g, r, w, aT, aE, 0.0)
+    q = O.quadrature_weights(r, w, aT)
+    l, m = W.alm_lm(12)
+    nn = n.copy()
+    nn[:, m == 0] = nn[:, m == 0].real
+    v = np.einsum("lij,li->lj", K, q)
+    ref = np.einsum("ij,ji->i", v[l], nn)
+    assert np.max(np.abs(out["aLT"] - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each must be caught by a pin above
+# ---------------------------------------------------------------------------
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    L = 5
+    a = W.random_alm(L, 1, seed=21)[:, 0]
+    mu = 0.2
+    ref = _gaunt_square(a, L, mu)
+
+    def gaunt_pin_fails():
+        got = _oracle_square(a, L, mu)
+        return np.max(np.abs(got - ref)) > 1e-8
+
+    def identity_pin_fails():
+        g = O.Grid(8, 9, 17)
+        aa = W.random_alm(8, 1, seed=2)
+        return np.max(np.abs(O.analysis(O.synthesis(aa, g), g) - aa)) > 1e-8
+
+    def direct_sum_pin_fails():
+        try:
+            test_synthesis_matches_direct_sum_of_spherical_harmonics()
+        except AssertionError:
+            return True
+        return False
+
+    assert not gaunt_pin_fails() and not identity_pin_fails() and not direct_sum_pin_fails()
+    mod = O.fnl_oracle
+
+    # 1. Condon-Shortley phase dropped from lambda_lm.  The squared-field projection cannot
+    # see it (the phase is a rotation by pi about z, and squaring commutes with rotations),
+    # so it is the map-level pin that must catch it.
+    orig_col = mod.lambda_column
+    monkeypatch.setattr(mod, "lambda_column", lambda m, lmax, x, mm=None: orig_col(m, lmax, x, mm) * (-1) ** m)
+    assert direct_sum_pin_fails() and not gaunt_pin_fails()
+    monkeypatch.undo()
+
+    # 2. <Phi_L^2> added instead of subtracted (Eq. 2)
+    orig_nl = O.phi_nonlinear
+    monkeypatch.setattr(O, "phi_nonlinear", lambda p, mu_, g: orig_nl(p, -np.asarray(mu_), g))
+    assert gaunt_pin_fails()
+    monkeypatch.undo()
+
+    # 3. GL weights replaced by equal weights in the analysis
+    orig_gl = mod.gauss_legendre
+    monkeypatch.setattr(mod, "gauss_legendre", lambda n: (orig_gl(n)[0], np.full(n, 2.0 / n)))
+    assert gaunt_pin_fails() and identity_pin_fails()
+    monkeypatch.undo()
+
+    # 4. the factor 2 of the m > 0 terms dropped from the synthesis
+    def half_syn(alm, grid):
+        alm = np.asarray(alm).reshape(np.asarray(alm).shape[0], -1)
+        a0 = np.zeros_like(alm)
+        a0[: grid.lmax + 1] = alm[: grid.lmax + 1]
+        return 0.5 * (orig_syn(alm, grid) + orig_syn(a0, grid))
+    orig_syn = O.synthesis
+    monkeypatch.setattr(O, "synthesis", half_syn)
+    monkeypatch.setattr(mod, "synthesis", half_syn)
+    assert gaunt_pin_fails() and identity_pin_fails()
+    monkeypatch.undo()
+
+    # 5. wrong sign of the phase in the forward DFT of the analysis
+    orig_rfft = np.fft.rfft
+    monkeypatch.setattr(mod.np.fft, "rfft", lambda x, axis=-1: np.conj(orig_rfft(x, axis=axis)))
+    assert identity_pin_fails()
+    monkeypatch.undo()
