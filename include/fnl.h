@@ -1,0 +1,196 @@
+/*
+ * fnl.h -- C ABI of libfnl: the local-f_NL a_lm generator of Elsner & Wandelt,
+ * "Improved simulation of non-Gaussian temperature and polarization CMB maps",
+ * run on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (Sect. 2, recipe steps (i)-(v)):
+ *   (i)   Phi_L,lm(r_i) = sum_j K_l[i,j] n_lm(r_j)                 Eq. 9, K_l K_l^T = P_Phi,l (Eq. 7)
+ *   (ii)  per shell r_i, synthesis of Phi_L on a Gauss-Legendre ring grid
+ *   (iii) Phi_NL = Phi_L^2 - <Phi_L^2>                              Eq. 2
+ *   (iv)  per shell, analysis of Phi_NL back to harmonic space
+ *   (v)   a^X_lm = sum_i w_i r_i^2 alpha^X_l(r_i) Phi_lm(r_i)       Eq. 5, X in {T, E}
+ *         a^X = a^X_L + f_NL a^X_NL                                  Eq. 3
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Spherical harmonics Y_lm(theta, phi) = lambda_lm(cos theta) e^{i m phi}, orthonormal,
+ *    Condon-Shortley phase.  Fields are real, so only m >= 0 is stored.
+ *  - a_lm layout ("m-major triangle"): entry (l, m), 0 <= m <= l <= lmax, sits at
+ *        idx(l, m) = m (2 lmax + 1 - m) / 2 + l,   nalm = (lmax + 1)(lmax + 2) / 2,
+ *    each entry a complex128 stored as two doubles (re, im).
+ *  - Per-shell coefficient arrays ("phi" arrays) are [nalm][nr][2] doubles: shell index
+ *    innermost.  Noise arrays are [nr][nalm][2] doubles (shell outermost).
+ *  - Maps are [nr][ntheta][nphi] doubles: ring j at x_j = cos theta_j, Gauss-Legendre nodes
+ *    ordered north to south, phi_k = 2 pi k / nphi.
+ *  - Pointers documented "device" must be device memory of the device the shells object
+ *    was made on; "host" pointers are ordinary host memory.  The caller owns every buffer
+ *    it passes.  The library owns only what fnl_make_shells allocates (tables and the
+ *    scratch used by the path), freed by fnl_shells_destroy.
+ *  - Every call except fnl_make_shells and fnl_shells_destroy is asynchronous on the
+ *    caller's CUDA stream (`stream`, a cudaStream_t; NULL = legacy default stream),
+ *    allocates nothing and does not synchronise.  Calls that share one shells object
+ *    share its scratch: they must not overlap on the GPU (use one stream, or order them).
+ *  - Errors: every call returns an fnl_status; on failure fnl_last_error() returns a
+ *    message (thread-local, valid until the next call on that thread).  Argument
+ *    errors are detected on the host before anything is launched.  No C++ exception
+ *    crosses this boundary.
+ */
+#ifndef FNL_H
+#define FNL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fnl_shells fnl_shells; /* opaque: device tables + scratch for one configuration */
+
+typedef enum {
+  FNL_OK = 0,
+  FNL_EINVAL = 1,       /* invalid argument (size, pointer, grid) */
+  FNL_ENOMEM = 2,       /* device or host allocation failed */
+  FNL_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+  FNL_EUNSUPPORTED = 4, /* valid request this build or device cannot run */
+  FNL_ETIMEOUT = 5      /* a bounded device-side wait expired */
+} fnl_status;
+
+typedef enum {
+  FNL_FP64 = 0,   /* every step in FP64 (SIMT DFMA) */
+  FNL_FP32 = 1,   /* Legendre, filter and FFT in FP32 (SIMT); tables and quadrature in FP64 */
+  FNL_BF16X2 = 2, /* Legendre GEMMs on tcgen05 tensor cores, operands split into 2 BF16 terms
+                     (3 products), FP32 accumulation; FFT and filter in FP32; tables and
+                     quadrature in FP64 */
+  FNL_BF16X3 = 3  /* as FNL_BF16X2 with 3 BF16 terms (6 products) */
+} fnl_precision;
+
+/* Description of one configuration (host memory; read during fnl_make_shells only). */
+typedef struct {
+  int lmax;    /* band limit, 1 <= lmax <= 4096 */
+  int nr;      /* number of radial shells, 1 <= nr <= 128 (mixed precisions: nr % 8 == 0) */
+  int ntheta;  /* Gauss-Legendre rings, ntheta >= lmax + 1 (exact square needs (3 lmax + 2) / 2) */
+  int nphi;    /* points per ring, 2/3/5-smooth, nphi >= 2 lmax + 2 (exact square needs 3 lmax + 1) */
+  const double* r;      /* host [nr]: radial nodes r_i (Mpc) */
+  const double* w;      /* host [nr]: radial quadrature weights w_i */
+  const double* K;      /* host [lmax+1][nr][nr] row-major filters K_l (lower triangle used), or
+                           NULL: K_l = chol(C_l + eps_l I) built from the covariance below */
+  double A, ns;         /* P(k) = A k^(ns - 4) (Eq. 7 with Eq. 8) */
+  double kmin, kmax;    /* k range of the trapezoid rule (Mpc^-1) */
+  int nk;               /* number of k points (>= 2) */
+  double jitter_rel;    /* eps_l = jitter_rel * mean(diag C_l) */
+  const double* alphaT; /* host [lmax+1][nr]: alpha^T_l(r_i) (Eq. 6 kernel for temperature) */
+  const double* alphaE; /* host [lmax+1][nr]: alpha^E_l(r_i) (E-mode polarization) */
+  const double* mu;     /* host [nr]: <Phi_L^2(r_i)> of Eq. 2, or NULL: the ensemble value
+                           mu_i = sum_l (2l+1)/(4 pi) (K_l K_l^T)_ii */
+  int prec;             /* fnl_precision */
+} fnl_shell_desc;
+
+/* Library version string. */
+const char* fnl_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* fnl_last_error(void);
+
+/* ---- set-up (S0; Sect. 3: auxiliary data computed once per configuration) ---------- */
+
+/* Build the device tables for `desc` on CUDA device `device`: Gauss-Legendre grid,
+ * lambda_lm(x_j) tables (FP64 three-term recurrence, converted to the precision's
+ * operand format), filters K_l (Eq. 9), quadrature weights q^X_l[i] = w_i r_i^2
+ * alpha^X_l(r_i) (Eq. 5), v^X_l = K_l^T q^X_l, mu_i (Eq. 2), FFT twiddles and the
+ * scratch of the path.  Synchronous; allocates.  *out receives the object. */
+fnl_status fnl_make_shells(const fnl_shell_desc* desc, int device, fnl_shells** out);
+
+/* Free everything fnl_make_shells allocated (NULL is ignored).  Synchronous. */
+void fnl_shells_destroy(fnl_shells* sh);
+
+/* Sizes of a shells object: any pointer may be NULL. */
+fnl_status fnl_shells_info(const fnl_shells* sh, int* lmax, int* nr, int* ntheta, int* nphi,
+                           int* prec, size_t* device_bytes);
+
+/* Copy mu_i (host [nr]) used by the object. */
+fnl_status fnl_shells_mu(const fnl_shells* sh, double* mu_out);
+
+/* ---- the hot path (S1-S5) ---------------------------------------------------------- */
+
+/* One realisation, Sect. 2 steps (i)-(v), entirely on the device.
+ *  seed, realisation: key of the counter-based noise (Philox4x64-10): the noise of shell j
+ *      and entry idx comes from counter (idx, j >> 1, realisation, 0), key (seed, 0);
+ *      Box-Muller of output words (0,1) for even j, (2,3) for odd j; m > 0 entries get
+ *      unit complex variance, m = 0 entries are real N(0, 1).
+ *  fnl:   f_NL of Eq. 1.
+ *  noise: device [nr][nalm][2] explicit n_lm(r_j) (imaginary part of m = 0 ignored), or
+ *      NULL to draw it from (seed, realisation).
+ *  aT, aE:     device [nalm][2]: a^X = a^X_L + f_NL a^X_NL (Eq. 3), or NULL.
+ *  aLT, aLE:   device [nalm][2]: a^X_L (Eq. 5 applied to Phi_L), or NULL.
+ *  aNLT, aNLE: device [nalm][2]: a^X_NL (Eq. 5 applied to Phi_NL), or NULL.
+ * Accumulation of the radial quadrature is FP64 in every precision. */
+fnl_status fnl_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl,
+                        const double* noise, double* aT, double* aE, double* aLT, double* aLE,
+                        double* aNLT, double* aNLE, void* stream);
+
+/* fnl_generate with host outputs: the same path, then the requested results (host
+ * [nalm][2] each, any may be NULL; pinned memory gives asynchronous copies) are copied
+ * device-to-host on `stream`.  The caller synchronises the stream before reading them. */
+fnl_status fnl_generate_host(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl,
+                             double* aT, double* aE, double* aNLT, double* aNLE, void* stream);
+
+/* Step (i) alone: phiL (device [nalm][nr][2]) = K_l n for the noise of fnl_generate
+ * (explicit `noise` or drawn from seed/realisation). */
+fnl_status fnl_filter(const fnl_shells* sh, uint64_t seed, uint64_t realisation,
+                      const double* noise, double* phiL, void* stream);
+
+/* Step (ii) alone: maps (device [nr][ntheta][nphi]) of the nr real fields whose
+ * coefficients are alm (device [nalm][nr][2]; imaginary part of m = 0 ignored). */
+fnl_status fnl_synth(const fnl_shells* sh, const double* alm, double* maps, void* stream);
+
+/* Step (iv) alone: alm (device [nalm][nr][2]) = Gauss-Legendre x DFT projection of maps
+ * (device [nr][ntheta][nphi]) onto Y_lm, l <= lmax. */
+fnl_status fnl_analyse(const fnl_shells* sh, const double* maps, double* alm, void* stream);
+
+/* Steps (ii)-(iv): phiNL (device [nalm][nr][2]) = analysis(synthesis(phiL)^2 - mu). */
+fnl_status fnl_square(const fnl_shells* sh, const double* phiL, double* phiNL, void* stream);
+
+/* Step (v) alone (Eq. 5 and Eq. 3): from phiL and/or phiNL (device [nalm][nr][2], either
+ * may be NULL and then counts as zero) form aT, aE, aLT, aLE, aNLT, aNLE (device
+ * [nalm][2] each, any may be NULL) with f_NL = fnl. */
+fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double* phiNL,
+                          double fnl, double* aT, double* aE, double* aLT, double* aLE,
+                          double* aNLT, double* aNLE, void* stream);
+
+/* ---- per-stage timing -------------------------------------------------------------- */
+
+/* Stages of fnl_generate timed when profiling is on (CUDA events recorded on the
+ * caller's stream between the kernels): 0 noise + filter (step (i)), 1 synthesis
+ * Legendre GEMM (step (ii)), 2 ring DFTs + square (steps (ii)-(iv)), 3 analysis
+ * Legendre GEMM (step (iv)), 4 radial quadrature (step (v)). */
+#define FNL_NSTAGES 5
+
+/* Turn event timing of fnl_generate on with a ring of `slots` calls (1..4096), or off
+ * (slots = 0).  Each profiled call records FNL_NSTAGES + 1 events on its stream; no call
+ * synchronises.  Not thread-safe with a concurrent fnl_generate on the same object. */
+fnl_status fnl_profile_enable(fnl_shells* sh, int slots);
+
+/* ms[0..n-1] (host, n <= FNL_NSTAGES) = stage durations summed over the profiled calls
+ * since the last read (at most `slots` of them, the most recent); *calls (nullable)
+ * receives their number.  Waits for those calls to finish and restarts the count. */
+fnl_status fnl_profile_read(fnl_shells* sh, double* ms, int n, int* calls);
+
+/* ---- host-side set-up helpers (no GPU needed) -------------------------------------- */
+
+/* n-point Gauss-Legendre rule: x (host [n], north to south, x_j = cos theta_j), w (host [n]). */
+fnl_status fnl_gauss_legendre(int n, double* x, double* w);
+
+/* Radial covariance of Eq. 7 on a uniform trapezoid k rule:
+ * C (host [lmax+1][nr][nr]) = (2/pi) sum_k wk k^2 A k^(ns-4) j_l(k r_i) j_l(k r_j). */
+fnl_status fnl_covariance(int lmax, int nr, const double* r, double A, double ns, double kmin,
+                          double kmax, int nk, double* C);
+
+/* K (host [lmax+1][nr][nr], lower triangular) = chol(C_l + jitter_rel mean(diag C_l) I). */
+fnl_status fnl_cholesky_filters(int lmax, int nr, const double* C, double jitter_rel, double* K);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FNL_H */

@@ -425,12 +425,12 @@ def phi_linear(K: np.ndarray, noise: np.ndarray) -> np.ndarray:
     noise [nr, nalm] complex (the imaginary part of m = 0 entries is ignored);
     returns [nalm, nr] complex."""
     L = K.shape[0] - 1
-    noise = np.array(noise, dtype=np.complex128)
-    noise[:, : L + 1] = noise[:, : L + 1].real
-    out = np.empty((noise.shape[1], K.shape[1]), dtype=np.complex128)
+    nt = np.array(np.asarray(noise, dtype=np.complex128).T)  # [nalm, nr]
+    nt[: L + 1, :] = nt[: L + 1, :].real
+    out = np.empty((nt.shape[0], K.shape[1]), dtype=np.complex128)
     for l in range(L + 1):
         rows = alm_index(l, np.arange(l + 1), L)  # (l, m) for m = 0..l
-        out[rows, :] = (K[l] @ noise[:, rows]).T
+        out[rows, :] = nt[rows, :] @ K[l].T
     return out
 
 

@@ -1,0 +1,543 @@
+// C ABI of libfnl: argument validation, set-up of the shells object and the entry points
+// that chain the kernels of the path (Sect. 2, recipe steps (i)-(v)).
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "fnl_internal.cuh"
+
+namespace fnl {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+fnl_status guard(const std::function<void()>& body) {
+  g_last_error.clear();
+  try {
+    body();
+    return FNL_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return FNL_ENOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return FNL_EINVAL;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return FNL_EINVAL;
+  }
+}
+
+// Keeps the caller's current device and restores it on exit.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    FNL_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) FNL_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool smooth235(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+void check_dev_ptr(const void* p, const char* name, bool nullable) {
+  if (!p) {
+    if (!nullable) throw Error(FNL_EINVAL, std::string(name) + " must not be NULL");
+    return;
+  }
+  if (((uintptr_t)p) % 16 != 0) throw Error(FNL_EINVAL, std::string(name) + " must be 16-byte aligned");
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(FNL_EINVAL, std::string(name) + " is not a pointer CUDA knows");
+  }
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    throw Error(FNL_EINVAL, std::string(name) + " must be device memory");
+}
+
+void check_shells(const fnl_shells* sh) {
+  if (!sh) throw Error(FNL_EINVAL, "shells object is NULL");
+}
+
+template <typename T>
+T* dalloc(fnl_shells* sh, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = sizeof(T) * (count ? count : 1);
+  FNL_CUDA(cudaMalloc(&p, bytes));
+  sh->allocations.push_back(p);
+  sh->device_bytes += bytes;
+  return (T*)p;
+}
+
+template <typename T>
+T* upload(fnl_shells* sh, const std::vector<T>& v) {
+  T* p = dalloc<T>(sh, v.size());
+  FNL_CUDA(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return p;
+}
+
+void free_shells(fnl_shells* sh) {
+  if (!sh) return;
+  for (auto& e : sh->ring)
+    if (e) cudaEventDestroy(e);
+  for (void* p : sh->allocations) cudaFree(p);
+  sh->allocations.clear();
+  delete sh;
+}
+
+void validate_desc(const fnl_shell_desc* d) {
+  FNL_REQUIRE(d, "desc is NULL");
+  FNL_REQUIRE(d->lmax >= 1 && d->lmax <= 4096, "lmax must be in [1, 4096]");
+  FNL_REQUIRE(d->nr >= 1 && d->nr <= 128, "nr must be in [1, 128]");
+  FNL_REQUIRE(d->ntheta >= d->lmax + 1, "ntheta must be >= lmax + 1");
+  FNL_REQUIRE(d->nphi >= 2 * d->lmax + 2, "nphi must be >= 2 lmax + 2");
+  FNL_REQUIRE(smooth235(d->nphi), "nphi must be 2/3/5-smooth");
+  FNL_REQUIRE(d->r && d->w, "r and w must not be NULL");
+  FNL_REQUIRE(d->alphaT && d->alphaE, "alphaT and alphaE must not be NULL");
+  FNL_REQUIRE(d->prec >= FNL_FP64 && d->prec <= FNL_BF16X3, "unknown precision");
+  if (!d->K) {
+    FNL_REQUIRE(d->nk >= 2, "nk must be >= 2");
+    FNL_REQUIRE(d->kmin > 0 && d->kmax > d->kmin, "need 0 < kmin < kmax");
+    FNL_REQUIRE(d->A > 0 && std::isfinite(d->ns), "need A > 0 and finite ns");
+    FNL_REQUIRE(d->jitter_rel >= 0, "jitter_rel must be >= 0");
+    for (int i = 0; i < d->nr; ++i) FNL_REQUIRE(d->r[i] > 0, "r_i must be > 0");
+  }
+  const size_t tsize = d->prec == FNL_FP64 ? sizeof(double) : sizeof(float);
+  FNL_REQUIRE(2 * 2 * tsize * (size_t)d->nphi <= 200 * 1024, "nphi too large for the shared-memory ring FFT");
+}
+
+}  // namespace
+}  // namespace fnl
+
+using namespace fnl;
+
+extern "C" {
+
+const char* fnl_version(void) { return "libfnl 0.1 (sm_103a)"; }
+
+const char* fnl_last_error(void) { return g_last_error.c_str(); }
+
+fnl_status fnl_gauss_legendre(int n, double* x, double* w) {
+  return guard([&] {
+    FNL_REQUIRE(n >= 1 && n <= 100000, "n must be in [1, 100000]");
+    FNL_REQUIRE(x && w, "x and w must not be NULL");
+    gauss_legendre(n, x, w);
+  });
+}
+
+fnl_status fnl_covariance(int lmax, int nr, const double* r, double A, double ns, double kmin, double kmax, int nk,
+                          double* C) {
+  return guard([&] {
+    FNL_REQUIRE(lmax >= 0 && lmax <= 4096 && nr >= 1 && nr <= 4096, "bad lmax or nr");
+    FNL_REQUIRE(r && C, "r and C must not be NULL");
+    FNL_REQUIRE(nk >= 2 && kmin > 0 && kmax > kmin, "need nk >= 2 and 0 < kmin < kmax");
+    for (int i = 0; i < nr; ++i) FNL_REQUIRE(r[i] > 0, "r_i must be > 0");
+    covariance(lmax, nr, r, A, ns, kmin, kmax, nk, C);
+  });
+}
+
+fnl_status fnl_cholesky_filters(int lmax, int nr, const double* C, double jitter_rel, double* K) {
+  return guard([&] {
+    FNL_REQUIRE(lmax >= 0 && nr >= 1 && C && K, "bad arguments");
+    cholesky_filters(lmax, nr, C, jitter_rel, K);
+  });
+}
+
+fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out) {
+  fnl_shells* sh = nullptr;
+  fnl_status st = guard([&] {
+    FNL_REQUIRE(out, "out must not be NULL");
+    *out = nullptr;
+    validate_desc(d);
+    if (d->prec == FNL_BF16X2 || d->prec == FNL_BF16X3)
+      throw Error(FNL_EUNSUPPORTED, "tensor-core precisions are not built into this library yet");
+    int ndev = 0;
+    FNL_CUDA(cudaGetDeviceCount(&ndev));
+    FNL_REQUIRE(device >= 0 && device < ndev, "no such CUDA device");
+    DeviceScope scope(device);
+    sh = new fnl_shells;
+    sh->device = device;
+    const int L = d->lmax, nr = d->nr;
+    sh->lmax = L;
+    sh->nr = nr;
+    sh->ntheta = d->ntheta;
+    sh->nphi = d->nphi;
+    sh->prec = d->prec;
+    sh->npairs = (d->ntheta + 1) / 2;
+    sh->C = 2 * nr;
+    sh->nalm = n_alm(L);
+    sh->real_is_double = (d->prec == FNL_FP64);
+    const int np = sh->npairs, C = sh->C;
+    const size_t ts = sh->real_is_double ? sizeof(double) : sizeof(float);
+
+    // ---- problem geometry
+    const int nmp = 2 * (L + 1);
+    sh->K.resize(nmp);
+    sh->KP.resize(nmp);
+    sh->row0.resize(nmp + 1);
+    sh->lam0.resize(nmp + 1);
+    int64_t rows = 0, lams = 0;
+    for (int mp = 0; mp < nmp; ++mp) {
+      const int k = k_of(L, mp / 2, mp % 2);
+      sh->K[mp] = k;
+      sh->KP[mp] = round_up(k, 16);
+      sh->row0[mp] = rows;
+      sh->lam0[mp] = lams;
+      rows += sh->KP[mp];
+      lams += (int64_t)np * sh->KP[mp];
+    }
+    sh->row0[nmp] = rows;
+    sh->lam0[nmp] = lams;
+    sh->rows_total = rows;
+    sh->lam_total = lams;
+
+    // ---- Gauss-Legendre grid (northern half)
+    std::vector<double> xg(d->ntheta), wg(d->ntheta);
+    gauss_legendre(d->ntheta, xg.data(), wg.data());
+    sh->x.assign(xg.begin(), xg.begin() + np);
+    sh->wgl.assign(wg.begin(), wg.begin() + np);
+
+    // ---- filters K_l (Eq. 9)
+    const size_t kk = (size_t)(L + 1) * nr * nr;
+    std::vector<double> Kf(kk);
+    if (d->K) {
+      for (int l = 0; l <= L; ++l)
+        for (int i = 0; i < nr; ++i)
+          for (int j = 0; j < nr; ++j)
+            Kf[((size_t)l * nr + i) * nr + j] = (j <= i) ? d->K[((size_t)l * nr + i) * nr + j] : 0.0;
+    } else {
+      std::vector<double> Cv(kk);
+      covariance(L, nr, d->r, d->A, d->ns, d->kmin, d->kmax, d->nk, Cv.data());
+      cholesky_filters(L, nr, Cv.data(), d->jitter_rel, Kf.data());
+    }
+    for (size_t i = 0; i < kk; ++i) FNL_REQUIRE(std::isfinite(Kf[i]), "filters contain non-finite values");
+
+    // ---- mu (Eq. 2), q^X and v^X (Eq. 5)
+    sh->mu.assign(nr, 0.0);
+    if (d->mu) {
+      for (int i = 0; i < nr; ++i) sh->mu[i] = d->mu[i];
+    } else {
+      for (int l = 0; l <= L; ++l)
+        for (int i = 0; i < nr; ++i) {
+          double s = 0.0;
+          for (int j = 0; j <= i; ++j) s += Kf[((size_t)l * nr + i) * nr + j] * Kf[((size_t)l * nr + i) * nr + j];
+          sh->mu[i] += (2.0 * l + 1.0) / (4.0 * M_PI) * s;
+        }
+    }
+    std::vector<double> qT((size_t)(L + 1) * nr), qE((size_t)(L + 1) * nr), vT(qT.size(), 0.0), vE(qE.size(), 0.0);
+    for (int l = 0; l <= L; ++l)
+      for (int i = 0; i < nr; ++i) {
+        const double f = d->w[i] * d->r[i] * d->r[i];
+        qT[(size_t)l * nr + i] = f * d->alphaT[(size_t)l * nr + i];
+        qE[(size_t)l * nr + i] = f * d->alphaE[(size_t)l * nr + i];
+      }
+    for (int l = 0; l <= L; ++l)
+      for (int i = 0; i < nr; ++i)
+        for (int j = 0; j <= i; ++j) {
+          const double k = Kf[((size_t)l * nr + i) * nr + j];
+          vT[(size_t)l * nr + j] += k * qT[(size_t)l * nr + i];
+          vE[(size_t)l * nr + j] += k * qE[(size_t)l * nr + i];
+        }
+
+    // ---- FFT plan and twiddles e^{-2 pi i k / nphi}
+    sh->fft = make_fft_plan(d->nphi);
+    std::vector<double> tw(2 * (size_t)d->nphi);
+    for (int k = 0; k < d->nphi; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)d->nphi;
+      tw[2 * k] = std::cos(a);
+      tw[2 * k + 1] = -std::sin(a);
+    }
+
+    // ---- SIMT tile lists: synthesis (rows = ring pairs), analysis (rows = degrees)
+    std::vector<Tile> ts_syn, ts_ana;
+    const int ctiles = (C + 63) / 64;
+    for (int mp = 0; mp < nmp; ++mp) {
+      if (sh->K[mp] == 0) continue;
+      for (int rt = 0; rt < (np + 63) / 64; ++rt)
+        for (int ct = 0; ct < ctiles; ++ct) ts_syn.push_back({mp, rt, ct, 0});
+      for (int rt = 0; rt < (sh->K[mp] + 63) / 64; ++rt)
+        for (int ct = 0; ct < ctiles; ++ct) ts_ana.push_back({mp, rt, ct, 0});
+    }
+    sh->n_tiles_syn = (int)ts_syn.size();
+    sh->n_tiles_ana = (int)ts_ana.size();
+
+    // ---- device side
+    sh->d_K = upload(sh, sh->K);
+    sh->d_row0 = upload(sh, sh->row0);
+    sh->d_lam0 = upload(sh, sh->lam0);
+    sh->d_x = upload(sh, sh->x);
+    sh->d_wgl = upload(sh, sh->wgl);
+    sh->d_vT = upload(sh, vT);
+    sh->d_vE = upload(sh, vE);
+    sh->d_qT = upload(sh, qT);
+    sh->d_qE = upload(sh, qE);
+    sh->d_mu = upload(sh, sh->mu);
+    sh->d_tiles_syn = upload(sh, ts_syn);
+    sh->d_tiles_ana = upload(sh, ts_ana);
+    if (sh->real_is_double) {
+      sh->d_Kf = upload(sh, Kf);
+      sh->d_tw = upload(sh, tw);
+    } else {
+      std::vector<float> kf(Kf.begin(), Kf.end()), twf(tw.begin(), tw.end());
+      sh->d_Kf = upload(sh, kf);
+      sh->d_tw = upload(sh, twf);
+    }
+    sh->d_lam = dalloc<unsigned char>(sh, ts * (size_t)sh->lam_total);
+    sh->d_phi = dalloc<unsigned char>(sh, ts * (size_t)sh->rows_total * C);
+    const size_t fg = ts * (size_t)nmp * np * C;
+    sh->d_F = dalloc<unsigned char>(sh, fg);
+    sh->d_G = dalloc<unsigned char>(sh, fg);
+    sh->d_aL = dalloc<double>(sh, 4 * (size_t)sh->nalm);
+    sh->d_aNL = dalloc<double>(sh, 4 * (size_t)sh->nalm);
+    sh->d_aOut = dalloc<double>(sh, 4 * (size_t)sh->nalm);
+    FNL_CUDA(cudaMemset(sh->d_phi, 0, ts * (size_t)sh->rows_total * C));
+    FNL_CUDA(cudaMemset(sh->d_F, 0, fg));
+    FNL_CUDA(cudaMemset(sh->d_G, 0, fg));
+    build_lambda_tables(sh, 0);
+    FNL_CUDA(cudaDeviceSynchronize());
+    *out = sh;
+  });
+  if (st != FNL_OK && sh) free_shells(sh);
+  return st;
+}
+
+void fnl_shells_destroy(fnl_shells* sh) {
+  if (!sh) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(sh->device);
+  cudaDeviceSynchronize();
+  free_shells(sh);
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+fnl_status fnl_shells_info(const fnl_shells* sh, int* lmax, int* nr, int* ntheta, int* nphi, int* prec,
+                           size_t* device_bytes) {
+  return guard([&] {
+    check_shells(sh);
+    if (lmax) *lmax = sh->lmax;
+    if (nr) *nr = sh->nr;
+    if (ntheta) *ntheta = sh->ntheta;
+    if (nphi) *nphi = sh->nphi;
+    if (prec) *prec = sh->prec;
+    if (device_bytes) *device_bytes = sh->device_bytes;
+  });
+}
+
+fnl_status fnl_shells_mu(const fnl_shells* sh, double* mu_out) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(mu_out, "mu_out must not be NULL");
+    for (int i = 0; i < sh->nr; ++i) mu_out[i] = sh->mu[i];
+  });
+}
+
+fnl_status fnl_filter(const fnl_shells* sh, uint64_t seed, uint64_t realisation, const double* noise, double* phiL,
+                      void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    check_dev_ptr(noise, "noise", true);
+    check_dev_ptr(phiL, "phiL", false);
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_filter(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, st);
+  });
+}
+
+fnl_status fnl_synth(const fnl_shells* sh, const double* alm, double* maps, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    check_dev_ptr(alm, "alm", false);
+    check_dev_ptr(maps, "maps", false);
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_alm_to_phi(sh, alm, st);
+    launch_synth_gemm(sh, st);
+    launch_ring_fft(sh, FFT_SYNTH_MAP, nullptr, maps, st);
+  });
+}
+
+fnl_status fnl_analyse(const fnl_shells* sh, const double* maps, double* alm, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    check_dev_ptr(maps, "maps", false);
+    check_dev_ptr(alm, "alm", false);
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_ring_fft(sh, FFT_ANALYSE_MAP, maps, nullptr, st);
+    launch_analysis_gemm(sh, st);
+    launch_phi_to_alm(sh, alm, st);
+  });
+}
+
+fnl_status fnl_square(const fnl_shells* sh, const double* phiL, double* phiNL, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    check_dev_ptr(phiL, "phiL", false);
+    check_dev_ptr(phiNL, "phiNL", false);
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_alm_to_phi(sh, phiL, st);
+    launch_synth_gemm(sh, st);
+    launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);
+    launch_analysis_gemm(sh, st);
+    launch_phi_to_alm(sh, phiNL, st);
+  });
+}
+
+fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double* phiNL, double fnl, double* aT,
+                          double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    check_dev_ptr(phiL, "phiL", true);
+    check_dev_ptr(phiNL, "phiNL", true);
+    for (auto pr : {std::make_pair((const void*)aT, "aT"), std::make_pair((const void*)aE, "aE"),
+                    std::make_pair((const void*)aLT, "aLT"), std::make_pair((const void*)aLE, "aLE"),
+                    std::make_pair((const void*)aNLT, "aNLT"), std::make_pair((const void*)aNLE, "aNLE")})
+      check_dev_ptr(pr.first, pr.second, true);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n2 = 2 * sh->nalm;
+    double* lT = aLT ? aLT : sh->d_aL;
+    double* lE = aLE ? aLE : sh->d_aL + n2;
+    double* nT = aNLT ? aNLT : sh->d_aNL;
+    double* nE = aNLE ? aNLE : sh->d_aNL + n2;
+    if (phiL) launch_quadrature(sh, phiL, 0, 0.0, nullptr, nullptr, nullptr, nullptr, lT, lE, 0, st);
+    else {
+      FNL_CUDA(cudaMemsetAsync(lT, 0, sizeof(double) * n2, st));
+      FNL_CUDA(cudaMemsetAsync(lE, 0, sizeof(double) * n2, st));
+    }
+    if (phiNL) launch_quadrature(sh, phiNL, 0, fnl, lT, lE, aT, aE, nT, nE, 0, st);
+    else {
+      FNL_CUDA(cudaMemsetAsync(nT, 0, sizeof(double) * n2, st));
+      FNL_CUDA(cudaMemsetAsync(nE, 0, sizeof(double) * n2, st));
+      launch_combine(sh, fnl, lT, lE, nT, nE, aT, aE, st);
+    }
+  });
+}
+
+namespace fnl {
+namespace {
+
+// Steps (i)-(v) for one realisation, outputs in device memory (NULL -> scratch).
+void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, const double* noise,
+                  double* aT, double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, cudaStream_t st) {
+  const int64_t n2 = 2 * sh->nalm;
+  double* lT = aLT ? aLT : sh->d_aL;
+  double* lE = aLE ? aLE : sh->d_aL + n2;
+  double* nT = aNLT ? aNLT : sh->d_aNL;
+  double* nE = aNLE ? aNLE : sh->d_aNL + n2;
+  fnl_shells* msh = const_cast<fnl_shells*>(sh);
+  cudaEvent_t* ev = nullptr;
+  if (sh->ring_slots) {
+    ev = msh->ring.data() + (size_t)sh->ring_head * (FNL_NSTAGES + 1);
+    msh->ring_head = (sh->ring_head + 1) % sh->ring_slots;
+    msh->ring_count = std::min(sh->ring_count + 1, sh->ring_slots);
+  }
+  auto mark = [&](int i) {
+    if (ev) FNL_CUDA(cudaEventRecord(ev[i], st));
+  };
+  mark(0);
+  launch_filter(sh, seed, realisation, noise, lT, lE, nullptr, st);        // (i)
+  mark(1);
+  launch_synth_gemm(sh, st);                                              // (ii) Legendre
+  mark(2);
+  launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);                  // (ii) DFT, (iii), (iv) DFT
+  mark(3);
+  launch_analysis_gemm(sh, st);                                           // (iv) Legendre
+  mark(4);
+  launch_quadrature(sh, nullptr, 1, fnl, lT, lE, aT, aE, nT, nE, 0, st);  // (v)
+  mark(5);
+}
+
+}  // namespace
+}  // namespace fnl
+
+fnl_status fnl_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, const double* noise,
+                        double* aT, double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    check_dev_ptr(noise, "noise", true);
+    for (auto pr : {std::make_pair((const void*)aT, "aT"), std::make_pair((const void*)aE, "aE"),
+                    std::make_pair((const void*)aLT, "aLT"), std::make_pair((const void*)aLE, "aLE"),
+                    std::make_pair((const void*)aNLT, "aNLT"), std::make_pair((const void*)aNLE, "aNLE")})
+      check_dev_ptr(pr.first, pr.second, true);
+    run_generate(sh, seed, realisation, fnl, noise, aT, aE, aLT, aLE, aNLT, aNLE, (cudaStream_t)stream);
+  });
+}
+
+fnl_status fnl_generate_host(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, double* aT,
+                             double* aE, double* aNLT, double* aNLE, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n2 = 2 * sh->nalm;
+    double* dT = sh->d_aOut;
+    double* dE = sh->d_aOut + n2;
+    run_generate(sh, seed, realisation, fnl, nullptr, dT, dE, nullptr, nullptr, nullptr, nullptr, st);
+    const size_t bytes = sizeof(double) * (size_t)n2;
+    if (aT) FNL_CUDA(cudaMemcpyAsync(aT, dT, bytes, cudaMemcpyDeviceToHost, st));
+    if (aE) FNL_CUDA(cudaMemcpyAsync(aE, dE, bytes, cudaMemcpyDeviceToHost, st));
+    if (aNLT) FNL_CUDA(cudaMemcpyAsync(aNLT, sh->d_aNL, bytes, cudaMemcpyDeviceToHost, st));
+    if (aNLE) FNL_CUDA(cudaMemcpyAsync(aNLE, sh->d_aNL + n2, bytes, cudaMemcpyDeviceToHost, st));
+  });
+}
+
+fnl_status fnl_profile_enable(fnl_shells* sh, int slots) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(slots >= 0 && slots <= 4096, "slots must be in [0, 4096]");
+    DeviceScope scope(sh->device);
+    FNL_CUDA(cudaDeviceSynchronize());
+    for (auto& e : sh->ring)
+      if (e) cudaEventDestroy(e);
+    sh->ring.assign((size_t)slots * (FNL_NSTAGES + 1), nullptr);
+    for (auto& e : sh->ring) FNL_CUDA(cudaEventCreate(&e));
+    sh->ring_slots = slots;
+    sh->ring_head = 0;
+    sh->ring_count = 0;
+  });
+}
+
+fnl_status fnl_profile_read(fnl_shells* sh, double* ms, int n, int* calls) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(ms && n >= 1 && n <= FNL_NSTAGES, "need 1 <= n <= FNL_NSTAGES and ms != NULL");
+    FNL_REQUIRE(sh->ring_slots > 0, "profiling is off");
+    DeviceScope scope(sh->device);
+    for (int i = 0; i < n; ++i) ms[i] = 0.0;
+    for (int c = 0; c < sh->ring_count; ++c) {
+      const int slot = (sh->ring_head - 1 - c + 2 * sh->ring_slots) % sh->ring_slots;
+      cudaEvent_t* ev = sh->ring.data() + (size_t)slot * (FNL_NSTAGES + 1);
+      FNL_CUDA(cudaEventSynchronize(ev[FNL_NSTAGES]));
+      for (int i = 0; i < n; ++i) {
+        float t = 0.f;
+        FNL_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+        ms[i] += t;
+      }
+    }
+    if (calls) *calls = sh->ring_count;
+    sh->ring_count = 0;
+  });
+}
+
+}  // extern "C"

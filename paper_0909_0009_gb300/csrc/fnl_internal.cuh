@@ -1,0 +1,171 @@
+// Internal declarations of libfnl (not part of the C ABI).
+//
+// Index conventions used by every kernel:
+//   L = lmax, nr shells, C = 2 nr real columns (column c = 2 i + {0: re, 1: im} of shell i).
+//   Legendre problems are indexed by mp = 2 m + p, p = parity of (l - m); problem (m, p)
+//   holds the K_mp = max(0, (L - m - p + 2) / 2) degrees l = m + p + 2 k, k < K_mp.
+//   Ring pairs jp < npairs = (ntheta + 1) / 2: north ring jp at x_jp >= 0, south ring
+//   ntheta - 1 - jp at -x_jp (the same ring for the equator of an odd grid).
+//   lambda_lm(-x) = (-1)^(l-m) lambda_lm(x) turns every transform into two half-size
+//   contractions per m: even (p = 0) and odd (p = 1) degrees over the northern rings.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "fnl.h"
+
+namespace fnl {
+
+// ---- error handling -----------------------------------------------------------------
+
+struct Error : std::runtime_error {
+  fnl_status code;
+  Error(fnl_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+
+#define FNL_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      throw ::fnl::Error(e_ == cudaErrorMemoryAllocation ? FNL_ENOMEM : FNL_ECUDA,      \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    }                                                                                   \
+  } while (0)
+
+#define FNL_REQUIRE(cond, msg)                                   \
+  do {                                                           \
+    if (!(cond)) throw ::fnl::Error(FNL_EINVAL, (msg));          \
+  } while (0)
+
+// ---- small helpers --------------------------------------------------------------------
+
+template <typename T>
+struct cplx {
+  T x, y;
+};
+
+inline int64_t n_alm(int L) { return (int64_t)(L + 1) * (L + 2) / 2; }
+__host__ __device__ inline int64_t alm_idx(int l, int m, int L) {
+  return (int64_t)m * (2 * L + 1 - m) / 2 + l;
+}
+__host__ __device__ inline int k_of(int L, int m, int p) {
+  int v = (L - m - p + 2) / 2;
+  return v > 0 ? v : 0;
+}
+inline int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+// Maximum number of FFT passes and the radices used.
+constexpr int kMaxRadix = 24;
+
+struct FftPlan {
+  int n = 0;
+  int nrad = 0;
+  int rad[kMaxRadix];
+};
+
+// Tile of a SIMT grouped GEMM: problem mp, row tile, column tile.
+struct Tile {
+  int mp, rt, ct, pad;
+};
+
+// ---- the shells object ---------------------------------------------------------------
+
+struct DeviceBuffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace fnl
+
+struct fnl_shells {
+  int device = 0;
+  int lmax = 0, nr = 0, ntheta = 0, nphi = 0, prec = 0;
+  int npairs = 0, C = 0;
+  int64_t nalm = 0;
+  bool real_is_double = true;  // SIMT real type: double (FP64) or float (FP32 and mixed)
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+
+  // problem geometry
+  std::vector<int> K;          // [2(L+1)]
+  std::vector<int> KP;         // K rounded up to 16
+  std::vector<int64_t> row0;   // first row of problem mp in the [rows][C] phi buffer (SIMT)
+  std::vector<int64_t> lam0;   // first element of problem mp in the SIMT lambda table
+  int64_t rows_total = 0, lam_total = 0;
+  int* d_K = nullptr;
+  int64_t* d_row0 = nullptr;
+  int64_t* d_lam0 = nullptr;
+
+  // host copies of set-up data
+  std::vector<double> x, wgl;      // [npairs] northern GL nodes and weights
+  std::vector<double> mu;          // [nr]
+
+  // device tables
+  double* d_x = nullptr;           // [npairs]
+  double* d_wgl = nullptr;         // [npairs]
+  void* d_lam = nullptr;           // SIMT table, real type, [lam_total]
+  void* d_Kf = nullptr;            // [L+1][nr][nr] real type
+  double* d_vT = nullptr;          // [L+1][nr]  v^X_l = K_l^T q^X_l
+  double* d_vE = nullptr;
+  double* d_qT = nullptr;          // [L+1][nr]  q^X_l[i] = w_i r_i^2 alpha^X_l(r_i)
+  double* d_qE = nullptr;
+  double* d_mu = nullptr;          // [nr]
+  void* d_tw = nullptr;            // [nphi] complex real type, e^{-2 pi i k / nphi}
+  fnl::FftPlan fft;
+
+  // scratch of the path
+  void* d_phi = nullptr;           // [rows_total][C] real type
+  void* d_F = nullptr;             // [2(L+1)][npairs][C] real type
+  void* d_G = nullptr;             // [2(L+1)][npairs][C] real type
+  double* d_aL = nullptr;          // [2][nalm][2]  a^T_L, a^E_L when the caller passes NULL
+  double* d_aNL = nullptr;         // [2][nalm][2]
+  double* d_aOut = nullptr;        // [2][nalm][2]  a^T, a^E of fnl_generate_host
+
+  // per-stage timing of fnl_generate
+  int ring_slots = 0;                 // 0: profiling off
+  int ring_head = 0, ring_count = 0;  // next slot, profiled calls since the last read
+  std::vector<cudaEvent_t> ring;      // [ring_slots][FNL_NSTAGES + 1]
+
+  // SIMT tile lists
+  fnl::Tile* d_tiles_syn = nullptr;
+  int n_tiles_syn = 0;
+  fnl::Tile* d_tiles_ana = nullptr;
+  int n_tiles_ana = 0;
+};
+
+namespace fnl {
+
+// ---- host set-up (setup_host.cpp) -------------------------------------------------------
+void gauss_legendre(int n, double* x, double* w);
+void covariance(int lmax, int nr, const double* r, double A, double ns, double kmin, double kmax,
+                int nk, double* C);
+void cholesky_filters(int lmax, int nr, const double* C, double jitter_rel, double* K);
+FftPlan make_fft_plan(int n);
+
+// ---- kernel launchers (simt_path.cu, ring_fft.cu, tables.cu) ---------------------------
+void build_lambda_tables(fnl_shells* sh, cudaStream_t st);
+void launch_filter(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise,
+                   double* aLT, double* aLE, double* phi_api, cudaStream_t st);
+void launch_synth_gemm(const fnl_shells* sh, cudaStream_t st);
+void launch_analysis_gemm(const fnl_shells* sh, cudaStream_t st);
+enum FftMode { FFT_SQUARE = 0, FFT_SYNTH_MAP = 1, FFT_ANALYSE_MAP = 2 };
+void launch_ring_fft(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out,
+                     cudaStream_t st);
+void launch_alm_to_phi(const fnl_shells* sh, const double* alm, cudaStream_t st);
+void launch_phi_to_alm(const fnl_shells* sh, double* alm, cudaStream_t st);
+void launch_quadrature(const fnl_shells* sh, const double* phi_api, int from_internal, double fnl,
+                       const double* aLT, const double* aLE, double* aT, double* aE,
+                       double* aNLT, double* aNLE, int accumulate_into_L, cudaStream_t st);
+void launch_combine(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE,
+                    const double* aNLT, const double* aNLE, double* aT, double* aE,
+                    cudaStream_t st);
+
+}  // namespace fnl

@@ -1,0 +1,250 @@
+// Ring transforms in phi (the DFT half of steps (ii) and (iv)) and the pointwise square
+// of step (iii), Eq. 2.  One block per (ring pair jp, shell s).
+//
+// The two real rings of a pair (north f_N, south f_S) are carried as one complex sequence
+// z = f_N + i f_S.  Their spectra F_N,m = E_m + O_m and F_S,m = E_m - O_m come from the
+// even/odd Legendre halves; Z_m = F_N,m + i F_S,m and Z_{-m} = conj(F_N,m) + i conj(F_S,m).
+//   SQUARE:      z = IDFT(Z); w = (Re z)^2 - mu_s + i ((Im z)^2 - mu_s); W = DFT(w);
+//                G_N,m = (W_m + conj W_{-m}) / 2, G_S,m = (W_m - conj W_{-m}) / (2 i), m <= lmax,
+//                scaled by (2 pi / nphi) w_jp and stored as S = G_N + G_S (even degrees) and
+//                D = G_N - G_S (odd degrees); the equator ring is counted once.
+//   SYNTH_MAP:   z = IDFT(Z) written to the two rings of the map.
+//   ANALYSE_MAP: W = DFT(f_N + i f_S) from the map, then as SQUARE.
+// Transforms are self-sorting mixed-radix (4, 2, 3, 5) Stockham passes between two shared
+// memory buffers; twiddles e^{-2 pi i k / nphi} come from a table computed on the host.
+#include <cmath>
+
+#include "fnl_internal.cuh"
+
+namespace fnl {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) {
+  return {a.x - b.x, a.y - b.y};
+}
+// i * s * a for s = +-1
+template <typename T>
+__device__ __forceinline__ cplx<T> imul(cplx<T> a, T s) {
+  return {-s * a.y, s * a.x};
+}
+
+// In-register DFT of size R: v'[q] = sum_r v[r] e^{sgn 2 pi i q r / R}.
+template <typename T>
+__device__ __forceinline__ void small_dft(cplx<T>* v, int R, T sgn) {
+  if (R == 2) {
+    const cplx<T> a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if (R == 4) {
+    const cplx<T> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const cplx<T> s13 = cadd(v[1], v[3]), d13 = imul(csub(v[1], v[3]), sgn);
+    v[0] = cadd(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[2] = csub(s02, s13);
+    v[3] = csub(d02, d13);
+  } else if (R == 3) {
+    const T c = (T)-0.5, s = sgn * (T)0.86602540378443864676;  // cos, sin of 2 pi / 3
+    const cplx<T> t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    const cplx<T> a = {v[0].x + c * t1.x, v[0].y + c * t1.y};
+    const cplx<T> b = imul(t2, s);
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(a, b);
+    v[2] = csub(a, b);
+  } else {  // R == 5
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;     // cos 2pi/5, cos 4pi/5
+    const T s1 = sgn * (T)0.95105651629515357212, s2 = sgn * (T)0.58778525229247312917;  // sin 2pi/5, sin 4pi/5
+    const cplx<T> t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const cplx<T> d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+    const cplx<T> a1 = {v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y};
+    const cplx<T> a2 = {v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y};
+    const cplx<T> b1 = {s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y};
+    const cplx<T> b2 = {s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y};
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(a1, imul(b1, (T)1));
+    v[4] = csub(a1, imul(b1, (T)1));
+    v[2] = cadd(a2, imul(b2, (T)1));
+    v[3] = csub(a2, imul(b2, (T)1));
+  }
+}
+
+// Stockham passes from src (ping-pong with dst); returns the buffer holding the result.
+// sgn = -1: forward DFT, +1: unnormalised inverse.
+template <typename T>
+__device__ cplx<T>* stockham(cplx<T>* src, cplx<T>* dst, const FftPlan& plan, const cplx<T>* __restrict__ tw,
+                             T sgn) {
+  const int N = plan.n;
+  int Ns = 1;
+  for (int p = 0; p < plan.nrad; ++p) {
+    const int R = plan.rad[p];
+    const int nb = N / R;
+    const int stride = N / (Ns * R);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      const int k = j % Ns;
+      cplx<T> v[5];
+      v[0] = src[j];
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tw[r * k * stride];
+        w.y *= -sgn;  // table holds e^{-2 pi i k/N}; conjugate for the inverse
+        v[r] = cmul(src[j + r * nb], w);
+      }
+      small_dft(v, R, sgn);
+      const int o = (j / Ns) * Ns * R + k;
+      for (int r = 0; r < R; ++r) dst[o + r * Ns] = v[r];
+    }
+    __syncthreads();
+    cplx<T>* t = src;
+    src = dst;
+    dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+template <typename T>
+struct FftArgs {
+  int L, nr, ntheta, npairs, C;
+  FftPlan plan;
+  const cplx<T>* tw;
+  const T* F;            // [2(L+1)][npairs][C]
+  T* G;                  // [2(L+1)][npairs][C]
+  const double* mu;      // [nr]
+  const double* wgl;     // [npairs]
+  const double* maps_in; // [nr][ntheta][nphi]
+  double* maps_out;      // [nr][ntheta][nphi]
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.plan.n;
+  cplx<T>* b0 = (cplx<T>*)smem;
+  cplx<T>* b1 = b0 + N;
+  const int jp = blockIdx.x, s = blockIdx.y;
+  const int south = a.ntheta - 1 - jp;
+  const bool equator = (south == jp);
+  const int L = a.L, np = a.npairs, C = a.C;
+  cplx<T>* res;
+  if (MODE == FFT_ANALYSE_MAP) {
+    const double* rn = a.maps_in + ((size_t)s * a.ntheta + jp) * N;
+    const double* rs = a.maps_in + ((size_t)s * a.ntheta + south) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) b0[k] = {(T)rn[k], (T)rs[k]};
+    __syncthreads();
+    res = b0;
+  } else {
+    for (int k = threadIdx.x; k < N; k += blockDim.x) b0[k] = {(T)0, (T)0};
+    __syncthreads();
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+      const T* e = a.F + ((size_t)(2 * m) * np + jp) * C + 2 * s;
+      const T* o = a.F + ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+      const cplx<T> E = {e[0], e[1]};
+      const cplx<T> O = (m < L) ? cplx<T>{o[0], o[1]} : cplx<T>{(T)0, (T)0};
+      const cplx<T> FN = cadd(E, O), FS = csub(E, O);
+      if (m == 0) {
+        b0[0] = {FN.x, FS.x};
+      } else {
+        b0[m] = {FN.x - FS.y, FN.y + FS.x};
+        b0[N - m] = {FN.x + FS.y, FS.x - FN.y};
+      }
+    }
+    __syncthreads();
+    res = stockham(b0, b1, a.plan, a.tw, (T)1);
+    if (MODE == FFT_SYNTH_MAP) {
+      double* rn = a.maps_out + ((size_t)s * a.ntheta + jp) * N;
+      double* rs = a.maps_out + ((size_t)s * a.ntheta + south) * N;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const cplx<T> z = res[k];
+        rn[k] = (double)z.x;
+        if (!equator) rs[k] = (double)z.y;
+      }
+      return;
+    }
+    const T mu = (T)a.mu[s];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      const cplx<T> z = res[k];
+      res[k] = {z.x * z.x - mu, z.y * z.y - mu};
+    }
+    __syncthreads();
+  }
+  cplx<T>* other = (res == b0) ? b1 : b0;
+  const cplx<T>* W = stockham(res, other, a.plan, a.tw, (T)-1);
+  const T scale = (T)(6.28318530717958647692 / N * a.wgl[jp]);
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const cplx<T> wm = W[m];
+    const cplx<T> wc = W[m == 0 ? 0 : N - m];
+    // G_N = (W_m + conj W_-m) / 2,  G_S = (W_m - conj W_-m) / (2 i)
+    const cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
+    const cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
+    cplx<T> S, D;
+    if (equator) {
+      S = {gn.x * scale, gn.y * scale};
+      D = S;
+    } else {
+      S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
+      D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
+    }
+    T* ge = a.G + ((size_t)(2 * m) * np + jp) * C + 2 * s;
+    T* go = a.G + ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+    ge[0] = S.x;
+    ge[1] = S.y;
+    go[0] = D.x;
+    go[1] = D.y;
+  }
+}
+
+template <typename T>
+void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
+  FftArgs<T> a;
+  a.L = sh->lmax;
+  a.nr = sh->nr;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.C = sh->C;
+  a.plan = sh->fft;
+  a.tw = (const cplx<T>*)sh->d_tw;
+  a.F = (const T*)sh->d_F;
+  a.G = (T*)sh->d_G;
+  a.mu = sh->d_mu;
+  a.wgl = sh->d_wgl;
+  a.maps_in = maps_in;
+  a.maps_out = maps_out;
+  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)sh->nphi;
+  dim3 grid(sh->npairs, sh->nr);
+  const int threads = sh->nphi >= 1024 ? 256 : 128;
+  switch (mode) {
+    case FFT_SQUARE:
+      FNL_CUDA(cudaFuncSetAttribute(k_ring_fft<T, FFT_SQUARE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      k_ring_fft<T, FFT_SQUARE><<<grid, threads, smem, st>>>(a);
+      break;
+    case FFT_SYNTH_MAP:
+      FNL_CUDA(cudaFuncSetAttribute(k_ring_fft<T, FFT_SYNTH_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      k_ring_fft<T, FFT_SYNTH_MAP><<<grid, threads, smem, st>>>(a);
+      break;
+    default:
+      FNL_CUDA(cudaFuncSetAttribute(k_ring_fft<T, FFT_ANALYSE_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      k_ring_fft<T, FFT_ANALYSE_MAP><<<grid, threads, smem, st>>>(a);
+      break;
+  }
+  FNL_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void launch_ring_fft(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
+  if (sh->real_is_double) fft_impl<double>(sh, mode, maps_in, maps_out, st);
+  else fft_impl<float>(sh, mode, maps_in, maps_out, st);
+}
+
+}  // namespace fnl

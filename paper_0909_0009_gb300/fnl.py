@@ -1,0 +1,280 @@
+"""Thin Python binding of libfnl (ctypes): argument marshalling only.
+
+Every step of the path runs in the CUDA kernels behind the C ABI declared in
+``include/fnl.h``; PyTorch only provides device memory and the current stream.
+Importing this module raises if ``libfnl.so`` has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfnl.so")
+
+FNL_FP64, FNL_FP32, FNL_BF16X2, FNL_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FNL_FP64, "fp32": FNL_FP32, "bf16x2": FNL_BF16X2, "bf16x3": FNL_BF16X3}
+STATUS = {0: "FNL_OK", 1: "FNL_EINVAL", 2: "FNL_ENOMEM", 3: "FNL_ECUDA", 4: "FNL_EUNSUPPORTED", 5: "FNL_ETIMEOUT"}
+
+# Every symbol include/fnl.h declares.
+EXPORTS = [
+    "fnl_version", "fnl_last_error", "fnl_make_shells", "fnl_shells_destroy", "fnl_shells_info",
+    "fnl_shells_mu", "fnl_generate", "fnl_filter", "fnl_synth", "fnl_analyse", "fnl_square",
+    "fnl_accumulate", "fnl_gauss_legendre", "fnl_covariance", "fnl_cholesky_filters",
+    "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host",
+]
+STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
+
+
+class FnlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ShellDesc(ctypes.Structure):
+    _fields_ = [
+        ("lmax", ctypes.c_int), ("nr", ctypes.c_int), ("ntheta", ctypes.c_int), ("nphi", ctypes.c_int),
+        ("r", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
+        ("K", ctypes.POINTER(ctypes.c_double)),
+        ("A", ctypes.c_double), ("ns", ctypes.c_double), ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
+        ("nk", ctypes.c_int), ("jitter_rel", ctypes.c_double),
+        ("alphaT", ctypes.POINTER(ctypes.c_double)), ("alphaE", ctypes.POINTER(ctypes.c_double)),
+        ("mu", ctypes.POINTER(ctypes.c_double)), ("prec", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfnl.so (built in-tree by paper_0909_0009_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_0909_0009_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, d, u64, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.fnl_version.restype = ctypes.c_char_p
+    lib.fnl_last_error.restype = ctypes.c_char_p
+    lib.fnl_make_shells.argtypes = [ctypes.POINTER(ShellDesc), i, ctypes.POINTER(vp)]
+    lib.fnl_shells_destroy.argtypes = [vp]
+    lib.fnl_shells_destroy.restype = None
+    lib.fnl_shells_info.argtypes = [vp] + [ctypes.POINTER(i)] * 5 + [ctypes.POINTER(ctypes.c_size_t)]
+    lib.fnl_shells_mu.argtypes = [vp, dp]
+    lib.fnl_generate.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.fnl_filter.argtypes = [vp, u64, u64, vp, vp, vp]
+    lib.fnl_synth.argtypes = [vp, vp, vp, vp]
+    lib.fnl_analyse.argtypes = [vp, vp, vp, vp]
+    lib.fnl_square.argtypes = [vp, vp, vp, vp]
+    lib.fnl_accumulate.argtypes = [vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
+    lib.fnl_gauss_legendre.argtypes = [i, dp, dp]
+    lib.fnl_covariance.argtypes = [i, i, dp, d, d, d, d, i, dp]
+    lib.fnl_cholesky_filters.argtypes = [i, i, dp, d, dp]
+    lib.fnl_profile_enable.argtypes = [vp, i]
+    lib.fnl_profile_read.argtypes = [vp, dp, i, ctypes.POINTER(i)]
+    lib.fnl_generate_host.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp]
+    for name in EXPORTS:
+        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise FnlError(code, _lib.fnl_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---- host helpers (no GPU needed) -----------------------------------------------------
+
+def gauss_legendre(n: int):
+    lib = load_library()
+    x = np.empty(n)
+    w = np.empty(n)
+    _check(lib.fnl_gauss_legendre(n, _dptr(x), _dptr(w)))
+    return x, w
+
+
+def covariance(lmax, r, A, ns, kmin, kmax, nk):
+    lib = load_library()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    C = np.empty((lmax + 1, r.size, r.size))
+    _check(lib.fnl_covariance(lmax, r.size, _dptr(r), A, ns, kmin, kmax, nk, _dptr(C)))
+    return C
+
+
+def cholesky_filters(C, jitter_rel):
+    lib = load_library()
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    K = np.empty_like(C)
+    _check(lib.fnl_cholesky_filters(C.shape[0] - 1, C.shape[1], _dptr(C), jitter_rel, _dptr(K)))
+    return K
+
+
+# ---- device objects -----------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Cov:
+    A: float = 1.6e-8
+    ns: float = 0.96
+    kmin: float = 1e-4
+    kmax: float = 0.3
+    nk: int = 4096
+    jitter_rel: float = 1e-10
+
+
+class Shells:
+    """Device tables and scratch for one configuration (wraps fnl_make_shells)."""
+
+    def __init__(self, lmax, nr, ntheta, nphi, r, w, alphaT, alphaE, K=None, cov: Cov | None = None,
+                 mu=None, prec="fp64", device=0):
+        lib = load_library()
+        cov = cov or Cov()
+        self._keep = []
+
+        def arr(a, shape):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+            self._keep.append(a)
+            return _dptr(a)
+
+        d = ShellDesc()
+        d.lmax, d.nr, d.ntheta, d.nphi = lmax, nr, ntheta, nphi
+        d.r, d.w = arr(r, (nr,)), arr(w, (nr,))
+        d.K = arr(K, (lmax + 1, nr, nr))
+        d.A, d.ns, d.kmin, d.kmax, d.nk, d.jitter_rel = cov.A, cov.ns, cov.kmin, cov.kmax, cov.nk, cov.jitter_rel
+        d.alphaT, d.alphaE = arr(alphaT, (lmax + 1, nr)), arr(alphaE, (lmax + 1, nr))
+        d.mu = arr(mu, (nr,))
+        d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        h = ctypes.c_void_p()
+        _check(lib.fnl_make_shells(ctypes.byref(d), device, ctypes.byref(h)))
+        self._keep = []
+        self.handle = h
+        self.lmax, self.nr, self.ntheta, self.nphi = lmax, nr, ntheta, nphi
+        self.nalm = (lmax + 1) * (lmax + 2) // 2
+        self.device = device
+        self.prec = d.prec
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.fnl_shells_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def mu(self) -> np.ndarray:
+        out = np.empty(self.nr)
+        _check(_lib.fnl_shells_mu(self.handle, _dptr(out)))
+        return out
+
+    @property
+    def device_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib.fnl_shells_info(self.handle, None, None, None, None, None, ctypes.byref(b)))
+        return b.value
+
+    def profile(self, slots: int = 256):
+        """Time the stages of fnl_generate with CUDA events on the launching stream
+        (a ring of `slots` calls; 0 turns profiling off)."""
+        _check(_lib.fnl_profile_enable(self.handle, int(slots)))
+
+    def stage_ms(self) -> tuple[dict, int]:
+        """Stage durations (ms) summed over the profiled calls since the last read, and their count."""
+        ms = np.zeros(len(STAGES))
+        n = ctypes.c_int()
+        _check(_lib.fnl_profile_read(self.handle, _dptr(ms), len(STAGES), ctypes.byref(n)))
+        return dict(zip(STAGES, ms.tolist())), n.value
+
+    def generate_host(self, seed: int, realisation: int, fnl: float, aT: np.ndarray, aE: np.ndarray,
+                      aNLT=None, aNLE=None, stream=None):
+        """fnl_generate with host outputs (complex128 arrays of nalm; pinned memory for async copies).
+        The caller synchronises the stream before reading them."""
+        def hp(a):
+            if a is None:
+                return None
+            assert a.dtype == np.complex128 and a.flags.c_contiguous and a.size == self.nalm
+            return ctypes.c_void_p(a.ctypes.data)
+        _check(_lib.fnl_generate_host(self.handle, seed, realisation, float(fnl), hp(aT), hp(aE), hp(aNLT),
+                                      hp(aNLE), _stream(stream)))
+
+    # -- tensors
+    def _alm(self, n=1):
+        torch = _torch()
+        return torch.empty((self.nalm,) if n == 1 else (self.nalm, n), dtype=torch.complex128,
+                           device=f"cuda:{self.device}")
+
+    def generate(self, seed: int, realisation: int, fnl: float, noise=None, parts: bool = True,
+                 out: dict | None = None, stream=None) -> dict:
+        """One realisation; returns complex128 tensors aT, aE (and aLT, aLE, aNLT, aNLE if parts)."""
+        names = ["aT", "aE"] + (["aLT", "aLE", "aNLT", "aNLE"] if parts else [])
+        if out is None:
+            out = {k: self._alm() for k in names}
+        ptrs = [_ptr(out.get(k)) for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]]
+        if noise is not None:
+            assert noise.dtype == _torch().complex128 and noise.is_contiguous() and noise.shape == (self.nr, self.nalm)
+        _check(_lib.fnl_generate(self.handle, seed, realisation, float(fnl), _ptr(noise), *ptrs, _stream(stream)))
+        return out
+
+    def filter(self, seed: int = 0, realisation: int = 0, noise=None, stream=None):
+        phi = self._alm(self.nr)
+        _check(_lib.fnl_filter(self.handle, seed, realisation, _ptr(noise), _ptr(phi), _stream(stream)))
+        return phi
+
+    def synth(self, alm, stream=None):
+        torch = _torch()
+        assert alm.dtype == torch.complex128 and alm.is_contiguous() and alm.shape == (self.nalm, self.nr)
+        maps = torch.empty((self.nr, self.ntheta, self.nphi), dtype=torch.float64, device=alm.device)
+        _check(_lib.fnl_synth(self.handle, _ptr(alm), _ptr(maps), _stream(stream)))
+        return maps
+
+    def analyse(self, maps, stream=None):
+        torch = _torch()
+        assert maps.dtype == torch.float64 and maps.is_contiguous() and maps.shape == (self.nr, self.ntheta, self.nphi)
+        alm = self._alm(self.nr)
+        _check(_lib.fnl_analyse(self.handle, _ptr(maps), _ptr(alm), _stream(stream)))
+        return alm
+
+    def square(self, phiL, stream=None):
+        torch = _torch()
+        assert phiL.dtype == torch.complex128 and phiL.is_contiguous() and phiL.shape == (self.nalm, self.nr)
+        out = self._alm(self.nr)
+        _check(_lib.fnl_square(self.handle, _ptr(phiL), _ptr(out), _stream(stream)))
+        return out
+
+    def accumulate(self, phiL=None, phiNL=None, fnl: float = 0.0, stream=None) -> dict:
+        out = {k: self._alm() for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]}
+        ptrs = [_ptr(out[k]) for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]]
+        _check(_lib.fnl_accumulate(self.handle, _ptr(phiL), _ptr(phiNL), float(fnl), *ptrs, _stream(stream)))
+        return out
