@@ -158,6 +158,11 @@ fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double
                           double fnl, double* aT, double* aE, double* aLT, double* aLE,
                           double* aNLT, double* aNLE, void* stream);
 
+/* Wait for all work on the object's device, then report FNL_ETIMEOUT if a bounded wait
+ * inside a tensor-core kernel expired since the last call (the kernels record it in a
+ * device word instead of hanging), else FNL_OK.  Clears the word. */
+fnl_status fnl_device_status(const fnl_shells* sh);
+
 /* ---- per-stage timing -------------------------------------------------------------- */
 
 /* Stages of fnl_generate timed when profiling is on (CUDA events recorded on the

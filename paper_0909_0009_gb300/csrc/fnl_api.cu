@@ -123,6 +123,133 @@ void validate_desc(const fnl_shell_desc* d) {
   FNL_REQUIRE(2 * 2 * tsize * (size_t)d->nphi <= 200 * 1024, "nphi too large for the shared-memory ring FFT");
 }
 
+// Tables, scratch, tile lists and tensor maps of the tensor-core forms.
+void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vector<double>& qE) {
+  const int L = sh->lmax, nr = sh->nr, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms;
+  const int Cpad = sh->Cpad;
+  const int64_t rows32 = sh->row32[nmp], rows16 = sh->rows_total, nslab = rows32 / 32;
+  typedef unsigned short bf16_t;
+  sh->phiT_stride = rows32 * Cpad;
+  sh->d_phiT = dalloc<bf16_t>(sh, (size_t)T * sh->phiT_stride);
+  sh->lsyn_stride = nslab * np * 32;
+  sh->d_lsyn = dalloc<bf16_t>(sh, (size_t)T * sh->lsyn_stride);
+  sh->lana_stride = rows16 * sh->npj;
+  sh->d_lana = dalloc<bf16_t>(sh, (size_t)T * sh->lana_stride);
+  sh->gt_stride = (int64_t)nmp * np * Cpad;
+  sh->d_GT = dalloc<bf16_t>(sh, (size_t)T * sh->gt_stride);
+  sh->d_F = dalloc<float>(sh, (size_t)nmp * np * Cpad);
+  sh->d_part = dalloc<float>(sh, 4 * (size_t)(Cpad / 128) * sh->nalm);
+  sh->d_err = dalloc<int>(sh, 1);
+  FNL_CUDA(cudaMemset(sh->d_phiT, 0, sizeof(bf16_t) * (size_t)T * sh->phiT_stride));
+  FNL_CUDA(cudaMemset(sh->d_lsyn, 0, sizeof(bf16_t) * (size_t)T * sh->lsyn_stride));
+  FNL_CUDA(cudaMemset(sh->d_lana, 0, sizeof(bf16_t) * (size_t)T * sh->lana_stride));
+  FNL_CUDA(cudaMemset(sh->d_GT, 0, sizeof(bf16_t) * (size_t)T * sh->gt_stride));
+  FNL_CUDA(cudaMemset(sh->d_F, 0, sizeof(float) * (size_t)nmp * np * Cpad));
+  FNL_CUDA(cudaMemset(sh->d_err, 0, sizeof(int)));
+  std::vector<float> q32(2 * qT.size());
+  for (size_t i = 0; i < qT.size(); ++i) {
+    q32[i] = (float)qT[i];
+    q32[qT.size() + i] = (float)qE[i];
+  }
+  sh->d_q32 = upload(sh, q32);
+  sh->d_row32 = upload(sh, sh->row32);
+  build_lambda_tables_mixed(sh, 0);
+
+  // synthesis tile width: fewest wasted ring pairs, each tile charged 16 columns of overhead
+  int best = 256, bestc = 1 << 30;
+  for (int n = 256; n >= 64; n -= 16) {
+    const int tiles = (np + n - 1) / n, cost = tiles * (n + 16);
+    if (cost < bestc) {
+      bestc = cost;
+      best = n;
+    }
+  }
+  sh->nsyn = best;
+  const int ctiles = Cpad / 128;
+  std::vector<TcTile> ts, ta;
+  for (int mp = 0; mp < nmp; ++mp) {
+    const int K = sh->K[mp];
+    if (!K) continue;
+    for (int n0 = 0; n0 < np; n0 += sh->nsyn)
+      for (int ct = 0; ct < ctiles; ++ct)
+        ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0});
+    for (int n0 = 0; n0 < K;) {
+      const int n = std::min(256, round_up(K - n0, 16));
+      for (int ct = 0; ct < ctiles; ++ct)
+        ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0});
+      n0 += n;
+    }
+  }
+  auto by_cost = [](const TcTile& a, const TcTile& b) { return a.nkb * a.nsize > b.nkb * b.nsize; };
+  std::stable_sort(ts.begin(), ts.end(), by_cost);
+  std::stable_sort(ta.begin(), ta.end(), by_cost);
+  sh->d_tc_syn = upload(sh, ts);
+  sh->d_tc_ana = upload(sh, ta);
+
+  // tensor maps (BF16): A operands MN-major with 128B swizzle, B operands K-major with 64B swizzle
+  for (int t = 0; t < T; ++t) {
+    const bf16_t* phi = (const bf16_t*)sh->d_phiT + (size_t)t * sh->phiT_stride;
+    const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
+    const bf16_t* gt = (const bf16_t*)sh->d_GT + (size_t)t * sh->gt_stride;
+    const bf16_t* lana = (const bf16_t*)sh->d_lana + (size_t)t * sh->lana_stride;
+    {
+      const uint64_t dims[2] = {(uint64_t)Cpad, (uint64_t)rows32};
+      const uint64_t str[1] = {(uint64_t)Cpad * 2};
+      const uint32_t box[2] = {64, 32};
+      sh->tc_syn.tmA[t] = make_tensor_map_bf16(phi, 2, dims, str, box, 128);
+    }
+    {
+      const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
+      const uint64_t str[2] = {64, (uint64_t)np * 64};
+      const uint32_t box[3] = {32, 16, 1};
+      sh->tc_syn.tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
+    }
+    {
+      const uint64_t dims[3] = {(uint64_t)Cpad, (uint64_t)np, (uint64_t)nmp};
+      const uint64_t str[2] = {(uint64_t)Cpad * 2, (uint64_t)np * Cpad * 2};
+      const uint32_t box[3] = {64, 32, 1};
+      sh->tc_ana.tmA[t] = make_tensor_map_bf16(gt, 3, dims, str, box, 128);
+    }
+    {
+      const uint64_t dims[2] = {(uint64_t)np, (uint64_t)rows16};
+      const uint64_t str[1] = {(uint64_t)sh->npj * 2};
+      const uint32_t box[2] = {32, 16};
+      sh->tc_ana.tmB[t] = make_tensor_map_bf16(lana, 2, dims, str, box, 64);
+    }
+  }
+  for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
+    a->nterms = T;
+    a->L = L;
+    a->nr = nr;
+    a->npairs = np;
+    a->Cpad = Cpad;
+    a->nalm = sh->nalm;
+    a->F = (float*)sh->d_F;
+    a->part = (float4*)sh->d_part;
+    a->alm_out = nullptr;
+    a->qT = sh->d_q32;
+    a->qE = sh->d_q32 + (size_t)(L + 1) * nr;
+    a->err = sh->d_err;
+  }
+  sh->tc_syn.tiles = sh->d_tc_syn;
+  sh->tc_syn.ntiles = (int)ts.size();
+  sh->tc_syn.mode = TC_SYNTH;
+  sh->tc_syn.nmax = sh->nsyn;
+  sh->tc_syn.stages = tc_stages(T, sh->nsyn);
+  sh->tc_ana.tiles = sh->d_tc_ana;
+  sh->tc_ana.ntiles = (int)ta.size();
+  sh->tc_ana.mode = TC_ANA_QUAD;
+  sh->tc_ana.nmax = 256;
+  sh->tc_ana.stages = tc_stages(T, 256);
+}
+
+void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st) {
+  TcArgs a = base;
+  a.mode = mode;
+  a.alm_out = alm_out;
+  launch_tc_gemm(a, sh->sms, st);
+}
+
 }  // namespace
 }  // namespace fnl
 
@@ -166,12 +293,18 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     FNL_REQUIRE(out, "out must not be NULL");
     *out = nullptr;
     validate_desc(d);
-    if (d->prec == FNL_BF16X2 || d->prec == FNL_BF16X3)
-      throw Error(FNL_EUNSUPPORTED, "tensor-core precisions are not built into this library yet");
+    const bool mixed = (d->prec == FNL_BF16X2 || d->prec == FNL_BF16X3);
     int ndev = 0;
     FNL_CUDA(cudaGetDeviceCount(&ndev));
     FNL_REQUIRE(device >= 0 && device < ndev, "no such CUDA device");
     DeviceScope scope(device);
+    if (mixed) {
+      int major = 0, minor = 0;
+      FNL_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device));
+      FNL_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device));
+      if (major != 10 || minor != 3)
+        throw Error(FNL_EUNSUPPORTED, "the tensor-core forms are built for sm_103a only");
+    }
     sh = new fnl_shells;
     sh->device = device;
     const int L = d->lmax, nr = d->nr;
@@ -184,6 +317,8 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     sh->C = 2 * nr;
     sh->nalm = n_alm(L);
     sh->real_is_double = (d->prec == FNL_FP64);
+    sh->nterms = d->prec == FNL_BF16X2 ? 2 : d->prec == FNL_BF16X3 ? 3 : 0;
+    FNL_CUDA(cudaDeviceGetAttribute(&sh->sms, cudaDevAttrMultiProcessorCount, device));
     const int np = sh->npairs, C = sh->C;
     const size_t ts = sh->real_is_double ? sizeof(double) : sizeof(float);
 
@@ -207,6 +342,15 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     sh->lam0[nmp] = lams;
     sh->rows_total = rows;
     sh->lam_total = lams;
+    sh->row32.resize(nmp + 1);
+    int64_t r32 = 0;
+    for (int mp = 0; mp < nmp; ++mp) {
+      sh->row32[mp] = r32;
+      r32 += round_up(sh->K[mp], 32);
+    }
+    sh->row32[nmp] = r32;
+    sh->Cpad = round_up(C, 128);
+    sh->npj = round_up(np, 8);
 
     // ---- Gauss-Legendre grid (northern half)
     std::vector<double> xg(d->ntheta), wg(d->ntheta);
@@ -299,18 +443,22 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
       sh->d_Kf = upload(sh, kf);
       sh->d_tw = upload(sh, twf);
     }
-    sh->d_lam = dalloc<unsigned char>(sh, ts * (size_t)sh->lam_total);
-    sh->d_phi = dalloc<unsigned char>(sh, ts * (size_t)sh->rows_total * C);
-    const size_t fg = ts * (size_t)nmp * np * C;
-    sh->d_F = dalloc<unsigned char>(sh, fg);
-    sh->d_G = dalloc<unsigned char>(sh, fg);
     sh->d_aL = dalloc<double>(sh, 4 * (size_t)sh->nalm);
     sh->d_aNL = dalloc<double>(sh, 4 * (size_t)sh->nalm);
     sh->d_aOut = dalloc<double>(sh, 4 * (size_t)sh->nalm);
-    FNL_CUDA(cudaMemset(sh->d_phi, 0, ts * (size_t)sh->rows_total * C));
-    FNL_CUDA(cudaMemset(sh->d_F, 0, fg));
-    FNL_CUDA(cudaMemset(sh->d_G, 0, fg));
-    build_lambda_tables(sh, 0);
+    if (!mixed) {
+      sh->d_lam = dalloc<unsigned char>(sh, ts * (size_t)sh->lam_total);
+      sh->d_phi = dalloc<unsigned char>(sh, ts * (size_t)sh->rows_total * C);
+      const size_t fg = ts * (size_t)nmp * np * C;
+      sh->d_F = dalloc<unsigned char>(sh, fg);
+      sh->d_G = dalloc<unsigned char>(sh, fg);
+      FNL_CUDA(cudaMemset(sh->d_phi, 0, ts * (size_t)sh->rows_total * C));
+      FNL_CUDA(cudaMemset(sh->d_F, 0, fg));
+      FNL_CUDA(cudaMemset(sh->d_G, 0, fg));
+      build_lambda_tables(sh, 0);
+    } else {
+      setup_mixed(sh, qT, qE);
+    }
     FNL_CUDA(cudaDeviceSynchronize());
     *out = sh;
   });
@@ -357,7 +505,8 @@ fnl_status fnl_filter(const fnl_shells* sh, uint64_t seed, uint64_t realisation,
     check_dev_ptr(noise, "noise", true);
     check_dev_ptr(phiL, "phiL", false);
     cudaStream_t st = (cudaStream_t)stream;
-    launch_filter(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, st);
+    if (sh->nterms) launch_filter_mixed(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, st);
+    else launch_filter(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, st);
   });
 }
 
@@ -368,8 +517,13 @@ fnl_status fnl_synth(const fnl_shells* sh, const double* alm, double* maps, void
     check_dev_ptr(alm, "alm", false);
     check_dev_ptr(maps, "maps", false);
     cudaStream_t st = (cudaStream_t)stream;
-    launch_alm_to_phi(sh, alm, st);
-    launch_synth_gemm(sh, st);
+    if (sh->nterms) {
+      launch_alm_to_terms(sh, alm, st);
+      launch_tc(sh, sh->tc_syn, TC_SYNTH, nullptr, st);
+    } else {
+      launch_alm_to_phi(sh, alm, st);
+      launch_synth_gemm(sh, st);
+    }
     launch_ring_fft(sh, FFT_SYNTH_MAP, nullptr, maps, st);
   });
 }
@@ -382,8 +536,12 @@ fnl_status fnl_analyse(const fnl_shells* sh, const double* maps, double* alm, vo
     check_dev_ptr(alm, "alm", false);
     cudaStream_t st = (cudaStream_t)stream;
     launch_ring_fft(sh, FFT_ANALYSE_MAP, maps, nullptr, st);
-    launch_analysis_gemm(sh, st);
-    launch_phi_to_alm(sh, alm, st);
+    if (sh->nterms) {
+      launch_tc(sh, sh->tc_ana, TC_ANA_STORE, alm, st);
+    } else {
+      launch_analysis_gemm(sh, st);
+      launch_phi_to_alm(sh, alm, st);
+    }
   });
 }
 
@@ -394,11 +552,18 @@ fnl_status fnl_square(const fnl_shells* sh, const double* phiL, double* phiNL, v
     check_dev_ptr(phiL, "phiL", false);
     check_dev_ptr(phiNL, "phiNL", false);
     cudaStream_t st = (cudaStream_t)stream;
-    launch_alm_to_phi(sh, phiL, st);
-    launch_synth_gemm(sh, st);
-    launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);
-    launch_analysis_gemm(sh, st);
-    launch_phi_to_alm(sh, phiNL, st);
+    if (sh->nterms) {
+      launch_alm_to_terms(sh, phiL, st);
+      launch_tc(sh, sh->tc_syn, TC_SYNTH, nullptr, st);
+      launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);
+      launch_tc(sh, sh->tc_ana, TC_ANA_STORE, phiNL, st);
+    } else {
+      launch_alm_to_phi(sh, phiL, st);
+      launch_synth_gemm(sh, st);
+      launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);
+      launch_analysis_gemm(sh, st);
+      launch_phi_to_alm(sh, phiNL, st);
+    }
   });
 }
 
@@ -455,15 +620,27 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
     if (ev) FNL_CUDA(cudaEventRecord(ev[i], st));
   };
   mark(0);
-  launch_filter(sh, seed, realisation, noise, lT, lE, nullptr, st);        // (i)
-  mark(1);
-  launch_synth_gemm(sh, st);                                              // (ii) Legendre
-  mark(2);
-  launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);                  // (ii) DFT, (iii), (iv) DFT
-  mark(3);
-  launch_analysis_gemm(sh, st);                                           // (iv) Legendre
-  mark(4);
-  launch_quadrature(sh, nullptr, 1, fnl, lT, lE, aT, aE, nT, nE, 0, st);  // (v)
+  if (sh->nterms) {
+    launch_filter_mixed(sh, seed, realisation, noise, lT, lE, nullptr, st);   // (i)
+    mark(1);
+    launch_tc(sh, sh->tc_syn, TC_SYNTH, nullptr, st);                         // (ii) Legendre
+    mark(2);
+    launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);                    // (ii) DFT, (iii), (iv) DFT
+    mark(3);
+    launch_tc(sh, sh->tc_ana, TC_ANA_QUAD, nullptr, st);                      // (iv) Legendre + (v)
+    mark(4);
+    launch_combine_mixed(sh, fnl, lT, lE, nT, nE, aT, aE, st);                // (v), Eq. 3
+  } else {
+    launch_filter(sh, seed, realisation, noise, lT, lE, nullptr, st);        // (i)
+    mark(1);
+    launch_synth_gemm(sh, st);                                              // (ii) Legendre
+    mark(2);
+    launch_ring_fft(sh, FFT_SQUARE, nullptr, nullptr, st);                  // (ii) DFT, (iii), (iv) DFT
+    mark(3);
+    launch_analysis_gemm(sh, st);                                           // (iv) Legendre
+    mark(4);
+    launch_quadrature(sh, nullptr, 1, fnl, lT, lE, aT, aE, nT, nE, 0, st);  // (v)
+  }
   mark(5);
 }
 
@@ -537,6 +714,21 @@ fnl_status fnl_profile_read(fnl_shells* sh, double* ms, int n, int* calls) {
     }
     if (calls) *calls = sh->ring_count;
     sh->ring_count = 0;
+  });
+}
+
+fnl_status fnl_device_status(const fnl_shells* sh) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    FNL_CUDA(cudaDeviceSynchronize());
+    if (!sh->d_err) return;
+    int e = 0;
+    FNL_CUDA(cudaMemcpy(&e, sh->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      FNL_CUDA(cudaMemset(sh->d_err, 0, sizeof(int)));
+      throw Error(FNL_ETIMEOUT, "a bounded wait in a tensor-core kernel expired (code " + std::to_string(e) + ")");
+    }
   });
 }
 

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "fnl.h"
+#include "tc_gemm.cuh"
 
 namespace fnl {
 
@@ -134,6 +135,29 @@ struct fnl_shells {
   int ring_head = 0, ring_count = 0;  // next slot, profiled calls since the last read
   std::vector<cudaEvent_t> ring;      // [ring_slots][FNL_NSTAGES + 1]
 
+  // mixed (tensor-core) forms
+  int nterms = 0;                  // BF16 terms per operand (0: SIMT forms)
+  int Cpad = 0;                    // columns padded to a multiple of 128
+  int npj = 0;                     // ring pairs padded to a multiple of 8 (row stride of Lambda_ana)
+  int nsyn = 0;                    // synthesis tile width (ring pairs)
+  int sms = 0;
+  std::vector<int64_t> row32;      // first Phi row of problem mp (rows padded to 32)
+  int64_t* d_row32 = nullptr;
+  void* d_phiT = nullptr;          // bf16 [nterms][rows32][Cpad]
+  int64_t phiT_stride = 0;
+  void* d_lsyn = nullptr;          // bf16 [nterms][slabs][npairs][32]
+  int64_t lsyn_stride = 0;
+  void* d_lana = nullptr;          // bf16 [nterms][rows16][npj]
+  int64_t lana_stride = 0;
+  void* d_GT = nullptr;            // bf16 [nterms][2(L+1)][npairs][Cpad]
+  int64_t gt_stride = 0;
+  void* d_part = nullptr;          // float4 [Cpad / 128][nalm]
+  float* d_q32 = nullptr;          // [2][L+1][nr]  q^T, q^E in FP32
+  int* d_err = nullptr;            // device error word of the tensor-core kernels
+  fnl::TcTile* d_tc_syn = nullptr;
+  fnl::TcTile* d_tc_ana = nullptr;
+  fnl::TcArgs tc_syn{}, tc_ana{};
+
   // SIMT tile lists
   fnl::Tile* d_tiles_syn = nullptr;
   int n_tiles_syn = 0;
@@ -167,5 +191,15 @@ void launch_quadrature(const fnl_shells* sh, const double* phi_api, int from_int
 void launch_combine(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE,
                     const double* aNLT, const double* aNLE, double* aT, double* aE,
                     cudaStream_t st);
+void launch_lambda_mm(const double* x, const double* fac, int npairs, int L, double* mant, int* expo,
+                      cudaStream_t st);
+
+// ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
+void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st);
+void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
+                         double* aLE, double* phi_api, cudaStream_t st);
+void launch_alm_to_terms(const fnl_shells* sh, const double* alm, cudaStream_t st);
+void launch_combine_mixed(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE, double* aNLT,
+                          double* aNLE, double* aT, double* aE, cudaStream_t st);
 
 }  // namespace fnl

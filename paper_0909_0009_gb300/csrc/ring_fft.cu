@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "fnl_internal.cuh"
+#include "mixed.cuh"
 
 namespace fnl {
 
@@ -112,7 +113,10 @@ __device__ cplx<T>* stockham(cplx<T>* src, cplx<T>* dst, const FftPlan& plan, co
 
 template <typename T>
 struct FftArgs {
-  int L, nr, ntheta, npairs, C;
+  int L, nr, ntheta, npairs, C;  // C: column stride of F and G
+  int nterms;                    // 0: G in the real type T; 2 or 3: G as BF16 terms in GT
+  int64_t gt_stride;             // elements between BF16 terms
+  __nv_bfloat16* GT;
   FftPlan plan;
   const cplx<T>* tw;
   const T* F;            // [2(L+1)][npairs][C]
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
   const int N = a.plan.n;
   cplx<T>* b0 = (cplx<T>*)smem;
   cplx<T>* b1 = b0 + N;
-  const int jp = blockIdx.x, s = blockIdx.y;
+  const int s = blockIdx.x, jp = blockIdx.y;
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
   const int L = a.L, np = a.npairs, C = a.C;
@@ -192,12 +196,21 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
       S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
       D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
     }
-    T* ge = a.G + ((size_t)(2 * m) * np + jp) * C + 2 * s;
-    T* go = a.G + ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
-    ge[0] = S.x;
-    ge[1] = S.y;
-    go[0] = D.x;
-    go[1] = D.y;
+    const size_t oe = ((size_t)(2 * m) * np + jp) * C + 2 * s;
+    const size_t oo = ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+    if (a.nterms) {
+      store_terms(a.GT + oe, a.gt_stride, a.nterms, (float)S.x);
+      store_terms(a.GT + oe + 1, a.gt_stride, a.nterms, (float)S.y);
+      store_terms(a.GT + oo, a.gt_stride, a.nterms, (float)D.x);
+      store_terms(a.GT + oo + 1, a.gt_stride, a.nterms, (float)D.y);
+    } else {
+      T* ge = a.G + oe;
+      T* go = a.G + oo;
+      ge[0] = S.x;
+      ge[1] = S.y;
+      go[0] = D.x;
+      go[1] = D.y;
+    }
   }
 }
 
@@ -208,7 +221,10 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   a.nr = sh->nr;
   a.ntheta = sh->ntheta;
   a.npairs = sh->npairs;
-  a.C = sh->C;
+  a.C = sh->nterms ? sh->Cpad : sh->C;
+  a.nterms = sh->nterms;
+  a.gt_stride = sh->gt_stride;
+  a.GT = (__nv_bfloat16*)sh->d_GT;
   a.plan = sh->fft;
   a.tw = (const cplx<T>*)sh->d_tw;
   a.F = (const T*)sh->d_F;
@@ -218,7 +234,7 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   a.maps_in = maps_in;
   a.maps_out = maps_out;
   const size_t smem = 2 * sizeof(cplx<T>) * (size_t)sh->nphi;
-  dim3 grid(sh->npairs, sh->nr);
+  dim3 grid(sh->nr, sh->npairs);
   const int threads = sh->nphi >= 1024 ? 256 : 128;
   switch (mode) {
     case FFT_SQUARE:

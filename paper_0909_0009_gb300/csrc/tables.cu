@@ -76,6 +76,12 @@ __global__ void k_lambda_table(const double* __restrict__ x, const double* __res
 
 }  // namespace
 
+void launch_lambda_mm(const double* x, const double* fac, int npairs, int L, double* mant, int* expo,
+                      cudaStream_t st) {
+  k_lambda_mm<<<(npairs + 127) / 128, 128, 0, st>>>(x, fac, npairs, L, mant, expo);
+  FNL_CUDA(cudaGetLastError());
+}
+
 void build_lambda_tables(fnl_shells* sh, cudaStream_t st) {
   const int L = sh->lmax, np = sh->npairs;
   std::vector<double> fac(L + 1, 0.0);

@@ -1,0 +1,450 @@
+// Legendre transforms of the mixed-precision forms on the 5th-generation tensor cores.
+//
+// Both transforms are batched GEMMs over the problems (m, parity) with the 2 N_r real
+// columns c of all shells as the M dimension (one or two 128-row tiles):
+//   synthesis (step (ii)):  F[mp][j][c]  = sum_k  Phi[mp][k][c] * Lambda_syn[mp][j][k]
+//                           M = c, N = ring pairs j, K = degrees k
+//   analysis  (step (iv)):  Phi[mp][k][c] = sum_j G[mp][j][c] * Lambda_ana[mp][k][j]
+//                           M = c, N = degrees k, K = ring pairs j
+// A (data: Phi or G) is stored with c contiguous and is read MN-major; B (the Legendre
+// tables) is stored K-contiguous.  Operands are split into BF16 terms x = x0 + x1 (+ x2)
+// and every product of terms whose indices sum to less than the term count is
+// accumulated in FP32 in tensor memory (3 products for 2 terms, 6 for 3 terms).
+//
+// Kernel structure (one persistent CTA per SM, 192 threads):
+//   warp 0      TMA producer: A tile 128 c x 32 k per term (two 64-column boxes, 128B
+//               swizzle), B tile N x 32 k per term (16-row boxes, 64B swizzle)
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues
+//               tcgen05.mma (M = 128, N = tile width, K = 16) from one thread
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator, then per mode:
+//               synthesis -> F (FP32); analysis -> radial quadrature of Eq. 5 reduced over
+//               the shells of the tile (T and E), or the per-shell coefficients.
+// Every mbarrier wait is bounded; on expiry the kernel records an error code and unwinds.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fnl_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace fnl {
+
+namespace {
+
+constexpr int kEpiWarps = 4;
+constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
+constexpr uint32_t kABytes = 8192;   // 128 c x 32 k bf16 (two 64 x 32 boxes)
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false (and records `code`) if the phase does not complete in time
+// or another role of this kernel has already recorded an error.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023) == 1023 && *(volatile int*)err != 0) return false;
+  }
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading/stride byte offsets,
+// version 1, swizzle layout (2 = 128B, 4 = 64B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)layout << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, A MN-major, B K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// Bounded rendezvous of the epilogue warps on an mbarrier (count = kEpiWarps): one arrive
+// per warp, then every lane waits for the phase.  Returns false if the wait expired.
+__device__ __forceinline__ bool epi_sync(uint64_t* bar, uint32_t parity, int lane, int* err) {
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+  const bool ok = mbar_wait(bar, parity, err, 5);
+  __syncwarp();
+  return ok;
+}
+
+// Sum of x over the 16 lanes of this lane's parity class, for 32 columns at once: after
+// the four exchange steps lane l holds the sums of columns (l & 30) and (l & 30) + 1.
+__device__ __forceinline__ void reduce_columns(float (&x)[32], int lane) {
+#pragma unroll
+  for (int o = 16, cnt = 32; o >= 2; o >>= 1, cnt >>= 1) {
+    const bool upper = (lane & o) != 0;
+    const int half = cnt >> 1;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < half) {
+        const float send = upper ? x[k] : x[k + half];
+        const float keep = upper ? x[k + half] : x[k];
+        x[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant__ TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = a.stages;
+  const uint32_t bBytes = (uint32_t)a.nmax * 64u;
+  const uint32_t stageBytes = (uint32_t)a.nterms * (kABytes + bBytes);
+  uint64_t* full = (uint64_t*)(smem + (size_t)S * stageBytes);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint64_t* epib = drain + 1;  // [2] rendezvous of the epilogue warps
+  uint32_t* tslot = (uint32_t*)(epib + 2);
+  float* red = (float*)(smem + (size_t)S * stageBytes + 1024);  // [4 warps][256 cols][2 fields][2 parities]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t sbase = smem_u32(smem);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    mbar_init(&epib[0], kEpiWarps);
+    mbar_init(&epib[1], kEpiWarps);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed = 0, armed_par = 0;  // stages with copies issued, and the parity armed
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        const TcTile tl = a.tiles[t];
+        for (int kb = 0; kb < tl.nkb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, a.err, 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[stage], (uint32_t)a.nterms * (kABytes + (uint32_t)tl.nsize * 64u));
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          const uint32_t st = sbase + (uint32_t)stage * stageBytes;
+          for (int tm = 0; tm < a.nterms; ++tm) {
+            const uint32_t sa = st + (uint32_t)tm * kABytes;
+            const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tm * bBytes;
+            if (a.mode == TC_SYNTH) {
+              // A: Phi rows r0 + 32 kb, columns c0 .. c0 + 127
+              tma_load_2d(sa, &a.tmA[tm], tl.c0, tl.r0 + 32 * kb, &full[stage]);
+              tma_load_2d(sa + 4096, &a.tmA[tm], tl.c0 + 64, tl.r0 + 32 * kb, &full[stage]);
+              // B: slab (r0 / 32 + kb), ring pairs n0 .. n0 + nsize - 1
+              for (int q = 0; q < tl.nsize / 16; ++q)
+                tma_load_3d(sb + 1024u * q, &a.tmB[tm], 0, tl.n0 + 16 * q, tl.r0 / 32 + kb, &full[stage]);
+            } else {
+              // A: G plane mp, ring pairs 32 kb .., columns c0 .. c0 + 127
+              tma_load_3d(sa, &a.tmA[tm], tl.c0, 32 * kb, tl.mp, &full[stage]);
+              tma_load_3d(sa + 4096, &a.tmA[tm], tl.c0 + 64, 32 * kb, tl.mp, &full[stage]);
+              // B: Lambda_ana rows r0 + n0 .., ring pairs 32 kb ..
+              for (int q = 0; q < tl.nsize / 16; ++q)
+                tma_load_2d(sb + 1024u * q, &a.tmB[tm], 32 * kb, tl.r0 + tl.n0 + 16 * q, &full[stage]);
+            }
+          }
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA unwinds (bounded)
+        for (int s = 0; s < S; ++s) {
+          if (!(armed >> s & 1u)) continue;
+          const uint32_t par = (armed_par >> s) & 1u;
+          for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(&full[s], par); ++i) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t aphase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        const TcTile tl = a.tiles[t];
+        if (!mbar_wait(&tempty[acc], aphase ^ 1, a.err, 2)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)acc * 256u;
+        const uint32_t idesc = idesc_bf16(tl.nsize);
+        for (int kb = 0; kb < tl.nkb; ++kb) {
+          if (!mbar_wait(&full[stage], phase, a.err, 3)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = sbase + (uint32_t)stage * stageBytes;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            for (int ta = 0; ta < a.nterms; ++ta) {
+              for (int tb = 0; ta + tb < a.nterms; ++tb) {
+                const uint32_t sa = st + (uint32_t)ta * kABytes + (uint32_t)ks * 2048u;
+                const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tb * bBytes + (uint32_t)ks * 32u;
+                const uint64_t ad = sdesc(sa, 4096, 1024, 2);  // MN-major, 128B swizzle
+                const uint64_t bd = sdesc(sb, 16, 512, 4);     // K-major, 64B swizzle
+                tc_mma(d, ad, bd, idesc, (kb | ks | ta | tb) ? 1u : 0u);
+              }
+            }
+          }
+          tc_commit(&empty[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[acc]);
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1;
+      }
+      // every MMA this thread issued has completed before TMEM is released (bounded)
+      tc_commit(drain);
+      for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(drain, 0); ++i) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int ew = warp - 2;
+    int acc = 0;
+    uint32_t aphase = 0, ephase = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      const TcTile tl = a.tiles[t];
+      if (!mbar_wait(&tfull[acc], aphase, a.err, 4)) break;
+      tc_fence_after();
+      const int m = tl.mp >> 1, p = tl.mp & 1;
+      const int c = tl.c0 + 32 * q + lane;
+      const bool cvalid = c < 2 * a.nr;
+      const int nch = (tl.nsize + 31) / 32;
+      for (int ch = 0; ch < nch; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t)acc * 256u + (uint32_t)(ch * 32) + ((uint32_t)(32 * q) << 16), v);
+        if (ch == nch - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+        if (a.mode == TC_SYNTH) {
+          if (cvalid) {
+            float* out = a.F + ((size_t)tl.mp * a.npairs) * a.Cpad + c;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int jr = tl.n0 + ch * 32 + j;
+              if (ch * 32 + j < tl.nsize && jr < a.npairs) out[(size_t)jr * a.Cpad] = v[j];
+            }
+          }
+        } else if (a.mode == TC_ANA_STORE) {
+          if (cvalid) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int k = tl.n0 + ch * 32 + j;
+              if (ch * 32 + j < tl.nsize && k < tl.kvalid) {
+                const int l = m + p + 2 * k;
+                a.alm_out[alm_idx(l, m, a.L) * (2 * a.nr) + c] = (double)v[j];
+              }
+            }
+          }
+        } else {
+          // radial quadrature (Eq. 5): sum over the shells of this tile of q^X_l[i] Phi_NL,lm(r_i)
+          float tx[32], ex[32];
+          const int i = c >> 1;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int k = tl.n0 + ch * 32 + j;
+            float qt = 0.f, qe = 0.f;
+            if (cvalid && ch * 32 + j < tl.nsize && k < tl.kvalid) {
+              const int l = m + p + 2 * k;
+              qt = a.qT[(size_t)l * a.nr + i];
+              qe = a.qE[(size_t)l * a.nr + i];
+            }
+            tx[j] = v[j] * qt;
+            ex[j] = v[j] * qe;
+          }
+          reduce_columns(tx, lane);
+          reduce_columns(ex, lane);
+          const int col = ch * 32 + (lane & 30);
+          float* rw = red + (size_t)ew * 1024;
+          const int r = lane & 1;
+          rw[(col + 0) * 4 + 0 * 2 + r] = tx[0];
+          rw[(col + 1) * 4 + 0 * 2 + r] = tx[1];
+          rw[(col + 0) * 4 + 1 * 2 + r] = ex[0];
+          rw[(col + 1) * 4 + 1 * 2 + r] = ex[1];
+        }
+      }
+      if (a.mode == TC_ANA_QUAD) {
+        if (!epi_sync(&epib[0], ephase, lane, a.err)) break;
+        const int tid = threadIdx.x - 64;
+        for (int n = tid; n < tl.nsize; n += 32 * kEpiWarps) {
+          const int k = tl.n0 + n;
+          if (k >= tl.kvalid) continue;
+          float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int w = 0; w < kEpiWarps; ++w) {
+            const float* rw = red + (size_t)w * 1024 + n * 4;
+            s.x += rw[0];
+            s.y += rw[1];
+            s.z += rw[2];
+            s.w += rw[3];
+          }
+          const int l = m + p + 2 * k;
+          a.part[(size_t)(tl.c0 >> 7) * a.nalm + alm_idx(l, m, a.L)] = s;
+        }
+        if (!epi_sync(&epib[1], ephase, lane, a.err)) break;
+        ephase ^= 1;
+      }
+      acc ^= 1;
+      if (acc == 0) aphase ^= 1;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    FNL_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error(FNL_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                                 const uint32_t* box, int swizzle_bytes) {
+  CUtensorMap m;
+  uint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base),
+                           (const cuuint64_t*)dims, (const cuuint64_t*)strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(FNL_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return m;
+}
+
+size_t tc_smem_bytes(int nterms, int nmax, int stages) {
+  const size_t stage = (size_t)nterms * (kABytes + (size_t)nmax * 64);
+  return 1024 /*alignment*/ + (size_t)stages * stage + 1024 /*barriers*/ + 4 * 256 * 4 * sizeof(float);
+}
+
+int tc_stages(int nterms, int nmax) {
+  int s = 6;
+  while (s > 2 && tc_smem_bytes(nterms, nmax, s) > 227 * 1024) --s;
+  return s;
+}
+
+void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st) {
+  const size_t smem = tc_smem_bytes(args.nterms, args.nmax, args.stages);
+  FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::max(1, std::min(args.ntiles, sms));
+  k_tc_gemm<<<grid, kThreadsTc, smem, st>>>(args);
+  FNL_CUDA(cudaGetLastError());
+}
+
+}  // namespace fnl

@@ -25,7 +25,7 @@ EXPORTS = [
     "fnl_version", "fnl_last_error", "fnl_make_shells", "fnl_shells_destroy", "fnl_shells_info",
     "fnl_shells_mu", "fnl_generate", "fnl_filter", "fnl_synth", "fnl_analyse", "fnl_square",
     "fnl_accumulate", "fnl_gauss_legendre", "fnl_covariance", "fnl_cholesky_filters",
-    "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host",
+    "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_profile_enable.argtypes = [vp, i]
     lib.fnl_profile_read.argtypes = [vp, dp, i, ctypes.POINTER(i)]
     lib.fnl_generate_host.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp]
+    lib.fnl_device_status.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -198,6 +199,10 @@ class Shells:
         out = np.empty(self.nr)
         _check(_lib.fnl_shells_mu(self.handle, _dptr(out)))
         return out
+
+    def device_status(self):
+        """Synchronise and raise FnlError(FNL_ETIMEOUT) if a bounded device wait expired."""
+        _check(_lib.fnl_device_status(self.handle))
 
     @property
     def device_bytes(self) -> int:
