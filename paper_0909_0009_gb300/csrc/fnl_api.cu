@@ -1,6 +1,7 @@
 // C ABI of libfnl: argument validation, set-up of the shells object and the entry points
 // that chain the kernels of the path (Sect. 2, recipe steps (i)-(v)).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <functional>
@@ -155,9 +156,13 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   sh->d_row32 = upload(sh, sh->row32);
   build_lambda_tables_mixed(sh, 0);
 
+  // Products of the leading terms and the correction products accumulate separately
+  // (two accumulators per tile, so tiles are at most 128 wide).
+  const int split = sh->tc_split;
+  const int nmax = split ? 128 : 256;
   // synthesis tile width: fewest wasted ring pairs, each tile charged 16 columns of overhead
-  int best = 256, bestc = 1 << 30;
-  for (int n = 256; n >= 64; n -= 16) {
+  int best = nmax, bestc = 1 << 30;
+  for (int n = nmax; n >= 64; n -= 16) {
     const int tiles = (np + n - 1) / n, cost = tiles * (n + 16);
     if (cost < bestc) {
       bestc = cost;
@@ -174,7 +179,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
       for (int ct = 0; ct < ctiles; ++ct)
         ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0});
     for (int n0 = 0; n0 < K;) {
-      const int n = std::min(256, round_up(K - n0, 16));
+      const int n = std::min(nmax, round_up(K - n0, 16));
       for (int ct = 0; ct < ctiles; ++ct)
         ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0});
       n0 += n;
@@ -219,6 +224,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   }
   for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
     a->nterms = T;
+    a->split = split;
     a->L = L;
     a->nr = nr;
     a->npairs = np;
@@ -239,8 +245,8 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   sh->tc_ana.tiles = sh->d_tc_ana;
   sh->tc_ana.ntiles = (int)ta.size();
   sh->tc_ana.mode = TC_ANA_QUAD;
-  sh->tc_ana.nmax = 256;
-  sh->tc_ana.stages = tc_stages(T, 256);
+  sh->tc_ana.nmax = nmax;
+  sh->tc_ana.stages = tc_stages(T, nmax);
 }
 
 void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st) {
@@ -318,6 +324,10 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     sh->nalm = n_alm(L);
     sh->real_is_double = (d->prec == FNL_FP64);
     sh->nterms = d->prec == FNL_BF16X2 ? 2 : d->prec == FNL_BF16X3 ? 3 : 0;
+    {
+      const char* e = std::getenv("FNL_TC_SPLIT");
+      sh->tc_split = e ? std::atoi(e) != 0 : 1;
+    }
     FNL_CUDA(cudaDeviceGetAttribute(&sh->sms, cudaDevAttrMultiProcessorCount, device));
     const int np = sh->npairs, C = sh->C;
     const size_t ts = sh->real_is_double ? sizeof(double) : sizeof(float);

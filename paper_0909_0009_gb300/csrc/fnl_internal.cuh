@@ -140,6 +140,7 @@ struct fnl_shells {
   int Cpad = 0;                    // columns padded to a multiple of 128
   int npj = 0;                     // ring pairs padded to a multiple of 8 (row stride of Lambda_ana)
   int nsyn = 0;                    // synthesis tile width (ring pairs)
+  int tc_split = 1;                // separate accumulators for leading and correction products
   int sms = 0;
   std::vector<int64_t> row32;      // first Phi row of problem mp (rows padded to 32)
   int64_t* d_row32 = nullptr;

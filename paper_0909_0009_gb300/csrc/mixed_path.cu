@@ -40,6 +40,11 @@ __device__ __forceinline__ float2 noise_value_f32(float2 g, int m) {
   return make_float2(g.x * h, g.y * h);
 }
 
+// Step (i) in FP32, MB = 4 orders m per iteration: every thread draws one Philox block
+// (two shells of one m), each K_l row read from shared memory feeds MB products, and the
+// eight warps form the MB x {T, E} dot products v^X_l . n.
+constexpr int kMB = 4;
+
 __global__ void __launch_bounds__(kThreads) k_filter_mixed(int L, int nr, int Cpad, int nterms, int64_t term_stride,
                                                            const float* __restrict__ Kf, const double* __restrict__ vT,
                                                            const double* __restrict__ vE, uint64_t seed, uint64_t real,
@@ -51,10 +56,9 @@ __global__ void __launch_bounds__(kThreads) k_filter_mixed(int L, int nr, int Cp
   extern __shared__ __align__(16) unsigned char smem[];
   const int l = L - blockIdx.x;
   const int C = 2 * nr;
-  float2* ns = (float2*)smem;              // [nr]
-  float* vs = (float*)(ns + nr);           // [2][nr]
-  float* red = vs + 2 * nr;                // [4][8]
-  float* Ks = red + 32;                    // [nr][nr + 1]
+  float2* ns = (float2*)smem;              // [kMB][nr]
+  float* vs = (float*)(ns + kMB * nr);     // [2][nr]
+  float* Ks = vs + 2 * nr;                 // [nr][nr + 1]
   const int ldk = nr + 1;
   const float* Kl = Kf + (size_t)l * nr * nr;
   for (int e = threadIdx.x; e < nr * nr; e += kThreads) Ks[(e / nr) * ldk + (e % nr)] = Kl[e];
@@ -64,64 +68,69 @@ __global__ void __launch_bounds__(kThreads) k_filter_mixed(int L, int nr, int Cp
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nalm = (int64_t)(L + 1) * (L + 2) / 2;
-  for (int m = 0; m <= l; ++m) {
-    const int64_t idx = alm_idx(l, m, L);
+  const int npair = (nr + 1) / 2;
+  for (int m0 = 0; m0 <= l; m0 += kMB) {
+    const int nm = min(kMB, l + 1 - m0);
     __syncthreads();
     if (noise) {
-      for (int j = threadIdx.x; j < nr; j += kThreads) {
-        const double2 v = ((const double2*)noise)[(size_t)j * nalm + idx];
-        ns[j] = make_float2((float)v.x, m == 0 ? 0.f : (float)v.y);
+      for (int t = threadIdx.x; t < nm * nr; t += kThreads) {
+        const int mb = t / nr, j = t % nr, m = m0 + mb;
+        const double2 v = ((const double2*)noise)[(size_t)j * nalm + alm_idx(l, m, L)];
+        ns[mb * nr + j] = make_float2((float)v.x, m == 0 ? 0.f : (float)v.y);
       }
     } else {
-      for (int jp = threadIdx.x; jp < (nr + 1) / 2; jp += kThreads) {
+      for (int t = threadIdx.x; t < nm * npair; t += kThreads) {
+        const int mb = t / npair, jp = t % npair, m = m0 + mb;
         uint64_t w[4];
-        noise_words(seed, real, idx, jp, w);
-        ns[2 * jp] = noise_value_f32(box_muller_f32(w[0], w[1]), m);
-        if (2 * jp + 1 < nr) ns[2 * jp + 1] = noise_value_f32(box_muller_f32(w[2], w[3]), m);
+        noise_words(seed, real, alm_idx(l, m, L), jp, w);
+        ns[mb * nr + 2 * jp] = noise_value_f32(box_muller_f32(w[0], w[1]), m);
+        if (2 * jp + 1 < nr) ns[mb * nr + 2 * jp + 1] = noise_value_f32(box_muller_f32(w[2], w[3]), m);
       }
     }
     __syncthreads();
-    float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
-    for (int j = threadIdx.x; j < nr; j += kThreads) {
-      const float2 n = ns[j];
-      tr += vs[j] * n.x;
-      ti += vs[j] * n.y;
-      er += vs[nr + j] * n.x;
-      ei += vs[nr + j] * n.y;
+    // a^X_L for the MB orders: warp w -> (order w >> 1, field w & 1)
+    if (warp < 2 * kMB) {
+      const int mb = warp >> 1, f = warp & 1;
+      if (mb < nm) {
+        float sr = 0.f, si = 0.f;
+        const float* v = vs + f * nr;
+        for (int j = lane; j < nr; j += 32) {
+          const float2 n = ns[mb * nr + j];
+          sr += v[j] * n.x;
+          si += v[j] * n.y;
+        }
+        for (int o = 16; o; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+          const int64_t idx = alm_idx(l, m0 + mb, L);
+          ((double2*)(f ? aLE : aLT))[idx] = make_double2((double)sr, (double)si);
+        }
+      }
     }
-    for (int o = 16; o; o >>= 1) {
-      tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      ti += __shfl_xor_sync(0xffffffffu, ti, o);
-      er += __shfl_xor_sync(0xffffffffu, er, o);
-      ei += __shfl_xor_sync(0xffffffffu, ei, o);
-    }
-    if (lane == 0) {
-      red[warp] = tr;
-      red[8 + warp] = ti;
-      red[16 + warp] = er;
-      red[24 + warp] = ei;
-    }
-    const int p = (l - m) & 1;
-    const int64_t row = row32[2 * m + p] + ((l - m) >> 1);
+    // Phi_L,lm(r_i) = sum_{j <= i} K_l[i, j] n_lm(r_j) for the MB orders
     for (int c = threadIdx.x; c < C; c += kThreads) {
       const int i = c >> 1, r = c & 1;
-      float acc = 0.f;
+      float acc[kMB] = {0.f, 0.f, 0.f, 0.f};
       const float* Ki = Ks + (size_t)i * ldk;
-      for (int j = 0; j <= i; ++j) acc += Ki[j] * (r ? ns[j].y : ns[j].x);
-      store_terms(phiT + row * Cpad + c, term_stride, nterms, acc);
-      if (phi_api) phi_api[((size_t)idx * nr + i) * 2 + r] = (double)acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        s0 += red[w];
-        s1 += red[8 + w];
-        s2 += red[16 + w];
-        s3 += red[24 + w];
+      for (int j = 0; j <= i; ++j) {
+        const float k = Ki[j];
+#pragma unroll
+        for (int mb = 0; mb < kMB; ++mb) {
+          const float2 n = ns[mb * nr + j];
+          acc[mb] += k * (r ? n.y : n.x);
+        }
       }
-      ((double2*)aLT)[idx] = make_double2(s0, s1);
-      ((double2*)aLE)[idx] = make_double2(s2, s3);
+#pragma unroll
+      for (int mb = 0; mb < kMB; ++mb) {
+        if (mb >= nm) break;
+        const int m = m0 + mb;
+        const int p = (l - m) & 1;
+        const int64_t row = row32[2 * m + p] + ((l - m) >> 1);
+        store_terms(phiT + row * Cpad + c, term_stride, nterms, acc[mb]);
+        if (phi_api) phi_api[((size_t)alm_idx(l, m, L) * nr + i) * 2 + r] = (double)acc[mb];
+      }
     }
   }
 }
@@ -250,8 +259,7 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, cudaStream_t st) {
   const int nr = sh->nr;
-  const size_t smem = sizeof(float2) * nr + sizeof(float) * 2 * nr + sizeof(float) * 32 +
-                      sizeof(float) * (size_t)nr * (nr + 1);
+  const size_t smem = sizeof(float2) * kMB * nr + sizeof(float) * 2 * nr + sizeof(float) * (size_t)nr * (nr + 1);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_mixed<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
                                                       (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,

@@ -13,6 +13,7 @@
 // Transforms are self-sorting mixed-radix (4, 2, 3, 5) Stockham passes between two shared
 // memory buffers; twiddles e^{-2 pi i k / nphi} come from a table computed on the host.
 #include <cmath>
+#include <type_traits>
 
 #include "fnl_internal.cuh"
 #include "mixed.cuh"
@@ -78,6 +79,40 @@ __device__ __forceinline__ void small_dft(cplx<T>* v, int R, T sgn) {
   }
 }
 
+// ---- in-place passes with compile-time radix (register staging) -------------------------
+// Every thread loads the inputs of its butterflies (at most MaxB<R> of them), the block
+// synchronises, then the outputs are written over the same buffer: one N-point buffer per
+// transform instead of two.  Supports N / (R * blockDim) <= kMaxB for every radix used.
+template <int R>
+struct MaxB {
+  static constexpr int v = R == 2 ? 4 : R == 3 ? 3 : R == 4 ? 2 : R == 5 ? 2 : 1;
+};
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_r(cplx<T> (&v)[R], T sgn) {
+  if constexpr (R == 8) {
+    // radix 8 as 2 x 4: v'[q] = sum_r v[r] w8^{qr}, w8 = e^{sgn 2 pi i / 8}
+    const T h = (T)0.70710678118654752440;
+    cplx<T> a[4] = {v[0], v[2], v[4], v[6]}, b[4] = {v[1], v[3], v[5], v[7]};
+    small_dft(a, 4, sgn);
+    small_dft(b, 4, sgn);
+    // twiddles w8^q for q = 0..3 applied to the odd half
+    const cplx<T> b1 = {h * (b[1].x - sgn * b[1].y), h * (b[1].y + sgn * b[1].x)};
+    const cplx<T> b2 = imul(b[2], sgn);
+    const cplx<T> b3 = {h * (-b[3].x - sgn * b[3].y), h * (-b[3].y + sgn * b[3].x)};
+    v[0] = cadd(a[0], b[0]);
+    v[4] = csub(a[0], b[0]);
+    v[1] = cadd(a[1], b1);
+    v[5] = csub(a[1], b1);
+    v[2] = cadd(a[2], b2);
+    v[6] = csub(a[2], b2);
+    v[3] = cadd(a[3], b3);
+    v[7] = csub(a[3], b3);
+  } else {
+    small_dft(v, R, sgn);
+  }
+}
+
 // Stockham passes from src (ping-pong with dst); returns the buffer holding the result.
 // sgn = -1: forward DFT, +1: unnormalised inverse.
 template <typename T>
@@ -91,14 +126,20 @@ __device__ cplx<T>* stockham(cplx<T>* src, cplx<T>* dst, const FftPlan& plan, co
     const int stride = N / (Ns * R);
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
       const int k = j % Ns;
-      cplx<T> v[5];
+      cplx<T> v[8];
       v[0] = src[j];
       for (int r = 1; r < R; ++r) {
         cplx<T> w = tw[r * k * stride];
         w.y *= -sgn;  // table holds e^{-2 pi i k/N}; conjugate for the inverse
         v[r] = cmul(src[j + r * nb], w);
       }
-      small_dft(v, R, sgn);
+      if (R == 8) {
+        cplx<T> v8[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+        dft_r<T, 8>(v8, sgn);
+        for (int r = 0; r < 8; ++r) v[r] = v8[r];
+      } else {
+        small_dft(v, R, sgn);
+      }
       const int o = (j / Ns) * Ns * R + k;
       for (int r = 0; r < R; ++r) dst[o + r * Ns] = v[r];
     }
@@ -109,6 +150,57 @@ __device__ cplx<T>* stockham(cplx<T>* src, cplx<T>* dst, const FftPlan& plan, co
     Ns *= R;
   }
   return src;
+}
+
+template <typename T, int R>
+__device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cplx<T>* __restrict__ tw, T sgn) {
+  constexpr int MB = MaxB<R>::v;
+  const int nb = N / R;
+  const int stride = N / (Ns * R);
+  cplx<T> v[MB][R];
+#pragma unroll
+  for (int b = 0; b < MB; ++b) {
+    const int j = threadIdx.x + b * blockDim.x;
+    if (j < nb) {
+      const int k = j % Ns;
+      v[b][0] = buf[j];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tw[r * k * stride];
+        w.y *= -sgn;
+        v[b][r] = cmul(buf[j + r * nb], w);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < MB; ++b) {
+    const int j = threadIdx.x + b * blockDim.x;
+    if (j < nb) {
+      dft_r<T, R>(v[b], sgn);
+      const int k = j % Ns;
+      const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[o + r * Ns] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __restrict__ tw, T sgn) {
+  int Ns = 1;
+  for (int p = 0; p < plan.nrad; ++p) {
+    const int R = plan.rad[p];
+    switch (R) {
+      case 8: pass_inplace<T, 8>(buf, plan.n, Ns, tw, sgn); break;
+      case 4: pass_inplace<T, 4>(buf, plan.n, Ns, tw, sgn); break;
+      case 2: pass_inplace<T, 2>(buf, plan.n, Ns, tw, sgn); break;
+      case 3: pass_inplace<T, 3>(buf, plan.n, Ns, tw, sgn); break;
+      default: pass_inplace<T, 5>(buf, plan.n, Ns, tw, sgn); break;
+    }
+    Ns *= R;
+  }
 }
 
 template <typename T>
@@ -214,6 +306,100 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
   }
 }
 
+// Group variant: block (shell group, ring pair), `group` shells handled one after the other
+// in a single in-place N-point buffer.  Used when every pass fits the register staging.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, int group) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.plan.n;
+  cplx<T>* buf = (cplx<T>*)smem;
+  const int jp = blockIdx.y;
+  const int south = a.ntheta - 1 - jp;
+  const bool equator = (south == jp);
+  const int L = a.L, np = a.npairs, C = a.C;
+  const T scale = (T)(6.28318530717958647692 / N * a.wgl[jp]);
+  for (int g = 0; g < group; ++g) {
+    const int s = blockIdx.x * group + g;
+    if (s >= a.nr) break;
+    if (MODE == FFT_ANALYSE_MAP) {
+      const double* rn = a.maps_in + ((size_t)s * a.ntheta + jp) * N;
+      const double* rs = a.maps_in + ((size_t)s * a.ntheta + south) * N;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = {(T)rn[k], (T)rs[k]};
+      __syncthreads();
+    } else {
+      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = {(T)0, (T)0};
+      __syncthreads();
+      for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        const cplx<T> E = *(const cplx<T>*)(a.F + ((size_t)(2 * m) * np + jp) * C + 2 * s);
+        const cplx<T> O = (m < L) ? *(const cplx<T>*)(a.F + ((size_t)(2 * m + 1) * np + jp) * C + 2 * s)
+                                  : cplx<T>{(T)0, (T)0};
+        const cplx<T> FN = cadd(E, O), FS = csub(E, O);
+        if (m == 0) {
+          buf[0] = {FN.x, FS.x};
+        } else {
+          buf[m] = {FN.x - FS.y, FN.y + FS.x};
+          buf[N - m] = {FN.x + FS.y, FS.x - FN.y};
+        }
+      }
+      __syncthreads();
+      fft_inplace(buf, a.plan, a.tw, (T)1);
+      if (MODE == FFT_SYNTH_MAP) {
+        double* rn = a.maps_out + ((size_t)s * a.ntheta + jp) * N;
+        double* rs = a.maps_out + ((size_t)s * a.ntheta + south) * N;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+          const cplx<T> z = buf[k];
+          rn[k] = (double)z.x;
+          if (!equator) rs[k] = (double)z.y;
+        }
+        __syncthreads();
+        continue;
+      }
+      const T mu = (T)a.mu[s];
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const cplx<T> z = buf[k];
+        buf[k] = {z.x * z.x - mu, z.y * z.y - mu};
+      }
+      __syncthreads();
+    }
+    fft_inplace(buf, a.plan, a.tw, (T)-1);
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+      const cplx<T> wm = buf[m];
+      const cplx<T> wc = buf[m == 0 ? 0 : N - m];
+      const cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
+      const cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
+      cplx<T> S, D;
+      if (equator) {
+        S = {gn.x * scale, gn.y * scale};
+        D = S;
+      } else {
+        S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
+        D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
+      }
+      const size_t oe = ((size_t)(2 * m) * np + jp) * C + 2 * s;
+      const size_t oo = ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+      if (a.nterms) {
+        store_terms(a.GT + oe, a.gt_stride, a.nterms, (float)S.x);
+        store_terms(a.GT + oe + 1, a.gt_stride, a.nterms, (float)S.y);
+        store_terms(a.GT + oo, a.gt_stride, a.nterms, (float)D.x);
+        store_terms(a.GT + oo + 1, a.gt_stride, a.nterms, (float)D.y);
+      } else {
+        *(cplx<T>*)(a.G + oe) = S;
+        *(cplx<T>*)(a.G + oo) = D;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+bool plan_fits_group(const FftPlan& p, int threads) {
+  for (int i = 0; i < p.nrad; ++i) {
+    const int R = p.rad[i];
+    const int mb = R == 2 ? 4 : R == 3 ? 3 : R == 4 ? 2 : R == 5 ? 2 : 1;
+    if (p.n / R > mb * threads) return false;
+  }
+  return true;
+}
+
 template <typename T>
 void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
   FftArgs<T> a;
@@ -233,9 +419,34 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   a.wgl = sh->d_wgl;
   a.maps_in = maps_in;
   a.maps_out = maps_out;
+  const int threads = sh->nphi >= 1024 ? 256 : 128;
+  const int gthreads = sh->nphi >= 2048 ? 512 : sh->nphi >= 1024 ? 256 : 128;
+  if (!std::is_same<T, double>::value && plan_fits_group(sh->fft, gthreads)) {
+    const int group = sh->nr >= 64 ? 4 : sh->nr >= 16 ? 2 : 1;
+    const size_t smem1 = sizeof(cplx<T>) * (size_t)sh->nphi;
+    dim3 g1((sh->nr + group - 1) / group, sh->npairs);
+    switch (mode) {
+      case FFT_SQUARE:
+        FNL_CUDA(cudaFuncSetAttribute(k_ring_fft_group<T, FFT_SQUARE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem1));
+        k_ring_fft_group<T, FFT_SQUARE><<<g1, gthreads, smem1, st>>>(a, group);
+        break;
+      case FFT_SYNTH_MAP:
+        FNL_CUDA(cudaFuncSetAttribute(k_ring_fft_group<T, FFT_SYNTH_MAP>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+        k_ring_fft_group<T, FFT_SYNTH_MAP><<<g1, gthreads, smem1, st>>>(a, group);
+        break;
+      default:
+        FNL_CUDA(cudaFuncSetAttribute(k_ring_fft_group<T, FFT_ANALYSE_MAP>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+        k_ring_fft_group<T, FFT_ANALYSE_MAP><<<g1, gthreads, smem1, st>>>(a, group);
+        break;
+    }
+    FNL_CUDA(cudaGetLastError());
+    return;
+  }
   const size_t smem = 2 * sizeof(cplx<T>) * (size_t)sh->nphi;
   dim3 grid(sh->nr, sh->npairs);
-  const int threads = sh->nphi >= 1024 ? 256 : 128;
   switch (mode) {
     case FFT_SQUARE:
       FNL_CUDA(cudaFuncSetAttribute(k_ring_fft<T, FFT_SQUARE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

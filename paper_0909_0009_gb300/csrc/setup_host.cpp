@@ -200,6 +200,7 @@ FftPlan make_fft_plan(int n) {
   FftPlan p;
   p.n = n;
   int v = n;
+  while (v % 8 == 0 && p.nrad < kMaxRadix) { p.rad[p.nrad++] = 8; v /= 8; }
   while (v % 4 == 0 && p.nrad < kMaxRadix) { p.rad[p.nrad++] = 4; v /= 4; }
   while (v % 2 == 0 && p.nrad < kMaxRadix) { p.rad[p.nrad++] = 2; v /= 2; }
   while (v % 3 == 0 && p.nrad < kMaxRadix) { p.rad[p.nrad++] = 3; v /= 3; }

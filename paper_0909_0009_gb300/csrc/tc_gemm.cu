@@ -270,13 +270,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           const uint32_t st = sbase + (uint32_t)stage * stageBytes;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
+            int corr = 0;  // correction products issued so far in this k step
             for (int ta = 0; ta < a.nterms; ++ta) {
               for (int tb = 0; ta + tb < a.nterms; ++tb) {
                 const uint32_t sa = st + (uint32_t)ta * kABytes + (uint32_t)ks * 2048u;
                 const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tb * bBytes + (uint32_t)ks * 32u;
                 const uint64_t ad = sdesc(sa, 4096, 1024, 2);  // MN-major, 128B swizzle
                 const uint64_t bd = sdesc(sb, 16, 512, 4);     // K-major, 64B swizzle
-                tc_mma(d, ad, bd, idesc, (kb | ks | ta | tb) ? 1u : 0u);
+                if (a.split && (ta | tb)) {
+                  // correction products accumulate in their own buffer, 128 columns further
+                  tc_mma(d + 128u, ad, bd, idesc, (kb | ks | corr) ? 1u : 0u);
+                  ++corr;
+                } else {
+                  tc_mma(d, ad, bd, idesc, (kb | ks | ta | tb) ? 1u : 0u);
+                }
               }
             }
           }
@@ -312,7 +319,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       const int nch = (tl.nsize + 31) / 32;
       for (int ch = 0; ch < nch; ++ch) {
         float v[32];
-        tmem_ld32(tmem + (uint32_t)acc * 256u + (uint32_t)(ch * 32) + ((uint32_t)(32 * q) << 16), v);
+        const uint32_t ta = tmem + (uint32_t)acc * 256u + (uint32_t)(ch * 32) + ((uint32_t)(32 * q) << 16);
+        tmem_ld32(ta, v);
+        if (a.split) {
+          float w[32];
+          tmem_ld32(ta + 128u, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
         if (ch == nch - 1) {
           tc_fence_before();
           __syncwarp();

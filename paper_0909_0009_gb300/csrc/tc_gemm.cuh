@@ -23,6 +23,8 @@ struct TcArgs {
   int ntiles;
   int mode;
   int nterms;           // 2 or 3
+  int split;            // 1: products of the leading terms and the correction products go to two
+                        //    separate accumulators (tile width <= 128), summed in the epilogue
   int nmax;             // largest tile width in this launch (B stage size)
   int stages;
   int L, nr, npairs, Cpad;

@@ -1,0 +1,123 @@
+"""GPU parity of the tensor-core forms (BF16-split Legendre GEMMs, FP32 ring FFT).
+
+Stages are compared with the FP64 oracle; whole realisations with the FP64 GPU path on
+the same Philox noise.  Bounds: the 2-term split (FNL_BF16X2) carries 16 significant
+bits per operand, the 3-term split (FNL_BF16X3) 24; with FP32 FFTs and accumulation the
+stage errors stay below the bounds written in each test, and a^X and a^X_NL of a full
+l_max = 1024 realisation stay within the 1e-5 precision target.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STAGE_BOUND = {"bf16x2": 2e-5, "bf16x3": 3e-6}
+TARGET = 1e-5
+
+
+def rel_l2(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    return float(np.linalg.norm((got - ref).ravel()) / max(np.linalg.norm(ref.ravel()), 1e-300))
+
+
+def cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_0909_0009_gb300 import build
+    build.build_library()
+    import paper_0909_0009_gb300.fnl as F
+    F.load_library()
+    return F
+
+
+class Pair:
+    """A mixed-precision shells object and the FP64 one, on the same filters and mu."""
+
+    def __init__(self, F, lmax, nr, ntheta, nphi, prec, K=None, store=True):
+        self.lmax, self.nr, self.ntheta, self.nphi = lmax, nr, ntheta, nphi
+        self.r, self.w = W.radial_grid(nr)
+        self.aT, self.aE = W.transfer_kernels(lmax, self.r)
+        self.K = W.random_lower_filters(lmax, nr, seed=lmax + nr, scale=8e-5) if K is None else K
+        self.mu = O.mu_ensemble(self.K)
+        self.grid = O.Grid(lmax, ntheta, nphi, store=store)
+        args = (lmax, nr, ntheta, nphi, self.r, self.w, self.aT, self.aE)
+        self.mx = F.Shells(*args, K=self.K, mu=self.mu, prec=prec)
+        self.d64 = F.Shells(*args, K=self.K, mu=self.mu, prec="fp64")
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
+@pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(32, 16, 49, 100), (96, 64, 145, 288), (128, 96, 193, 400)])
+def test_stages_match_oracle(F, prec, lmax, nr, ntheta, nphi):
+    c = Pair(F, lmax, nr, ntheta, nphi, prec)
+    bound = STAGE_BOUND[prec]
+    a = W.random_alm(lmax, nr, seed=21)
+    assert rel_l2(host(c.mx.synth(cuda(a))), O.synthesis(a, c.grid)) < bound
+    maps = np.random.default_rng(22).standard_normal((nr, ntheta, nphi))
+    assert rel_l2(host(c.mx.analyse(cuda(maps))), O.analysis(maps, c.grid)) < bound
+    phiL = O.phi_linear(c.K, O.philox_noise(lmax, nr, 5, 0))
+    assert rel_l2(host(c.mx.square(cuda(phiL))), O.phi_nonlinear(phiL, c.mu, c.grid)) < 3 * bound
+    c.mx.device_status()
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
+def test_filter_matches_oracle(F, prec):
+    c = Pair(F, 64, 32, 97, 200, prec)
+    phi = host(c.mx.filter(seed=7, realisation=2))
+    # FP32 filter on FP32 noise from the same Philox words
+    assert rel_l2(phi, O.phi_linear(c.K, O.philox_noise(64, 32, 7, 2))) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
+@pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(7, 8, 12, 25), (40, 16, 61, 125), (256, 64, 385, 800)])
+def test_generate_matches_fp64_path(F, prec, lmax, nr, ntheta, nphi):
+    c = Pair(F, lmax, nr, ntheta, nphi, prec)
+    for seed, fnl in ((1, 50.0), (2, 0.0)):
+        a = c.mx.generate(seed, 0, fnl)
+        b = c.d64.generate(seed, 0, fnl)
+        for k in ("aT", "aE", "aLT", "aLE"):
+            assert rel_l2(host(a[k]), host(b[k])) < 1e-6, k
+        for k in ("aNLT", "aNLE"):
+            assert rel_l2(host(a[k]), host(b[k])) < TARGET, (k, rel_l2(host(a[k]), host(b[k])))
+    c.mx.device_status()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3"])
+def test_generate_against_oracle_small(F, prec):
+    c = Pair(F, 32, 16, 49, 100, prec)
+    n = O.philox_noise(32, 16, 1, 0)
+    ref = O.generate(c.K, n, c.grid, c.r, c.w, c.aT, c.aE, 100.0, mu=c.mu)
+    out = c.mx.generate(1, 0, 100.0)
+    for k in ("aT", "aE", "aNLT", "aNLE"):
+        assert rel_l2(host(out[k]), ref[k]) < TARGET, k
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16x3"])
+def test_full_size_within_precision_target(F, prec):
+    """l_max = 1024, N_r = 128, 1537 x 3200, covariance filters: the mixed form against the
+    FP64 GPU path on the same noise, for a^X and for a^X_NL on its own."""
+    wl = W.FULL
+    r, w = W.radial_grid(wl.nr)
+    aT, aE = W.transfer_kernels(wl.lmax, r)
+    args = (wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE)
+    mx = F.Shells(*args, prec=prec)
+    d64 = F.Shells(*args, prec="fp64")
+    a = mx.generate(1, 0, wl.fnl[0])
+    b = d64.generate(1, 0, wl.fnl[0])
+    errs = {k: rel_l2(host(a[k]), host(b[k])) for k in ("aT", "aE", "aNLT", "aNLE")}
+    for k, e in errs.items():
+        assert e < TARGET, errs
+    mx.device_status()
