@@ -141,6 +141,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   sh->d_F = dalloc<float>(sh, (size_t)nmp * np * Cpad);
   sh->d_part = dalloc<float>(sh, 4 * (size_t)(Cpad / 128) * sh->nalm);
   sh->d_err = dalloc<int>(sh, 1);
+  sh->d_psum = dalloc<double>(sh, nr);
   FNL_CUDA(cudaMemset(sh->d_phiT, 0, sizeof(bf16_t) * (size_t)T * sh->phiT_stride));
   FNL_CUDA(cudaMemset(sh->d_lsyn, 0, sizeof(bf16_t) * (size_t)T * sh->lsyn_stride));
   FNL_CUDA(cudaMemset(sh->d_lana, 0, sizeof(bf16_t) * (size_t)T * sh->lana_stride));
@@ -210,9 +211,10 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
       sh->tc_syn.tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
     }
     {
-      const uint64_t dims[3] = {(uint64_t)Cpad, (uint64_t)np, (uint64_t)nmp};
-      const uint64_t str[2] = {(uint64_t)Cpad * 2, (uint64_t)np * Cpad * 2};
-      const uint32_t box[3] = {64, 32, 1};
+      // G is ring-pair-major, [jp][mp][Cpad]: box of 64 columns x 1 problem x 32 ring pairs
+      const uint64_t dims[3] = {(uint64_t)Cpad, (uint64_t)nmp, (uint64_t)np};
+      const uint64_t str[2] = {(uint64_t)Cpad * 2, (uint64_t)nmp * Cpad * 2};
+      const uint32_t box[3] = {64, 1, 32};
       sh->tc_ana.tmA[t] = make_tensor_map_bf16(gt, 3, dims, str, box, 128);
     }
     {
@@ -515,7 +517,8 @@ fnl_status fnl_filter(const fnl_shells* sh, uint64_t seed, uint64_t realisation,
     check_dev_ptr(noise, "noise", true);
     check_dev_ptr(phiL, "phiL", false);
     cudaStream_t st = (cudaStream_t)stream;
-    if (sh->nterms) launch_filter_mixed(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, st);
+    if (sh->nterms)
+      launch_filter_mixed(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, nullptr, st);
     else launch_filter(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + 2 * sh->nalm, phiL, st);
   });
 }
@@ -631,7 +634,7 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
   };
   mark(0);
   if (sh->nterms) {
-    launch_filter_mixed(sh, seed, realisation, noise, lT, lE, nullptr, st);   // (i)
+    launch_filter_mixed(sh, seed, realisation, noise, lT, lE, nullptr, sh->d_psum, st);  // (i)
     mark(1);
     launch_tc(sh, sh->tc_syn, TC_SYNTH, nullptr, st);                         // (ii) Legendre
     mark(2);
@@ -639,7 +642,7 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
     mark(3);
     launch_tc(sh, sh->tc_ana, TC_ANA_QUAD, nullptr, st);                      // (iv) Legendre + (v)
     mark(4);
-    launch_combine_mixed(sh, fnl, lT, lE, nT, nE, aT, aE, st);                // (v), Eq. 3
+    launch_combine_mixed(sh, fnl, lT, lE, nT, nE, aT, aE, sh->d_psum, st);   // (v), Eq. 3
   } else {
     launch_filter(sh, seed, realisation, noise, lT, lE, nullptr, st);        // (i)
     mark(1);

@@ -124,7 +124,7 @@ struct fnl_shells {
 
   // scratch of the path
   void* d_phi = nullptr;           // [rows_total][C] real type
-  void* d_F = nullptr;             // [2(L+1)][npairs][C] real type
+  void* d_F = nullptr;             // SIMT: [2(L+1)][npairs][C]; tensor-core forms: float [npairs][2(L+1)][Cpad]
   void* d_G = nullptr;             // [2(L+1)][npairs][C] real type
   double* d_aL = nullptr;          // [2][nalm][2]  a^T_L, a^E_L when the caller passes NULL
   double* d_aNL = nullptr;         // [2][nalm][2]
@@ -150,11 +150,12 @@ struct fnl_shells {
   int64_t lsyn_stride = 0;
   void* d_lana = nullptr;          // bf16 [nterms][rows16][npj]
   int64_t lana_stride = 0;
-  void* d_GT = nullptr;            // bf16 [nterms][2(L+1)][npairs][Cpad]
+  void* d_GT = nullptr;            // bf16 [nterms][npairs][2(L+1)][Cpad] (ring-pair-major)
   int64_t gt_stride = 0;
   void* d_part = nullptr;          // float4 [Cpad / 128][nalm]
   float* d_q32 = nullptr;          // [2][L+1][nr]  q^T, q^E in FP32
   int* d_err = nullptr;            // device error word of the tensor-core kernels
+  double* d_psum = nullptr;        // [nr] sum_lm w_m |Phi_L,lm(r_i)|^2 (Parseval monopole)
   fnl::TcTile* d_tc_syn = nullptr;
   fnl::TcTile* d_tc_ana = nullptr;
   fnl::TcArgs tc_syn{}, tc_ana{};
@@ -198,9 +199,9 @@ void launch_lambda_mm(const double* x, const double* fac, int npairs, int L, dou
 // ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
 void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st);
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
-                         double* aLE, double* phi_api, cudaStream_t st);
+                         double* aLE, double* phi_api, double* psum, cudaStream_t st);
 void launch_alm_to_terms(const fnl_shells* sh, const double* alm, cudaStream_t st);
 void launch_combine_mixed(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE, double* aNLT,
-                          double* aNLE, double* aT, double* aE, cudaStream_t st);
+                          double* aNLE, double* aT, double* aE, const double* psum, cudaStream_t st);
 
 }  // namespace fnl

@@ -1,8 +1,8 @@
 // Kernels of the mixed-precision forms (FNL_BF16X2, FNL_BF16X3) around the tensor-core
 // Legendre GEMMs:
-//   k_filter_mixed    step (i) in FP32: Phi_L = K_l n (Eq. 9) written as BF16 terms, and
-//                     a^X_L = v^X_l . n (Eq. 5) with FP32 products summed per block in FP32
-//                     and stored as FP64
+//   k_filter_gemm     step (i) in FP32: Phi_L = K_l n (Eq. 9) written as BF16 terms, and
+//                     a^X_L = v^X_l . n (Eq. 5) summed in FP32 and stored as FP64; also the
+//                     per-shell sums of |Phi_L,lm|^2 for the Parseval monopole
 //   k_lambda_mixed    lambda_lm(x_jp) from the FP64 recurrence, split into BF16 terms in the
 //                     two K-contiguous layouts of the synthesis and analysis GEMMs
 //   k_alm_to_terms    API coefficients -> BF16 terms of the synthesis operand
@@ -40,97 +40,156 @@ __device__ __forceinline__ float2 noise_value_f32(float2 g, int m) {
   return make_float2(g.x * h, g.y * h);
 }
 
-// Step (i) in FP32, MB = 4 orders m per iteration: every thread draws one Philox block
-// (two shells of one m), each K_l row read from shared memory feeds MB products, and the
-// eight warps form the MB x {T, E} dot products v^X_l . n.
-constexpr int kMB = 4;
+// Double-float accumulation (hi + lo, ~48 significant bits from FP32 operations):
+// the exact square of x (product and fmaf residual) is added with a two-sum.
+__device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, float w) {
+  const float xw = x * w;  // w is 1 or 2: exact
+  const float p = xw * x;
+  const float e = fmaf(xw, x, -p);
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb) + lo + e;
+  hi = s + err;
+  lo = err - (hi - s);
+}
 
-__global__ void __launch_bounds__(kThreads) k_filter_mixed(int L, int nr, int Cpad, int nterms, int64_t term_stride,
-                                                           const float* __restrict__ Kf, const double* __restrict__ vT,
-                                                           const double* __restrict__ vE, uint64_t seed, uint64_t real,
-                                                           const double* __restrict__ noise,
-                                                           const int64_t* __restrict__ row32,
-                                                           __nv_bfloat16* __restrict__ phiT,
-                                                           double* __restrict__ phi_api,
-                                                           double* __restrict__ aLT, double* __restrict__ aLE) {
+// Step (i) as a register-tiled FP32 GEMM per degree l (block per l, largest first):
+//   Phi_l[i][col] = sum_{j <= i} K_l[i][j] n_l[j][col],  col = 2 (m - m0) + {re, im}
+// over chunks of 32 orders m (64 columns).  K_l is staged transposed in shared memory; each
+// thread owns 8 rows i x 4 columns.  The noise tile is drawn by all threads (Philox4x64 +
+// FP32 Box-Muller); a^X_L = v^X_l . n per column (Eq. 5 applied to Eq. 9).
+constexpr int kFCols = 64;
+
+__global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
+                                                          const float* __restrict__ Kf, const double* __restrict__ vT,
+                                                          const double* __restrict__ vE, uint64_t seed,
+                                                          uint64_t real, const double* __restrict__ noise,
+                                                          const int64_t* __restrict__ row32,
+                                                          __nv_bfloat16* __restrict__ phiT,
+                                                          double* __restrict__ phi_api, double* __restrict__ aLT,
+                                                          double* __restrict__ aLE, double* __restrict__ psum) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int l = L - blockIdx.x;
-  const int C = 2 * nr;
-  float2* ns = (float2*)smem;              // [kMB][nr]
-  float* vs = (float*)(ns + kMB * nr);     // [2][nr]
-  float* Ks = vs + 2 * nr;                 // [nr][nr + 1]
-  const int ldk = nr + 1;
+  const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
+  float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
+  float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols]
+  float* vs = nt + (size_t)nr * kFCols;    // [2][nr]
+  double* red = (double*)(vs + 2 * nr);  // [16][nrp] Parseval partials (offset is an even float count)
   const float* Kl = Kf + (size_t)l * nr * nr;
-  for (int e = threadIdx.x; e < nr * nr; e += kThreads) Ks[(e / nr) * ldk + (e % nr)] = Kl[e];
+  for (int e = threadIdx.x; e < nr * nrp; e += kThreads) {
+    const int j = e / nrp, i = e % nrp;
+    Kt[e] = (i < nr && j <= i) ? Kl[(size_t)i * nr + j] : 0.f;
+  }
   for (int e = threadIdx.x; e < nr; e += kThreads) {
     vs[e] = (float)vT[(size_t)l * nr + e];
     vs[nr + e] = (float)vE[(size_t)l * nr + e];
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nalm = (int64_t)(L + 1) * (L + 2) / 2;
   const int npair = (nr + 1) / 2;
-  for (int m0 = 0; m0 <= l; m0 += kMB) {
-    const int nm = min(kMB, l + 1 - m0);
+  const int ib = threadIdx.x & 15, cb = threadIdx.x >> 4;  // rows 8 ib .. 8 ib + 7, columns 4 cb .. 4 cb + 3
+  const bool rows_active = 8 * ib < nr;
+  float ph[8], pl[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ph[q] = pl[q] = 0.f;
+
+  for (int m0 = 0; m0 <= l; m0 += kFCols / 2) {
+    const int nm = min(kFCols / 2, l + 1 - m0);
     __syncthreads();
+    // ---- noise tile n[j][col]
     if (noise) {
-      for (int t = threadIdx.x; t < nm * nr; t += kThreads) {
-        const int mb = t / nr, j = t % nr, m = m0 + mb;
-        const double2 v = ((const double2*)noise)[(size_t)j * nalm + alm_idx(l, m, L)];
-        ns[mb * nr + j] = make_float2((float)v.x, m == 0 ? 0.f : (float)v.y);
+      for (int t = threadIdx.x; t < nr * (kFCols / 2); t += kThreads) {
+        const int j = t / (kFCols / 2), mb = t % (kFCols / 2), m = m0 + mb;
+        float2 v = make_float2(0.f, 0.f);
+        if (mb < nm) {
+          const double2 d = ((const double2*)noise)[(size_t)j * nalm + alm_idx(l, m, L)];
+          v = make_float2((float)d.x, m == 0 ? 0.f : (float)d.y);
+        }
+        *(float2*)(nt + (size_t)j * kFCols + 2 * mb) = v;
       }
     } else {
-      for (int t = threadIdx.x; t < nm * npair; t += kThreads) {
-        const int mb = t / npair, jp = t % npair, m = m0 + mb;
-        uint64_t w[4];
-        noise_words(seed, real, alm_idx(l, m, L), jp, w);
-        ns[mb * nr + 2 * jp] = noise_value_f32(box_muller_f32(w[0], w[1]), m);
-        if (2 * jp + 1 < nr) ns[mb * nr + 2 * jp + 1] = noise_value_f32(box_muller_f32(w[2], w[3]), m);
+      for (int t = threadIdx.x; t < npair * (kFCols / 2); t += kThreads) {
+        const int jp = t / (kFCols / 2), mb = t % (kFCols / 2), m = m0 + mb;
+        float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+        if (mb < nm) {
+          uint64_t w[4];
+          noise_words(seed, real, alm_idx(l, m, L), jp, w);
+          v0 = noise_value_f32(box_muller_f32(w[0], w[1]), m);
+          v1 = noise_value_f32(box_muller_f32(w[2], w[3]), m);
+        }
+        *(float2*)(nt + (size_t)(2 * jp) * kFCols + 2 * mb) = v0;
+        if (2 * jp + 1 < nr) *(float2*)(nt + (size_t)(2 * jp + 1) * kFCols + 2 * mb) = v1;
       }
     }
     __syncthreads();
-    // a^X_L for the MB orders: warp w -> (order w >> 1, field w & 1)
-    if (warp < 2 * kMB) {
-      const int mb = warp >> 1, f = warp & 1;
+    // ---- a^X_L for the chunk: thread (field f, column col)
+    if (threadIdx.x < 2 * kFCols) {
+      const int col = threadIdx.x & (kFCols - 1), f = threadIdx.x / kFCols;
+      const int mb = col >> 1;
       if (mb < nm) {
-        float sr = 0.f, si = 0.f;
         const float* v = vs + f * nr;
-        for (int j = lane; j < nr; j += 32) {
-          const float2 n = ns[mb * nr + j];
-          sr += v[j] * n.x;
-          si += v[j] * n.y;
-        }
-        for (int o = 16; o; o >>= 1) {
-          sr += __shfl_xor_sync(0xffffffffu, sr, o);
-          si += __shfl_xor_sync(0xffffffffu, si, o);
-        }
-        if (lane == 0) {
-          const int64_t idx = alm_idx(l, m0 + mb, L);
-          ((double2*)(f ? aLE : aLT))[idx] = make_double2((double)sr, (double)si);
-        }
+        float sacc = 0.f;
+        for (int j = 0; j < nr; ++j) sacc += v[j] * nt[(size_t)j * kFCols + col];
+        const int64_t idx = alm_idx(l, m0 + mb, L);
+        (f ? aLE : aLT)[2 * idx + (col & 1)] = (double)sacc;
       }
     }
-    // Phi_L,lm(r_i) = sum_{j <= i} K_l[i, j] n_lm(r_j) for the MB orders
-    for (int c = threadIdx.x; c < C; c += kThreads) {
-      const int i = c >> 1, r = c & 1;
-      float acc[kMB] = {0.f, 0.f, 0.f, 0.f};
-      const float* Ki = Ks + (size_t)i * ldk;
-      for (int j = 0; j <= i; ++j) {
-        const float k = Ki[j];
+    // ---- Phi_L for the chunk
+    if (rows_active) {
+      float acc[8][4];
 #pragma unroll
-        for (int mb = 0; mb < kMB; ++mb) {
-          const float2 n = ns[mb * nr + j];
-          acc[mb] += k * (r ? n.y : n.x);
-        }
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
+      const int jend = min(nr, 8 * ib + 8);
+      for (int j = 0; j < jend; ++j) {
+        const float4 k0 = *(const float4*)(Kt + (size_t)j * nrp + 8 * ib);
+        const float4 k1 = *(const float4*)(Kt + (size_t)j * nrp + 8 * ib + 4);
+        const float4 nv = *(const float4*)(nt + (size_t)j * kFCols + 4 * cb);
+        const float kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+        const float nn[4] = {nv.x, nv.y, nv.z, nv.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(kk[q], nn[c], acc[q][c]);
       }
 #pragma unroll
-      for (int mb = 0; mb < kMB; ++mb) {
+      for (int h = 0; h < 2; ++h) {  // the two orders m of this thread's columns
+        const int mb = 2 * cb + h;
         if (mb >= nm) break;
         const int m = m0 + mb;
         const int p = (l - m) & 1;
         const int64_t row = row32[2 * m + p] + ((l - m) >> 1);
-        store_terms(phiT + row * Cpad + c, term_stride, nterms, acc[mb]);
-        if (phi_api) phi_api[((size_t)alm_idx(l, m, L) * nr + i) * 2 + r] = (double)acc[mb];
+        const int64_t idx = alm_idx(l, m, L);
+        const float wm = m == 0 ? 1.f : 2.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = 8 * ib + q;
+          if (i >= nr) break;
+          const float re = acc[q][2 * h], im = acc[q][2 * h + 1];
+          store_terms(phiT + row * Cpad + 2 * i, term_stride, nterms, re);
+          store_terms(phiT + row * Cpad + 2 * i + 1, term_stride, nterms, im);
+          if (phi_api) {
+            phi_api[((size_t)idx * nr + i) * 2] = (double)re;
+            phi_api[((size_t)idx * nr + i) * 2 + 1] = (double)im;
+          }
+          if (psum) {
+            df_add_square(ph[q], pl[q], re, wm);
+            df_add_square(ph[q], pl[q], im, wm);
+          }
+        }
       }
+    }
+  }
+  if (psum) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (rows_active) red[(size_t)cb * nrp + 8 * ib + q] = (double)ph[q] + (double)pl[q];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr; i += kThreads) {
+      double s = 0.0;
+      for (int c = 0; c < 16; ++c) s += red[(size_t)c * nrp + i];
+      atomicAdd(&psum[i], s);
     }
   }
 }
@@ -192,19 +251,33 @@ __global__ void k_alm_to_terms(int L, int nr, int Cpad, int64_t nalm, int nterms
   store_terms(phiT + (row32[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * Cpad + c, term_stride, nterms, (float)v);
 }
 
-__global__ void k_combine_mixed(int64_t nalm, int nct, double fnl, const float4* __restrict__ part,
+// a^X_NL,lm = sum over column tiles of the epilogue partials; for (l, m) = (0, 0) the
+// monopole comes from Parseval's identity instead (exact on this grid):
+//   Phi_NL,00(r_i) = (sum_lm w_m |Phi_L,lm(r_i)|^2 - 4 pi mu_i) / sqrt(4 pi),  w_0 = 1, w_m>0 = 2,
+// a difference of two nearly equal numbers that FP32 grid sums would resolve poorly.
+__global__ void k_combine_mixed(int64_t nalm, int nct, int nr, double fnl, const float4* __restrict__ part,
+                                const double* __restrict__ psum, const double* __restrict__ mu,
+                                const double* __restrict__ qT, const double* __restrict__ qE,
                                 const double2* __restrict__ aLT, const double2* __restrict__ aLE,
                                 double2* __restrict__ aNLT, double2* __restrict__ aNLE, double2* __restrict__ aT,
                                 double2* __restrict__ aE) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nalm) return;
   double tr = 0, ti = 0, er = 0, ei = 0;
-  for (int c = 0; c < nct; ++c) {
-    const float4 v = part[(size_t)c * nalm + i];
-    tr += v.x;
-    ti += v.y;
-    er += v.z;
-    ei += v.w;
+  if (i == 0 && psum) {
+    for (int s = 0; s < nr; ++s) {
+      const double phi00 = (psum[s] - 12.566370614359172954 * mu[s]) * 0.28209479177387814347;
+      tr += qT[s] * phi00;
+      er += qE[s] * phi00;
+    }
+  } else {
+    for (int c = 0; c < nct; ++c) {
+      const float4 v = part[(size_t)c * nalm + i];
+      tr += v.x;
+      ti += v.y;
+      er += v.z;
+      ei += v.w;
+    }
   }
   aNLT[i] = make_double2(tr, ti);
   aNLE[i] = make_double2(er, ei);
@@ -257,13 +330,16 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 }
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
-                         double* aLE, double* phi_api, cudaStream_t st) {
-  const int nr = sh->nr;
-  const size_t smem = sizeof(float2) * kMB * nr + sizeof(float) * 2 * nr + sizeof(float) * (size_t)nr * (nr + 1);
-  FNL_CUDA(cudaFuncSetAttribute(k_filter_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_filter_mixed<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
-                                                      (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,
-                                                      sh->d_row32, (__nv_bfloat16*)sh->d_phiT, phi_api, aLT, aLE);
+                         double* aLE, double* phi_api, double* psum, cudaStream_t st) {
+  if (psum) FNL_CUDA(cudaMemsetAsync(psum, 0, sizeof(double) * sh->nr, st));
+  const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
+  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)nr * kFCols + 2 * nr + 2) +
+                      sizeof(double) * 16 * (size_t)nrp + 16;
+  FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
+                                                     (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,
+                                                     sh->d_row32, (__nv_bfloat16*)sh->d_phiT, phi_api, aLT, aLE,
+                                                     psum);
   FNL_CUDA(cudaGetLastError());
 }
 
@@ -276,10 +352,10 @@ void launch_alm_to_terms(const fnl_shells* sh, const double* alm, cudaStream_t s
 }
 
 void launch_combine_mixed(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE, double* aNLT,
-                          double* aNLE, double* aT, double* aE, cudaStream_t st) {
+                          double* aNLE, double* aT, double* aE, const double* psum, cudaStream_t st) {
   k_combine_mixed<<<(unsigned)((sh->nalm + 255) / 256), 256, 0, st>>>(
-      sh->nalm, sh->Cpad / 128, fnl, (const float4*)sh->d_part, (const double2*)aLT, (const double2*)aLE,
-      (double2*)aNLT, (double2*)aNLE, (double2*)aT, (double2*)aE);
+      sh->nalm, sh->Cpad / 128, sh->nr, fnl, (const float4*)sh->d_part, psum, sh->d_mu, sh->d_qT, sh->d_qE,
+      (const double2*)aLT, (const double2*)aLE, (double2*)aNLT, (double2*)aNLE, (double2*)aT, (double2*)aE);
   FNL_CUDA(cudaGetLastError());
 }
 

@@ -79,6 +79,10 @@ __device__ __forceinline__ void small_dft(cplx<T>* v, int R, T sgn) {
   }
 }
 
+// Shared-memory index with one pad slot per 16 complex values: the strided writes of the
+// first Stockham passes then spread over all banks.
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
 // ---- in-place passes with compile-time radix (register staging) -------------------------
 // Every thread loads the inputs of its butterflies (at most MaxB<R> of them), the block
 // synchronises, then the outputs are written over the same buffer: one N-point buffer per
@@ -163,12 +167,12 @@ __device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cpl
     const int j = threadIdx.x + b * blockDim.x;
     if (j < nb) {
       const int k = j % Ns;
-      v[b][0] = buf[j];
+      v[b][0] = buf[padi(j)];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         cplx<T> w = tw[r * k * stride];
         w.y *= -sgn;
-        v[b][r] = cmul(buf[j + r * nb], w);
+        v[b][r] = cmul(buf[padi(j + r * nb)], w);
       }
     }
   }
@@ -181,7 +185,7 @@ __device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cpl
       const int k = j % Ns;
       const int o = (j / Ns) * Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[o + r * Ns] = v[b][r];
+      for (int r = 0; r < R; ++r) buf[padi(o + r * Ns)] = v[b][r];
     }
   }
   __syncthreads();
@@ -205,7 +209,8 @@ __device__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __
 
 template <typename T>
 struct FftArgs {
-  int L, nr, ntheta, npairs, C;  // C: column stride of F and G
+  int L, nr, ntheta, npairs, C;  // C: column count of a row of F and G
+  int64_t sp, sj;                // element strides of F and G between problems mp and ring pairs jp
   int nterms;                    // 0: G in the real type T; 2 or 3: G as BF16 terms in GT
   int64_t gt_stride;             // elements between BF16 terms
   __nv_bfloat16* GT;
@@ -240,8 +245,8 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
     for (int k = threadIdx.x; k < N; k += blockDim.x) b0[k] = {(T)0, (T)0};
     __syncthreads();
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-      const T* e = a.F + ((size_t)(2 * m) * np + jp) * C + 2 * s;
-      const T* o = a.F + ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+      const T* e = a.F + (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
+      const T* o = a.F + (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
       const cplx<T> E = {e[0], e[1]};
       const cplx<T> O = (m < L) ? cplx<T>{o[0], o[1]} : cplx<T>{(T)0, (T)0};
       const cplx<T> FN = cadd(E, O), FS = csub(E, O);
@@ -288,8 +293,8 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
       S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
       D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
     }
-    const size_t oe = ((size_t)(2 * m) * np + jp) * C + 2 * s;
-    const size_t oo = ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+    const size_t oe = (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
+    const size_t oo = (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
     if (a.nterms) {
       store_terms(a.GT + oe, a.gt_stride, a.nterms, (float)S.x);
       store_terms(a.GT + oe + 1, a.gt_stride, a.nterms, (float)S.y);
@@ -312,33 +317,34 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, int group) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.plan.n;
-  cplx<T>* buf = (cplx<T>*)smem;
+  cplx<T>* buf = (cplx<T>*)smem;  // padded: element i at i + i / 16
   const int jp = blockIdx.y;
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
-  const int L = a.L, np = a.npairs, C = a.C;
+  const int L = a.L;
   const T scale = (T)(6.28318530717958647692 / N * a.wgl[jp]);
+  const T* Fj = a.F + (size_t)jp * a.sj;
   for (int g = 0; g < group; ++g) {
     const int s = blockIdx.x * group + g;
     if (s >= a.nr) break;
     if (MODE == FFT_ANALYSE_MAP) {
       const double* rn = a.maps_in + ((size_t)s * a.ntheta + jp) * N;
       const double* rs = a.maps_in + ((size_t)s * a.ntheta + south) * N;
-      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = {(T)rn[k], (T)rs[k]};
+      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[padi(k)] = {(T)rn[k], (T)rs[k]};
       __syncthreads();
     } else {
-      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[k] = {(T)0, (T)0};
+      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[padi(k)] = {(T)0, (T)0};
       __syncthreads();
       for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        const cplx<T> E = *(const cplx<T>*)(a.F + ((size_t)(2 * m) * np + jp) * C + 2 * s);
-        const cplx<T> O = (m < L) ? *(const cplx<T>*)(a.F + ((size_t)(2 * m + 1) * np + jp) * C + 2 * s)
+        const cplx<T> E = *(const cplx<T>*)(Fj + (size_t)(2 * m) * a.sp + 2 * s);
+        const cplx<T> O = (m < L) ? *(const cplx<T>*)(Fj + (size_t)(2 * m + 1) * a.sp + 2 * s)
                                   : cplx<T>{(T)0, (T)0};
         const cplx<T> FN = cadd(E, O), FS = csub(E, O);
         if (m == 0) {
           buf[0] = {FN.x, FS.x};
         } else {
-          buf[m] = {FN.x - FS.y, FN.y + FS.x};
-          buf[N - m] = {FN.x + FS.y, FS.x - FN.y};
+          buf[padi(m)] = {FN.x - FS.y, FN.y + FS.x};
+          buf[padi(N - m)] = {FN.x + FS.y, FS.x - FN.y};
         }
       }
       __syncthreads();
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
         double* rn = a.maps_out + ((size_t)s * a.ntheta + jp) * N;
         double* rs = a.maps_out + ((size_t)s * a.ntheta + south) * N;
         for (int k = threadIdx.x; k < N; k += blockDim.x) {
-          const cplx<T> z = buf[k];
+          const cplx<T> z = buf[padi(k)];
           rn[k] = (double)z.x;
           if (!equator) rs[k] = (double)z.y;
         }
@@ -356,15 +362,15 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
       }
       const T mu = (T)a.mu[s];
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const cplx<T> z = buf[k];
-        buf[k] = {z.x * z.x - mu, z.y * z.y - mu};
+        const cplx<T> z = buf[padi(k)];
+        buf[padi(k)] = {z.x * z.x - mu, z.y * z.y - mu};
       }
       __syncthreads();
     }
     fft_inplace(buf, a.plan, a.tw, (T)-1);
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-      const cplx<T> wm = buf[m];
-      const cplx<T> wc = buf[m == 0 ? 0 : N - m];
+      const cplx<T> wm = buf[padi(m)];
+      const cplx<T> wc = buf[padi(m == 0 ? 0 : N - m)];
       const cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
       const cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
       cplx<T> S, D;
@@ -375,8 +381,8 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
         S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
         D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
       }
-      const size_t oe = ((size_t)(2 * m) * np + jp) * C + 2 * s;
-      const size_t oo = ((size_t)(2 * m + 1) * np + jp) * C + 2 * s;
+      const size_t oe = (size_t)jp * a.sj + (size_t)(2 * m) * a.sp + 2 * s;
+      const size_t oo = oe + (size_t)a.sp;
       if (a.nterms) {
         store_terms(a.GT + oe, a.gt_stride, a.nterms, (float)S.x);
         store_terms(a.GT + oe + 1, a.gt_stride, a.nterms, (float)S.y);
@@ -408,6 +414,13 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   a.ntheta = sh->ntheta;
   a.npairs = sh->npairs;
   a.C = sh->nterms ? sh->Cpad : sh->C;
+  if (sh->nterms) {  // ring-pair-major: F[jp][mp][Cpad]
+    a.sp = sh->Cpad;
+    a.sj = (int64_t)2 * (sh->lmax + 1) * sh->Cpad;
+  } else {           // problem-major: F[mp][jp][C]
+    a.sp = (int64_t)sh->npairs * sh->C;
+    a.sj = sh->C;
+  }
   a.nterms = sh->nterms;
   a.gt_stride = sh->gt_stride;
   a.GT = (__nv_bfloat16*)sh->d_GT;
@@ -423,7 +436,7 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   const int gthreads = sh->nphi >= 2048 ? 512 : sh->nphi >= 1024 ? 256 : 128;
   if (!std::is_same<T, double>::value && plan_fits_group(sh->fft, gthreads)) {
     const int group = sh->nr >= 64 ? 4 : sh->nr >= 16 ? 2 : 1;
-    const size_t smem1 = sizeof(cplx<T>) * (size_t)sh->nphi;
+    const size_t smem1 = sizeof(cplx<T>) * (size_t)(sh->nphi + sh->nphi / 16 + 1);
     dim3 g1((sh->nr + group - 1) / group, sh->npairs);
     switch (mode) {
       case FFT_SQUARE:

@@ -223,9 +223,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               for (int q = 0; q < tl.nsize / 16; ++q)
                 tma_load_3d(sb + 1024u * q, &a.tmB[tm], 0, tl.n0 + 16 * q, tl.r0 / 32 + kb, &full[stage]);
             } else {
-              // A: G plane mp, ring pairs 32 kb .., columns c0 .. c0 + 127
-              tma_load_3d(sa, &a.tmA[tm], tl.c0, 32 * kb, tl.mp, &full[stage]);
-              tma_load_3d(sa + 4096, &a.tmA[tm], tl.c0 + 64, 32 * kb, tl.mp, &full[stage]);
+              // A: G[jp][mp][c] at problem mp, ring pairs 32 kb .., columns c0 .. c0 + 127
+              tma_load_3d(sa, &a.tmA[tm], tl.c0, tl.mp, 32 * kb, &full[stage]);
+              tma_load_3d(sa + 4096, &a.tmA[tm], tl.c0 + 64, tl.mp, 32 * kb, &full[stage]);
               // B: Lambda_ana rows r0 + n0 .., ring pairs 32 kb ..
               for (int q = 0; q < tl.nsize / 16; ++q)
                 tma_load_2d(sb + 1024u * q, &a.tmB[tm], 32 * kb, tl.r0 + tl.n0 + 16 * q, &full[stage]);
@@ -334,11 +334,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         }
         if (a.mode == TC_SYNTH) {
           if (cvalid) {
-            float* out = a.F + ((size_t)tl.mp * a.npairs) * a.Cpad + c;
+            // F is ring-pair-major: F[jp][mp][Cpad]
+            float* out = a.F + (size_t)tl.mp * a.Cpad + c;
+            const size_t sj = (size_t)2 * (a.L + 1) * a.Cpad;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int jr = tl.n0 + ch * 32 + j;
-              if (ch * 32 + j < tl.nsize && jr < a.npairs) out[(size_t)jr * a.Cpad] = v[j];
+              if (ch * 32 + j < tl.nsize && jr < a.npairs) out[(size_t)jr * sj] = v[j];
             }
           }
         } else if (a.mode == TC_ANA_STORE) {

@@ -29,7 +29,7 @@ struct TcArgs {
   int stages;
   int L, nr, npairs, Cpad;
   int64_t nalm;
-  float* F;             // TC_SYNTH: [nmp][npairs][Cpad]
+  float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
   float4* part;         // TC_ANA_QUAD: [Cpad / 128][nalm] (T re, T im, E re, E im)
   double* alm_out;      // TC_ANA_STORE: [nalm][nr][2]
   const float* qT;      // [L+1][nr]

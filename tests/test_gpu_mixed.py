@@ -16,6 +16,9 @@ pytestmark = pytest.mark.gpu
 
 STAGE_BOUND = {"bf16x2": 2e-5, "bf16x3": 3e-6}
 TARGET = 1e-5
+# a^X_NL bound for the small cases: few terms per sum, so the 2-term split's 2^-17 operand
+# error does not average down there
+NL_BOUND = {"bf16x2": 3e-5, "bf16x3": TARGET}
 
 
 def rel_l2(got, ref):
@@ -90,7 +93,7 @@ def test_generate_matches_fp64_path(F, prec, lmax, nr, ntheta, nphi):
         for k in ("aT", "aE", "aLT", "aLE"):
             assert rel_l2(host(a[k]), host(b[k])) < 1e-6, k
         for k in ("aNLT", "aNLE"):
-            assert rel_l2(host(a[k]), host(b[k])) < TARGET, (k, rel_l2(host(a[k]), host(b[k])))
+            assert rel_l2(host(a[k]), host(b[k])) < NL_BOUND[prec], (k, rel_l2(host(a[k]), host(b[k])))
     c.mx.device_status()
 
 
@@ -105,7 +108,7 @@ def test_generate_against_oracle_small(F, prec):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["bf16x3"])
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
 def test_full_size_within_precision_target(F, prec):
     """l_max = 1024, N_r = 128, 1537 x 3200, covariance filters: the mixed form against the
     FP64 GPU path on the same noise, for a^X and for a^X_NL on its own."""
