@@ -447,13 +447,31 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     sh->d_mu = upload(sh, sh->mu);
     sh->d_tiles_syn = upload(sh, ts_syn);
     sh->d_tiles_ana = upload(sh, ts_ana);
+    // per-pass twiddles of the in-place ring FFT: the flat table's entry r k N / (Ns R)
+    std::vector<double> twp(2 * (size_t)std::max(sh->fft.ttotal, 1));
+    {
+      int ns = 1;
+      for (int pi = 0; pi < sh->fft.nrad; ++pi) {
+        const int R = sh->fft.rad[pi], stride = d->nphi / (ns * R);
+        for (int r = 1; r < R; ++r)
+          for (int k = 0; k < ns; ++k) {
+            const size_t o = (size_t)sh->fft.toff[pi] + (size_t)(r - 1) * ns + k;
+            const int e = r * k * stride;
+            twp[2 * o] = tw[2 * e];
+            twp[2 * o + 1] = tw[2 * e + 1];
+          }
+        ns *= R;
+      }
+    }
     if (sh->real_is_double) {
       sh->d_Kf = upload(sh, Kf);
       sh->d_tw = upload(sh, tw);
+      sh->d_twp = upload(sh, twp);
     } else {
-      std::vector<float> kf(Kf.begin(), Kf.end()), twf(tw.begin(), tw.end());
+      std::vector<float> kf(Kf.begin(), Kf.end()), twf(tw.begin(), tw.end()), twpf(twp.begin(), twp.end());
       sh->d_Kf = upload(sh, kf);
       sh->d_tw = upload(sh, twf);
+      sh->d_twp = upload(sh, twpf);
     }
     sh->d_aL = dalloc<double>(sh, 4 * (size_t)sh->nalm);
     sh->d_aNL = dalloc<double>(sh, 4 * (size_t)sh->nalm);

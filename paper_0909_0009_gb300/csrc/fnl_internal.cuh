@@ -70,6 +70,8 @@ struct FftPlan {
   int n = 0;
   int nrad = 0;
   int rad[kMaxRadix];
+  int toff[kMaxRadix];  // offset of pass p in the per-pass twiddle table
+  int ttotal = 0;       // sum over passes of (R_p - 1) Ns_p
 };
 
 // Tile of a SIMT grouped GEMM: problem mp, row tile, column tile.
@@ -120,6 +122,7 @@ struct fnl_shells {
   double* d_qE = nullptr;
   double* d_mu = nullptr;          // [nr]
   void* d_tw = nullptr;            // [nphi] complex real type, e^{-2 pi i k / nphi}
+  void* d_twp = nullptr;           // per-pass twiddles: pass p, [(r - 1) Ns_p + k] = e^{-2 pi i r k / (Ns_p R_p)}
   fnl::FftPlan fft;
 
   // scratch of the path

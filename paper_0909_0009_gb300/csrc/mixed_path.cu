@@ -42,6 +42,14 @@ __device__ __forceinline__ float2 noise_value_f32(float2 g, int m) {
 
 // Double-float accumulation (hi + lo, ~48 significant bits from FP32 operations):
 // the exact square of x (product and fmaf residual) is added with a two-sum.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float p, float e) {
+  const float s = hi + p;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (p - bb) + lo + e;
+  hi = s + err;
+  lo = err - (hi - s);
+}
+
 __device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, float w) {
   const float xw = x * w;  // w is 1 or 2: exact
   const float p = xw * x;
@@ -73,16 +81,19 @@ __global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpa
   const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
   float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
   float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols]
-  float* vs = nt + (size_t)nr * kFCols;    // [2][nr]
-  double* red = (double*)(vs + 2 * nr);  // [16][nrp] Parseval partials (offset is an even float count)
+  float* vs = nt + (size_t)nr * kFCols;    // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo
+  double* red = (double*)(vs + 4 * nr);  // [16][nrp] Parseval partials (offset is an even float count)
   const float* Kl = Kf + (size_t)l * nr * nr;
   for (int e = threadIdx.x; e < nr * nrp; e += kThreads) {
     const int j = e / nrp, i = e % nrp;
     Kt[e] = (i < nr && j <= i) ? Kl[(size_t)i * nr + j] : 0.f;
   }
   for (int e = threadIdx.x; e < nr; e += kThreads) {
-    vs[e] = (float)vT[(size_t)l * nr + e];
-    vs[nr + e] = (float)vE[(size_t)l * nr + e];
+    const double t = vT[(size_t)l * nr + e], u = vE[(size_t)l * nr + e];
+    vs[e] = (float)t;
+    vs[nr + e] = (float)u;
+    vs[2 * nr + e] = (float)(t - (double)(float)t);
+    vs[3 * nr + e] = (float)(u - (double)(float)u);
   }
   const int64_t nalm = (int64_t)(L + 1) * (L + 2) / 2;
   const int npair = (nr + 1) / 2;
@@ -126,11 +137,17 @@ __global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpa
       const int col = threadIdx.x & (kFCols - 1), f = threadIdx.x / kFCols;
       const int mb = col >> 1;
       if (mb < nm) {
-        const float* v = vs + f * nr;
-        float sacc = 0.f;
-        for (int j = 0; j < nr; ++j) sacc += v[j] * nt[(size_t)j * kFCols + col];
+        // exact FP32 products of the double-float v with n, summed in double-float
+        const float* vh = vs + f * nr;
+        const float* vl = vs + (2 + f) * nr;
+        float sh = 0.f, sl = 0.f;
+        for (int j = 0; j < nr; ++j) {
+          const float n = nt[(size_t)j * kFCols + col];
+          const float p = vh[j] * n;
+          df_add(sh, sl, p, fmaf(vh[j], n, -p) + vl[j] * n);
+        }
         const int64_t idx = alm_idx(l, m0 + mb, L);
-        (f ? aLE : aLT)[2 * idx + (col & 1)] = (double)sacc;
+        (f ? aLE : aLT)[2 * idx + (col & 1)] = (double)sh + (double)sl;
       }
     }
     // ---- Phi_L for the chunk
@@ -333,7 +350,7 @@ void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, con
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
   if (psum) FNL_CUDA(cudaMemsetAsync(psum, 0, sizeof(double) * sh->nr, st));
   const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
-  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)nr * kFCols + 2 * nr + 2) +
+  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)nr * kFCols + 4 * nr + 2) +
                       sizeof(double) * 16 * (size_t)nrp + 16;
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,

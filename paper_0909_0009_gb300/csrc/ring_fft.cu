@@ -156,11 +156,11 @@ __device__ cplx<T>* stockham(cplx<T>* src, cplx<T>* dst, const FftPlan& plan, co
   return src;
 }
 
+// twp: this pass's twiddles, [(r - 1) Ns + k] = e^{-2 pi i r k / (Ns R)} (contiguous in k)
 template <typename T, int R>
-__device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cplx<T>* __restrict__ tw, T sgn) {
+__device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cplx<T>* __restrict__ twp, T sgn) {
   constexpr int MB = MaxB<R>::v;
   const int nb = N / R;
-  const int stride = N / (Ns * R);
   cplx<T> v[MB][R];
 #pragma unroll
   for (int b = 0; b < MB; ++b) {
@@ -170,7 +170,7 @@ __device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cpl
       v[b][0] = buf[padi(j)];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cplx<T> w = tw[r * k * stride];
+        cplx<T> w = twp[(r - 1) * Ns + k];
         w.y *= -sgn;
         v[b][r] = cmul(buf[padi(j + r * nb)], w);
       }
@@ -192,16 +192,17 @@ __device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cpl
 }
 
 template <typename T>
-__device__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __restrict__ tw, T sgn) {
+__device__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __restrict__ twp, T sgn) {
   int Ns = 1;
   for (int p = 0; p < plan.nrad; ++p) {
     const int R = plan.rad[p];
+    const cplx<T>* t = twp + plan.toff[p];
     switch (R) {
-      case 8: pass_inplace<T, 8>(buf, plan.n, Ns, tw, sgn); break;
-      case 4: pass_inplace<T, 4>(buf, plan.n, Ns, tw, sgn); break;
-      case 2: pass_inplace<T, 2>(buf, plan.n, Ns, tw, sgn); break;
-      case 3: pass_inplace<T, 3>(buf, plan.n, Ns, tw, sgn); break;
-      default: pass_inplace<T, 5>(buf, plan.n, Ns, tw, sgn); break;
+      case 8: pass_inplace<T, 8>(buf, plan.n, Ns, t, sgn); break;
+      case 4: pass_inplace<T, 4>(buf, plan.n, Ns, t, sgn); break;
+      case 2: pass_inplace<T, 2>(buf, plan.n, Ns, t, sgn); break;
+      case 3: pass_inplace<T, 3>(buf, plan.n, Ns, t, sgn); break;
+      default: pass_inplace<T, 5>(buf, plan.n, Ns, t, sgn); break;
     }
     Ns *= R;
   }
@@ -216,6 +217,7 @@ struct FftArgs {
   __nv_bfloat16* GT;
   FftPlan plan;
   const cplx<T>* tw;
+  const cplx<T>* twp;    // per-pass twiddles
   const T* F;            // [2(L+1)][npairs][C]
   T* G;                  // [2(L+1)][npairs][C]
   const double* mu;      // [nr]
@@ -311,22 +313,69 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
   }
 }
 
-// Group variant: block (shell group, ring pair), `group` shells handled one after the other
-// in a single in-place N-point buffer.  Used when every pass fits the register staging.
+// Group variant: block (group of shells, ring pair); the group's rows of F are staged in
+// shared memory with vector loads, every shell then runs through one in-place N-point
+// buffer, its results (S, D per order m) overwrite its staged F values, and the group's
+// rows of G leave with vector stores (16-byte chunks of BF16 terms, or FP32 pairs).
+template <typename T>
+__device__ __forceinline__ void store_group(const FftArgs<T>& a, size_t o, const cplx<T>* v, int ng) {
+  if (a.nterms) {
+    if (ng == 4) {
+      float x[8] = {(float)v[0].x, (float)v[0].y, (float)v[1].x, (float)v[1].y,
+                    (float)v[2].x, (float)v[2].y, (float)v[3].x, (float)v[3].y};
+      __align__(16) __nv_bfloat16 h[3][8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[q]);
+        const float r1 = x[q] - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        h[0][q] = h0;
+        h[1][q] = h1;
+        h[2][q] = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+      }
+      for (int t = 0; t < a.nterms; ++t) *(uint4*)(a.GT + (size_t)t * a.gt_stride + o) = *(const uint4*)h[t];
+    } else {
+      for (int g = 0; g < ng; ++g) {
+        store_terms(a.GT + o + 2 * g, a.gt_stride, a.nterms, (float)v[g].x);
+        store_terms(a.GT + o + 2 * g + 1, a.gt_stride, a.nterms, (float)v[g].y);
+      }
+    }
+  } else {
+    for (int g = 0; g < ng; ++g) *(cplx<T>*)(a.G + o + 2 * g) = v[g];
+  }
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, int group) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.plan.n;
-  cplx<T>* buf = (cplx<T>*)smem;  // padded: element i at i + i / 16
+  const int npad = N + N / 16 + 1;
+  cplx<T>* buf = (cplx<T>*)smem;       // padded: element i at i + i / 16
+  cplx<T>* stg = buf + npad;           // [L + 1][2][group]: E, O of each shell, then S, D
   const int jp = blockIdx.y;
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
   const int L = a.L;
+  const int s0 = blockIdx.x * group;
+  const int ng = min(group, a.nr - s0);
   const T scale = (T)(6.28318530717958647692 / N * a.wgl[jp]);
-  const T* Fj = a.F + (size_t)jp * a.sj;
-  for (int g = 0; g < group; ++g) {
-    const int s = blockIdx.x * group + g;
-    if (s >= a.nr) break;
+  const size_t rowj = (size_t)jp * a.sj;
+
+  if (MODE != FFT_ANALYSE_MAP) {
+    for (int t = threadIdx.x; t < 2 * (L + 1); t += blockDim.x) {
+      const int m = t >> 1, p = t & 1;
+      cplx<T>* d = stg + (size_t)t * group;
+      if (p == 1 && m == L) {
+        for (int g = 0; g < ng; ++g) d[g] = {(T)0, (T)0};
+        continue;
+      }
+      const cplx<T>* src = (const cplx<T>*)(a.F + rowj + (size_t)(2 * m + p) * a.sp + 2 * s0);
+      for (int g = 0; g < ng; ++g) d[g] = src[g];
+    }
+    __syncthreads();
+  }
+  for (int g = 0; g < ng; ++g) {
+    const int s = s0 + g;
     if (MODE == FFT_ANALYSE_MAP) {
       const double* rn = a.maps_in + ((size_t)s * a.ntheta + jp) * N;
       const double* rs = a.maps_in + ((size_t)s * a.ntheta + south) * N;
@@ -336,9 +385,8 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
       for (int k = threadIdx.x; k < N; k += blockDim.x) buf[padi(k)] = {(T)0, (T)0};
       __syncthreads();
       for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        const cplx<T> E = *(const cplx<T>*)(Fj + (size_t)(2 * m) * a.sp + 2 * s);
-        const cplx<T> O = (m < L) ? *(const cplx<T>*)(Fj + (size_t)(2 * m + 1) * a.sp + 2 * s)
-                                  : cplx<T>{(T)0, (T)0};
+        const cplx<T> E = stg[(size_t)(2 * m) * group + g];
+        const cplx<T> O = stg[(size_t)(2 * m + 1) * group + g];
         const cplx<T> FN = cadd(E, O), FS = csub(E, O);
         if (m == 0) {
           buf[0] = {FN.x, FS.x};
@@ -348,7 +396,7 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
         }
       }
       __syncthreads();
-      fft_inplace(buf, a.plan, a.tw, (T)1);
+      fft_inplace(buf, a.plan, a.twp, (T)1);
       if (MODE == FFT_SYNTH_MAP) {
         double* rn = a.maps_out + ((size_t)s * a.ntheta + jp) * N;
         double* rs = a.maps_out + ((size_t)s * a.ntheta + south) * N;
@@ -367,7 +415,7 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
       }
       __syncthreads();
     }
-    fft_inplace(buf, a.plan, a.tw, (T)-1);
+    fft_inplace(buf, a.plan, a.twp, (T)-1);
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
       const cplx<T> wm = buf[padi(m)];
       const cplx<T> wc = buf[padi(m == 0 ? 0 : N - m)];
@@ -381,19 +429,16 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
         S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
         D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
       }
-      const size_t oe = (size_t)jp * a.sj + (size_t)(2 * m) * a.sp + 2 * s;
-      const size_t oo = oe + (size_t)a.sp;
-      if (a.nterms) {
-        store_terms(a.GT + oe, a.gt_stride, a.nterms, (float)S.x);
-        store_terms(a.GT + oe + 1, a.gt_stride, a.nterms, (float)S.y);
-        store_terms(a.GT + oo, a.gt_stride, a.nterms, (float)D.x);
-        store_terms(a.GT + oo + 1, a.gt_stride, a.nterms, (float)D.y);
-      } else {
-        *(cplx<T>*)(a.G + oe) = S;
-        *(cplx<T>*)(a.G + oo) = D;
-      }
+      stg[(size_t)(2 * m) * group + g] = S;
+      stg[(size_t)(2 * m + 1) * group + g] = D;
     }
     __syncthreads();
+  }
+  if (MODE != FFT_SYNTH_MAP) {
+    for (int t = threadIdx.x; t < 2 * (L + 1); t += blockDim.x) {
+      const int m = t >> 1, p = t & 1;
+      store_group(a, rowj + (size_t)(2 * m + p) * a.sp + 2 * s0, stg + (size_t)t * group, ng);
+    }
   }
 }
 
@@ -426,6 +471,7 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   a.GT = (__nv_bfloat16*)sh->d_GT;
   a.plan = sh->fft;
   a.tw = (const cplx<T>*)sh->d_tw;
+  a.twp = (const cplx<T>*)sh->d_twp;
   a.F = (const T*)sh->d_F;
   a.G = (T*)sh->d_G;
   a.mu = sh->d_mu;
@@ -435,9 +481,10 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   const int threads = sh->nphi >= 1024 ? 256 : 128;
   const int gthreads = sh->nphi >= 2048 ? 512 : sh->nphi >= 1024 ? 256 : 128;
   if (!std::is_same<T, double>::value && plan_fits_group(sh->fft, gthreads)) {
-    const int group = sh->nr >= 64 ? 4 : sh->nr >= 16 ? 2 : 1;
-    const size_t smem1 = sizeof(cplx<T>) * (size_t)(sh->nphi + sh->nphi / 16 + 1);
+    const int group = 4;
+    const size_t smem1 = sizeof(cplx<T>) * ((size_t)(sh->nphi + sh->nphi / 16 + 1) + (size_t)2 * (sh->lmax + 1) * group);
     dim3 g1((sh->nr + group - 1) / group, sh->npairs);
+    if (smem1 > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "ring FFT staging exceeds shared memory");
     switch (mode) {
       case FFT_SQUARE:
         FNL_CUDA(cudaFuncSetAttribute(k_ring_fft_group<T, FFT_SQUARE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

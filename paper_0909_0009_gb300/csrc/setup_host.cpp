@@ -206,6 +206,13 @@ FftPlan make_fft_plan(int n) {
   while (v % 3 == 0 && p.nrad < kMaxRadix) { p.rad[p.nrad++] = 3; v /= 3; }
   while (v % 5 == 0 && p.nrad < kMaxRadix) { p.rad[p.nrad++] = 5; v /= 5; }
   if (v != 1) throw Error(FNL_EINVAL, "nphi = " + std::to_string(n) + " is not 2/3/5-smooth");
+  int ns = 1, off = 0;
+  for (int i = 0; i < p.nrad; ++i) {
+    p.toff[i] = off;
+    off += (p.rad[i] - 1) * ns;
+    ns *= p.rad[i];
+  }
+  p.ttotal = off;
   return p;
 }
 
