@@ -68,25 +68,29 @@ __device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, flo
 // FP32 Box-Muller); a^X_L = v^X_l . n per column (Eq. 5 applied to Eq. 9).
 constexpr int kFCols = 64;
 
-__global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
-                                                          const float* __restrict__ Kf, const double* __restrict__ vT,
-                                                          const double* __restrict__ vE, uint64_t seed,
-                                                          uint64_t real, const double* __restrict__ noise,
-                                                          const int64_t* __restrict__ row32,
-                                                          __nv_bfloat16* __restrict__ phiT,
-                                                          double* __restrict__ phi_api, double* __restrict__ aLT,
-                                                          double* __restrict__ aLE, double* __restrict__ psum) {
+__global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
+                                                             const float* __restrict__ Kf,
+                                                             const double* __restrict__ vT,
+                                                             const double* __restrict__ vE, uint64_t seed,
+                                                             uint64_t real, const double* __restrict__ noise,
+                                                             const int64_t* __restrict__ row32,
+                                                             __nv_bfloat16* __restrict__ phiT,
+                                                             double* __restrict__ phi_api, double* __restrict__ aLT,
+                                                             double* __restrict__ aLE, double* __restrict__ psum) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int l = L - blockIdx.x;
   const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
   float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
-  float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols]
+  float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols] noise tile, then [kFCols][nr] output tile
   float* vs = nt + (size_t)nr * kFCols;    // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo
-  double* red = (double*)(vs + 4 * nr);  // [16][nrp] Parseval partials (offset is an even float count)
   const float* Kl = Kf + (size_t)l * nr * nr;
   for (int e = threadIdx.x; e < nr * nrp; e += kThreads) {
-    const int j = e / nrp, i = e % nrp;
-    Kt[e] = (i < nr && j <= i) ? Kl[(size_t)i * nr + j] : 0.f;
+    const int i = e / nr, j = e % nr;       // global reads along j
+    if (i < nrp) Kt[(size_t)j * nrp + i] = (i < nr && j <= i) ? Kl[(size_t)i * nr + j] : 0.f;
+  }
+  for (int e = threadIdx.x; e < nr * (nrp - nr); e += kThreads) {
+    const int j = e / (nrp - nr), i = nr + e % (nrp - nr);
+    Kt[(size_t)j * nrp + i] = 0.f;
   }
   for (int e = threadIdx.x; e < nr; e += kThreads) {
     const double t = vT[(size_t)l * nr + e], u = vE[(size_t)l * nr + e];
@@ -99,9 +103,9 @@ __global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpa
   const int npair = (nr + 1) / 2;
   const int ib = threadIdx.x & 15, cb = threadIdx.x >> 4;  // rows 8 ib .. 8 ib + 7, columns 4 cb .. 4 cb + 3
   const bool rows_active = 8 * ib < nr;
-  float ph[8], pl[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) ph[q] = pl[q] = 0.f;
+  // write-out phase: thread -> shell ws = threadIdx.x % 128, orders mb = threadIdx.x / 128 (+2 ...)
+  const int ws = threadIdx.x & 127, wh = threadIdx.x >> 7;
+  float ph = 0.f, pl = 0.f;  // sum_m w_m |Phi_L,lm(r_ws)|^2 over this thread's orders (double-float)
 
   for (int m0 = 0; m0 <= l; m0 += kFCols / 2) {
     const int nm = min(kFCols / 2, l + 1 - m0);
@@ -132,12 +136,11 @@ __global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpa
       }
     }
     __syncthreads();
-    // ---- a^X_L for the chunk: thread (field f, column col)
+    // ---- a^X_L for the chunk: thread (field f, column col); exact products, double-float sum
     if (threadIdx.x < 2 * kFCols) {
       const int col = threadIdx.x & (kFCols - 1), f = threadIdx.x / kFCols;
       const int mb = col >> 1;
       if (mb < nm) {
-        // exact FP32 products of the double-float v with n, summed in double-float
         const float* vh = vs + f * nr;
         const float* vl = vs + (2 + f) * nr;
         float sh = 0.f, sl = 0.f;
@@ -150,13 +153,13 @@ __global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpa
         (f ? aLE : aLT)[2 * idx + (col & 1)] = (double)sh + (double)sl;
       }
     }
-    // ---- Phi_L for the chunk
+    // ---- Phi_L for the chunk: 8 x 4 register tile per thread
+    float acc[8][4];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
     if (rows_active) {
-      float acc[8][4];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
       const int jend = min(nr, 8 * ib + 8);
       for (int j = 0; j < jend; ++j) {
         const float4 k0 = *(const float4*)(Kt + (size_t)j * nrp + 8 * ib);
@@ -169,46 +172,50 @@ __global__ void __launch_bounds__(kThreads) k_filter_gemm(int L, int nr, int Cpa
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(kk[q], nn[c], acc[q][c]);
       }
+    }
+    __syncthreads();  // the noise tile is no longer read: reuse it as the output tile [col][i]
+    if (rows_active) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {  // the two orders m of this thread's columns
-        const int mb = 2 * cb + h;
-        if (mb >= nm) break;
+      for (int q = 0; q < 8; ++q) {
+        const int i = 8 * ib + q;
+        if (i >= nr) break;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) nt[(size_t)(4 * cb + c) * nr + i] = acc[q][c];
+      }
+    }
+    __syncthreads();
+    // ---- write-out: rows (l, m) of Phi as BF16 terms, c = 2 i + {re, im} contiguous
+    if (ws < nr) {
+      for (int mb = wh; mb < nm; mb += kThreads / 128) {
         const int m = m0 + mb;
         const int p = (l - m) & 1;
         const int64_t row = row32[2 * m + p] + ((l - m) >> 1);
-        const int64_t idx = alm_idx(l, m, L);
-        const float wm = m == 0 ? 1.f : 2.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int i = 8 * ib + q;
-          if (i >= nr) break;
-          const float re = acc[q][2 * h], im = acc[q][2 * h + 1];
-          store_terms(phiT + row * Cpad + 2 * i, term_stride, nterms, re);
-          store_terms(phiT + row * Cpad + 2 * i + 1, term_stride, nterms, im);
-          if (phi_api) {
-            phi_api[((size_t)idx * nr + i) * 2] = (double)re;
-            phi_api[((size_t)idx * nr + i) * 2 + 1] = (double)im;
-          }
-          if (psum) {
-            df_add_square(ph[q], pl[q], re, wm);
-            df_add_square(ph[q], pl[q], im, wm);
-          }
+        const float re = nt[(size_t)(2 * mb) * nr + ws], im = nt[(size_t)(2 * mb + 1) * nr + ws];
+        __nv_bfloat162 t0, t1, t2;
+        const __nv_bfloat16 r0 = __float2bfloat16_rn(re), i0 = __float2bfloat16_rn(im);
+        const float rr1 = re - __bfloat162float(r0), ir1 = im - __bfloat162float(i0);
+        const __nv_bfloat16 r1 = __float2bfloat16_rn(rr1), i1 = __float2bfloat16_rn(ir1);
+        t0.x = r0; t0.y = i0;
+        t1.x = r1; t1.y = i1;
+        t2.x = __float2bfloat16_rn(rr1 - __bfloat162float(r1));
+        t2.y = __float2bfloat16_rn(ir1 - __bfloat162float(i1));
+        __nv_bfloat16* dst = phiT + row * Cpad + 2 * ws;
+        *(__nv_bfloat162*)dst = t0;
+        *(__nv_bfloat162*)(dst + term_stride) = t1;
+        if (nterms > 2) *(__nv_bfloat162*)(dst + 2 * term_stride) = t2;
+        if (phi_api) {
+          const int64_t idx = alm_idx(l, m, L);
+          *(double2*)(phi_api + ((size_t)idx * nr + ws) * 2) = make_double2((double)re, (double)im);
+        }
+        if (psum) {
+          const float wm = m == 0 ? 1.f : 2.f;
+          df_add_square(ph, pl, re, wm);
+          df_add_square(ph, pl, im, wm);
         }
       }
     }
   }
-  if (psum) {
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (rows_active) red[(size_t)cb * nrp + 8 * ib + q] = (double)ph[q] + (double)pl[q];
-    __syncthreads();
-    for (int i = threadIdx.x; i < nr; i += kThreads) {
-      double s = 0.0;
-      for (int c = 0; c < 16; ++c) s += red[(size_t)c * nrp + i];
-      atomicAdd(&psum[i], s);
-    }
-  }
+  if (psum && ws < nr) atomicAdd(&psum[ws], (double)ph + (double)pl);
 }
 
 __device__ __forceinline__ double flushed(double v) { return fabs(v) < 1e-290 ? 0.0 : v; }
@@ -350,8 +357,7 @@ void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, con
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
   if (psum) FNL_CUDA(cudaMemsetAsync(psum, 0, sizeof(double) * sh->nr, st));
   const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
-  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)nr * kFCols + 4 * nr + 2) +
-                      sizeof(double) * 16 * (size_t)nrp + 16;
+  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)nr * kFCols + 4 * nr);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
                                                      (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,

@@ -158,7 +158,7 @@ __device__ cplx<T>* stockham(cplx<T>* src, cplx<T>* dst, const FftPlan& plan, co
 
 // twp: this pass's twiddles, [(r - 1) Ns + k] = e^{-2 pi i r k / (Ns R)} (contiguous in k)
 template <typename T, int R>
-__device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cplx<T>* __restrict__ twp, T sgn) {
+__device__ __forceinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cplx<T>* __restrict__ twp, T sgn) {
   constexpr int MB = MaxB<R>::v;
   const int nb = N / R;
   cplx<T> v[MB][R];
@@ -192,7 +192,7 @@ __device__ __noinline__ void pass_inplace(cplx<T>* buf, int N, int Ns, const cpl
 }
 
 template <typename T>
-__device__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __restrict__ twp, T sgn) {
+__device__ __noinline__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __restrict__ twp, T sgn) {
   int Ns = 1;
   for (int p = 0; p < plan.nrad; ++p) {
     const int R = plan.rad[p];
@@ -206,6 +206,52 @@ __device__ void fft_inplace(cplx<T>* buf, const FftPlan& plan, const cplx<T>* __
     }
     Ns *= R;
   }
+}
+
+// Ping-pong variant: one butterfly in flight per thread (load, transform, store), so only
+// R complex values are live; the result alternates between the two padded buffers.
+template <typename T, int R>
+__device__ __forceinline__ void pass_pp(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int N, int Ns,
+                                        const cplx<T>* __restrict__ twp, T sgn) {
+  const int nb = N / R;
+#pragma unroll 1
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int k = j % Ns;
+    cplx<T> v[R];
+    v[0] = src[padi(j)];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cplx<T> w = twp[(r - 1) * Ns + k];
+      w.y *= -sgn;
+      v[r] = cmul(src[padi(j + r * nb)], w);
+    }
+    dft_r<T, R>(v, sgn);
+    const int o = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[padi(o + r * Ns)] = v[r];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ cplx<T>* fft_pp(cplx<T>* a, cplx<T>* b, const FftPlan& plan, const cplx<T>* __restrict__ twp, T sgn) {
+  int Ns = 1;
+  for (int p = 0; p < plan.nrad; ++p) {
+    const int R = plan.rad[p];
+    const cplx<T>* t = twp + plan.toff[p];
+    switch (R) {
+      case 8: pass_pp<T, 8>(a, b, plan.n, Ns, t, sgn); break;
+      case 4: pass_pp<T, 4>(a, b, plan.n, Ns, t, sgn); break;
+      case 2: pass_pp<T, 2>(a, b, plan.n, Ns, t, sgn); break;
+      case 3: pass_pp<T, 3>(a, b, plan.n, Ns, t, sgn); break;
+      default: pass_pp<T, 5>(a, b, plan.n, Ns, t, sgn); break;
+    }
+    cplx<T>* x = a;
+    a = b;
+    b = x;
+    Ns *= R;
+  }
+  return a;
 }
 
 template <typename T>
@@ -320,7 +366,20 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
 template <typename T>
 __device__ __forceinline__ void store_group(const FftArgs<T>& a, size_t o, const cplx<T>* v, int ng) {
   if (a.nterms) {
-    if (ng == 4) {
+    if (ng == 2) {
+      float x[4] = {(float)v[0].x, (float)v[0].y, (float)v[1].x, (float)v[1].y};
+      __align__(8) __nv_bfloat16 h[3][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[q]);
+        const float r1 = x[q] - __bfloat162float(h0);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        h[0][q] = h0;
+        h[1][q] = h1;
+        h[2][q] = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+      }
+      for (int t = 0; t < a.nterms; ++t) *(uint2*)(a.GT + (size_t)t * a.gt_stride + o) = *(const uint2*)h[t];
+    } else if (ng == 4) {
       float x[8] = {(float)v[0].x, (float)v[0].y, (float)v[1].x, (float)v[1].y,
                     (float)v[2].x, (float)v[2].y, (float)v[3].x, (float)v[3].y};
       __align__(16) __nv_bfloat16 h[3][8];
@@ -350,8 +409,10 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.plan.n;
   const int npad = N + N / 16 + 1;
-  cplx<T>* buf = (cplx<T>*)smem;       // padded: element i at i + i / 16
-  cplx<T>* stg = buf + npad;           // [L + 1][2][group]: E, O of each shell, then S, D
+  cplx<T>* bufA = (cplx<T>*)smem;      // two padded buffers: element i at i + i / 16
+  cplx<T>* bufB = bufA + npad;
+  cplx<T>* stg = bufB + npad;          // [group][2 (L + 1)]: E, O of each shell, then S, D
+  const int ns2 = 2 * (a.L + 1);
   const int jp = blockIdx.y;
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
@@ -362,41 +423,41 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
   const size_t rowj = (size_t)jp * a.sj;
 
   if (MODE != FFT_ANALYSE_MAP) {
-    for (int t = threadIdx.x; t < 2 * (L + 1); t += blockDim.x) {
+    for (int t = threadIdx.x; t < ns2; t += blockDim.x) {
       const int m = t >> 1, p = t & 1;
-      cplx<T>* d = stg + (size_t)t * group;
       if (p == 1 && m == L) {
-        for (int g = 0; g < ng; ++g) d[g] = {(T)0, (T)0};
+        for (int g = 0; g < ng; ++g) stg[(size_t)g * ns2 + t] = {(T)0, (T)0};
         continue;
       }
       const cplx<T>* src = (const cplx<T>*)(a.F + rowj + (size_t)(2 * m + p) * a.sp + 2 * s0);
-      for (int g = 0; g < ng; ++g) d[g] = src[g];
+      for (int g = 0; g < ng; ++g) stg[(size_t)g * ns2 + t] = src[g];
     }
     __syncthreads();
   }
   for (int g = 0; g < ng; ++g) {
     const int s = s0 + g;
+    cplx<T>* buf = bufA;  // holds the data entering the forward transform
     if (MODE == FFT_ANALYSE_MAP) {
       const double* rn = a.maps_in + ((size_t)s * a.ntheta + jp) * N;
       const double* rs = a.maps_in + ((size_t)s * a.ntheta + south) * N;
       for (int k = threadIdx.x; k < N; k += blockDim.x) buf[padi(k)] = {(T)rn[k], (T)rs[k]};
       __syncthreads();
     } else {
-      for (int k = threadIdx.x; k < N; k += blockDim.x) buf[padi(k)] = {(T)0, (T)0};
+      for (int k = threadIdx.x; k < N; k += blockDim.x) bufA[padi(k)] = {(T)0, (T)0};
       __syncthreads();
       for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        const cplx<T> E = stg[(size_t)(2 * m) * group + g];
-        const cplx<T> O = stg[(size_t)(2 * m + 1) * group + g];
+        const cplx<T> E = stg[(size_t)g * ns2 + 2 * m];
+        const cplx<T> O = stg[(size_t)g * ns2 + 2 * m + 1];
         const cplx<T> FN = cadd(E, O), FS = csub(E, O);
         if (m == 0) {
-          buf[0] = {FN.x, FS.x};
+          bufA[0] = {FN.x, FS.x};
         } else {
-          buf[padi(m)] = {FN.x - FS.y, FN.y + FS.x};
-          buf[padi(N - m)] = {FN.x + FS.y, FS.x - FN.y};
+          bufA[padi(m)] = {FN.x - FS.y, FN.y + FS.x};
+          bufA[padi(N - m)] = {FN.x + FS.y, FS.x - FN.y};
         }
       }
       __syncthreads();
-      fft_inplace(buf, a.plan, a.twp, (T)1);
+      buf = fft_pp(bufA, bufB, a.plan, a.twp, (T)1);
       if (MODE == FFT_SYNTH_MAP) {
         double* rn = a.maps_out + ((size_t)s * a.ntheta + jp) * N;
         double* rs = a.maps_out + ((size_t)s * a.ntheta + south) * N;
@@ -415,10 +476,10 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
       }
       __syncthreads();
     }
-    fft_inplace(buf, a.plan, a.twp, (T)-1);
+    const cplx<T>* W = fft_pp(buf, buf == bufA ? bufB : bufA, a.plan, a.twp, (T)-1);
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-      const cplx<T> wm = buf[padi(m)];
-      const cplx<T> wc = buf[padi(m == 0 ? 0 : N - m)];
+      const cplx<T> wm = W[padi(m)];
+      const cplx<T> wc = W[padi(m == 0 ? 0 : N - m)];
       const cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
       const cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
       cplx<T> S, D;
@@ -429,27 +490,22 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
         S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
         D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
       }
-      stg[(size_t)(2 * m) * group + g] = S;
-      stg[(size_t)(2 * m + 1) * group + g] = D;
+      stg[(size_t)g * ns2 + 2 * m] = S;
+      stg[(size_t)g * ns2 + 2 * m + 1] = D;
     }
     __syncthreads();
   }
   if (MODE != FFT_SYNTH_MAP) {
-    for (int t = threadIdx.x; t < 2 * (L + 1); t += blockDim.x) {
+    for (int t = threadIdx.x; t < ns2; t += blockDim.x) {
       const int m = t >> 1, p = t & 1;
-      store_group(a, rowj + (size_t)(2 * m + p) * a.sp + 2 * s0, stg + (size_t)t * group, ng);
+      cplx<T> v[4];
+      for (int g = 0; g < ng; ++g) v[g] = stg[(size_t)g * ns2 + t];
+      store_group(a, rowj + (size_t)(2 * m + p) * a.sp + 2 * s0, v, ng);
     }
   }
 }
 
-bool plan_fits_group(const FftPlan& p, int threads) {
-  for (int i = 0; i < p.nrad; ++i) {
-    const int R = p.rad[i];
-    const int mb = R == 2 ? 4 : R == 3 ? 3 : R == 4 ? 2 : R == 5 ? 2 : 1;
-    if (p.n / R > mb * threads) return false;
-  }
-  return true;
-}
+bool plan_fits_group(const FftPlan&, int) { return true; }
 
 template <typename T>
 void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
@@ -481,8 +537,8 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   const int threads = sh->nphi >= 1024 ? 256 : 128;
   const int gthreads = sh->nphi >= 2048 ? 512 : sh->nphi >= 1024 ? 256 : 128;
   if (!std::is_same<T, double>::value && plan_fits_group(sh->fft, gthreads)) {
-    const int group = 4;
-    const size_t smem1 = sizeof(cplx<T>) * ((size_t)(sh->nphi + sh->nphi / 16 + 1) + (size_t)2 * (sh->lmax + 1) * group);
+    const int group = 2;
+    const size_t smem1 = sizeof(cplx<T>) * (2 * (size_t)(sh->nphi + sh->nphi / 16 + 1) + (size_t)2 * (sh->lmax + 1) * group);
     dim3 g1((sh->nr + group - 1) / group, sh->npairs);
     if (smem1 > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "ring FFT staging exceeds shared memory");
     switch (mode) {
