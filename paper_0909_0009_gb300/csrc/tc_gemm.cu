@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
 
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
-    if (lane == 0) {
+    // The whole warp walks the loop (converged); lane 0 waits and issues.
+    {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -204,10 +205,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
         for (int kb = 0; kb < tl.nkb; ++kb) {
-          if (!mbar_wait(&empty[stage], phase ^ 1, a.err, 1)) {
+          int good = 1;
+          if (lane == 0) good = mbar_wait(&empty[stage], phase ^ 1, a.err, 1);
+          good = __shfl_sync(0xffffffffu, good, 0);
+          if (!good) {
             ok = false;
             break;
           }
+          if (lane == 0) {
           mbar_expect_tx(&full[stage], (uint32_t)a.nterms * (kABytes + (uint32_t)tl.nsize * 64u));
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
@@ -231,13 +236,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
                 tma_load_2d(sb + 1024u * q, &a.tmB[tm], 32 * kb, tl.r0 + tl.n0 + 16 * q, &full[stage]);
             }
           }
+          }  // lane 0
+          __syncwarp();
           if (++stage == S) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
-      if (!ok) {
+      if (!ok && lane == 0) {
         // let the copies already issued land before the CTA unwinds (bounded)
         for (int s = 0; s < S; ++s) {
           if (!(armed >> s & 1u)) continue;
@@ -246,10 +253,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           }
         }
       }
+      __syncwarp();
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    // The whole warp walks the loop (converged); lane 0 waits, issues and commits.
+    {
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -257,51 +266,64 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       bool ok = true;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
-        if (!mbar_wait(&tempty[acc], aphase ^ 1, a.err, 2)) break;
+        int good = 1;
+        if (lane == 0) good = mbar_wait(&tempty[acc], aphase ^ 1, a.err, 2);
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)acc * 256u;
         const uint32_t idesc = idesc_bf16(tl.nsize);
         for (int kb = 0; kb < tl.nkb; ++kb) {
-          if (!mbar_wait(&full[stage], phase, a.err, 3)) {
+          good = 1;
+          if (lane == 0) good = mbar_wait(&full[stage], phase, a.err, 3);
+          good = __shfl_sync(0xffffffffu, good, 0);
+          if (!good) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = sbase + (uint32_t)stage * stageBytes;
+          if (lane == 0) {
+            const uint32_t st = sbase + (uint32_t)stage * stageBytes;
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            int corr = 0;  // correction products issued so far in this k step
-            for (int ta = 0; ta < a.nterms; ++ta) {
-              for (int tb = 0; ta + tb < a.nterms; ++tb) {
-                const uint32_t sa = st + (uint32_t)ta * kABytes + (uint32_t)ks * 2048u;
-                const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tb * bBytes + (uint32_t)ks * 32u;
-                const uint64_t ad = sdesc(sa, 4096, 1024, 2);  // MN-major, 128B swizzle
-                const uint64_t bd = sdesc(sb, 16, 512, 4);     // K-major, 64B swizzle
-                if (a.split && (ta | tb)) {
-                  // correction products accumulate in their own buffer, 128 columns further
-                  tc_mma(d + 128u, ad, bd, idesc, (kb | ks | corr) ? 1u : 0u);
-                  ++corr;
-                } else {
-                  tc_mma(d, ad, bd, idesc, (kb | ks | ta | tb) ? 1u : 0u);
+            for (int ks = 0; ks < 2; ++ks) {
+              int corr = 0;  // correction products issued so far in this k step
+              for (int ta = 0; ta < a.nterms; ++ta) {
+                for (int tb = 0; ta + tb < a.nterms; ++tb) {
+                  const uint32_t sa = st + (uint32_t)ta * kABytes + (uint32_t)ks * 2048u;
+                  const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tb * bBytes + (uint32_t)ks * 32u;
+                  const uint64_t ad = sdesc(sa, 4096, 1024, 2);  // MN-major, 128B swizzle
+                  const uint64_t bd = sdesc(sb, 16, 512, 4);     // K-major, 64B swizzle
+                  if (a.split && (ta | tb)) {
+                    // correction products accumulate in their own buffer, 128 columns further
+                    tc_mma(d + 128u, ad, bd, idesc, (kb | ks | corr) ? 1u : 0u);
+                    ++corr;
+                  } else {
+                    tc_mma(d, ad, bd, idesc, (kb | ks | ta | tb) ? 1u : 0u);
+                  }
                 }
               }
             }
+            tc_commit(&empty[stage]);
           }
-          tc_commit(&empty[stage]);
+          __syncwarp();
           if (++stage == S) {
             stage = 0;
             phase ^= 1;
           }
         }
         if (!ok) break;
-        tc_commit(&tfull[acc]);
+        if (lane == 0) tc_commit(&tfull[acc]);
+        __syncwarp();
         acc ^= 1;
         if (acc == 0) aphase ^= 1;
       }
-      // every MMA this thread issued has completed before TMEM is released (bounded)
-      tc_commit(drain);
-      for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(drain, 0); ++i) {
+      // every MMA this warp issued has completed before TMEM is released (bounded)
+      if (lane == 0) {
+        tc_commit(drain);
+        for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(drain, 0); ++i) {
+        }
       }
+      __syncwarp();
     }
   } else {
     // ------------------------------------------------------------------ epilogue

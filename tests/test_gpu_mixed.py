@@ -90,9 +90,10 @@ def test_generate_matches_fp64_path(F, prec, lmax, nr, ntheta, nphi):
     for seed, fnl in ((1, 50.0), (2, 0.0)):
         a = c.mx.generate(seed, 0, fnl)
         b = c.d64.generate(seed, 0, fnl)
-        for k in ("aT", "aE", "aLT", "aLE"):
+        for k in ("aLT", "aLE"):
             assert rel_l2(host(a[k]), host(b[k])) < 1e-6, k
-        for k in ("aNLT", "aNLE"):
+        # a^X carries f_NL times the error of a^X_NL
+        for k in ("aT", "aE", "aNLT", "aNLE"):
             assert rel_l2(host(a[k]), host(b[k])) < NL_BOUND[prec], (k, rel_l2(host(a[k]), host(b[k])))
     c.mx.device_status()
 
