@@ -10,6 +10,7 @@
 //                     a^X = a^X_L + f_NL a^X_NL (Eq. 3)
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -68,6 +69,11 @@ __device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, flo
 // FP32 Box-Muller); a^X_L = v^X_l . n per column (Eq. 5 applied to Eq. 9).
 constexpr int kFCols = 64;
 
+__host__ __device__ inline int out_stride(int nrp) {
+  const int s = nrp + nrp / 8;
+  return s + ((4 - s % 8) + 8) % 8;
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
                                                              const float* __restrict__ Kf,
                                                              const double* __restrict__ vT,
@@ -81,8 +87,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
   const int l = L - blockIdx.x;
   const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
   float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
-  float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols] noise tile, then [kFCols][nr] output tile
-  float* vs = nt + (size_t)nr * kFCols;    // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo
+  // output tile [col][i] with row stride os (i at i + i / 8, os = 4 mod 8): the 8-row thread
+  // tiles then write to distinct banks
+  const int os = out_stride(nrp);
+  float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols] noise tile, then [kFCols][os] output tile
+  float* vs = nt + (size_t)max(nr * kFCols, kFCols * os);  // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo
   const float* Kl = Kf + (size_t)l * nr * nr;
   for (int e = threadIdx.x; e < nr * nrp; e += kThreads) {
     const int i = e / nr, j = e % nr;       // global reads along j
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
         const int i = 8 * ib + q;
         if (i >= nr) break;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) nt[(size_t)(4 * cb + c) * nr + i] = acc[q][c];
+        for (int c = 0; c < 4; ++c) nt[(size_t)(4 * cb + c) * os + i + (i >> 3)] = acc[q][c];
       }
     }
     __syncthreads();
@@ -190,7 +199,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
         const int m = m0 + mb;
         const int p = (l - m) & 1;
         const int64_t row = row32[2 * m + p] + ((l - m) >> 1);
-        const float re = nt[(size_t)(2 * mb) * nr + ws], im = nt[(size_t)(2 * mb + 1) * nr + ws];
+        const float re = nt[(size_t)(2 * mb) * os + ws + (ws >> 3)];
+        const float im = nt[(size_t)(2 * mb + 1) * os + ws + (ws >> 3)];
         __nv_bfloat162 t0, t1, t2;
         const __nv_bfloat16 r0 = __float2bfloat16_rn(re), i0 = __float2bfloat16_rn(im);
         const float rr1 = re - __bfloat162float(r0), ir1 = im - __bfloat162float(i0);
@@ -357,7 +367,7 @@ void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, con
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
   if (psum) FNL_CUDA(cudaMemsetAsync(psum, 0, sizeof(double) * sh->nr, st));
   const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
-  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)nr * kFCols + 4 * nr);
+  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)std::max(nr * kFCols, kFCols * out_stride(nrp)) + 4 * nr);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
                                                      (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,

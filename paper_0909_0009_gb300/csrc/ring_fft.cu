@@ -413,6 +413,8 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
   cplx<T>* bufB = bufA + npad;
   cplx<T>* stg = bufB + npad;          // [group][2 (L + 1)]: E, O of each shell, then S, D
   const int ns2 = 2 * (a.L + 1);
+  cplx<T>* twp = stg + (size_t)group * ns2;  // per-pass twiddles, copied once per block
+  for (int k = threadIdx.x; k < a.plan.ttotal; k += blockDim.x) twp[k] = a.twp[k];
   const int jp = blockIdx.y;
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
         }
       }
       __syncthreads();
-      buf = fft_pp(bufA, bufB, a.plan, a.twp, (T)1);
+      buf = fft_pp(bufA, bufB, a.plan, twp, (T)1);
       if (MODE == FFT_SYNTH_MAP) {
         double* rn = a.maps_out + ((size_t)s * a.ntheta + jp) * N;
         double* rs = a.maps_out + ((size_t)s * a.ntheta + south) * N;
@@ -476,7 +478,7 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
       }
       __syncthreads();
     }
-    const cplx<T>* W = fft_pp(buf, buf == bufA ? bufB : bufA, a.plan, a.twp, (T)-1);
+    const cplx<T>* W = fft_pp(buf, buf == bufA ? bufB : bufA, a.plan, twp, (T)-1);
     for (int m = threadIdx.x; m <= L; m += blockDim.x) {
       const cplx<T> wm = W[padi(m)];
       const cplx<T> wc = W[padi(m == 0 ? 0 : N - m)];
@@ -538,7 +540,8 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
   const int gthreads = sh->nphi >= 2048 ? 512 : sh->nphi >= 1024 ? 256 : 128;
   if (!std::is_same<T, double>::value && plan_fits_group(sh->fft, gthreads)) {
     const int group = 2;
-    const size_t smem1 = sizeof(cplx<T>) * (2 * (size_t)(sh->nphi + sh->nphi / 16 + 1) + (size_t)2 * (sh->lmax + 1) * group);
+    const size_t smem1 = sizeof(cplx<T>) * (2 * (size_t)(sh->nphi + sh->nphi / 16 + 1) +
+                                            (size_t)2 * (sh->lmax + 1) * group + (size_t)sh->fft.ttotal);
     dim3 g1((sh->nr + group - 1) / group, sh->npairs);
     if (smem1 > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "ring FFT staging exceeds shared memory");
     switch (mode) {
