@@ -163,6 +163,38 @@ fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double
  * device word instead of hanging), else FNL_OK.  Clears the word. */
 fnl_status fnl_device_status(const fnl_shells* sh);
 
+/* ---- step (v) without any allocation ---------------------------------------------- */
+
+/* Largest (lmax + 1) * nr that fnl_accumulate_noalloc accepts. */
+#define FNL_NOALLOC_MAX_LNR 524288
+
+/* fnl_accumulate without a shells object and without allocating device memory, for
+ * callers that may not allocate: programs whose device memory belongs to another
+ * allocator (a cudaMalloc outside it fails or fragments its pool), latency-bound loops
+ * (cudaMalloc and cudaFree can synchronise the device), plug-ins held to a fixed memory
+ * budget.  The paper has no counterpart: it is the radial quadrature of Eq. 5 and the sum
+ * of Eq. 3, with the weights q^X_l[i] = w_i r_i^2 alpha^X_l(r_i) formed on each call into a
+ * fixed array inside the library instead of a table made by fnl_make_shells.
+ *  r, w:            device [nr] radial nodes and weights (8-byte aligned).
+ *  alphaT, alphaE:  device [lmax+1][nr] alpha^X_l(r_i) (8-byte aligned).
+ *  phiL, phiNL:     device [nalm][nr][2], either may be NULL and then counts as zero.
+ *  aT ... aNLE:     device [nalm][2] as in fnl_accumulate, any may be NULL.
+ * Every device pointer must belong to the current device; the call runs on `stream`.
+ * Sizes: 0 <= lmax <= 4096, 1 <= nr <= 128 and (lmax + 1) * nr <= FNL_NOALLOC_MAX_LNR,
+ * else FNL_EINVAL before anything runs.  The array holds 2 * FNL_NOALLOC_MAX_LNR doubles
+ * (8 MiB) on every GPU that loads the library, until the process exits.
+ * Set-up: the first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress, which may load the library's device code); make
+ * that first call before any stream capture begins.
+ * Every call uses the same array, and keeps in it the weights of the last call: each call
+ * rewrites every weight it reads before reading it, so nothing there has to start at zero,
+ * but calls that overlap on the GPU (concurrent streams, or threads sharing a device)
+ * race on it: order them. */
+fnl_status fnl_accumulate_noalloc(int lmax, int nr, const double* r, const double* w,
+                                  const double* alphaT, const double* alphaE, const double* phiL,
+                                  const double* phiNL, double fnl, double* aT, double* aE,
+                                  double* aLT, double* aLE, double* aNLT, double* aNLE, void* stream);
+
 /* ---- per-stage timing -------------------------------------------------------------- */
 
 /* Stages of fnl_generate timed when profiling is on (CUDA events recorded on the

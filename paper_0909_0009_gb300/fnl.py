@@ -26,6 +26,7 @@ EXPORTS = [
     "fnl_shells_mu", "fnl_generate", "fnl_filter", "fnl_synth", "fnl_analyse", "fnl_square",
     "fnl_accumulate", "fnl_gauss_legendre", "fnl_covariance", "fnl_cholesky_filters",
     "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
+    "fnl_accumulate_noalloc",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -81,6 +82,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_profile_read.argtypes = [vp, dp, i, ctypes.POINTER(i)]
     lib.fnl_generate_host.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp]
     lib.fnl_device_status.argtypes = [vp]
+    lib.fnl_accumulate_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -283,3 +285,29 @@ class Shells:
         ptrs = [_ptr(out[k]) for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]]
         _check(_lib.fnl_accumulate(self.handle, _ptr(phiL), _ptr(phiNL), float(fnl), *ptrs, _stream(stream)))
         return out
+
+
+NOALLOC_OUTPUTS = ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]
+
+
+def accumulate_noalloc(lmax, nr, r, w, alphaT, alphaE, phiL=None, phiNL=None, fnl: float = 0.0, out=None,
+                       stream=None):
+    """Step (v) through fnl_accumulate_noalloc, which allocates no device memory.
+
+    For callers that may not allocate (their device memory belongs to another allocator,
+    or cudaMalloc's device synchronisation is not acceptable where they run): every array
+    is the caller's, on the current device -- r, w (float64 [nr]), alphaT, alphaE (float64
+    [lmax+1, nr]), phiL, phiNL (complex128 [nalm, nr] or None) -- and ``out`` maps any of
+    aT, aE, aLT, aLE, aNLT, aNLE to a complex128 [nalm] tensor the call fills.  This wrapper
+    allocates nothing either.  Calls share one scratch array in the library: calls that
+    overlap on the GPU race.
+    """
+    lib = load_library()
+    out = out or {}
+    bad = set(out) - set(NOALLOC_OUTPUTS)
+    if bad:
+        raise ValueError(f"unknown outputs {sorted(bad)}")
+    ptrs = [_ptr(out.get(k)) for k in NOALLOC_OUTPUTS]
+    _check(lib.fnl_accumulate_noalloc(int(lmax), int(nr), _ptr(r), _ptr(w), _ptr(alphaT), _ptr(alphaE), _ptr(phiL),
+                                      _ptr(phiNL), float(fnl), *ptrs, _stream(stream)))
+    return out
