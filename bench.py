@@ -6,8 +6,13 @@ Philox noise + radial filter, synthesis Legendre GEMM, ring DFTs + square, analy
 Legendre GEMM, radial quadrature for T and E.  Default workload: l_max = 1024,
 N_r = 128 shells, 1537 x 3200 Gauss-Legendre grid, f_NL = 30.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|fp64|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x2|bf16x3|fp32|fp64]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+The default form is bf16x2 (Legendre GEMMs on tcgen05 with 2-term BF16 operands, FP32
+FFT and filter, FP64 tables and quadrature).  Beside it the line carries the FP64 GPU
+path on the same filters and noise: its throughput ("fp64") and the relative l2 error of
+a^T, a^E, a^T_NL and a^E_NL of the mixed form against it ("rel_err").
 
 Multi-GPU (torchrun, one rank per GPU): independent realisations per rank, no
 data-path collective ("replicas only"); value = realisations of all ranks / max time.
@@ -212,10 +217,11 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16x2", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16x2", "bf16x3"])
     ap.add_argument("--workload", default=W.FULL.name, choices=sorted(W.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 comparator (mixed runs)")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the FP64 comparator beside a mixed run (0: skip it)")
     args = ap.parse_args()
     wl = W.WORKLOADS[args.workload]
     if args.steps is None:
@@ -238,8 +244,12 @@ def main():
 
     r, w = W.radial_grid(wl.nr)
     aT, aE = W.transfer_kernels(wl.lmax, r)
-    cov = F.Cov(W.COV.A, W.COV.ns, W.COV.kmin, W.COV.kmax, W.COV.nk, W.COV.jitter_rel)
-    sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, cov=cov, prec=args.prec, device=local)
+    # filters K_l = chol(C_l + eps_l I) of the Eq. 7 covariance, built once on the host and
+    # shared by the timed form and its FP64 comparator
+    C = F.covariance(wl.lmax, r, W.COV.A, W.COV.ns, W.COV.kmin, W.COV.kmax, W.COV.nk)
+    K = F.cholesky_filters(C, W.COV.jitter_rel)
+    del C
+    sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=args.prec, device=local)
     fnl = wl.fnl[-1]
     stream = torch.cuda.current_stream()
     out = {k: sh._alm() for k in ("aT", "aE", "aLT", "aLE", "aNLT", "aNLE")}
@@ -289,6 +299,36 @@ def main():
         dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
     e2e_value = world * e2e_steps / float(t_e2e.item())
 
+    # ---- the FP64 GPU path on the same filters and noise: throughput and the error of the
+    # timed form against it (the metric's "mixed vs FP64")
+    fp64 = None
+    if args.prec != "fp64" and args.fp64_steps > 0:
+        ref = sh.generate(1, 0, fnl)
+        d64 = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec="fp64", device=local)
+        b = d64.generate(1, 0, fnl)
+        torch.cuda.synchronize()
+        rel = {}
+        for k in ("aT", "aE", "aNLT", "aNLE"):
+            rel[k] = float(torch.linalg.vector_norm(ref[k] - b[k]) / torch.linalg.vector_norm(b[k]))
+        out64 = {k: d64._alm() for k in ("aT", "aE", "aLT", "aLE", "aNLT", "aNLE")}
+        d64.generate(1, 10_000, fnl, out=out64)
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(args.fp64_steps):
+            d64.generate(1, rank * args.fp64_steps + i, fnl, out=out64)
+        f1.record(stream)
+        barrier()
+        t64 = torch.tensor([f0.elapsed_time(f1)], dtype=torch.float64, device=f"cuda:{local}")
+        if world > 1:
+            dist.all_reduce(t64, op=dist.ReduceOp.MAX)
+        fp64 = {"value": world * args.fp64_steps / (float(t64.item()) / 1e3), "unit": UNIT,
+                "steps": args.fp64_steps, "rel_err": rel, "rel_err_bound": 1e-5,
+                "seed": "seed 1, realisation 0, same filters and Philox noise"}
+        d64.close()
+        del d64, out64, ref, b
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -336,6 +376,9 @@ def main():
         "gpu_launches": 5 * args.steps,
         "clocks": clk,
     }
+    if fp64 is not None:
+        line["fp64"] = fp64
+        line["speedup_vs_fp64"] = value / fp64["value"]
     if not args.no_cpu_baseline and world == 1:
         per_real, sample_s = oracle_sample(wl, shells=2)
         line["cpu_baseline"] = {"value": 1.0 / per_real, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
