@@ -155,6 +155,14 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   }
   sh->d_q32 = upload(sh, q32);
   sh->d_row32 = upload(sh, sh->row32);
+  {
+    std::vector<float> tw2, tw1;
+    ring_square_tables(sh->nphi, tw2, tw1);
+    if (!tw2.empty()) {
+      sh->d_sqtw2 = upload(sh, tw2);
+      sh->d_sqtw1 = upload(sh, tw1);
+    }
+  }
   build_lambda_tables_mixed(sh, 0);
 
   // Products of the leading terms and the correction products accumulate separately

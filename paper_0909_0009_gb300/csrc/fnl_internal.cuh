@@ -154,6 +154,8 @@ struct fnl_shells {
   void* d_lana = nullptr;          // bf16 [nterms][rows16][npj]
   int64_t lana_stride = 0;
   void* d_GT = nullptr;            // bf16 [nterms][npairs][2(L+1)][Cpad] (ring-pair-major)
+  void* d_sqtw2 = nullptr;         // float2 twiddles of the specialised ring kernel (NULL: none for nphi)
+  void* d_sqtw1 = nullptr;
   int64_t gt_stride = 0;
   void* d_part = nullptr;          // float4 [Cpad / 128][nalm]
   float* d_q32 = nullptr;          // [2][L+1][nr]  q^T, q^E in FP32
@@ -186,6 +188,8 @@ void launch_filter(const fnl_shells* sh, uint64_t seed, uint64_t real, const dou
 void launch_synth_gemm(const fnl_shells* sh, cudaStream_t st);
 void launch_analysis_gemm(const fnl_shells* sh, cudaStream_t st);
 enum FftMode { FFT_SQUARE = 0, FFT_SYNTH_MAP = 1, FFT_ANALYSE_MAP = 2 };
+bool launch_ring_square(const fnl_shells* sh, cudaStream_t st);
+void ring_square_tables(int nphi, std::vector<float>& tw2, std::vector<float>& tw1);
 void launch_ring_fft(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out,
                      cudaStream_t st);
 void launch_alm_to_phi(const fnl_shells* sh, const double* alm, cudaStream_t st);

@@ -511,6 +511,7 @@ bool plan_fits_group(const FftPlan&, int) { return true; }
 
 template <typename T>
 void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
+  if (std::is_same<T, float>::value && mode == FFT_SQUARE && launch_ring_square(sh, st)) return;
   FftArgs<T> a;
   a.L = sh->lmax;
   a.nr = sh->nr;
