@@ -167,8 +167,10 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
 
   // Products of the leading terms and the correction products accumulate separately
   // (two accumulators per tile, so tiles are at most 128 wide).
+  // Tiles up to 256 wide in both directions (fewer, wider MMAs; the leading and correction
+  // accumulators then fill the 512 TMEM columns, one set per CTA); B in 64-row TMA boxes.
   const int split = sh->tc_split;
-  const int nmax = split ? 128 : 256;
+  const int nmax = 256, nmax_ana = 256, bbox = 64;
   // synthesis tile width: fewest wasted ring pairs, each tile charged 16 columns of overhead
   int best = nmax, bestc = 1 << 30;
   for (int n = nmax; n >= 64; n -= 16) {
@@ -188,7 +190,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
       for (int ct = 0; ct < ctiles; ++ct)
         ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0});
     for (int n0 = 0; n0 < K;) {
-      const int n = std::min(nmax, round_up(K - n0, 16));
+      const int n = std::min(nmax_ana, round_up(K - n0, 16));
       for (int ct = 0; ct < ctiles; ++ct)
         ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0});
       n0 += n;
@@ -215,8 +217,10 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
     {
       const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
       const uint64_t str[2] = {64, (uint64_t)np * 64};
-      const uint32_t box[3] = {32, 16, 1};
+      const uint32_t box[3] = {32, (uint32_t)bbox, 1};
       sh->tc_syn.tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
+      const uint32_t box16[3] = {32, 16, 1};
+      sh->tc_syn.tmB16[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box16, 64);
     }
     {
       // G is ring-pair-major, [jp][mp][Cpad]: box of 64 columns x 1 problem x 32 ring pairs
@@ -228,13 +232,22 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
     {
       const uint64_t dims[2] = {(uint64_t)np, (uint64_t)rows16};
       const uint64_t str[1] = {(uint64_t)sh->npj * 2};
-      const uint32_t box[2] = {32, 16};
+      const uint32_t box[2] = {32, (uint32_t)bbox};
       sh->tc_ana.tmB[t] = make_tensor_map_bf16(lana, 2, dims, str, box, 64);
+      const uint32_t box16[2] = {32, 16};
+      sh->tc_ana.tmB16[t] = make_tensor_map_bf16(lana, 2, dims, str, box16, 64);
     }
   }
+  // accumulators: the correction accumulator sits `cols` columns after the leading one;
+  // as many accumulator sets as fit in the 512 TMEM columns (at most 2)
   for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
+    const int nm = a == &sh->tc_syn ? sh->nsyn : nmax_ana;
+    const int cols = nm <= 128 ? 128 : 256;
     a->nterms = T;
     a->split = split;
+    a->bbox = bbox;
+    a->cols = cols;
+    a->nbuf = std::min(2, 512 / (split ? 2 * cols : cols));
     a->L = L;
     a->nr = nr;
     a->npairs = np;
@@ -255,8 +268,8 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   sh->tc_ana.tiles = sh->d_tc_ana;
   sh->tc_ana.ntiles = (int)ta.size();
   sh->tc_ana.mode = TC_ANA_QUAD;
-  sh->tc_ana.nmax = nmax;
-  sh->tc_ana.stages = tc_stages(T, nmax);
+  sh->tc_ana.nmax = nmax_ana;
+  sh->tc_ana.stages = tc_stages(T, nmax_ana);
 }
 
 void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st) {
@@ -335,8 +348,7 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     sh->real_is_double = (d->prec == FNL_FP64);
     sh->nterms = d->prec == FNL_BF16X2 ? 2 : d->prec == FNL_BF16X3 ? 3 : 0;
     {
-      const char* e = std::getenv("FNL_TC_SPLIT");
-      sh->tc_split = e ? std::atoi(e) != 0 : 1;
+      sh->tc_split = 1;
     }
     FNL_CUDA(cudaDeviceGetAttribute(&sh->sms, cudaDevAttrMultiProcessorCount, device));
     const int np = sh->npairs, C = sh->C;

@@ -13,9 +13,13 @@
 //
 // Kernel structure (one persistent CTA per SM, 192 threads):
 //   warp 0      TMA producer: A tile 128 c x 32 k per term (two 64-column boxes, 128B
-//               swizzle), B tile N x 32 k per term (16-row boxes, 64B swizzle)
-//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues
-//               tcgen05.mma (M = 128, N = tile width, K = 16) from one thread
+//               swizzle), B tile N x 32 k per term (64-row boxes and a 16-row remainder,
+//               64B swizzle)
+//   warp 1      allocates 512 TMEM columns and issues tcgen05.mma (M = 128, N = tile width
+//               up to 256, K = 16) from one thread; the descriptors of every term and k step
+//               are constant offsets from one base per stage.  The leading product and the
+//               correction products accumulate in two TMEM accumulators (`cols` apart); the
+//               accumulator sets that fit (1 for 256-wide tiles, 2 for 128) rotate over tiles
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator, then per mode:
 //               synthesis -> F (FP32); analysis -> radial quadrature of Eq. 5 reduced over
 //               the shells of the tile (T and E), or the per-shell coefficients.
@@ -152,6 +156,33 @@ __device__ __forceinline__ void reduce_columns(float (&x)[32], int lane) {
   }
 }
 
+// The MMAs of one 32-deep k block: two k steps of 16, every product of terms (ta, tb) with
+// ta + tb < NT.  da, db: descriptors of term 0 of A and B in this stage; the other terms and
+// k steps are constant offsets (descriptor start addresses count 16-byte units).  With
+// SPLIT the leading product accumulates in d and the corrections in dc, alternating.
+template <int NT, bool SPLIT>
+__device__ __forceinline__ void issue_kblock(uint64_t da, uint64_t db, uint32_t bterm16, uint32_t d, uint32_t dc,
+                                             uint32_t idesc, bool first) {
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    int corr = 0;
+#pragma unroll
+    for (int ta = 0; ta < NT; ++ta) {
+#pragma unroll
+      for (int tb = 0; ta + tb < NT; ++tb) {
+        const uint64_t ad = da + (uint64_t)((ta * kABytes + ks * 2048) >> 4);
+        const uint64_t bd = db + (uint64_t)(tb * bterm16 + ((ks * 32) >> 4));
+        if (SPLIT && (ta | tb)) {
+          tc_mma(dc, ad, bd, idesc, (first && ks == 0 && corr == 0) ? 0u : 1u);
+          ++corr;
+        } else {
+          tc_mma(d, ad, bd, idesc, (first && ks == 0 && ta == 0 && tb == 0) ? 0u : 1u);
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -225,15 +256,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               tma_load_2d(sa, &a.tmA[tm], tl.c0, tl.r0 + 32 * kb, &full[stage]);
               tma_load_2d(sa + 4096, &a.tmA[tm], tl.c0 + 64, tl.r0 + 32 * kb, &full[stage]);
               // B: slab (r0 / 32 + kb), ring pairs n0 .. n0 + nsize - 1
-              for (int q = 0; q < tl.nsize / 16; ++q)
-                tma_load_3d(sb + 1024u * q, &a.tmB[tm], 0, tl.n0 + 16 * q, tl.r0 / 32 + kb, &full[stage]);
+              int q = 0;
+              for (; q + a.bbox <= tl.nsize; q += a.bbox)
+                tma_load_3d(sb + 64u * q, &a.tmB[tm], 0, tl.n0 + q, tl.r0 / 32 + kb, &full[stage]);
+              for (; q < tl.nsize; q += 16)
+                tma_load_3d(sb + 64u * q, &a.tmB16[tm], 0, tl.n0 + q, tl.r0 / 32 + kb, &full[stage]);
             } else {
               // A: G[jp][mp][c] at problem mp, ring pairs 32 kb .., columns c0 .. c0 + 127
               tma_load_3d(sa, &a.tmA[tm], tl.c0, tl.mp, 32 * kb, &full[stage]);
               tma_load_3d(sa + 4096, &a.tmA[tm], tl.c0 + 64, tl.mp, 32 * kb, &full[stage]);
               // B: Lambda_ana rows r0 + n0 .., ring pairs 32 kb ..
-              for (int q = 0; q < tl.nsize / 16; ++q)
-                tma_load_2d(sb + 1024u * q, &a.tmB[tm], 32 * kb, tl.r0 + tl.n0 + 16 * q, &full[stage]);
+              int q = 0;
+              for (; q + a.bbox <= tl.nsize; q += a.bbox)
+                tma_load_2d(sb + 64u * q, &a.tmB[tm], 32 * kb, tl.r0 + tl.n0 + q, &full[stage]);
+              for (; q < tl.nsize; q += 16)
+                tma_load_2d(sb + 64u * q, &a.tmB16[tm], 32 * kb, tl.r0 + tl.n0 + q, &full[stage]);
             }
           }
           }  // lane 0
@@ -259,6 +296,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     // ------------------------------------------------------------------ MMA issuer
     // The whole warp walks the loop (converged); lane 0 waits, issues and commits.
     {
+      const uint64_t da0 = sdesc(sbase, 4096, 1024, 2);                                   // A: MN-major, 128B swizzle
+      const uint64_t db0 = sdesc(sbase + (uint32_t)a.nterms * kABytes, 16, 512, 4);       // B: K-major, 64B swizzle
+      const uint32_t bterm16 = bBytes >> 4;
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -271,7 +311,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         good = __shfl_sync(0xffffffffu, good, 0);
         if (!good) break;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)acc * 256u;
+        const uint32_t d = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols);
         const uint32_t idesc = idesc_bf16(tl.nsize);
         for (int kb = 0; kb < tl.nkb; ++kb) {
           good = 1;
@@ -283,25 +323,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           }
           tc_fence_after();
           if (lane == 0) {
-            const uint32_t st = sbase + (uint32_t)stage * stageBytes;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              int corr = 0;  // correction products issued so far in this k step
-              for (int ta = 0; ta < a.nterms; ++ta) {
-                for (int tb = 0; ta + tb < a.nterms; ++tb) {
-                  const uint32_t sa = st + (uint32_t)ta * kABytes + (uint32_t)ks * 2048u;
-                  const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tb * bBytes + (uint32_t)ks * 32u;
-                  const uint64_t ad = sdesc(sa, 4096, 1024, 2);  // MN-major, 128B swizzle
-                  const uint64_t bd = sdesc(sb, 16, 512, 4);     // K-major, 64B swizzle
-                  if (a.split && (ta | tb)) {
-                    // correction products accumulate in their own buffer, 128 columns further
-                    tc_mma(d + 128u, ad, bd, idesc, (kb | ks | corr) ? 1u : 0u);
-                    ++corr;
-                  } else {
-                    tc_mma(d, ad, bd, idesc, (kb | ks | ta | tb) ? 1u : 0u);
-                  }
-                }
-              }
+            const uint32_t so = (uint32_t)stage * (stageBytes >> 4);
+            const uint64_t da = da0 + so, db = db0 + so;
+            const bool first = kb == 0;
+            const uint32_t dc = d + (uint32_t)a.cols;
+            if (a.nterms == 2) {
+              if (a.split) issue_kblock<2, true>(da, db, bterm16, d, dc, idesc, first);
+              else issue_kblock<2, false>(da, db, bterm16, d, dc, idesc, first);
+            } else {
+              if (a.split) issue_kblock<3, true>(da, db, bterm16, d, dc, idesc, first);
+              else issue_kblock<3, false>(da, db, bterm16, d, dc, idesc, first);
             }
             tc_commit(&empty[stage]);
           }
@@ -314,8 +345,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         if (!ok) break;
         if (lane == 0) tc_commit(&tfull[acc]);
         __syncwarp();
-        acc ^= 1;
-        if (acc == 0) aphase ^= 1;
+        if (++acc == a.nbuf) {
+          acc = 0;
+          aphase ^= 1;
+        }
       }
       // every MMA this warp issued has completed before TMEM is released (bounded)
       if (lane == 0) {
@@ -341,11 +374,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       const int nch = (tl.nsize + 31) / 32;
       for (int ch = 0; ch < nch; ++ch) {
         float v[32];
-        const uint32_t ta = tmem + (uint32_t)acc * 256u + (uint32_t)(ch * 32) + ((uint32_t)(32 * q) << 16);
+        const uint32_t ta = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols) + (uint32_t)(ch * 32) +
+                            ((uint32_t)(32 * q) << 16);
         tmem_ld32(ta, v);
         if (a.split) {
           float w[32];
-          tmem_ld32(ta + 128u, w);
+          tmem_ld32(ta + (uint32_t)a.cols, w);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
@@ -424,8 +458,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         if (!epi_sync(&epib[1], ephase, lane, a.err)) break;
         ephase ^= 1;
       }
-      acc ^= 1;
-      if (acc == 0) aphase ^= 1;
+      if (++acc == a.nbuf) {
+        acc = 0;
+        aphase ^= 1;
+      }
     }
   }
 

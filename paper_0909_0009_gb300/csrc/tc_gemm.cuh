@@ -18,7 +18,8 @@ struct TcTile {
 
 struct TcArgs {
   CUtensorMap tmA[3];   // per BF16 term: Phi (synthesis) or G (analysis)
-  CUtensorMap tmB[3];   // per BF16 term: Lambda_syn or Lambda_ana
+  CUtensorMap tmB[3];   // per BF16 term: Lambda_syn or Lambda_ana, boxes of bbox rows
+  CUtensorMap tmB16[3]; // the same operands in 16-row boxes (tile remainders)
   const TcTile* tiles;
   int ntiles;
   int mode;
@@ -26,6 +27,9 @@ struct TcArgs {
   int split;            // 1: products of the leading terms and the correction products go to two
                         //    separate accumulators (tile width <= 128), summed in the epilogue
   int nmax;             // largest tile width in this launch (B stage size)
+  int bbox;             // rows of one B box (multiple of 16)
+  int cols;             // TMEM columns between the leading and the correction accumulator
+  int nbuf;             // accumulator sets in TMEM (double buffering when 2)
   int stages;
   int L, nr, npairs, Cpad;
   int64_t nalm;
