@@ -22,6 +22,10 @@ numpy matmul, numpy.fft.rfft/irfft (a DFT of a Hermitian-symmetric spectrum),
 numpy.linalg.cholesky.  Nothing is blocked, fused or reordered beyond the
 definitions written in each docstring.
 
+The adjoint (``generate_backward`` and the transposes it chains) is the chain rule
+through these steps; its pins are the dot-product test of every transpose against its
+pinned forward map and central finite differences of a loss through ``generate``.
+
 Pins (tests/test_oracle_pins.py, CPU): Gauss-Legendre rule vs numpy's leggauss;
 lambda_lm vs scipy's spherical harmonics and orthonormality; j_l vs scipy;
 Philox vs numpy.random.Philox; Gaunt brute force (Racah 3j) for Phi_L^2 at
@@ -486,9 +490,111 @@ def generate(K, noise, grid: Grid, r, w, alphaT, alphaE, fnl: float, mu=None, sh
     return out
 
 
+# ---------------------------------------------------------------------------
+# Adjoint of the generator (differentiation form): gradients of a real loss L of
+# a^T and a^E with respect to the white noise n and to f_NL.  Complex numbers are
+# treated as pairs of reals, and a gradient array holds dL/dRe + i dL/dIm.  Each
+# function below is the transpose, under the real inner product <u, v> =
+# sum Re(conj(u) v), of the corresponding forward map above.
+# ---------------------------------------------------------------------------
+
+def synthesis_adjoint(fbar: np.ndarray, grid: Grid) -> np.ndarray:
+    """Transpose of ``synthesis``: fbar [nsh, n_theta, n_phi] real -> [nalm, nsh].
+
+    The forward map is f_jk = sum_l [Re a_l0 lambda_l0 + 2 sum_{m>0} lambda_lm (Re a_lm cos m phi_k
+    - Im a_lm sin m phi_k)], so dL/dRe a_lm = c_m sum_jk lambda_lm(x_j) cos(m phi_k) fbar_jk and
+    dL/dIm a_lm = -c_m sum_jk lambda_lm(x_j) sin(m phi_k) fbar_jk, with c_0 = 1, c_m = 2 (m > 0),
+    and 0 for Im a_l0 (the forward ignores it).  sum_k fbar_jk e^{-i m phi_k} is rfft(fbar)_m."""
+    L = grid.lmax
+    fbar = np.asarray(fbar, dtype=np.float64)
+    if fbar.ndim == 2:
+        fbar = fbar[None]
+    nsh = fbar.shape[0]
+    Fb = np.fft.rfft(fbar, axis=-1)  # [nsh, ntheta, nphi/2+1]
+    out = np.zeros((n_alm(L), nsh), dtype=np.complex128)
+    for m in range(L + 1):
+        rows = alm_index(np.arange(m, L + 1), m, L)
+        c = 1.0 if m == 0 else 2.0
+        out[rows, :] = c * (grid.lam(m) @ Fb[:, :, m].T)
+    out[: L + 1, :] = out[: L + 1, :].real
+    return out
+
+
+def analysis_adjoint(abar: np.ndarray, grid: Grid) -> np.ndarray:
+    """Transpose of ``analysis``: abar [nalm, nsh] -> [nsh, n_theta, n_phi] real.
+
+    The forward map is Re a_lm = W_j sum lambda_lm cos(m phi_k) f_jk and Im a_lm =
+    -W_j sum lambda_lm sin(m phi_k) f_jk with W_j = w_j 2 pi / n_phi, so
+    dL/df_jk = W_j sum_lm lambda_lm(x_j) Re(abar_lm e^{i m phi_k}) over m >= 0, every m once:
+    an inverse real DFT of B_m(x_j) = sum_l lambda_lm abar_lm with the m > 0 terms halved
+    (irfft doubles them)."""
+    L = grid.lmax
+    abar = np.asarray(abar, dtype=np.complex128)
+    if abar.ndim == 1:
+        abar = abar[:, None]
+    nsh = abar.shape[1]
+    B = np.zeros((nsh, grid.ntheta, grid.nphi // 2 + 1), dtype=np.complex128)
+    for m in range(L + 1):
+        rows = alm_index(np.arange(m, L + 1), m, L)
+        B[:, :, m] = (grid.lam(m).T @ abar[rows, :]).T * (1.0 if m == 0 else 0.5)
+    f = np.fft.irfft(B, n=grid.nphi, axis=-1) * grid.nphi
+    return f * (grid.w * (2.0 * math.pi / grid.nphi))[None, :, None]
+
+
+def phi_linear_adjoint(K: np.ndarray, phibar: np.ndarray) -> np.ndarray:
+    """Transpose of ``phi_linear``: phibar [nalm, nr] -> noise gradient [nr, nalm],
+    nbar_lm(r_j) = sum_i K_l[i, j] phibar_lm(r_i); 0 for Im n_l0 (the forward ignores it)."""
+    L = K.shape[0] - 1
+    phibar = np.asarray(phibar, dtype=np.complex128)
+    out = np.empty((phibar.shape[0], K.shape[2]), dtype=np.complex128)
+    for l in range(L + 1):
+        rows = alm_index(l, np.arange(l + 1), L)
+        out[rows, :] = phibar[rows, :] @ K[l]
+    out[: L + 1, :] = out[: L + 1, :].real
+    return out.T.copy()
+
+
+def radial_quadrature_adjoint(abar: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Transpose of ``radial_quadrature``: abar [nalm] -> [nalm, nr], phibar_lm(r_i) = q_l[i] abar_lm."""
+    L = q.shape[0] - 1
+    ls, _ = _lm_arrays(L)
+    return np.asarray(abar, dtype=np.complex128)[:, None] * q[ls, :]
+
+
+def _lm_arrays(L: int):
+    ls = np.concatenate([np.arange(m, L + 1) for m in range(L + 1)])
+    ms = np.concatenate([np.full(L + 1 - m, m) for m in range(L + 1)])
+    return ls, ms
+
+
+def generate_backward(K, noise, grid: Grid, r, w, alphaT, alphaE, fnl: float, gT, gE, mu=None):
+    """Gradients of a real loss L(a^T, a^E) given gX = dL/da^X (pairs, [nalm] complex):
+    returns (dL/dn [nr, nalm] complex, dL/df_NL float).
+
+    By the chain rule through the forward recipe, with q^X the quadrature weights:
+      dL/df_NL      = sum_X <gX, a^X_NL>
+      dL/dPhi_NL    = f_NL sum_X q^X gX                        (quadrature, Eq. 5)
+      dL/dg         = analysis^T(dL/dPhi_NL)                    (step (iv))
+      dL/df         = 2 f dL/dg, f = synthesis(Phi_L)           (square, Eq. 2; mu is a constant)
+      dL/dPhi_L     = synthesis^T(dL/df) + sum_X q^X gX         (step (ii) and the linear part)
+      dL/dn         = phi_linear^T(dL/dPhi_L)                   (step (i), Eq. 9)"""
+    fw = generate(K, noise, grid, r, w, alphaT, alphaE, fnl, mu=mu)
+    gT = np.asarray(gT, dtype=np.complex128)
+    gE = np.asarray(gE, dtype=np.complex128)
+    dfnl = float(np.sum((np.conj(gT) * fw["aNLT"]).real) + np.sum((np.conj(gE) * fw["aNLE"]).real))
+    qT = quadrature_weights(r, w, alphaT)
+    qE = quadrature_weights(r, w, alphaE)
+    lin = radial_quadrature_adjoint(gT, qT) + radial_quadrature_adjoint(gE, qE)
+    gbar = analysis_adjoint(fnl * lin, grid)
+    f = synthesis(fw["phiL"], grid)
+    phibar = synthesis_adjoint(2.0 * f * gbar, grid) + lin
+    return phi_linear_adjoint(K, phibar), dfnl
+
+
 __all__ = [
     "FOUR_PI", "FLUSH", "gauss_legendre", "lambda_mm", "lambda_column", "lambda_table", "Grid",
     "synthesis", "analysis", "spherical_jn_table", "k_rule", "covariance", "filters",
     "mu_ensemble", "philox4x64", "philox_noise", "phi_linear", "phi_nonlinear",
-    "quadrature_weights", "radial_quadrature", "generate",
+    "quadrature_weights", "radial_quadrature", "generate", "synthesis_adjoint", "analysis_adjoint",
+    "phi_linear_adjoint", "radial_quadrature_adjoint", "generate_backward",
 ]

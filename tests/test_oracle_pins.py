@@ -453,3 +453,103 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(mod.np.fft, "rfft", lambda x, axis=-1: np.conj(orig_rfft(x, axis=axis)))
     assert identity_pin_fails()
     monkeypatch.undo()
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (differentiation form): transposes by the dot-product test against the pinned
+# forward maps, and the whole gradient by central finite differences
+# ---------------------------------------------------------------------------
+
+def _rdot(u, v):
+    return float(np.sum((np.conj(np.asarray(u)) * np.asarray(v)).real))
+
+
+def _random_alm(L, nsh, rng, real_m0=False):
+    a = rng.standard_normal((W.n_alm(L), nsh)) + 1j * rng.standard_normal((W.n_alm(L), nsh))
+    if real_m0:
+        a[: L + 1] = a[: L + 1].real
+    return a
+
+
+@pytest.mark.parametrize("L,nt,nph", [(6, 10, 19), (9, 14, 30)])
+def test_transform_adjoints_pass_the_dot_product_test(L, nt, nph):
+    rng = np.random.default_rng(11)
+    grid = O.Grid(L, nt, nph)
+    a = _random_alm(L, 3, rng)            # the imaginary part of m = 0 is ignored by synthesis
+    F = rng.standard_normal((3, nt, nph))
+    assert _rdot(O.synthesis(a, grid), F) == pytest.approx(_rdot(a, O.synthesis_adjoint(F, grid)), rel=1e-12)
+    B = _random_alm(L, 3, rng)
+    assert _rdot(O.analysis(F, grid), B) == pytest.approx(_rdot(F, O.analysis_adjoint(B, grid)), rel=1e-12)
+
+
+def test_filter_and_quadrature_adjoints_pass_the_dot_product_test():
+    rng = np.random.default_rng(12)
+    L, nr = 7, 5
+    K = W.random_lower_filters(L, nr, seed=2, scale=1.0)
+    n = _random_alm(L, nr, rng).T
+    P = _random_alm(L, nr, rng)
+    assert _rdot(O.phi_linear(K, n), P) == pytest.approx(_rdot(n, O.phi_linear_adjoint(K, P)), rel=1e-12)
+    q = rng.standard_normal((L + 1, nr))
+    A = _random_alm(L, 1, rng)[:, 0]
+    assert _rdot(O.radial_quadrature(P, q), A) == pytest.approx(
+        _rdot(P, O.radial_quadrature_adjoint(A, q)), rel=1e-12)
+
+
+def _loss_and_grad(out, dT, dE, wT, wE):
+    """L = sum_idx wX |a^X - d^X|^2 and its pair gradients gX = 2 wX (a^X - d^X)."""
+    rT, rE = out["aT"] - dT, out["aE"] - dE
+    L = float(np.sum(wT * np.abs(rT) ** 2) + np.sum(wE * np.abs(rE) ** 2))
+    return L, 2 * wT * rT, 2 * wE * rE
+
+
+def test_generate_backward_matches_central_differences():
+    L, nr = 8, 5
+    nt, nph = W.grid_for_lmax(L)
+    grid = O.Grid(L, nt, nph)
+    r, w = W.radial_grid(nr)
+    aT, aE = W.transfer_kernels(L, r)
+    K = W.random_lower_filters(L, nr, seed=4, scale=0.3)
+    mu = O.mu_ensemble(K)
+    rng = np.random.default_rng(13)
+    noise = _random_alm(L, nr, rng, real_m0=True).T
+    d = O.generate(K, _random_alm(L, nr, rng, real_m0=True).T, grid, r, w, aT, aE, 20.0, mu=mu)
+    wT = rng.uniform(0.5, 2.0, W.n_alm(L))
+    wE = rng.uniform(0.5, 2.0, W.n_alm(L))
+    fnl = 35.0
+    loss = lambda n, f: _loss_and_grad(O.generate(K, n, grid, r, w, aT, aE, f, mu=mu), d["aT"], d["aE"], wT, wE)[0]
+    _, gT, gE = _loss_and_grad(O.generate(K, noise, grid, r, w, aT, aE, fnl, mu=mu), d["aT"], d["aE"], wT, wE)
+    gn, gf = O.generate_backward(K, noise, grid, r, w, aT, aE, fnl, gT, gE, mu=mu)
+    eps = 1e-6
+    for k in range(6):
+        v = _random_alm(L, nr, rng, real_m0=True).T
+        fd = (loss(noise + eps * v, fnl) - loss(noise - eps * v, fnl)) / (2 * eps)
+        assert _rdot(gn, v) == pytest.approx(fd, rel=1e-7, abs=1e-9 * abs(fd))
+    fd = (loss(noise, fnl + eps) - loss(noise, fnl - eps)) / (2 * eps)
+    assert gf == pytest.approx(fd, rel=1e-7)
+    assert np.all(gn[:, : L + 1].imag == 0.0)
+
+
+def test_planted_adjoint_mistakes_fail_central_differences():
+    """Dropping the m > 0 doubling of the synthesis transpose, or the linear branch, changes
+    the gradient by far more than the finite-difference tolerance."""
+    L, nr = 6, 4
+    nt, nph = W.grid_for_lmax(L)
+    grid = O.Grid(L, nt, nph)
+    r, w = W.radial_grid(nr)
+    aT, aE = W.transfer_kernels(L, r)
+    K = W.random_lower_filters(L, nr, seed=5, scale=0.3)
+    rng = np.random.default_rng(14)
+    noise = _random_alm(L, nr, rng, real_m0=True).T
+    gT = _random_alm(L, 1, rng)[:, 0]
+    gE = _random_alm(L, 1, rng)[:, 0]
+    good, _ = O.generate_backward(K, noise, grid, r, w, aT, aE, 25.0, gT, gE)
+    qT = O.quadrature_weights(r, w, aT)
+    qE = O.quadrature_weights(r, w, aE)
+    fw = O.generate(K, noise, grid, r, w, aT, aE, 25.0)
+    lin = O.radial_quadrature_adjoint(gT, qT) + O.radial_quadrature_adjoint(gE, qE)
+    gbar = O.analysis_adjoint(25.0 * lin, grid)
+    f = O.synthesis(fw["phiL"], grid)
+    no_lin = O.phi_linear_adjoint(K, O.synthesis_adjoint(2.0 * f * gbar, grid))
+    undoubled = O.phi_linear_adjoint(K, O.synthesis_adjoint(2.0 * f * gbar, grid) * 0.5 + lin)
+    for bad in (no_lin, undoubled):
+        assert np.linalg.norm(bad - good) > 1e-3 * np.linalg.norm(good)
