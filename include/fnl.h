@@ -129,6 +129,24 @@ fnl_status fnl_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisatio
                         const double* noise, double* aT, double* aE, double* aLT, double* aLE,
                         double* aNLT, double* aNLE, void* stream);
 
+/* Adjoint of fnl_generate (the differentiation form).  For a real loss L of a^T and a^E:
+ *  gT, gE: device [nalm][2] dL/da^X as pairs (dL/dRe, dL/dIm), or NULL for zero.
+ *  grad_noise: device [nr][nalm][2], or NULL: dL/dn for the noise n of the same call
+ *      (explicit `noise`, else the Philox draw of seed and realisation); the imaginary part
+ *      of every m = 0 entry is 0, as the forward ignores it.
+ *  grad_fnl: device double, or NULL: dL/df_NL = sum_X <gX, a^X_NL>.
+ *  aNLT, aNLE: device [nalm][2] a^X_NL of the forward call, or NULL: then they are
+ *      recomputed (one more forward pass) when grad_fnl is requested.
+ * The chain rule through steps (i)-(v) (Eq. 9, the synthesis, Eq. 2, the analysis, Eq. 5,
+ * Eq. 3), with mu a constant: dL/dPhi_NL = f_NL q^X gX; dL/dPhi_L = c_m analysis(2 f s) +
+ * q^X gX, s the synthesis of dL/dPhi_NL with m > 0 halved, c_0 = 1 and c_m = 2; dL/dn =
+ * K_l^T dL/dPhi_L.  The maps f and s are recomputed on the ring grid, not stored.
+ * FNL_FP64 and FNL_FP32 objects only (FNL_EUNSUPPORTED otherwise). */
+fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl,
+                                 const double* noise, const double* gT, const double* gE,
+                                 const double* aNLT, const double* aNLE, double* grad_noise,
+                                 double* grad_fnl, void* stream);
+
 /* fnl_generate with host outputs: the same path, then the requested results (host
  * [nalm][2] each, any may be NULL; pinned memory gives asynchronous copies) are copied
  * device-to-host on `stream`.  The caller synchronises the stream before reading them. */

@@ -712,6 +712,52 @@ fnl_status fnl_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisatio
   });
 }
 
+fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl,
+                                 const double* noise, const double* gT, const double* gE, const double* aNLT,
+                                 const double* aNLE, double* grad_noise, double* grad_fnl, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    DeviceScope scope(sh->device);
+    if (sh->nterms)
+      throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward runs in the FNL_FP64 and FNL_FP32 forms");
+    check_dev_ptr(noise, "noise", true);
+    check_dev_ptr(gT, "gT", true);
+    check_dev_ptr(gE, "gE", true);
+    check_dev_ptr(aNLT, "aNLT", true);
+    check_dev_ptr(aNLE, "aNLE", true);
+    check_dev_ptr(grad_noise, "grad_noise", true);
+    if (grad_fnl) {
+      if (((uintptr_t)grad_fnl) % 8 != 0) throw Error(FNL_EINVAL, "grad_fnl must be 8-byte aligned");
+      cudaPointerAttributes attr;
+      if (cudaPointerGetAttributes(&attr, grad_fnl) != cudaSuccess ||
+          (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        throw Error(FNL_EINVAL, "grad_fnl must be device memory");
+      }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n2 = 2 * sh->nalm;
+    if (grad_fnl) {
+      if (!aNLT || !aNLE) {
+        // a^X_NL of the forward call, recomputed into the object's scratch
+        run_generate(sh, seed, realisation, fnl, noise, nullptr, nullptr, nullptr, nullptr, sh->d_aNL,
+                     sh->d_aNL + n2, st);
+        aNLT = sh->d_aNL;
+        aNLE = sh->d_aNL + n2;
+      }
+      launch_dot_fnl(sh, gT, gE, aNLT, aNLE, grad_fnl, st);
+    }
+    if (!grad_noise) return;
+    launch_filter(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + n2, nullptr, st);  // Phi_L rows
+    launch_synth_gemm(sh, st);                                                          // F of f
+    launch_adjoint_source(sh, fnl, gT, gE, st);                                         // rows of H~
+    launch_synth_gemm_to(sh, sh->d_G, st);                                              // F of s, in G
+    launch_ring_product(sh, st);                                                        // G = DFT(2 f s)
+    launch_analysis_gemm(sh, st);                                                       // rows of analysis(2 f s)
+    launch_adjoint_filter(sh, gT, gE, grad_noise, st);                                  // K^T (c_m rows + q g)
+  });
+}
+
 fnl_status fnl_generate_host(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, double* aT,
                              double* aE, double* aNLT, double* aNLE, void* stream) {
   return guard([&] {

@@ -186,6 +186,7 @@ void build_lambda_tables(fnl_shells* sh, cudaStream_t st);
 void launch_filter(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise,
                    double* aLT, double* aLE, double* phi_api, cudaStream_t st);
 void launch_synth_gemm(const fnl_shells* sh, cudaStream_t st);
+void launch_synth_gemm_to(const fnl_shells* sh, void* out, cudaStream_t st);  // SIMT: phi rows -> out
 void launch_analysis_gemm(const fnl_shells* sh, cudaStream_t st);
 enum FftMode { FFT_SQUARE = 0, FFT_SYNTH_MAP = 1, FFT_ANALYSE_MAP = 2 };
 bool launch_ring_square(const fnl_shells* sh, cudaStream_t st);
@@ -202,6 +203,14 @@ void launch_combine(const fnl_shells* sh, double fnl, const double* aLT, const d
                     cudaStream_t st);
 void launch_lambda_mm(const double* x, const double* fac, int npairs, int L, double* mant, int* expo,
                       cudaStream_t st);
+
+// ---- adjoint of the SIMT forms (adjoint.cu, ring_fft.cu) -------------------------------------
+void launch_adjoint_source(const fnl_shells* sh, double fnl, const double* gT, const double* gE, cudaStream_t st);
+void launch_ring_product(const fnl_shells* sh, cudaStream_t st);
+void launch_adjoint_filter(const fnl_shells* sh, const double* gT, const double* gE, double* grad_noise,
+                           cudaStream_t st);
+void launch_dot_fnl(const fnl_shells* sh, const double* gT, const double* gE, const double* aNLT,
+                    const double* aNLE, double* out, cudaStream_t st);
 
 // ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
 void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st);

@@ -359,6 +359,79 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
   }
 }
 
+// Product mode of the adjoint: per (shell, ring pair) the spectra F1 = a.F and F2 = a.G (both
+// in the SIMT layout) are taken to the ring values z1, z2 (north + i south) as in the square,
+// w = 2 Re z1 Re z2 + i 2 Im z1 Im z2, and W = DFT(w) is written over F2 as S and D (same
+// scale and equator rule as the square).  Each block reads its entries of F2 before it writes.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.plan.n;
+  cplx<T>* b0 = (cplx<T>*)smem;
+  cplx<T>* b1 = b0 + N;
+  cplx<T>* b2 = b1 + N;
+  cplx<T>* b3 = b2 + N;
+  const int s = blockIdx.x, jp = blockIdx.y;
+  const int south = a.ntheta - 1 - jp;
+  const bool equator = (south == jp);
+  const int L = a.L;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    b0[k] = {(T)0, (T)0};
+    b2[k] = {(T)0, (T)0};
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const size_t oe = (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
+    const size_t oo = (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
+    const T* src[2] = {a.F, a.G};
+    cplx<T>* dst[2] = {b0, b2};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const cplx<T> E = {src[q][oe], src[q][oe + 1]};
+      const cplx<T> O = (m < L) ? cplx<T>{src[q][oo], src[q][oo + 1]} : cplx<T>{(T)0, (T)0};
+      const cplx<T> FN = cadd(E, O), FS = csub(E, O);
+      if (m == 0) {
+        dst[q][0] = {FN.x, FS.x};
+      } else {
+        dst[q][m] = {FN.x - FS.y, FN.y + FS.x};
+        dst[q][N - m] = {FN.x + FS.y, FS.x - FN.y};
+      }
+    }
+  }
+  __syncthreads();
+  cplx<T>* z1 = stockham(b0, b1, a.plan, a.tw, (T)1);
+  cplx<T>* z2 = stockham(b2, b3, a.plan, a.tw, (T)1);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const cplx<T> u = z1[k], v = z2[k];
+    z1[k] = {(T)2 * u.x * v.x, (T)2 * u.y * v.y};
+  }
+  __syncthreads();
+  const cplx<T>* W = stockham(z1, z1 == b0 ? b1 : b0, a.plan, a.tw, (T)-1);
+  const T scale = (T)(6.28318530717958647692 / N * a.wgl[jp]);
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const cplx<T> wm = W[m];
+    const cplx<T> wc = W[m == 0 ? 0 : N - m];
+    const cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
+    const cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
+    cplx<T> S, D;
+    if (equator) {
+      S = {gn.x * scale, gn.y * scale};
+      D = S;
+    } else {
+      S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
+      D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
+    }
+    T* ge = a.G + (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
+    T* go = a.G + (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
+    ge[0] = S.x;
+    ge[1] = S.y;
+    if (m < L) {
+      go[0] = D.x;
+      go[1] = D.y;
+    }
+  }
+}
+
 // Group variant: block (group of shells, ring pair); the group's rows of F are staged in
 // shared memory with vector loads, every shell then runs through one in-place N-point
 // buffer, its results (S, D per order m) overwrite its staged F values, and the group's
@@ -588,6 +661,36 @@ void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* map
 }
 
 }  // namespace
+
+template <typename T>
+void ring_product_impl(const fnl_shells* sh, cudaStream_t st) {
+  FftArgs<T> a{};
+  a.L = sh->lmax;
+  a.nr = sh->nr;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.C = sh->C;
+  a.sp = (int64_t)sh->npairs * sh->C;
+  a.sj = sh->C;
+  a.plan = sh->fft;
+  a.tw = (const cplx<T>*)sh->d_tw;
+  a.twp = (const cplx<T>*)sh->d_twp;
+  a.F = (const T*)sh->d_F;
+  a.G = (T*)sh->d_G;
+  a.mu = sh->d_mu;
+  a.wgl = sh->d_wgl;
+  const size_t smem = 4 * sizeof(cplx<T>) * (size_t)sh->nphi;
+  if (smem > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "nphi too large for the adjoint ring product");
+  FNL_CUDA(cudaFuncSetAttribute(k_ring_product<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_ring_product<T><<<dim3(sh->nr, sh->npairs), sh->nphi >= 1024 ? 256 : 128, smem, st>>>(a);
+  FNL_CUDA(cudaGetLastError());
+}
+
+void launch_ring_product(const fnl_shells* sh, cudaStream_t st) {
+  if (sh->nterms) throw Error(FNL_EUNSUPPORTED, "the adjoint ring product runs in the SIMT forms");
+  if (sh->real_is_double) ring_product_impl<double>(sh, st);
+  else ring_product_impl<float>(sh, st);
+}
 
 void launch_ring_fft(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
   if (sh->real_is_double) fft_impl<double>(sh, mode, maps_in, maps_out, st);

@@ -378,6 +378,18 @@ void launch_synth_gemm(const fnl_shells* sh, cudaStream_t st) {
   FNL_CUDA(cudaGetLastError());
 }
 
+void launch_synth_gemm_to(const fnl_shells* sh, void* out, cudaStream_t st) {
+  if (sh->real_is_double)
+    k_synth_gemm<double><<<sh->n_tiles_syn, kThreads, 0, st>>>(sh->d_tiles_syn, sh->d_K, sh->d_lam0, sh->d_row0,
+                                                              (const double*)sh->d_lam, (const double*)sh->d_phi,
+                                                              (double*)out, sh->npairs, sh->C);
+  else
+    k_synth_gemm<float><<<sh->n_tiles_syn, kThreads, 0, st>>>(sh->d_tiles_syn, sh->d_K, sh->d_lam0, sh->d_row0,
+                                                             (const float*)sh->d_lam, (const float*)sh->d_phi,
+                                                             (float*)out, sh->npairs, sh->C);
+  FNL_CUDA(cudaGetLastError());
+}
+
 void launch_analysis_gemm(const fnl_shells* sh, cudaStream_t st) {
   if (sh->real_is_double)
     k_analysis_gemm<double><<<sh->n_tiles_ana, kThreads, 0, st>>>(

@@ -26,7 +26,7 @@ EXPORTS = [
     "fnl_shells_mu", "fnl_generate", "fnl_filter", "fnl_synth", "fnl_analyse", "fnl_square",
     "fnl_accumulate", "fnl_gauss_legendre", "fnl_covariance", "fnl_cholesky_filters",
     "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
-    "fnl_accumulate_noalloc",
+    "fnl_accumulate_noalloc", "fnl_generate_backward",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_generate_host.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp]
     lib.fnl_device_status.argtypes = [vp]
     lib.fnl_accumulate_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
+    lib.fnl_generate_backward.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -253,6 +254,24 @@ class Shells:
             assert noise.dtype == _torch().complex128 and noise.is_contiguous() and noise.shape == (self.nr, self.nalm)
         _check(_lib.fnl_generate(self.handle, seed, realisation, float(fnl), _ptr(noise), *ptrs, _stream(stream)))
         return out
+
+    def generate_backward(self, seed: int, realisation: int, fnl: float, gT=None, gE=None, noise=None,
+                          aNLT=None, aNLE=None, want_noise: bool = True, want_fnl: bool = True, stream=None):
+        """Adjoint of ``generate`` (fnl_generate_backward): given gX = dL/da^X of a real loss
+        (complex128 [nalm], dL/dRe + i dL/dIm, or None for zero), returns (dL/dn as complex128
+        [nr, nalm] or None, dL/df_NL as a float64 0-d tensor or None) for the noise of the same
+        call (explicit ``noise``, else the Philox draw of seed and realisation).  aNLT/aNLE from
+        the forward call spare one forward pass when dL/df_NL is wanted."""
+        torch = _torch()
+        for t in (gT, gE, noise, aNLT, aNLE):
+            if t is not None:
+                assert t.dtype == torch.complex128 and t.is_contiguous()
+        gn = torch.empty((self.nr, self.nalm), dtype=torch.complex128,
+                         device=f"cuda:{self.device}") if want_noise else None
+        gf = torch.empty((), dtype=torch.float64, device=f"cuda:{self.device}") if want_fnl else None
+        _check(_lib.fnl_generate_backward(self.handle, seed, realisation, float(fnl), _ptr(noise), _ptr(gT),
+                                          _ptr(gE), _ptr(aNLT), _ptr(aNLE), _ptr(gn), _ptr(gf), _stream(stream)))
+        return gn, gf
 
     def filter(self, seed: int = 0, realisation: int = 0, noise=None, stream=None):
         phi = self._alm(self.nr)
