@@ -181,6 +181,49 @@ fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double
  * device word instead of hanging), else FNL_OK.  Clears the word. */
 fnl_status fnl_device_status(const fnl_shells* sh);
 
+/* ---- batching form: many realisations of uneven l_max and N_r in one graph --------- */
+
+typedef struct fnl_batch fnl_batch; /* opaque: streams, events and the captured graph */
+
+/* A batch of n instances; instance i runs the path of shells[i] (objects of any l_max, N_r,
+ * grid and precision, all on one device; one object may appear several times).  Instances
+ * that share an object share its scratch and run in batch order on one stream; the
+ * distinct objects are dealt, largest first (work ~ (l_max + 1)^3 N_r), to up to `nstreams`
+ * streams (0: 4).  The batch keeps the pointers, not the objects: they must outlive it.
+ * Allocates host memory, CUDA streams and events; no device memory. */
+fnl_status fnl_batch_create(fnl_shells* const* shells, int n, int nstreams, fnl_batch** out);
+
+/* Synchronise the batch's streams and free it (NULL is ignored). */
+void fnl_batch_destroy(fnl_batch* b);
+
+/* Number of instances, of streams, and (lanes: host [n] or NULL) the stream of each instance. */
+fnl_status fnl_batch_info(const fnl_batch* b, int* n, int* nstreams, int* lanes);
+
+/* Steps (i)-(v) of every instance: instance i draws its Philox noise from (seeds[i],
+ * realisations[i]) as fnl_generate does, uses f_NL = fnl[i] and writes a^T, a^E (Eq. 3) to
+ * aT[i], aE[i] (device [nalm_i][2]).  seeds, realisations, fnl, aT, aE: host arrays of n.
+ * The launches of all instances are captured into one CUDA graph (the first call
+ * instantiates it, later calls update it in place) and the graph is launched on `stream`:
+ * asynchronous, one graph launch per call.  Each instance's result equals that of
+ * fnl_generate with the same arguments.  The call itself begins a stream capture, so it
+ * cannot be made while `stream`'s thread is capturing.  Calls on one batch, and calls on
+ * its shells objects, must not overlap on the GPU. */
+fnl_status fnl_generate_batch(fnl_batch* b, const uint64_t* seeds, const uint64_t* realisations,
+                              const double* fnl, double* const* aT, double* const* aE, void* stream);
+
+/* Autotuner of the tensor-core forms: times whole realisations (one warm-up and two timed,
+ * CUDA events on `stream`) for each candidate tile shape of the two Legendre GEMMs --
+ * synthesis tiles of up to 256 or 128 ring pairs, analysis tiles of up to 256 or 128
+ * degrees -- and keeps the fastest.  The shape changes no result (every output sums its
+ * k blocks in the same order).  *nsyn, *nana (nullable) receive the chosen widths (64 for
+ * the SIMT forms, whose tiles are fixed and which this call leaves alone).  Synchronous. */
+fnl_status fnl_shells_autotune(fnl_shells* sh, void* stream, int* nsyn, int* nana);
+
+/* Set the tile shape of the tensor-core GEMMs by hand: synthesis tiles of at most syn_cap
+ * ring pairs, analysis tiles of at most ana_cap degrees, multiples of 16 in [64, 256].
+ * Synchronises the device.  FNL_EINVAL for the SIMT forms. */
+fnl_status fnl_shells_set_tiles(fnl_shells* sh, int syn_cap, int ana_cap);
+
 /* ---- step (v) without any allocation ---------------------------------------------- */
 
 /* Largest (lmax + 1) * nr that fnl_accumulate_noalloc accepts. */

@@ -16,8 +16,6 @@ static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
-namespace {
-
 fnl_status guard(const std::function<void()>& body) {
   g_last_error.clear();
   try {
@@ -38,17 +36,15 @@ fnl_status guard(const std::function<void()>& body) {
   }
 }
 
-// Keeps the caller's current device and restores it on exit.
-struct DeviceScope {
-  int prev = -1;
-  explicit DeviceScope(int dev) {
-    FNL_CUDA(cudaGetDevice(&prev));
-    if (prev != dev) FNL_CUDA(cudaSetDevice(dev));
-  }
-  ~DeviceScope() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
+DeviceScope::DeviceScope(int dev) {
+  FNL_CUDA(cudaGetDevice(&prev));
+  if (prev != dev) FNL_CUDA(cudaSetDevice(dev));
+}
+DeviceScope::~DeviceScope() {
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+namespace {
 
 bool smooth235(int n) {
   if (n < 1) return false;
@@ -56,6 +52,8 @@ bool smooth235(int n) {
     while (n % p == 0) n /= p;
   return n == 1;
 }
+
+}  // namespace
 
 void check_dev_ptr(const void* p, const char* name, bool nullable) {
   if (!p) {
@@ -76,6 +74,8 @@ void check_dev_ptr(const void* p, const char* name, bool nullable) {
 void check_shells(const fnl_shells* sh) {
   if (!sh) throw Error(FNL_EINVAL, "shells object is NULL");
 }
+
+namespace {
 
 template <typename T>
 T* dalloc(fnl_shells* sh, size_t count) {
@@ -142,6 +142,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   sh->d_part = dalloc<float>(sh, 4 * (size_t)(Cpad / 128) * sh->nalm);
   sh->d_err = dalloc<int>(sh, 1);
   sh->d_psum = dalloc<double>(sh, nr);
+  sh->d_psum_part = dalloc<double>(sh, (size_t)(L + 1) * 2 * nr);
   FNL_CUDA(cudaMemset(sh->d_phiT, 0, sizeof(bf16_t) * (size_t)T * sh->phiT_stride));
   FNL_CUDA(cudaMemset(sh->d_lsyn, 0, sizeof(bf16_t) * (size_t)T * sh->lsyn_stride));
   FNL_CUDA(cudaMemset(sh->d_lana, 0, sizeof(bf16_t) * (size_t)T * sh->lana_stride));
@@ -165,44 +166,20 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   }
   build_lambda_tables_mixed(sh, 0);
 
-  // Products of the leading terms and the correction products accumulate separately
-  // (two accumulators per tile, so tiles are at most 128 wide).
-  // Tiles up to 256 wide in both directions (fewer, wider MMAs; the leading and correction
-  // accumulators then fill the 512 TMEM columns, one set per CTA); B in 64-row TMA boxes.
-  const int split = sh->tc_split;
-  const int nmax = 256, nmax_ana = 256, bbox = 64;
-  // synthesis tile width: fewest wasted ring pairs, each tile charged 16 columns of overhead
-  int best = nmax, bestc = 1 << 30;
-  for (int n = nmax; n >= 64; n -= 16) {
-    const int tiles = (np + n - 1) / n, cost = tiles * (n + 16);
-    if (cost < bestc) {
-      bestc = cost;
-      best = n;
+  // tile lists: capacity for the narrowest tiles configure_tc accepts, then the default shapes
+  {
+    int64_t cap_syn = 0, cap_ana = 0;
+    for (int mp = 0; mp < nmp; ++mp) {
+      const int K = sh->K[mp];
+      if (!K) continue;
+      cap_syn += (int64_t)((np + kTcMinWidth - 1) / kTcMinWidth) * (Cpad / 128);
+      cap_ana += (int64_t)((K + kTcMinWidth - 1) / kTcMinWidth) * (Cpad / 128);
     }
+    sh->d_tc_syn = dalloc<TcTile>(sh, (size_t)cap_syn);
+    sh->d_tc_ana = dalloc<TcTile>(sh, (size_t)cap_ana);
   }
-  sh->nsyn = best;
-  const int ctiles = Cpad / 128;
-  std::vector<TcTile> ts, ta;
-  for (int mp = 0; mp < nmp; ++mp) {
-    const int K = sh->K[mp];
-    if (!K) continue;
-    for (int n0 = 0; n0 < np; n0 += sh->nsyn)
-      for (int ct = 0; ct < ctiles; ++ct)
-        ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0});
-    for (int n0 = 0; n0 < K;) {
-      const int n = std::min(nmax_ana, round_up(K - n0, 16));
-      for (int ct = 0; ct < ctiles; ++ct)
-        ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0});
-      n0 += n;
-    }
-  }
-  auto by_cost = [](const TcTile& a, const TcTile& b) { return a.nkb * a.nsize > b.nkb * b.nsize; };
-  std::stable_sort(ts.begin(), ts.end(), by_cost);
-  std::stable_sort(ta.begin(), ta.end(), by_cost);
-  sh->d_tc_syn = upload(sh, ts);
-  sh->d_tc_ana = upload(sh, ta);
-
   // tensor maps (BF16): A operands MN-major with 128B swizzle, B operands K-major with 64B swizzle
+  const int bbox = kTcBBox;
   for (int t = 0; t < T; ++t) {
     const bf16_t* phi = (const bf16_t*)sh->d_phiT + (size_t)t * sh->phiT_stride;
     const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
@@ -238,16 +215,10 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
       sh->tc_ana.tmB16[t] = make_tensor_map_bf16(lana, 2, dims, str, box16, 64);
     }
   }
-  // accumulators: the correction accumulator sits `cols` columns after the leading one;
-  // as many accumulator sets as fit in the 512 TMEM columns (at most 2)
   for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
-    const int nm = a == &sh->tc_syn ? sh->nsyn : nmax_ana;
-    const int cols = nm <= 128 ? 128 : 256;
     a->nterms = T;
-    a->split = split;
-    a->bbox = bbox;
-    a->cols = cols;
-    a->nbuf = std::min(2, 512 / (split ? 2 * cols : cols));
+    a->split = sh->tc_split;
+    a->bbox = kTcBBox;
     a->L = L;
     a->nr = nr;
     a->npairs = np;
@@ -260,17 +231,71 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
     a->qE = sh->d_q32 + (size_t)(L + 1) * nr;
     a->err = sh->d_err;
   }
-  sh->tc_syn.tiles = sh->d_tc_syn;
-  sh->tc_syn.ntiles = (int)ts.size();
   sh->tc_syn.mode = TC_SYNTH;
-  sh->tc_syn.nmax = sh->nsyn;
-  sh->tc_syn.stages = tc_stages(T, sh->nsyn);
-  sh->tc_ana.tiles = sh->d_tc_ana;
-  sh->tc_ana.ntiles = (int)ta.size();
   sh->tc_ana.mode = TC_ANA_QUAD;
-  sh->tc_ana.nmax = nmax_ana;
-  sh->tc_ana.stages = tc_stages(T, nmax_ana);
+  configure_tc(sh, 256, 256);
 }
+
+}  // namespace
+
+// Tile shapes of the two tensor-core GEMMs.  Synthesis tiles are `nsyn` ring pairs wide, the
+// width <= syn_cap that wastes the fewest ring pairs (each tile charged 16 columns of
+// overhead); analysis tiles cover up to `ana_cap` degrees.  Both caps are multiples of 16 in
+// [kTcMinWidth, 256].  Products of the leading terms and the correction products accumulate
+// in two separate accumulators `cols` apart; as many accumulator sets as fit in the 512 TMEM
+// columns (at most 2) rotate over tiles, so 128-wide tiles double-buffer the epilogue and
+// 256-wide tiles issue half as many, wider MMAs.  The shape changes no result: every output
+// element sums its k blocks in the same order whatever the tiling.
+void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap) {
+  FNL_REQUIRE(syn_cap >= kTcMinWidth && syn_cap <= 256 && syn_cap % 16 == 0 && ana_cap >= kTcMinWidth &&
+                  ana_cap <= 256 && ana_cap % 16 == 0,
+              "tile widths must be multiples of 16 in [64, 256]");
+  const int L = sh->lmax, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms;
+  int best = syn_cap, bestc = 1 << 30;
+  for (int n = syn_cap; n >= kTcMinWidth; n -= 16) {
+    const int tiles = (np + n - 1) / n, cost = tiles * (n + 16);
+    if (cost < bestc) {
+      bestc = cost;
+      best = n;
+    }
+  }
+  sh->nsyn = best;
+  sh->nana = ana_cap;
+  const int ctiles = sh->Cpad / 128;
+  std::vector<TcTile> ts, ta;
+  for (int mp = 0; mp < nmp; ++mp) {
+    const int K = sh->K[mp];
+    if (!K) continue;
+    for (int n0 = 0; n0 < np; n0 += sh->nsyn)
+      for (int ct = 0; ct < ctiles; ++ct)
+        ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0});
+    for (int n0 = 0; n0 < K;) {
+      const int n = std::min(ana_cap, round_up(K - n0, 16));
+      for (int ct = 0; ct < ctiles; ++ct)
+        ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0});
+      n0 += n;
+    }
+  }
+  auto by_cost = [](const TcTile& a, const TcTile& b) { return a.nkb * a.nsize > b.nkb * b.nsize; };
+  std::stable_sort(ts.begin(), ts.end(), by_cost);
+  std::stable_sort(ta.begin(), ta.end(), by_cost);
+  FNL_CUDA(cudaMemcpy(sh->d_tc_syn, ts.data(), sizeof(TcTile) * ts.size(), cudaMemcpyHostToDevice));
+  FNL_CUDA(cudaMemcpy(sh->d_tc_ana, ta.data(), sizeof(TcTile) * ta.size(), cudaMemcpyHostToDevice));
+  int widest_ana = 16;
+  for (const TcTile& t : ta) widest_ana = std::max(widest_ana, t.nsize);
+  for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
+    const bool syn = a == &sh->tc_syn;
+    const int nm = syn ? sh->nsyn : widest_ana;
+    a->cols = nm <= 128 ? 128 : 256;
+    a->nbuf = std::min(2, 512 / (a->split ? 2 * a->cols : a->cols));
+    a->nmax = nm;
+    a->stages = tc_stages(T, nm);
+    a->tiles = syn ? sh->d_tc_syn : sh->d_tc_ana;
+    a->ntiles = (int)(syn ? ts.size() : ta.size());
+  }
+}
+
+namespace {
 
 void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st) {
   TcArgs a = base;
@@ -649,12 +674,14 @@ fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double
   });
 }
 
+}  // extern "C"
+
 namespace fnl {
-namespace {
 
 // Steps (i)-(v) for one realisation, outputs in device memory (NULL -> scratch).
 void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, const double* noise,
-                  double* aT, double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, cudaStream_t st) {
+                  double* aT, double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, cudaStream_t st,
+                  bool mark_events) {
   const int64_t n2 = 2 * sh->nalm;
   double* lT = aLT ? aLT : sh->d_aL;
   double* lE = aLE ? aLE : sh->d_aL + n2;
@@ -662,7 +689,7 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
   double* nE = aNLE ? aNLE : sh->d_aNL + n2;
   fnl_shells* msh = const_cast<fnl_shells*>(sh);
   cudaEvent_t* ev = nullptr;
-  if (sh->ring_slots) {
+  if (sh->ring_slots && mark_events) {
     ev = msh->ring.data() + (size_t)sh->ring_head * (FNL_NSTAGES + 1);
     msh->ring_head = (sh->ring_head + 1) % sh->ring_slots;
     msh->ring_count = std::min(sh->ring_count + 1, sh->ring_slots);
@@ -695,8 +722,9 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
   mark(5);
 }
 
-}  // namespace
 }  // namespace fnl
+
+extern "C" {
 
 fnl_status fnl_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, const double* noise,
                         double* aT, double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, void* stream) {

@@ -14,6 +14,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -143,6 +144,7 @@ struct fnl_shells {
   int Cpad = 0;                    // columns padded to a multiple of 128
   int npj = 0;                     // ring pairs padded to a multiple of 8 (row stride of Lambda_ana)
   int nsyn = 0;                    // synthesis tile width (ring pairs)
+  int nana = 0;                    // analysis tile width cap (degrees)
   int tc_split = 1;                // separate accumulators for leading and correction products
   int sms = 0;
   std::vector<int64_t> row32;      // first Phi row of problem mp (rows padded to 32)
@@ -161,6 +163,7 @@ struct fnl_shells {
   float* d_q32 = nullptr;          // [2][L+1][nr]  q^T, q^E in FP32
   int* d_err = nullptr;            // device error word of the tensor-core kernels
   double* d_psum = nullptr;        // [nr] sum_lm w_m |Phi_L,lm(r_i)|^2 (Parseval monopole)
+  double* d_psum_part = nullptr;   // [(L+1) * 2][nr] the filter's partials of d_psum
   fnl::TcTile* d_tc_syn = nullptr;
   fnl::TcTile* d_tc_ana = nullptr;
   fnl::TcArgs tc_syn{}, tc_ana{};
@@ -173,6 +176,28 @@ struct fnl_shells {
 };
 
 namespace fnl {
+
+// ---- entry-point plumbing (fnl_api.cu) -----------------------------------------------------
+// Runs `body`, turning exceptions into a status and the thread's last-error message.
+fnl_status guard(const std::function<void()>& body);
+// Makes `dev` current for the scope and restores the caller's device on exit.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev);
+  ~DeviceScope();
+};
+void check_dev_ptr(const void* p, const char* name, bool nullable);
+void check_shells(const fnl_shells* sh);
+// Steps (i)-(v) of one realisation; NULL outputs go to the object's scratch.  `mark` records
+// the per-stage profiling events when profiling is on.
+void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl, const double* noise,
+                  double* aT, double* aE, double* aLT, double* aLE, double* aNLT, double* aNLE, cudaStream_t st,
+                  bool mark = true);
+// Tile shapes of the tensor-core GEMMs (mixed forms): widths capped at syn_cap ring pairs and
+// ana_cap degrees, multiples of 16 in [kTcMinWidth, 256].
+constexpr int kTcMinWidth = 64;
+constexpr int kTcBBox = 64;
+void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap);
 
 // ---- host set-up (setup_host.cpp) -------------------------------------------------------
 void gauss_legendre(int n, double* x, double* w);

@@ -225,7 +225,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
       }
     }
   }
-  if (psum && ws < nr) atomicAdd(&psum[ws], (double)ph + (double)pl);
+  // one partial per (l, half of the orders, shell): summed in a fixed order by k_psum_reduce,
+  // so the monopole (and every result) is reproducible bit for bit
+  if (psum && ws < nr) psum[((size_t)blockIdx.x * (kThreads / 128) + wh) * nr + ws] = (double)ph + (double)pl;
+}
+
+// psum[s] = sum over the filter's partials of shell s, in a fixed order.
+__global__ void k_psum_reduce(int nparts, int nr, const double* __restrict__ part, double* __restrict__ psum) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nr) return;
+  double acc = 0.0;
+  for (int e = 0; e < nparts; ++e) acc += part[(size_t)e * nr + s];
+  psum[s] = acc;
 }
 
 __device__ __forceinline__ double flushed(double v) { return fabs(v) < 1e-290 ? 0.0 : v; }
@@ -365,15 +376,18 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
-  if (psum) FNL_CUDA(cudaMemsetAsync(psum, 0, sizeof(double) * sh->nr, st));
   const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
   const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)std::max(nr * kFCols, kFCols * out_stride(nrp)) + 4 * nr);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
                                                      (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,
                                                      sh->d_row32, (__nv_bfloat16*)sh->d_phiT, phi_api, aLT, aLE,
-                                                     psum);
+                                                     psum ? sh->d_psum_part : nullptr);
   FNL_CUDA(cudaGetLastError());
+  if (psum) {
+    k_psum_reduce<<<(nr + 127) / 128, 128, 0, st>>>((sh->lmax + 1) * (kThreads / 128), nr, sh->d_psum_part, psum);
+    FNL_CUDA(cudaGetLastError());
+  }
 }
 
 void launch_alm_to_terms(const fnl_shells* sh, const double* alm, cudaStream_t st) {

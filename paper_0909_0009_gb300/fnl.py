@@ -26,7 +26,8 @@ EXPORTS = [
     "fnl_shells_mu", "fnl_generate", "fnl_filter", "fnl_synth", "fnl_analyse", "fnl_square",
     "fnl_accumulate", "fnl_gauss_legendre", "fnl_covariance", "fnl_cholesky_filters",
     "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
-    "fnl_accumulate_noalloc", "fnl_generate_backward",
+    "fnl_accumulate_noalloc", "fnl_generate_backward", "fnl_batch_create", "fnl_batch_destroy",
+    "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -84,8 +85,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_device_status.argtypes = [vp]
     lib.fnl_accumulate_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
     lib.fnl_generate_backward.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.fnl_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
+    lib.fnl_batch_destroy.argtypes = [vp]
+    lib.fnl_batch_destroy.restype = None
+    lib.fnl_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.fnl_generate_batch.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), dp, ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), vp]
+    lib.fnl_shells_autotune.argtypes = [vp, vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.fnl_shells_set_tiles.argtypes = [vp, i, i]
     for name in EXPORTS:
-        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy"):
+        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -237,6 +246,16 @@ class Shells:
         _check(_lib.fnl_generate_host(self.handle, seed, realisation, float(fnl), hp(aT), hp(aE), hp(aNLT),
                                       hp(aNLE), _stream(stream)))
 
+    def autotune(self, stream=None) -> tuple[int, int]:
+        """fnl_shells_autotune: time the candidate tile shapes, keep the fastest; returns
+        (synthesis width, analysis width cap)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fnl_shells_autotune(self.handle, _stream(stream), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_tiles(self, syn_cap: int, ana_cap: int):
+        _check(_lib.fnl_shells_set_tiles(self.handle, int(syn_cap), int(ana_cap)))
+
     # -- tensors
     def _alm(self, n=1):
         torch = _torch()
@@ -303,6 +322,51 @@ class Shells:
         out = {k: self._alm() for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]}
         ptrs = [_ptr(out[k]) for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]]
         _check(_lib.fnl_accumulate(self.handle, _ptr(phiL), _ptr(phiNL), float(fnl), *ptrs, _stream(stream)))
+        return out
+
+
+class Batch:
+    """Batching form (fnl_batch_create / fnl_generate_batch): n instances over shells objects
+    of any l_max and N_r, launched as one captured CUDA graph per call."""
+
+    def __init__(self, shells: list, nstreams: int = 0):
+        lib = load_library()
+        self.shells = list(shells)  # keeps the objects alive as long as the batch
+        arr = (ctypes.c_void_p * len(self.shells))(*[s.handle.value for s in self.shells])
+        h = ctypes.c_void_p()
+        _check(lib.fnl_batch_create(arr, len(self.shells), int(nstreams), ctypes.byref(h)))
+        self.handle = h
+        self.n = len(self.shells)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.fnl_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lanes(self) -> list:
+        n, ns = ctypes.c_int(), ctypes.c_int()
+        lanes = (ctypes.c_int * self.n)()
+        _check(_lib.fnl_batch_info(self.handle, ctypes.byref(n), ctypes.byref(ns), lanes))
+        return list(lanes)
+
+    def generate(self, seeds, realisations, fnl, out=None, stream=None) -> list:
+        """Returns (or fills) a list of (aT, aE) complex128 tensors, one pair per instance."""
+        if out is None:
+            out = [(s._alm(), s._alm()) for s in self.shells]
+        n = self.n
+        sd = (ctypes.c_uint64 * n)(*[int(x) for x in seeds])
+        rl = (ctypes.c_uint64 * n)(*[int(x) for x in realisations])
+        fv = np.ascontiguousarray(fnl, dtype=np.float64)
+        assert fv.size == n
+        pT = (ctypes.c_void_p * n)(*[o[0].data_ptr() for o in out])
+        pE = (ctypes.c_void_p * n)(*[o[1].data_ptr() for o in out])
+        _check(_lib.fnl_generate_batch(self.handle, sd, rl, _dptr(fv), pT, pE, _stream(stream)))
         return out
 
 
