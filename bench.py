@@ -250,6 +250,7 @@ def main():
     K = F.cholesky_filters(C, W.COV.jitter_rel)
     del C
     sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=args.prec, device=local)
+    tiles = sh.autotune()  # tile shapes of the tensor-core GEMMs, picked by timing (set-up, untimed)
     fnl = wl.fnl[-1]
     stream = torch.cuda.current_stream()
     out = {k: sh._alm() for k in ("aT", "aE", "aLT", "aLE", "aNLT", "aNLE")}
@@ -373,7 +374,8 @@ def main():
                 "d2h_bytes_per_step": 2 * sh.nalm * 16, "steps": e2e_steps,
                 "note": "fnl_generate_host: inputs are the (seed, realisation, f_NL) scalars; a^T and a^E "
                         "copied to pinned host memory every step"},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": (6 if args.prec in ("bf16x2", "bf16x3") else 5) * args.steps,
+        "tiles": {"synthesis": tiles[0], "analysis": tiles[1]},
         "clocks": clk,
     }
     if fp64 is not None:

@@ -178,47 +178,29 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
     sh->d_tc_syn = dalloc<TcTile>(sh, (size_t)cap_syn);
     sh->d_tc_ana = dalloc<TcTile>(sh, (size_t)cap_ana);
   }
-  // tensor maps (BF16): A operands MN-major with 128B swizzle, B operands K-major with 64B swizzle
-  const int bbox = kTcBBox;
+  // tensor maps of the A operands (BF16, MN-major, 128B swizzle): boxes of 64 columns x 64 k x
+  // both 64-column halves of a 128-column tile, through a view whose last dimension steps over
+  // the halves (128 B apart).  The B maps depend on the tile width: configure_tc builds them.
   for (int t = 0; t < T; ++t) {
     const bf16_t* phi = (const bf16_t*)sh->d_phiT + (size_t)t * sh->phiT_stride;
-    const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
     const bf16_t* gt = (const bf16_t*)sh->d_GT + (size_t)t * sh->gt_stride;
-    const bf16_t* lana = (const bf16_t*)sh->d_lana + (size_t)t * sh->lana_stride;
     {
-      const uint64_t dims[2] = {(uint64_t)Cpad, (uint64_t)rows32};
-      const uint64_t str[1] = {(uint64_t)Cpad * 2};
-      const uint32_t box[2] = {64, 32};
-      sh->tc_syn.tmA[t] = make_tensor_map_bf16(phi, 2, dims, str, box, 128);
+      const uint64_t dims[3] = {64, (uint64_t)rows32, (uint64_t)Cpad / 64};
+      const uint64_t str[2] = {(uint64_t)Cpad * 2, 128};
+      const uint32_t box[3] = {64, (uint32_t)kTcStageK, 2};
+      sh->tc_syn.tmA[t] = make_tensor_map_bf16(phi, 3, dims, str, box, 128);
     }
     {
-      const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
-      const uint64_t str[2] = {64, (uint64_t)np * 64};
-      const uint32_t box[3] = {32, (uint32_t)bbox, 1};
-      sh->tc_syn.tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
-      const uint32_t box16[3] = {32, 16, 1};
-      sh->tc_syn.tmB16[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box16, 64);
-    }
-    {
-      // G is ring-pair-major, [jp][mp][Cpad]: box of 64 columns x 1 problem x 32 ring pairs
-      const uint64_t dims[3] = {(uint64_t)Cpad, (uint64_t)nmp, (uint64_t)np};
-      const uint64_t str[2] = {(uint64_t)Cpad * 2, (uint64_t)nmp * Cpad * 2};
-      const uint32_t box[3] = {64, 1, 32};
-      sh->tc_ana.tmA[t] = make_tensor_map_bf16(gt, 3, dims, str, box, 128);
-    }
-    {
-      const uint64_t dims[2] = {(uint64_t)np, (uint64_t)rows16};
-      const uint64_t str[1] = {(uint64_t)sh->npj * 2};
-      const uint32_t box[2] = {32, (uint32_t)bbox};
-      sh->tc_ana.tmB[t] = make_tensor_map_bf16(lana, 2, dims, str, box, 64);
-      const uint32_t box16[2] = {32, 16};
-      sh->tc_ana.tmB16[t] = make_tensor_map_bf16(lana, 2, dims, str, box16, 64);
+      // G is ring-pair-major, [jp][mp][Cpad]: box of 64 columns x 1 problem x 64 ring pairs x 2 halves
+      const uint64_t dims[4] = {64, (uint64_t)nmp, (uint64_t)np, (uint64_t)Cpad / 64};
+      const uint64_t str[3] = {(uint64_t)Cpad * 2, (uint64_t)nmp * Cpad * 2, 128};
+      const uint32_t box[4] = {64, 1, (uint32_t)kTcStageK, 2};
+      sh->tc_ana.tmA[t] = make_tensor_map_bf16(gt, 4, dims, str, box, 128);
     }
   }
   for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
     a->nterms = T;
     a->split = sh->tc_split;
-    a->bbox = kTcBBox;
     a->L = L;
     a->nr = nr;
     a->npairs = np;
@@ -289,9 +271,32 @@ void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap) {
     a->cols = nm <= 128 ? 128 : 256;
     a->nbuf = std::min(2, 512 / (a->split ? 2 * a->cols : a->cols));
     a->nmax = nm;
-    a->stages = tc_stages(T, nm);
+    a->stages = tc_stages(T, nm, a->mode);
     a->tiles = syn ? sh->d_tc_syn : sh->d_tc_ana;
     a->ntiles = (int)(syn ? ts.size() : ta.size());
+  }
+  // tensor maps of the B operands (BF16, K-major, 64B swizzle): boxes of nmax rows x two
+  // 32-deep slabs (64 k per stage); rows past the table are zero-filled
+  typedef unsigned short bf16_t;
+  const int64_t nslab = sh->row32[nmp] / 32, rows16 = sh->rows_total;
+  for (int t = 0; t < T; ++t) {
+    const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
+    const bf16_t* lana = (const bf16_t*)sh->d_lana + (size_t)t * sh->lana_stride;
+    {
+      // Lambda_syn [slab][jp][32 k]
+      const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
+      const uint64_t str[2] = {64, (uint64_t)np * 64};
+      const uint32_t box[3] = {32, (uint32_t)sh->tc_syn.nmax, 2};
+      sh->tc_syn.tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
+    }
+    {
+      // Lambda_ana [row16][npj]: 32 ring pairs x rows x blocks of 32 ring pairs (64 B apart;
+      // npj is a multiple of 32, so every block stays inside its row)
+      const uint64_t dims[3] = {32, (uint64_t)rows16, (uint64_t)sh->npj / 32};
+      const uint64_t str[2] = {(uint64_t)sh->npj * 2, 64};
+      const uint32_t box[3] = {32, (uint32_t)sh->tc_ana.nmax, 2};
+      sh->tc_ana.tmB[t] = make_tensor_map_bf16(lana, 3, dims, str, box, 64);
+    }
   }
 }
 
@@ -407,7 +412,7 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     }
     sh->row32[nmp] = r32;
     sh->Cpad = round_up(C, 128);
-    sh->npj = round_up(np, 8);
+    sh->npj = round_up(np, 32);
 
     // ---- Gauss-Legendre grid (northern half)
     std::vector<double> xg(d->ntheta), wg(d->ntheta);

@@ -142,7 +142,7 @@ struct fnl_shells {
   // mixed (tensor-core) forms
   int nterms = 0;                  // BF16 terms per operand (0: SIMT forms)
   int Cpad = 0;                    // columns padded to a multiple of 128
-  int npj = 0;                     // ring pairs padded to a multiple of 8 (row stride of Lambda_ana)
+  int npj = 0;                     // ring pairs padded to a multiple of 32 (row stride of Lambda_ana)
   int nsyn = 0;                    // synthesis tile width (ring pairs)
   int nana = 0;                    // analysis tile width cap (degrees)
   int tc_split = 1;                // separate accumulators for leading and correction products
@@ -196,7 +196,6 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
 // Tile shapes of the tensor-core GEMMs (mixed forms): widths capped at syn_cap ring pairs and
 // ana_cap degrees, multiples of 16 in [kTcMinWidth, 256].
 constexpr int kTcMinWidth = 64;
-constexpr int kTcBBox = 64;
 void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap);
 
 // ---- host set-up (setup_host.cpp) -------------------------------------------------------

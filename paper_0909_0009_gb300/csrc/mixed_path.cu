@@ -230,13 +230,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
   if (psum && ws < nr) psum[((size_t)blockIdx.x * (kThreads / 128) + wh) * nr + ws] = (double)ph + (double)pl;
 }
 
-// psum[s] = sum over the filter's partials of shell s, in a fixed order.
-__global__ void k_psum_reduce(int nparts, int nr, const double* __restrict__ part, double* __restrict__ psum) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nr) return;
+// psum[s] = sum over the filter's partials of shell s = blockIdx.x: strided per-thread sums,
+// then a tree over the block, both in a fixed order (the result does not depend on timing).
+__global__ void __launch_bounds__(256) k_psum_reduce(int nparts, int nr, const double* __restrict__ part,
+                                                     double* __restrict__ psum) {
+  __shared__ double red[256];
+  const int s = blockIdx.x;
   double acc = 0.0;
-  for (int e = 0; e < nparts; ++e) acc += part[(size_t)e * nr + s];
-  psum[s] = acc;
+  for (int e = threadIdx.x; e < nparts; e += 256) acc += part[(size_t)e * nr + s];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) psum[s] = red[0];
 }
 
 __device__ __forceinline__ double flushed(double v) { return fabs(v) < 1e-290 ? 0.0 : v; }
@@ -385,7 +393,7 @@ void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, con
                                                      psum ? sh->d_psum_part : nullptr);
   FNL_CUDA(cudaGetLastError());
   if (psum) {
-    k_psum_reduce<<<(nr + 127) / 128, 128, 0, st>>>((sh->lmax + 1) * (kThreads / 128), nr, sh->d_psum_part, psum);
+    k_psum_reduce<<<nr, 256, 0, st>>>((sh->lmax + 1) * (kThreads / 128), nr, sh->d_psum_part, psum);
     FNL_CUDA(cudaGetLastError());
   }
 }

@@ -12,12 +12,14 @@
 // accumulated in FP32 in tensor memory (3 products for 2 terms, 6 for 3 terms).
 //
 // Kernel structure (one persistent CTA per SM, 192 threads):
-//   warp 0      TMA producer: A tile 128 c x 32 k per term (two 64-column boxes, 128B
-//               swizzle), B tile N x 32 k per term (64-row boxes and a 16-row remainder,
-//               64B swizzle)
+//   warp 0      TMA producer, stages 64 deep in k: per term one box of A (128 c x 64 k: both
+//               64-column halves through a 3D/4D view, 128B swizzle) and one of B (nmax rows x
+//               two 32-deep slabs, 64B swizzle).  Few, large boxes: the copy engine's cost
+//               is per box, and 4 KB boxes cap it near a fifth of what 32 KB boxes move
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma (M = 128, N = tile width
-//               up to 256, K = 16) from one thread; the descriptors of every term and k step
-//               are constant offsets from one base per stage.  The leading product and the
+//               up to 256, K = 16) from one thread, up to 4 k steps per stage and one commit
+//               per stage (each commit costs the pipe a few hundred cycles); the descriptors of
+//               every term and k step are constant offsets from one base per stage.  The leading product and the
 //               correction products accumulate in two TMEM accumulators (`cols` apart); the
 //               accumulator sets that fit (1 for 256-wide tiles, 2 for 128) rotate over tiles
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator, then per mode:
@@ -39,7 +41,6 @@ namespace {
 
 constexpr int kEpiWarps = 4;
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
-constexpr uint32_t kABytes = 8192;   // 128 c x 32 k bf16 (two 64 x 32 boxes)
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -84,6 +85,13 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
       ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, int w,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -156,27 +164,30 @@ __device__ __forceinline__ void reduce_columns(float (&x)[32], int lane) {
   }
 }
 
-// The MMAs of one 32-deep k block: two k steps of 16, every product of terms (ta, tb) with
-// ta + tb < NT.  da, db: descriptors of term 0 of A and B in this stage; the other terms and
-// k steps are constant offsets (descriptor start addresses count 16-byte units).  With
-// SPLIT the leading product accumulates in d and the corrections in dc, alternating.
+// The MMAs of one stage: nh (1 or 2) slabs of 32 k, each two k steps of 16, every product of
+// terms (ta, tb) with ta + tb < NT.  da, db: descriptors of term 0 of A and B in this stage;
+// the other terms and k steps are constant offsets (descriptor start addresses count 16-byte
+// units): A k step kk starts 16 rows (2048 B) further, B slab h sits nmax * 64 B after slab 0
+// and its second k step 32 B into the swizzled rows.  With SPLIT the leading product
+// accumulates in d and the corrections in dc.
 template <int NT, bool SPLIT>
-__device__ __forceinline__ void issue_kblock(uint64_t da, uint64_t db, uint32_t bterm16, uint32_t d, uint32_t dc,
-                                             uint32_t idesc, bool first) {
+__device__ __forceinline__ void issue_stage(uint64_t da, uint64_t db, uint32_t bterm16, uint32_t bslab16, int nh,
+                                            uint32_t d, uint32_t dc, uint32_t idesc, bool first) {
 #pragma unroll
-  for (int ks = 0; ks < 2; ++ks) {
+  for (int kk = 0; kk < 4; ++kk) {
+    if (kk >= 2 * nh) break;
     int corr = 0;
 #pragma unroll
     for (int ta = 0; ta < NT; ++ta) {
 #pragma unroll
       for (int tb = 0; ta + tb < NT; ++tb) {
-        const uint64_t ad = da + (uint64_t)((ta * kABytes + ks * 2048) >> 4);
-        const uint64_t bd = db + (uint64_t)(tb * bterm16 + ((ks * 32) >> 4));
+        const uint64_t ad = da + (uint64_t)((ta * kTcABytes + kk * 2048u) >> 4);
+        const uint64_t bd = db + (uint64_t)(tb * bterm16 + (kk >> 1) * bslab16 + (((kk & 1) * 32) >> 4));
         if (SPLIT && (ta | tb)) {
-          tc_mma(dc, ad, bd, idesc, (first && ks == 0 && corr == 0) ? 0u : 1u);
+          tc_mma(dc, ad, bd, idesc, (first && kk == 0 && corr == 0) ? 0u : 1u);
           ++corr;
         } else {
-          tc_mma(d, ad, bd, idesc, (first && ks == 0 && ta == 0 && tb == 0) ? 0u : 1u);
+          tc_mma(d, ad, bd, idesc, (first && kk == 0 && ta == 0 && tb == 0) ? 0u : 1u);
         }
       }
     }
@@ -187,8 +198,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = a.stages;
-  const uint32_t bBytes = (uint32_t)a.nmax * 64u;
-  const uint32_t stageBytes = (uint32_t)a.nterms * (kABytes + bBytes);
+  const uint32_t bBytes = (uint32_t)a.nmax * 128u;  // B bytes per term and stage (two slabs)
+  const uint32_t stageBytes = (uint32_t)a.nterms * (kTcABytes + bBytes);
   uint64_t* full = (uint64_t*)(smem + (size_t)S * stageBytes);
   uint64_t* empty = full + S;
   uint64_t* tfull = empty + S;
@@ -235,7 +246,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       uint32_t armed = 0, armed_par = 0;  // stages with copies issued, and the parity armed
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
-        for (int kb = 0; kb < tl.nkb; ++kb) {
+        const int nst = (tl.nkb + 1) / 2;
+        for (int sg = 0; sg < nst; ++sg) {
           int good = 1;
           if (lane == 0) good = mbar_wait(&empty[stage], phase ^ 1, a.err, 1);
           good = __shfl_sync(0xffffffffu, good, 0);
@@ -244,35 +256,27 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             break;
           }
           if (lane == 0) {
-          mbar_expect_tx(&full[stage], (uint32_t)a.nterms * (kABytes + (uint32_t)tl.nsize * 64u));
-          armed |= 1u << stage;
-          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-          const uint32_t st = sbase + (uint32_t)stage * stageBytes;
-          for (int tm = 0; tm < a.nterms; ++tm) {
-            const uint32_t sa = st + (uint32_t)tm * kABytes;
-            const uint32_t sb = st + (uint32_t)a.nterms * kABytes + (uint32_t)tm * bBytes;
-            if (a.mode == TC_SYNTH) {
-              // A: Phi rows r0 + 32 kb, columns c0 .. c0 + 127
-              tma_load_2d(sa, &a.tmA[tm], tl.c0, tl.r0 + 32 * kb, &full[stage]);
-              tma_load_2d(sa + 4096, &a.tmA[tm], tl.c0 + 64, tl.r0 + 32 * kb, &full[stage]);
-              // B: slab (r0 / 32 + kb), ring pairs n0 .. n0 + nsize - 1
-              int q = 0;
-              for (; q + a.bbox <= tl.nsize; q += a.bbox)
-                tma_load_3d(sb + 64u * q, &a.tmB[tm], 0, tl.n0 + q, tl.r0 / 32 + kb, &full[stage]);
-              for (; q < tl.nsize; q += 16)
-                tma_load_3d(sb + 64u * q, &a.tmB16[tm], 0, tl.n0 + q, tl.r0 / 32 + kb, &full[stage]);
-            } else {
-              // A: G[jp][mp][c] at problem mp, ring pairs 32 kb .., columns c0 .. c0 + 127
-              tma_load_3d(sa, &a.tmA[tm], tl.c0, tl.mp, 32 * kb, &full[stage]);
-              tma_load_3d(sa + 4096, &a.tmA[tm], tl.c0 + 64, tl.mp, 32 * kb, &full[stage]);
-              // B: Lambda_ana rows r0 + n0 .., ring pairs 32 kb ..
-              int q = 0;
-              for (; q + a.bbox <= tl.nsize; q += a.bbox)
-                tma_load_2d(sb + 64u * q, &a.tmB[tm], 32 * kb, tl.r0 + tl.n0 + q, &full[stage]);
-              for (; q < tl.nsize; q += 16)
-                tma_load_2d(sb + 64u * q, &a.tmB16[tm], 32 * kb, tl.r0 + tl.n0 + q, &full[stage]);
+            // boxes past the end of a tensor are zero-filled; a second slab past the tile's
+            // last k block is loaded but never read by the MMAs
+            mbar_expect_tx(&full[stage], stageBytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            const uint32_t st = sbase + (uint32_t)stage * stageBytes;
+            for (int tm = 0; tm < a.nterms; ++tm) {
+              const uint32_t sa = st + (uint32_t)tm * kTcABytes;
+              const uint32_t sb = st + (uint32_t)a.nterms * kTcABytes + (uint32_t)tm * bBytes;
+              if (a.mode == TC_SYNTH) {
+                // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
+                tma_load_3d(sa, &a.tmA[tm], 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, &full[stage]);
+                // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
+                tma_load_3d(sb, &a.tmB[tm], 0, tl.n0, tl.r0 / 32 + 2 * sg, &full[stage]);
+              } else {
+                // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
+                tma_load_4d(sa, &a.tmA[tm], 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, &full[stage]);
+                // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
+                tma_load_3d(sb, &a.tmB[tm], 0, tl.r0 + tl.n0, 2 * sg, &full[stage]);
+              }
             }
-          }
           }  // lane 0
           __syncwarp();
           if (++stage == S) {
@@ -296,9 +300,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     // ------------------------------------------------------------------ MMA issuer
     // The whole warp walks the loop (converged); lane 0 waits, issues and commits.
     {
-      const uint64_t da0 = sdesc(sbase, 4096, 1024, 2);                                   // A: MN-major, 128B swizzle
-      const uint64_t db0 = sdesc(sbase + (uint32_t)a.nterms * kABytes, 16, 512, 4);       // B: K-major, 64B swizzle
-      const uint32_t bterm16 = bBytes >> 4;
+      // A: MN-major, 128B swizzle, halves 64 k x 128 B apart; B: K-major, 64B swizzle
+      const uint64_t da0 = sdesc(sbase, (uint32_t)kTcStageK * 128u, 1024, 2);
+      const uint64_t db0 = sdesc(sbase + (uint32_t)a.nterms * kTcABytes, 16, 512, 4);
+      const uint32_t bterm16 = bBytes >> 4, bslab16 = ((uint32_t)a.nmax * 64u) >> 4;
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -313,7 +318,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols);
         const uint32_t idesc = idesc_bf16(tl.nsize);
-        for (int kb = 0; kb < tl.nkb; ++kb) {
+        const int nst = (tl.nkb + 1) / 2;
+        for (int sg = 0; sg < nst; ++sg) {
           good = 1;
           if (lane == 0) good = mbar_wait(&full[stage], phase, a.err, 3);
           good = __shfl_sync(0xffffffffu, good, 0);
@@ -325,14 +331,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           if (lane == 0) {
             const uint32_t so = (uint32_t)stage * (stageBytes >> 4);
             const uint64_t da = da0 + so, db = db0 + so;
-            const bool first = kb == 0;
+            const bool first = sg == 0;
+            const int nh = min(2, tl.nkb - 2 * sg);
             const uint32_t dc = d + (uint32_t)a.cols;
             if (a.nterms == 2) {
-              if (a.split) issue_kblock<2, true>(da, db, bterm16, d, dc, idesc, first);
-              else issue_kblock<2, false>(da, db, bterm16, d, dc, idesc, first);
+              if (a.split) issue_stage<2, true>(da, db, bterm16, bslab16, nh, d, dc, idesc, first);
+              else issue_stage<2, false>(da, db, bterm16, bslab16, nh, d, dc, idesc, first);
             } else {
-              if (a.split) issue_kblock<3, true>(da, db, bterm16, d, dc, idesc, first);
-              else issue_kblock<3, false>(da, db, bterm16, d, dc, idesc, first);
+              if (a.split) issue_stage<3, true>(da, db, bterm16, bslab16, nh, d, dc, idesc, first);
+              else issue_stage<3, false>(da, db, bterm16, bslab16, nh, d, dc, idesc, first);
             }
             tc_commit(&empty[stage]);
           }
@@ -502,19 +509,21 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
   return m;
 }
 
-size_t tc_smem_bytes(int nterms, int nmax, int stages) {
-  const size_t stage = (size_t)nterms * (kABytes + (size_t)nmax * 64);
-  return 1024 /*alignment*/ + (size_t)stages * stage + 1024 /*barriers*/ + 4 * 256 * 4 * sizeof(float);
+size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode) {
+  const size_t stage = (size_t)nterms * (kTcABytes + (size_t)nmax * 128);
+  const size_t red = mode == TC_SYNTH ? 0 : 4 * 256 * 4 * sizeof(float);  // epilogue reduction (analysis)
+  return 1024 /*alignment*/ + (size_t)stages * stage + 1024 /*barriers*/ + red;
 }
 
-int tc_stages(int nterms, int nmax) {
+int tc_stages(int nterms, int nmax, int mode) {
   int s = 6;
-  while (s > 2 && tc_smem_bytes(nterms, nmax, s) > 227 * 1024) --s;
+  while (s > 1 && tc_smem_bytes(nterms, nmax, s, mode) > 227 * 1024) --s;
   return s;
 }
 
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(args.nterms, args.nmax, args.stages);
+  const size_t smem = tc_smem_bytes(args.nterms, args.nmax, args.stages, args.mode);
+  if (smem > 227 * 1024 || args.stages < 1) throw Error(FNL_EUNSUPPORTED, "tensor-core tile does not fit shared memory");
   FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::max(1, std::min(args.ntiles, sms));
   k_tc_gemm<<<grid, kThreadsTc, smem, st>>>(args);

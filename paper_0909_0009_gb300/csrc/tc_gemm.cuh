@@ -16,18 +16,22 @@ struct TcTile {
   int mp, c0, n0, nsize, nkb, r0, kvalid, pad;
 };
 
+// Operands arrive in stages 64 deep in k: per BF16 term one TMA box of A (128 columns x 64 k,
+// both 64-column halves, MN-major, 128B swizzle) and one of B (nmax rows x 64 k as two
+// 32-deep slabs, K-major, 64B swizzle), and one commit releases the stage.
+constexpr int kTcStageK = 64;
+constexpr uint32_t kTcABytes = 128u * kTcStageK * 2u;  // A bytes per term and stage
+
 struct TcArgs {
-  CUtensorMap tmA[3];   // per BF16 term: Phi (synthesis) or G (analysis)
-  CUtensorMap tmB[3];   // per BF16 term: Lambda_syn or Lambda_ana, boxes of bbox rows
-  CUtensorMap tmB16[3]; // the same operands in 16-row boxes (tile remainders)
+  CUtensorMap tmA[3];   // per BF16 term: Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves}
+  CUtensorMap tmB[3];   // per BF16 term: Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs}
   const TcTile* tiles;
   int ntiles;
   int mode;
   int nterms;           // 2 or 3
   int split;            // 1: products of the leading terms and the correction products go to two
                         //    separate accumulators (tile width <= 128), summed in the epilogue
-  int nmax;             // largest tile width in this launch (B stage size)
-  int bbox;             // rows of one B box (multiple of 16)
+  int nmax;             // largest tile width in this launch (rows of every B box)
   int cols;             // TMEM columns between the leading and the correction accumulator
   int nbuf;             // accumulator sets in TMEM (double buffering when 2)
   int stages;
@@ -43,8 +47,8 @@ struct TcArgs {
 
 CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                                  const uint32_t* box, int swizzle_bytes);
-size_t tc_smem_bytes(int nterms, int nmax, int stages);
-int tc_stages(int nterms, int nmax);
+size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode);
+int tc_stages(int nterms, int nmax, int mode);
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st);
 
 }  // namespace fnl
