@@ -64,15 +64,17 @@ __device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, flo
 
 // Step (i) as a register-tiled FP32 GEMM per degree l (block per l, largest first):
 //   Phi_l[i][col] = sum_{j <= i} K_l[i][j] n_l[j][col],  col = 2 (m - m0) + {re, im}
-// over chunks of 32 orders m (64 columns).  K_l is staged transposed in shared memory; each
-// thread owns 8 rows i x 4 columns.  The noise tile is drawn by all threads (Philox4x64 +
-// FP32 Box-Muller); a^X_L = v^X_l . n per column (Eq. 5 applied to Eq. 9).
+// over chunks of 32 orders m (64 columns).  K_l is staged transposed in shared memory.  K_l is
+// lower triangular, so row tile t (rows 4t .. 4t + 3) needs 4t + 4 terms: each thread owns
+// the 4-row tiles r and nt4 - 1 - r (r = thread row, warp-uniform up to one) times 4 columns,
+// which gives every thread and every warp the same number of multiply-adds.  The noise tile
+// is drawn by all threads (Philox4x64 + FP32 Box-Muller); a^X_L = v^X_l . n per column
+// (Eq. 5 applied to Eq. 9), each dot product split over two threads.
 constexpr int kFCols = 64;
 
-__host__ __device__ inline int out_stride(int nrp) {
-  const int s = nrp + nrp / 8;
-  return s + ((4 - s % 8) + 8) % 8;
-}
+// Row stride of the output tile [col][i]: a multiple of 4 floats with an odd quotient, so
+// that the float4 stores of 8 lanes (consecutive column blocks) hit distinct bank quads.
+__host__ __device__ inline int out_stride(int nrp) { return nrp + 4; }
 
 __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
                                                              const float* __restrict__ Kf,
@@ -87,11 +89,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
   const int l = L - blockIdx.x;
   const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
   float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
-  // output tile [col][i] with row stride os (i at i + i / 8, os = 4 mod 8): the 8-row thread
-  // tiles then write to distinct banks
+  // output tile [col][i], row stride os (see out_stride)
   const int os = out_stride(nrp);
   float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols] noise tile, then [kFCols][os] output tile
-  float* vs = nt + (size_t)max(nr * kFCols, kFCols * os);  // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo
+  // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo; then [2][kFCols][2] partial a^X_L sums (dfp)
+  float* vs = nt + (size_t)max(nr * kFCols, kFCols * os);
+                                                            // then [2][kFCols][2] (dfp below)
   const float* Kl = Kf + (size_t)l * nr * nr;
   for (int e = threadIdx.x; e < nr * nrp; e += kThreads) {
     const int i = e / nr, j = e % nr;       // global reads along j
@@ -110,8 +113,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
   }
   const int64_t nalm = (int64_t)(L + 1) * (L + 2) / 2;
   const int npair = (nr + 1) / 2;
-  const int ib = threadIdx.x & 15, cb = threadIdx.x >> 4;  // rows 8 ib .. 8 ib + 7, columns 4 cb .. 4 cb + 3
-  const bool rows_active = 8 * ib < nr;
+  // GEMM: thread row r = tid / 16 owns row tiles ta = r and tb = nt4 - 1 - r, columns 4 cb ..
+  const int r4 = threadIdx.x >> 4, cb = threadIdx.x & 15;
+  const int nt4 = nrp / 4, ta = r4, tb = nt4 - 1 - r4;
+  const bool rows_active = r4 < nt4 / 2;
+  const int ja = min(nr, 4 * ta + 4), jb = min(nr, 4 * tb + 4);
+  float* dfp = vs + 4 * nr;                // [2][kFCols][2]: second halves of the a^X_L sums
   // write-out phase: thread -> shell ws = threadIdx.x % 128, orders mb = threadIdx.x / 128 (+2 ...)
   const int ws = threadIdx.x & 127, wh = threadIdx.x >> 7;
   float ph = 0.f, pl = 0.f;  // sum_m w_m |Phi_L,lm(r_ws)|^2 over this thread's orders (double-float)
@@ -145,35 +152,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
       }
     }
     __syncthreads();
-    // ---- a^X_L for the chunk: thread (field f, column col); exact products, double-float sum
-    if (threadIdx.x < 2 * kFCols) {
-      const int col = threadIdx.x & (kFCols - 1), f = threadIdx.x / kFCols;
-      const int mb = col >> 1;
-      if (mb < nm) {
-        const float* vh = vs + f * nr;
-        const float* vl = vs + (2 + f) * nr;
-        float sh = 0.f, sl = 0.f;
-        for (int j = 0; j < nr; ++j) {
-          const float n = nt[(size_t)j * kFCols + col];
-          const float p = vh[j] * n;
-          df_add(sh, sl, p, fmaf(vh[j], n, -p) + vl[j] * n);
-        }
-        const int64_t idx = alm_idx(l, m0 + mb, L);
-        (f ? aLE : aLT)[2 * idx + (col & 1)] = (double)sh + (double)sl;
+    // ---- a^X_L for the chunk: thread (half h, field f, column col) sums half of the j range;
+    // exact products, double-float sums; the second halves are added after the next barrier
+    const int acol = threadIdx.x & (kFCols - 1), af = (threadIdx.x >> 6) & 1, ah = threadIdx.x >> 7;
+    const bool a_active = (acol >> 1) < nm;
+    float sh = 0.f, sl = 0.f;
+    if (a_active) {
+      const float* vh = vs + af * nr;
+      const float* vl = vs + (2 + af) * nr;
+      const int j0 = ah ? nr / 2 : 0, j1 = ah ? nr : nr / 2;
+      for (int j = j0; j < j1; ++j) {
+        const float n = nt[(size_t)j * kFCols + acol];
+        const float p = vh[j] * n;
+        df_add(sh, sl, p, fmaf(vh[j], n, -p) + vl[j] * n);
+      }
+      if (ah) {
+        dfp[(af * kFCols + acol) * 2] = sh;
+        dfp[(af * kFCols + acol) * 2 + 1] = sl;
       }
     }
-    // ---- Phi_L for the chunk: 8 x 4 register tile per thread
+    // ---- Phi_L for the chunk: row tiles ta and tb x 4 columns per thread
     float acc[8][4];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[q][c] = 0.f;
     if (rows_active) {
-      const int jend = min(nr, 8 * ib + 8);
-      for (int j = 0; j < jend; ++j) {
-        const float4 k0 = *(const float4*)(Kt + (size_t)j * nrp + 8 * ib);
-        const float4 k1 = *(const float4*)(Kt + (size_t)j * nrp + 8 * ib + 4);
-        const float4 nv = *(const float4*)(nt + (size_t)j * kFCols + 4 * cb);
+      const float* kta = Kt + 4 * ta;
+      const float* ktb = Kt + 4 * tb;
+      const float* nvp = nt + 4 * cb;
+      int j = 0;
+      for (; j < ja; ++j) {
+        const float4 k0 = *(const float4*)(kta + (size_t)j * nrp);
+        const float4 k1 = *(const float4*)(ktb + (size_t)j * nrp);
+        const float4 nv = *(const float4*)(nvp + (size_t)j * kFCols);
         const float kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
         const float nn[4] = {nv.x, nv.y, nv.z, nv.w};
 #pragma unroll
@@ -181,15 +193,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(kk[q], nn[c], acc[q][c]);
       }
+      for (; j < jb; ++j) {
+        const float4 k1 = *(const float4*)(ktb + (size_t)j * nrp);
+        const float4 nv = *(const float4*)(nvp + (size_t)j * kFCols);
+        const float kk[4] = {k1.x, k1.y, k1.z, k1.w};
+        const float nn[4] = {nv.x, nv.y, nv.z, nv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[4 + q][c] = fmaf(kk[q], nn[c], acc[4 + q][c]);
+      }
     }
     __syncthreads();  // the noise tile is no longer read: reuse it as the output tile [col][i]
+    if (a_active && !ah) {
+      df_add(sh, sl, dfp[(af * kFCols + acol) * 2], dfp[(af * kFCols + acol) * 2 + 1]);
+      const int64_t idx = alm_idx(l, m0 + (acol >> 1), L);
+      (af ? aLE : aLT)[2 * idx + (acol & 1)] = (double)sh + (double)sl;
+    }
     if (rows_active) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int i = 8 * ib + q;
-        if (i >= nr) break;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) nt[(size_t)(4 * cb + c) * os + i + (i >> 3)] = acc[q][c];
+      for (int c = 0; c < 4; ++c) {
+        float* o = nt + (size_t)(4 * cb + c) * os;
+        *(float4*)(o + 4 * ta) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+        *(float4*)(o + 4 * tb) = make_float4(acc[4][c], acc[5][c], acc[6][c], acc[7][c]);
       }
     }
     __syncthreads();
@@ -199,8 +225,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
         const int m = m0 + mb;
         const int p = (l - m) & 1;
         const int64_t row = row32[2 * m + p] + ((l - m) >> 1);
-        const float re = nt[(size_t)(2 * mb) * os + ws + (ws >> 3)];
-        const float im = nt[(size_t)(2 * mb + 1) * os + ws + (ws >> 3)];
+        const float re = nt[(size_t)(2 * mb) * os + ws];
+        const float im = nt[(size_t)(2 * mb + 1) * os + ws];
         __nv_bfloat162 t0, t1, t2;
         const __nv_bfloat16 r0 = __float2bfloat16_rn(re), i0 = __float2bfloat16_rn(im);
         const float rr1 = re - __bfloat162float(r0), ir1 = im - __bfloat162float(i0);
@@ -385,7 +411,8 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
   const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
-  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)std::max(nr * kFCols, kFCols * out_stride(nrp)) + 4 * nr);
+  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)std::max(nr * kFCols, kFCols * out_stride(nrp)) +
+                                      4 * nr + 4 * kFCols);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
                                                      (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,
