@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the FP64 comparator beside a mixed run (0: skip it)")
+    ap.add_argument("--tiles", default="auto",
+                    help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
     wl = W.WORKLOADS[args.workload]
     if args.steps is None:
@@ -250,7 +252,13 @@ def main():
     K = F.cholesky_filters(C, W.COV.jitter_rel)
     del C
     sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=args.prec, device=local)
-    tiles = sh.autotune()  # tile shapes of the tensor-core GEMMs, picked by timing (set-up, untimed)
+    if args.tiles == "auto":
+        tiles = sh.autotune()  # tile shapes of the tensor-core GEMMs, picked by timing (set-up, untimed)
+    elif args.prec in ("bf16x2", "bf16x3"):
+        tiles = tuple(int(x) for x in args.tiles.split(","))
+        sh.set_tiles(*tiles)
+    else:
+        tiles = (64, 64)
     fnl = wl.fnl[-1]
     stream = torch.cuda.current_stream()
     out = {k: sh._alm() for k in ("aT", "aE", "aLT", "aLE", "aNLT", "aNLE")}

@@ -258,9 +258,24 @@ void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap) {
       n0 += n;
     }
   }
-  auto by_cost = [](const TcTile& a, const TcTile& b) { return a.nkb * a.nsize > b.nkb * b.nsize; };
-  std::stable_sort(ts.begin(), ts.end(), by_cost);
-  std::stable_sort(ta.begin(), ta.end(), by_cost);
+  // largest problems first (the CTAs take tiles round robin), but the tiles of one problem
+  // stay adjacent: they share its operand slab (Phi or G rows, Lambda rows across column
+  // tiles), which then comes from L2 instead of DRAM for all but the first of them
+  auto group_sort = [](std::vector<TcTile>& v) {
+    std::vector<std::pair<int64_t, int>> groups;  // (cost, first index) per problem
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (i == 0 || v[i].mp != v[i - 1].mp) groups.push_back({0, (int)i});
+      groups.back().first += (int64_t)v[i].nkb * v[i].nsize;
+    }
+    std::stable_sort(groups.begin(), groups.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<TcTile> out;
+    out.reserve(v.size());
+    for (const auto& g : groups)
+      for (size_t i = g.second; i < v.size() && v[i].mp == v[g.second].mp; ++i) out.push_back(v[i]);
+    v.swap(out);
+  };
+  group_sort(ts);
+  group_sort(ta);
   FNL_CUDA(cudaMemcpy(sh->d_tc_syn, ts.data(), sizeof(TcTile) * ts.size(), cudaMemcpyHostToDevice));
   FNL_CUDA(cudaMemcpy(sh->d_tc_ana, ta.data(), sizeof(TcTile) * ta.size(), cudaMemcpyHostToDevice));
   int widest_ana = 16;
