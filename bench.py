@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -61,6 +62,41 @@ def fft_bytes(lmax: int, ntheta: int, nr: int, real_bytes: int) -> float:
     """HBM bytes of the ring kernel: read F (even+odd, 2 N_r reals per (m, pair)) and write G."""
     npairs = (ntheta + 1) // 2
     return 2.0 * 2 * (lmax + 1) * npairs * (2 * nr) * real_bytes
+
+
+def fft_flops(ntheta: int, nphi: int, nr: int) -> float:
+    """FFT flops of the ring kernel by the usual 5 N log2 N count per complex N-point
+    transform: per (ring pair, shell) one inverse and one forward transform of nphi points."""
+    npairs = (ntheta + 1) // 2
+    return npairs * nr * 2 * 5.0 * nphi * math.log2(nphi)
+
+
+def filter_flops(lmax: int, nr: int) -> float:
+    """Step (i): Phi_L = K_l n with K_l lower triangular, per (l, m) and real/imaginary part
+    nr (nr + 1) / 2 multiply-adds = nr (nr + 1) flops."""
+    return W.n_alm(lmax) * 2 * nr * (nr + 1.0)
+
+
+def gemm_bytes(lmax: int, ntheta: int, nr: int, nterms: int) -> dict:
+    """Algorithmic HBM bytes of the two Legendre GEMMs of the tensor-core forms: each lambda
+    table once (nterms BF16 terms per entry), the data operand once (Phi_L as BF16 terms for
+    the synthesis, G as BF16 terms for the analysis) and F written once in FP32."""
+    npairs = (ntheta + 1) // 2
+    cols = 2 * nr
+    lam = W.n_alm(lmax) * npairs * 2.0 * nterms
+    fg = 2 * (lmax + 1) * npairs * cols
+    return {"synthesis_gemm": lam + W.n_alm(lmax) * cols * 2.0 * nterms + fg * 4.0,
+            "analysis_gemm": lam + fg * 2.0 * nterms}
+
+
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# a one-pass metric taken on the full-size command of the launch-list summary under
+# profiles/), keyed by stage and workload.  Cleared whenever the kernel changes.
+TRAFFIC = {
+    ("ring_fft_square", "lmax1024_nr128", "bf16x2"): 3.185e9,
+}
+
+FP32_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 lanes x FMA x max SM clock
 
 
 # ---------------------------------------------------------------------------------------
@@ -201,6 +237,86 @@ def run_reference(args, wl: W.Workload):
     return 0
 
 
+def measure_batch(F, prec: str, device: int, reps: int = 3) -> dict:
+    """Batching form: the 64 realisations of uneven l_max in {128, 256, 512, 1024} and N_r in
+    {32, 64, 96, 128} (grids by the exact-square rule, f_NL uniform in [-50, 50]) as one
+    captured graph (fnl_generate_batch), tile shapes from the autotuner, against the same
+    realisations as single fnl_generate calls on one stream.  Filters: seeded lower-triangular
+    matrices of the covariance's amplitude (the cost does not depend on their values)."""
+    import torch
+    insts = W.batch_instances()
+    objs = {}
+    for x in insts:
+        key = (x.lmax, x.nr)
+        if key not in objs:
+            r, w = W.radial_grid(x.nr)
+            aT, aE = W.transfer_kernels(x.lmax, r)
+            K = W.random_lower_filters(x.lmax, x.nr, seed=x.lmax + x.nr, scale=8e-5)
+            objs[key] = F.Shells(x.lmax, x.nr, x.ntheta, x.nphi, r, w, aT, aE, K=K, prec=prec, device=device)
+            objs[key].autotune()
+    shells = [objs[(x.lmax, x.nr)] for x in insts]
+    b = F.Batch(shells)
+    seeds = [x.seed for x in insts]
+    reals = [x.realisation for x in insts]
+    fnls = [x.fnl for x in insts]
+    out = b.generate(seeds, reals, fnls)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(reps):
+        b.generate([s_ + 7919 * (i + 1) for s_ in seeds], reals, fnls, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / reps
+    e0.record(stream)
+    for s_, sd, rl, f in zip(shells, seeds, reals, fnls):
+        s_.generate(sd, rl, f, parts=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1)
+    lm = sorted({x.lmax for x in insts})
+    d = {"workload": "uneven64: l_max in {128,256,512,1024}, N_r in {32,64,96,128}, 64 realisations",
+         "value": len(insts) / (t_graph / 1e3), "unit": UNIT, "ms_per_graph_launch": t_graph,
+         "single_calls_ms": t_single, "speedup_vs_single_calls": t_single / t_graph,
+         "graph_launches_per_batch": 1, "streams": len(set(b.lanes())), "distinct_configurations": len(objs),
+         "nphi": {str(l): W.grid_for_lmax(l)[1] for l in lm}}
+    b.close()
+    for s_ in objs.values():
+        s_.close()
+    return d
+
+
+def measure_adjoint(F, device: int, reps: int = 3) -> dict:
+    """Differentiation form at l_max = 512, N_r = 96 (769 x 1600): fnl_generate and
+    fnl_generate_backward (dL/dn and dL/df_NL, maps recomputed) in FP64 and FP32."""
+    import torch
+    wl = W.GRAD
+    r, w = W.radial_grid(wl.nr)
+    aT, aE = W.transfer_kernels(wl.lmax, r)
+    K = W.random_lower_filters(wl.lmax, wl.nr, seed=2, scale=8e-5)
+    stream = torch.cuda.current_stream()
+    res = {"workload": wl.name, "lmax": wl.lmax, "nr": wl.nr, "ntheta": wl.ntheta, "nphi": wl.nphi}
+    for prec in ("fp64", "fp32"):
+        sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=prec, device=device)
+        g = torch.randn(sh.nalm, dtype=torch.complex128, device=f"cuda:{device}")
+        fw = sh.generate(2, 0, wl.fnl[0])
+        sh.generate_backward(2, 0, wl.fnl[0], gT=g, gE=g, aNLT=fw["aNLT"], aNLE=fw["aNLE"])
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for i in range(reps):
+            fw = sh.generate(2, i, wl.fnl[0], out=fw)
+        e1.record(stream)
+        for i in range(reps):
+            sh.generate_backward(2, i, wl.fnl[0], gT=g, gE=g, aNLT=fw["aNLT"], aNLE=fw["aNLE"])
+        e2.record(stream)
+        torch.cuda.synchronize()
+        res[prec] = {"forward_ms": e0.elapsed_time(e1) / reps, "backward_ms": e1.elapsed_time(e2) / reps}
+        sh.close()
+    return res
+
+
 def config_of(wl: W.Workload, prec: str) -> dict:
     return {"workload": wl.name, "lmax": wl.lmax, "nr": wl.nr, "ntheta": wl.ntheta, "nphi": wl.nphi,
             "fnl": wl.fnl[-1], "precision": prec,
@@ -222,6 +338,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the FP64 comparator beside a mixed run (0: skip it)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--tiles", default="auto",
                     help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
@@ -338,46 +456,76 @@ def main():
         d64.close()
         del d64, out64, ref, b
 
+    batch = None if args.no_batch or args.prec not in ("bf16x2", "bf16x3") else measure_batch(F, args.prec, local)
+    adjoint = None if args.no_adjoint else measure_adjoint(F, local)
+
     if rank != 0:
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel, from the live stage events
+    # ---- rooflines of every stage from the live stage events; the dominant one is the
+    # line's "roofline".  Each stage is measured against what bounds it: the tensor pipe
+    # (executed MMA flops) for the Legendre GEMMs, the FP32 pipes for the filter and the
+    # ring FFTs (ALU-issue bound: see the design doc), HBM for the quadrature.
     pk, pk_kind = peaks()
     per_stage = {k: v / max(calls, 1) for k, v in stage_sum.items()}
-    dom = max(per_stage, key=per_stage.get)
+    mixed = args.prec in ("bf16x2", "bf16x3")
+    nterm = 2 if args.prec == "bf16x2" else 3
+    mult = {"bf16x2": 3, "bf16x3": 6}.get(args.prec, 1)
     flops_dir = legendre_flops(wl.lmax, wl.ntheta, wl.nr)
+    gb = gemm_bytes(wl.lmax, wl.ntheta, wl.nr, nterm) if mixed else {}
     real_bytes = 8 if args.prec == "fp64" else 4
-    if dom in ("synthesis_gemm", "analysis_gemm"):
-        if args.prec == "fp64":
-            peak, bound, unit = 1.25, "alu", "TFLOP/s"
-            peak_note = "nominal GB300 FP64 rate (no measured FP64 peak); see DESIGN.md"
-        elif args.prec == "fp32":
-            peak, bound, unit = 2070e6 * 152 * 128 * 2 / 1e12, "alu", "TFLOP/s"
-            peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz"
+    stages = {}
+    for st_name, ms_ in per_stage.items():
+        sec = ms_ / 1e3
+        if st_name in ("synthesis_gemm", "analysis_gemm"):
+            if mixed:
+                e = {"bound": "tensor", "achieved": flops_dir * mult / sec / 1e12, "peak": pk["bf16_tflops_sustained"],
+                     "unit": "TFLOP/s", "peak_source": f"bf16 sustained ({pk_kind}); executed = {mult} x useful flops",
+                     "hbm_frac": gb[st_name] / sec / 1e9 / pk["hbm_gbs"]}
+            elif args.prec == "fp32":
+                e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": FP32_TFLOPS, "unit": "TFLOP/s",
+                     "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz"}
+            else:
+                e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}
+        elif st_name == "ring_fft_square":
+            e = {"bound": "alu", "achieved": fft_flops(wl.ntheta, wl.nphi, wl.nr) / sec / 1e12,
+                 "peak": FP32_TFLOPS if args.prec != "fp64" else 1.25, "unit": "TFLOP/s",
+                 "peak_source": ("FP32 pipes: 152 SMs x 128 lanes x 2 flops x 2070 MHz" if args.prec != "fp64"
+                                 else "nominal GB300 FP64 rate") + "; flops by 5 N log2 N",
+                 "hbm_frac": fft_bytes(wl.lmax, wl.ntheta, wl.nr, real_bytes) / sec / 1e9 / pk["hbm_gbs"]}
+        elif st_name == "filter":
+            e = {"bound": "alu", "achieved": filter_flops(wl.lmax, wl.nr) / sec / 1e12,
+                 "peak": FP32_TFLOPS if args.prec != "fp64" else 1.25, "unit": "TFLOP/s",
+                 "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz"}
         else:
-            nterm = 3 if args.prec == "bf16x2" else 6
-            peak, bound, unit = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s"
-            peak_note = f"bf16 sustained ({pk_kind}); executed = {nterm} x useful flops"
-        mult = 1 if args.prec in ("fp64", "fp32") else (3 if args.prec == "bf16x2" else 6)
-        achieved = flops_dir * mult / (per_stage[dom] / 1e3) / 1e12
-    else:
-        bytes_ = fft_bytes(wl.lmax, wl.ntheta, wl.nr, real_bytes)
-        peak, bound, unit = pk["hbm_gbs"], "hbm", "GB/s"
-        peak_note = f"HBM copy ({pk_kind})"
-        achieved = bytes_ / (per_stage[dom] / 1e3) / 1e9
-    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
-                "stage_ms": {k: round(v, 4) for k, v in per_stage.items()}}
+            if mixed:  # epilogue partials (float4 per column tile) and a^X_L in, a^X and a^X_NL out
+                qb = W.n_alm(wl.lmax) * ((wl.nr * 2 + 127) // 128 * 16 + 2 * 16 + 4 * 16)
+            else:      # Phi_NL rows and a^X_L in, a^X and a^X_NL out
+                qb = W.n_alm(wl.lmax) * (2 * wl.nr * real_bytes + 2 * 16 + 4 * 16)
+            e = {"bound": "hbm", "achieved": qb / sec / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "peak_source": f"HBM copy ({pk_kind})"}
+        e["frac"] = e["achieved"] / e["peak"]
+        e["ms"] = round(ms_, 4)
+        stages[st_name] = e
+    dom = max(per_stage, key=per_stage.get)
+    roofline = dict(stages[dom])
+    roofline["kernel"] = dom
+    tr = TRAFFIC.get((dom, wl.name, args.prec))
+    roofline["traffic"] = tr
+    if dom == "ring_fft_square":
+        roofline["algorithmic_bytes"] = fft_bytes(wl.lmax, wl.ntheta, wl.nr, real_bytes)
+    roofline["stage_ms"] = {k: round(v, 4) for k, v in per_stage.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "bf16x2": "bf16x2-split/f32", "bf16x3": "bf16x3-split/f32"}[args.prec],
-        "data": "synthetic", "config": config_of(wl, args.prec), "roofline": roofline,
+        "data": "synthetic", "config": config_of(wl, args.prec), "roofline": roofline, "stages": stages,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 2 * sh.nalm * 16, "steps": e2e_steps,
                 "note": "fnl_generate_host: inputs are the (seed, realisation, f_NL) scalars; a^T and a^E "
@@ -386,6 +534,10 @@ def main():
         "tiles": {"synthesis": tiles[0], "analysis": tiles[1]},
         "clocks": clk,
     }
+    if batch is not None:
+        line["batch"] = batch
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if fp64 is not None:
         line["fp64"] = fp64
         line["speedup_vs_fp64"] = value / fp64["value"]
