@@ -1,0 +1,59 @@
+"""Run a few realisations of one configuration through the C ABI and print the stage times.
+
+For profilers and quick timing of a configuration that is not one of the named workloads:
+
+  python -m paper_0909_0009_gb300.run_case --lmax 512 --nr 128 --ntheta 769 --nphi 3200 \
+      --prec bf16x2 --tiles 112,128 --reps 3
+
+Filters are seeded lower-triangular matrices of the covariance's amplitude (the cost of the
+path does not depend on their values); noise is the Philox draw of (seed 1, realisation i).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--lmax", type=int, required=True)
+    ap.add_argument("--nr", type=int, required=True)
+    ap.add_argument("--ntheta", type=int, required=True)
+    ap.add_argument("--nphi", type=int, required=True)
+    ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16x2", "bf16x3"])
+    ap.add_argument("--tiles", default="", help="'synthesis,analysis' tile widths of the tensor-core forms")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--fnl", type=float, default=20.0)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import workloads as W
+    from paper_0909_0009_gb300 import fnl as F
+
+    F.load_library()
+    r, w = W.radial_grid(args.nr)
+    aT, aE = W.transfer_kernels(args.lmax, r)
+    K = W.random_lower_filters(args.lmax, args.nr, seed=1, scale=8e-5)
+    sh = F.Shells(args.lmax, args.nr, args.ntheta, args.nphi, r, w, aT, aE, K=K, prec=args.prec)
+    if args.tiles:
+        sh.set_tiles(*(int(x) for x in args.tiles.split(",")))
+    sh.profile(max(args.reps, 1))
+    for i in range(args.reps):
+        sh.generate(1, i, args.fnl)
+    torch.cuda.synchronize()
+    sh.device_status()
+    ms, calls = sh.stage_ms()
+    per = {k: round(v / max(calls, 1), 4) for k, v in ms.items()}
+    print(f"l_max={args.lmax} N_r={args.nr} grid {args.ntheta}x{args.nphi} {args.prec}: "
+          f"{sh.device_bytes / 1e9:.2f} GB on the device; ms per realisation {per}")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
