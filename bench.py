@@ -317,6 +317,32 @@ def measure_adjoint(F, device: int, reps: int = 3) -> dict:
     return res
 
 
+# ---------------------------------------------------------------------------------------
+# replicas over realisations (one process per GPU): the only cross-rank logic of the path
+# ---------------------------------------------------------------------------------------
+
+def realisation_of(rank: int, steps: int, i: int) -> int:
+    """Realisation index of step i on `rank`: ranks draw disjoint blocks of `steps`
+    realisations of one seed, so N ranks generate N x steps distinct maps with no data-path
+    exchange (the noise is a function of (seed, realisation) only)."""
+    return rank * steps + i
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The job's time: the maximum of the ranks' times (a MAX all-reduce; identity at N = 1)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, seconds: float) -> float:
+    """Whole-job realisations per second: every rank's realisations over the slowest rank's time."""
+    return world * steps / seconds
+
+
 def config_of(wl: W.Workload, prec: str) -> dict:
     return {"workload": wl.name, "lmax": wl.lmax, "nr": wl.nr, "ntheta": wl.ntheta, "nphi": wl.nphi,
             "fnl": wl.fnl[-1], "precision": prec,
@@ -399,18 +425,15 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        sh.generate(1, rank * args.steps + i, fnl, out=out)
+        sh.generate(1, realisation_of(rank, args.steps, i), fnl, out=out)
     e1.record(stream)
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     stage_sum, calls = sh.stage_ms()
     sh.profile(0)
-    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
+    value = job_throughput(world, args.steps, ms_max / 1e3)
 
     # ---- end to end: the same step through the host-output entry point (pinned buffers)
     h_aT = torch.empty(sh.nalm, dtype=torch.complex128, pin_memory=True).numpy()
@@ -419,12 +442,9 @@ def main():
     barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        sh.generate_host(1, rank * args.steps + i, fnl, h_aT, h_aE)
+        sh.generate_host(1, realisation_of(rank, args.steps, i), fnl, h_aT, h_aE)
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_steps / float(t_e2e.item())
+    e2e_value = job_throughput(world, e2e_steps, max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{local}"))
 
     # ---- the FP64 GPU path on the same filters and noise: throughput and the error of the
     # timed form against it (the metric's "mixed vs FP64")
@@ -444,13 +464,11 @@ def main():
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for i in range(args.fp64_steps):
-            d64.generate(1, rank * args.fp64_steps + i, fnl, out=out64)
+            d64.generate(1, realisation_of(rank, args.fp64_steps, i), fnl, out=out64)
         f1.record(stream)
         barrier()
-        t64 = torch.tensor([f0.elapsed_time(f1)], dtype=torch.float64, device=f"cuda:{local}")
-        if world > 1:
-            dist.all_reduce(t64, op=dist.ReduceOp.MAX)
-        fp64 = {"value": world * args.fp64_steps / (float(t64.item()) / 1e3), "unit": UNIT,
+        t64 = max_over_ranks(f0.elapsed_time(f1), dist, f"cuda:{local}")
+        fp64 = {"value": job_throughput(world, args.fp64_steps, t64 / 1e3), "unit": UNIT,
                 "steps": args.fp64_steps, "rel_err": rel, "rel_err_bound": 1e-5,
                 "seed": "seed 1, realisation 0, same filters and Philox noise"}
         d64.close()
