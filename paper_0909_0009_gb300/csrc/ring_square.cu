@@ -8,7 +8,9 @@
 // and writes S = G_N + G_S and D = G_N - G_S (G_N,m = (W_m + conj W_{N-m}) / 2,
 // G_S,m = (W_m - conj W_{N-m}) / (2 i)), scaled by (2 pi / N) times the GL weight, as BF16 terms.
 //
-// Factorisation N = N1 * P * Q (N1 = 25 = 5 x 5; P, Q in {4, 8, 16}).  With
+// Factorisation N = N1 * P * Q (N1 = 25 = 5 x 5; (P, Q) = (16, 8) for 3200, (25, 5) for 3125 =
+// 5^5, (8, 8) for 1600, (8, 4) for 800); a shell's group is P Q threads rounded up to whole
+// warps (the extra threads sit out phase 2).  With
 // k = k1 + N1 (a + P b) and n = (c + Q d) + P Q n1 the inverse DFT runs as
 //   phase 1a  DFT_Q over b              (thread per (k1, a))
 //   phase 1b  x w_PQ^{a c}, DFT_P over a (thread per (k1, c))
@@ -251,8 +253,9 @@ __device__ __forceinline__ void store_pair_terms(__nv_bfloat16* p, int64_t strid
 }
 
 template <int N1, int P, int Q, int PAD, int G>
-__global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
-  constexpr int T = P * Q;           // threads of one shell group
+__global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_square(const SqArgs a) {
+  constexpr int T = P * Q;             // tasks of phase 2 (one (c, d) each)
+  constexpr int TG = (T + 31) / 32 * 32;  // threads of one shell group (whole warps)
   constexpr int N = N1 * P * Q;
   constexpr int S = N1 * P + PAD;    // stride of the b|c index
   constexpr int NB = N1 * P + S * (Q - 1);  // buffer length per shell (complex)
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
 
   const int groups = a.nr / G;
   const int items = groups * a.npairs;
-  const int g = threadIdx.x / T, u = threadIdx.x % T;
+  const int g = threadIdx.x / TG, u = threadIdx.x % TG;
   float2* B = buf + (size_t)g * NB;
   const int nrows = 2 * L + 1;  // problem (m = L, p = 1) is empty
 
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
 
     // phase 1a: DFT_Q over b (inverse), entries in l_max < k < N - l_max are zero
 #pragma unroll 1
-    for (int t = u; t < N1 * P; t += T) {
+    for (int t = u; t < N1 * P; t += TG) {
       const int base = t;  // k1 + N1 a
       float2 v[Q];
 #pragma unroll
@@ -320,10 +323,10 @@ __global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
 #pragma unroll
       for (int c = 0; c < Q; ++c) B[base + S * c] = v[c];
     }
-    group_sync<T>(g);
+    group_sync<TG>(g);
     // phase 1b: twiddle w_PQ^(a c), DFT_P over a (inverse)
 #pragma unroll 1
-    for (int t = u; t < N1 * Q; t += T) {
+    for (int t = u; t < N1 * Q; t += TG) {
       const int c = t % Q, k1 = t / Q;
       const int base = k1 + S * c;
       float2 v[P];
@@ -336,10 +339,10 @@ __global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
 #pragma unroll
       for (int d = 0; d < P; ++d) B[base + N1 * d] = v[d];
     }
-    group_sync<T>(g);
+    group_sync<TG>(g);
     // phase 2: twiddle w_N^(k1 n2), DFT_N1 (inverse) -> ring values, square, DFT_N1 (forward),
     // twiddle w_N^(-k1 n2)
-    {
+    if (u < T) {
       const int d = u % P, c = u / P;
       const int base = N1 * d + S * c;
       const float mu = (float)a.mu[s0 + g];
@@ -357,10 +360,10 @@ __global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) B[base + k1] = k1 ? cmulc(v[k1], w[k1 * T]) : v[k1];
     }
-    group_sync<T>(g);
+    group_sync<TG>(g);
     // phase 3a: DFT_P over d (forward), twiddle w_PQ^(-a c)
 #pragma unroll 1
-    for (int t = u; t < N1 * Q; t += T) {
+    for (int t = u; t < N1 * Q; t += TG) {
       const int c = t % Q, k1 = t / Q;
       const int base = k1 + S * c;
       float2 v[P];
@@ -370,11 +373,11 @@ __global__ void __launch_bounds__(G * P * Q, 1) k_ring_square(const SqArgs a) {
 #pragma unroll
       for (int aa = 0; aa < P; ++aa) B[base + N1 * aa] = aa ? cmulc(v[aa], tw1[aa * Q + c]) : v[aa];
     }
-    group_sync<T>(g);
+    group_sync<TG>(g);
     // phase 3b: DFT_Q over c (forward); W_k at k + PAD (k / (N1 P)), kept for k <= l_max and
     // k >= N - l_max
 #pragma unroll 1
-    for (int t = u; t < N1 * P; t += T) {
+    for (int t = u; t < N1 * P; t += TG) {
       const int base = t;
       float2 v[Q];
 #pragma unroll
@@ -423,21 +426,21 @@ struct SqConfig {
 };
 
 // Sizes with a specialised kernel: N = 25 P Q.
-constexpr SqConfig kSqConfigs[] = {{3200, 25, 16, 8, 4}, {1600, 25, 8, 8, 8}, {800, 25, 8, 4, 8}};
+constexpr SqConfig kSqConfigs[] = {{3200, 25, 16, 8, 4}, {3125, 25, 25, 5, 4}, {1600, 25, 8, 8, 8}, {800, 25, 8, 4, 8}};
 
 template <int N1, int P, int Q, int PAD, int G>
 void launch_sq(const SqArgs& a, int sms, cudaStream_t st) {
-  constexpr int T = P * Q, N = N1 * P * Q, S = N1 * P + PAD, NB = N1 * P + S * (Q - 1);
+  constexpr int T = P * Q, TG = (T + 31) / 32 * 32, N = N1 * P * Q, S = N1 * P + PAD, NB = N1 * P + S * (Q - 1);
   const size_t smem = sizeof(float2) * ((size_t)G * NB + (size_t)(2 * a.L + 1) * G + (size_t)N1 * T + T);
   if (smem > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "ring square staging exceeds shared memory");
   (void)N;
   auto kern = k_ring_square<N1, P, Q, PAD, G>;
   FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * T, smem));
+  FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * TG, smem));
   const int items = (a.nr / G) * a.npairs;
   const int grid = std::max(1, std::min(items, sms * std::max(per_sm, 1)));
-  kern<<<grid, G * T, smem, st>>>(a);
+  kern<<<grid, G * TG, smem, st>>>(a);
   FNL_CUDA(cudaGetLastError());
 }
 
@@ -493,6 +496,10 @@ bool launch_ring_square(const fnl_shells* sh, cudaStream_t st) {
     case 3200:
       if (sh->nr % 4 || 2 * sh->lmax + 2 > 3200) return false;
       launch_sq<25, 16, 8, 2, 4>(a, sh->sms, st);
+      return true;
+    case 3125:
+      if (sh->nr % 4 || 2 * sh->lmax + 2 > 3125) return false;
+      launch_sq<25, 25, 5, 2, 4>(a, sh->sms, st);
       return true;
     case 1600:
       if (sh->nr % 8 || 2 * sh->lmax + 2 > 1600) return false;
