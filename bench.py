@@ -279,7 +279,8 @@ def measure_batch(F, prec: str, device: int, reps: int = 3) -> dict:
     d = {"workload": "uneven64: l_max in {128,256,512,1024}, N_r in {32,64,96,128}, 64 realisations",
          "value": len(insts) / (t_graph / 1e3), "unit": UNIT, "ms_per_graph_launch": t_graph,
          "single_calls_ms": t_single, "speedup_vs_single_calls": t_single / t_graph,
-         "graph_launches_per_batch": 1, "streams": len(set(b.lanes())), "distinct_configurations": len(objs),
+         "graph_launches_per_batch": 1, "multi_instance": b.multi, "tiles": list(b.tiles()),
+         "distinct_configurations": len(objs),
          "nphi": {str(l): W.grid_for_lmax(l)[1] for l in lm}}
     b.close()
     for s_ in objs.values():

@@ -186,17 +186,30 @@ fnl_status fnl_device_status(const fnl_shells* sh);
 typedef struct fnl_batch fnl_batch; /* opaque: streams, events and the captured graph */
 
 /* A batch of n instances; instance i runs the path of shells[i] (objects of any l_max, N_r,
- * grid and precision, all on one device; one object may appear several times).  Instances
- * that share an object share its scratch and run in batch order on one stream; the
- * distinct objects are dealt, largest first (work ~ (l_max + 1)^3 N_r), to up to `nstreams`
- * streams (0: 4).  The batch keeps the pointers, not the objects: they must outlive it.
- * Allocates host memory, CUDA streams and events; no device memory. */
+ * grid and precision, all on one device; one object may appear several times).  Every
+ * instance gets scratch of its own: a repeated object of the tensor-core forms is given
+ * scratch clones that share its tables (device memory the batch allocates and frees).
+ *  - Multi-instance mode, when every instance is in one tensor-core form, has a ring length
+ *    with a specialised ring kernel (800, 1600, 3125, 3200; N_r a multiple of its shell
+ *    group) and n <= 64: each stage of the path is one launch over all instances (the ring
+ *    stage one per ring length present).  The tile shape, common to all instances, is picked
+ *    here by timing whole batches, and set on the shells objects (synchronous).
+ *  - Stream mode otherwise: instances are dealt, largest first (work ~ (l_max + 1)^3 N_r), to
+ *    up to `nstreams` streams (0: 4); repeated objects of the FP64/FP32 forms share their
+ *    scratch and stay on one stream.
+ * The batch keeps the pointers: the objects must outlive it.  Allocates host memory, CUDA
+ * streams and events, and device memory for clones and the multi-instance arguments. */
 fnl_status fnl_batch_create(fnl_shells* const* shells, int n, int nstreams, fnl_batch** out);
+
+/* Tile widths of the multi-instance launches (synthesis ring pairs, analysis degrees), or 0
+ * for a batch in stream mode. */
+fnl_status fnl_batch_tiles(const fnl_batch* b, int* nsyn, int* nana);
 
 /* Synchronise the batch's streams and free it (NULL is ignored). */
 void fnl_batch_destroy(fnl_batch* b);
 
-/* Number of instances, of streams, and (lanes: host [n] or NULL) the stream of each instance. */
+/* Number of instances, of streams (0 in multi-instance mode), and (lanes: host [n] or NULL)
+ * the stream of each instance. */
 fnl_status fnl_batch_info(const fnl_batch* b, int* n, int* nstreams, int* lanes);
 
 /* Steps (i)-(v) of every instance: instance i draws its Philox noise from (seeds[i],
@@ -205,7 +218,7 @@ fnl_status fnl_batch_info(const fnl_batch* b, int* n, int* nstreams, int* lanes)
  * The launches of all instances are captured into one CUDA graph (the first call
  * instantiates it, later calls update it in place) and the graph is launched on `stream`:
  * asynchronous, one graph launch per call.  Each instance's result equals that of
- * fnl_generate with the same arguments.  The call itself begins a stream capture, so it
+ * fnl_generate with the same arguments on its shells object (bit for bit).  The call itself begins a stream capture, so it
  * cannot be made while `stream`'s thread is capturing.  Calls on one batch, and calls on
  * its shells objects, must not overlap on the GPU. */
 fnl_status fnl_generate_batch(fnl_batch* b, const uint64_t* seeds, const uint64_t* realisations,

@@ -1,34 +1,91 @@
-// Batching form: many realisations of uneven l_max and N_r launched as one CUDA graph, and
-// the autotuner that picks the tensor-core tile shapes of each configuration.
+// Batching form: many realisations of uneven l_max and N_r in one captured CUDA graph, and
+// the autotuners that pick the tensor-core tile shapes.
 //
 // A batch holds n instances, each a (shells object, seed, realisation, f_NL) of steps
-// (i)-(v) (Sect. 2).  Instances that share a shells object share its scratch and run in
-// batch order on one stream; the distinct objects are spread over up to `nstreams`
-// streams, largest first (work ~ (l_max + 1)^3 N_r), so that small configurations run
-// beside large ones.  Every call captures the launches of all instances (fork and join
-// through events) into a graph; the first call instantiates it, later calls update the
-// executable graph in place (only kernel arguments change) and launch it on the caller's
-// stream, so a batch of 64 realisations costs one graph launch on the host.
+// (i)-(v) (Sect. 2).  Every instance gets scratch of its own: the first instance of a
+// shells object uses the object's, later ones use scratch clones that share its tables.
+//
+// Multi-instance mode (every instance in a tensor-core form with a specialised ring kernel,
+// at most kTcMaxInst of them): each stage is ONE launch over all instances --
+//   k_filter_multi + k_psum_multi   step (i): blocks are (instance, degree), largest first
+//   k_tc_gemm<true>, synthesis      step (ii) Legendre: one persistent tile list over all
+//                                   instances (instance tensor maps in constant memory)
+//   k_ring_square<.., true>         steps (ii)-(iv) ring DFTs and square, one launch per ring
+//                                   length present (the kernel is specialised per length)
+//   k_tc_gemm<true>, analysis       steps (iv), (v)
+//   k_combine_multi                 Eq. 3
+// so a batch of 64 uneven realisations is 6 + (ring lengths) launches, captured once into a
+// graph and replayed with new keys and outputs.  The tile shape, the same for every instance
+// of a launch, is picked by timing whole batches (fnl_batch_create).
+//
+// Stream mode (any other batch: SIMT forms, ring lengths without a specialised kernel):
+// instances are dealt, largest first (work ~ (l_max + 1)^3 N_r), to up to `nstreams`
+// streams; instances that share scratch (repeated SIMT objects) stay on one stream.
+#include <cuda_runtime.h>
+
 #include <algorithm>
+#include <map>
 #include <numeric>
 #include <vector>
 
 #include "fnl_internal.cuh"
 
+using fnl::CombineInst;
+using fnl::FilterInst;
+using fnl::TcArgs;
+using fnl::TcInst;
+using fnl::TcTile;
+
 struct fnl_batch {
   int device = 0;
   int n = 0;
-  std::vector<fnl_shells*> sh;           // per instance
-  std::vector<int> lane;                 // per instance: stream index
-  std::vector<std::vector<int>> order;   // per stream: instances in launch order
-  std::vector<cudaStream_t> streams;     // [nstreams]; streams[0] also begins the capture
-  std::vector<cudaEvent_t> joins;        // [nstreams]
+  std::vector<fnl_shells*> sh;      // per instance: the caller's object
+  std::vector<fnl_shells*> run;     // per instance: the object whose scratch it uses
+  std::vector<fnl_shells*> clones;  // owned scratch clones
+  bool multi = false;
+  // stream mode
+  std::vector<int> lane;
+  std::vector<std::vector<int>> order;
+  std::vector<cudaStream_t> streams;  // streams[0] also begins the capture
+  std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  // multi-instance mode
+  int syn_w = 0, ana_w = 0;           // tile widths of both GEMM launches
+  std::vector<int> versions;          // tile versions of the owners when the arrays were built
+  std::vector<void*> dev;             // device arrays (owned)
+  void* pinned = nullptr;             // host tensor maps (owned, pinned)
+  FilterInst* d_finst = nullptr;
+  int2* d_blocks = nullptr;
+  int nblocks = 0, max_nr = 0;
+  TcArgs tsyn{}, tana{};
+  CUtensorMap* h_maps_syn = nullptr;
+  CUtensorMap* h_maps_ana = nullptr;
+  struct Ring {
+    const fnl_shells* proto;
+    void* d_args;
+    int* d_item0;
+    int ninst, maxL, items;
+  };
+  std::vector<Ring> rings;
+  CombineInst* d_cinst = nullptr;
+  int64_t max_nalm = 0;
   cudaGraphExec_t exec = nullptr;
 };
 
 namespace fnl {
 namespace {
+
+double work_of(const fnl_shells* s) { return (double)(s->lmax + 1) * (s->lmax + 1) * (s->lmax + 1) * s->nr; }
+
+const fnl_shells* owner_of(const fnl_shells* s) { return s->owner ? s->owner : s; }
+
+void free_multi_arrays(fnl_batch* b) {
+  for (void* p : b->dev) cudaFree(p);
+  b->dev.clear();
+  if (b->pinned) cudaFreeHost(b->pinned);
+  b->pinned = nullptr;
+  b->rings.clear();
+}
 
 void free_batch(fnl_batch* b) {
   if (!b) return;
@@ -38,10 +95,239 @@ void free_batch(fnl_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   for (cudaStream_t s : b->streams)
     if (s) cudaStreamDestroy(s);
+  free_multi_arrays(b);
+  for (fnl_shells* c : b->clones) destroy_clone(c);
   delete b;
 }
 
-double work_of(const fnl_shells* s) { return (double)(s->lmax + 1) * (s->lmax + 1) * (s->lmax + 1) * s->nr; }
+template <typename T>
+T* upload_vec(fnl_batch* b, const std::vector<T>& v) {
+  void* p = nullptr;
+  FNL_CUDA(cudaMalloc(&p, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  b->dev.push_back(p);
+  FNL_CUDA(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return (T*)p;
+}
+
+// Tile shape `w` on every owner (exact widths), clones refreshed, launch arrays rebuilt.
+void build_multi(fnl_batch* b, int syn_w, int ana_w) {
+  FNL_CUDA(cudaDeviceSynchronize());
+  free_multi_arrays(b);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  std::vector<const fnl_shells*> owners;
+  for (fnl_shells* r : b->run)
+    if (std::find(owners.begin(), owners.end(), owner_of(r)) == owners.end()) owners.push_back(owner_of(r));
+  for (const fnl_shells* o : owners) configure_tc(const_cast<fnl_shells*>(o), syn_w, ana_w, true);
+  for (fnl_shells* c : b->clones) refresh_clone(c, c->owner);
+  b->syn_w = syn_w;
+  b->ana_w = ana_w;
+  b->versions.clear();
+  for (fnl_shells* r : b->run) b->versions.push_back(owner_of(r)->tiles_version);
+  const int n = b->n;
+
+  // step (i): instances and (instance, degree) blocks, largest degree first
+  std::vector<FilterInst> fi(n);
+  std::vector<int2> blocks;
+  std::vector<CombineInst> ci(n);
+  b->max_nr = 0;
+  b->max_nalm = 0;
+  for (int i = 0; i < n; ++i) {
+    const fnl_shells* s = b->run[i];
+    const int64_t n2 = 2 * s->nalm;
+    fi[i] = FilterInst{s->lmax, s->nr, s->Cpad, s->nterms, s->phiT_stride, (const float*)s->d_Kf, s->d_vT, s->d_vE,
+                       s->d_row32, (__nv_bfloat16*)s->d_phiT, s->d_aL, s->d_aL + n2, s->d_psum_part, s->d_psum};
+    ci[i] = CombineInst{s->nalm, s->Cpad / 128, s->nr, (const float4*)s->d_part, s->d_psum, s->d_mu, s->d_qT,
+                        s->d_qE, (const double2*)s->d_aL, (const double2*)(s->d_aL + n2), (double2*)s->d_aNL,
+                        (double2*)(s->d_aNL + n2)};
+    for (int l = 0; l <= s->lmax; ++l) blocks.push_back(make_int2(i, l));
+    b->max_nr = std::max(b->max_nr, s->nr);
+    b->max_nalm = std::max(b->max_nalm, s->nalm);
+  }
+  std::stable_sort(blocks.begin(), blocks.end(), [](const int2& a, const int2& c) { return a.y > c.y; });
+  b->d_finst = upload_vec(b, fi);
+  b->d_blocks = upload_vec(b, blocks);
+  b->nblocks = (int)blocks.size();
+  b->d_cinst = upload_vec(b, ci);
+
+  // Legendre GEMMs: one tile list over all instances, the tiles of one (instance, problem)
+  // adjacent, groups largest first; instance maps for the constant table
+  FNL_CUDA(cudaMallocHost(&b->pinned, sizeof(CUtensorMap) * 12 * (size_t)n));
+  b->h_maps_syn = (CUtensorMap*)b->pinned;
+  b->h_maps_ana = b->h_maps_syn + 6 * (size_t)n;
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<TcInst> insts(n);
+    std::vector<std::pair<int64_t, std::vector<TcTile>>> groups;
+    for (int i = 0; i < n; ++i) {
+      const fnl_shells* s = b->run[i];
+      insts[i] = s->tci[dir];
+      CUtensorMap* maps = (dir ? b->h_maps_ana : b->h_maps_syn) + 6 * (size_t)i;
+      for (int t = 0; t < 3; ++t) {
+        maps[t] = s->tci[dir].tmA[t];
+        maps[3 + t] = s->tci[dir].tmB[t];
+      }
+      const std::vector<TcTile>& tl = dir ? s->tiles_ana_h : s->tiles_syn_h;
+      for (size_t k = 0; k < tl.size(); ++k) {
+        if (k == 0 || tl[k].mp != tl[k - 1].mp) groups.push_back({0, {}});
+        TcTile t = tl[k];
+        t.inst = i;
+        groups.back().first += (int64_t)t.nkb * t.nsize;
+        groups.back().second.push_back(t);
+      }
+    }
+    std::stable_sort(groups.begin(), groups.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+    std::vector<TcTile> tiles;
+    for (const auto& g : groups) tiles.insert(tiles.end(), g.second.begin(), g.second.end());
+    TcArgs a = dir ? b->run[0]->tc_ana : b->run[0]->tc_syn;
+    a.one = TcInst{};
+    a.multi = 1;
+    a.insts = upload_vec(b, insts);
+    a.tiles = upload_vec(b, tiles);
+    a.ntiles = (int)tiles.size();
+    a.alm_out = nullptr;
+    a.err = b->run[0]->d_err;
+    (dir ? b->tana : b->tsyn) = a;
+  }
+
+  // ring kernels: one launch per ring length
+  std::map<int, std::vector<int>> by_n;
+  for (int i = 0; i < n; ++i) by_n[b->run[i]->nphi].push_back(i);
+  const size_t asz = ring_square_args_size();
+  for (const auto& kv : by_n) {
+    fnl_batch::Ring r{};
+    r.proto = b->run[kv.second[0]];
+    r.ninst = (int)kv.second.size();
+    std::vector<unsigned char> args(asz * r.ninst);
+    std::vector<int> item0(1, 0);
+    const int G = ring_square_group(r.proto);
+    for (int k = 0; k < r.ninst; ++k) {
+      const fnl_shells* s = b->run[kv.second[k]];
+      ring_square_args(s, args.data() + asz * k);
+      item0.push_back(item0.back() + (s->nr / G) * s->npairs);
+      r.maxL = std::max(r.maxL, s->lmax);
+    }
+    r.items = item0.back();
+    r.d_args = upload_vec(b, args);
+    r.d_item0 = upload_vec(b, item0);
+    b->rings.push_back(r);
+  }
+}
+
+// The launches of one batch call on `st` (no synchronisation; captured by the caller).
+void enqueue_multi(fnl_batch* b, const uint64_t* seeds, const uint64_t* reals, const double* fnl, double* const* aT,
+                   double* const* aE, cudaStream_t st) {
+  MultiKeys keys{};
+  MultiOut out{};
+  for (int i = 0; i < b->n; ++i) {
+    keys.seed[i] = seeds[i];
+    keys.real[i] = reals[i];
+    out.fnl[i] = fnl[i];
+    out.aT[i] = (double2*)aT[i];
+    out.aE[i] = (double2*)aE[i];
+  }
+  launch_filter_multi(b->d_finst, b->d_blocks, b->nblocks, keys, b->max_nr, b->n, st);
+  upload_tc_maps(b->h_maps_syn, b->n, st);
+  launch_tc_gemm(b->tsyn, b->run[0]->sms, st);
+  for (const fnl_batch::Ring& r : b->rings)
+    launch_ring_square_multi(r.proto, r.d_args, r.d_item0, r.ninst, r.maxL, r.items, st);
+  upload_tc_maps(b->h_maps_ana, b->n, st);
+  launch_tc_gemm(b->tana, b->run[0]->sms, st);
+  launch_combine_multi(b->d_cinst, b->max_nalm, b->n, out, st);
+}
+
+void enqueue_streams(fnl_batch* b, const uint64_t* seeds, const uint64_t* reals, const double* fnl, double* const* aT,
+                     double* const* aE, cudaStream_t cap) {
+  FNL_CUDA(cudaEventRecord(b->fork, cap));
+  for (size_t l = 1; l < b->streams.size(); ++l) FNL_CUDA(cudaStreamWaitEvent(b->streams[l], b->fork, 0));
+  for (size_t l = 0; l < b->streams.size(); ++l) {
+    for (int i : b->order[l])
+      run_generate(b->run[i], seeds[i], reals[i], fnl[i], nullptr, aT[i], aE[i], nullptr, nullptr, nullptr, nullptr,
+                   b->streams[l], false);
+    if (l) {
+      FNL_CUDA(cudaEventRecord(b->joins[l], b->streams[l]));
+      FNL_CUDA(cudaStreamWaitEvent(cap, b->joins[l], 0));
+    }
+  }
+}
+
+// Capture one call into a graph, update or instantiate the batch's executable graph and
+// launch it on `stream`.
+void run_batch(fnl_batch* b, const uint64_t* seeds, const uint64_t* reals, const double* fnl, double* const* aT,
+               double* const* aE, cudaStream_t stream) {
+  cudaStream_t cap = b->streams[0];
+  cudaGraph_t graph = nullptr;
+  FNL_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  try {
+    if (b->multi) enqueue_multi(b, seeds, reals, fnl, aT, aE, cap);
+    else enqueue_streams(b, seeds, reals, fnl, aT, aE, cap);
+  } catch (...) {
+    cudaStreamEndCapture(cap, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    throw;
+  }
+  FNL_CUDA(cudaStreamEndCapture(cap, &graph));
+  bool ok = false;
+  if (b->exec) {
+    cudaGraphExecUpdateResultInfo info;
+    ok = cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (!ok) e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  FNL_CUDA(e);
+  FNL_CUDA(cudaGraphLaunch(b->exec, stream));
+}
+
+// Multi-instance tile shapes tried by fnl_batch_create: whole batches are timed (one
+// warm-up, two timed, keys 0 and outputs in the instances' scratch) for each.
+void autotune_multi(fnl_batch* b) {
+  const int cand[][2] = {{112, 128}, {128, 128}, {96, 128}, {112, 256}};
+  std::vector<uint64_t> z(b->n, 0);
+  std::vector<double> f(b->n, 1.0);
+  std::vector<double*> oT(b->n), oE(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    oT[i] = b->run[i]->d_aOut;
+    oE[i] = b->run[i]->d_aOut + 2 * b->run[i]->nalm;
+  }
+  cudaEvent_t e0, e1;
+  FNL_CUDA(cudaEventCreate(&e0));
+  FNL_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bs = cand[0][0], ba = cand[0][1];
+  cudaStream_t st = b->streams[0];
+  try {
+    for (const auto& c : cand) {
+      build_multi(b, c[0], c[1]);
+      run_batch(b, z.data(), z.data(), f.data(), oT.data(), oE.data(), st);
+      FNL_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < 2; ++r) run_batch(b, z.data(), z.data(), f.data(), oT.data(), oE.data(), st);
+      FNL_CUDA(cudaEventRecord(e1, st));
+      FNL_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      FNL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bs = c[0];
+        ba = c[1];
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  build_multi(b, bs, ba);
+}
 
 }  // namespace
 }  // namespace fnl
@@ -60,43 +346,69 @@ fnl_status fnl_batch_create(fnl_shells* const* shells, int n, int nstreams, fnl_
     for (int i = 0; i < n; ++i) {
       check_shells(shells[i]);
       FNL_REQUIRE(shells[i]->device == shells[0]->device, "every instance must live on one device");
+      FNL_REQUIRE(!shells[i]->owner, "a batch takes shells objects made by fnl_make_shells");
     }
+    DeviceScope scope(shells[0]->device);
     b = new fnl_batch;
     b->device = shells[0]->device;
     b->n = n;
     b->sh.assign(shells, shells + n);
-    // distinct objects, largest first, dealt to the least-loaded stream
-    std::vector<fnl_shells*> distinct;
-    for (fnl_shells* s : b->sh)
-      if (std::find(distinct.begin(), distinct.end(), s) == distinct.end()) distinct.push_back(s);
-    std::vector<double> load_of(distinct.size(), 0.0);
-    for (int i = 0; i < n; ++i)
-      load_of[std::find(distinct.begin(), distinct.end(), b->sh[i]) - distinct.begin()] += work_of(b->sh[i]);
-    std::vector<int> idx(distinct.size());
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return load_of[a] > load_of[c]; });
-    const int ns = std::max(1, std::min<int>(nstreams ? nstreams : 4, (int)distinct.size()));
-    std::vector<double> lane_load(ns, 0.0);
-    std::vector<int> lane_of_obj(distinct.size(), 0);
-    for (int k : idx) {
-      const int l = (int)(std::min_element(lane_load.begin(), lane_load.end()) - lane_load.begin());
-      lane_of_obj[k] = l;
-      lane_load[l] += load_of[k];
-    }
-    b->lane.resize(n);
-    b->order.assign(ns, {});
+    // scratch of each instance: the object's own for its first instance, clones after
+    b->run.resize(n);
+    std::vector<fnl_shells*> seen;
     for (int i = 0; i < n; ++i) {
-      b->lane[i] = lane_of_obj[std::find(distinct.begin(), distinct.end(), b->sh[i]) - distinct.begin()];
-      b->order[b->lane[i]].push_back(i);
+      fnl_shells* s = shells[i];
+      if (std::find(seen.begin(), seen.end(), s) == seen.end() || !s->nterms) {
+        seen.push_back(s);
+        b->run[i] = s;
+      } else {
+        b->clones.push_back(clone_scratch(s));
+        b->run[i] = b->clones.back();
+      }
     }
-    DeviceScope scope(b->device);
-    b->streams.assign(ns, nullptr);
-    b->joins.assign(ns, nullptr);
-    for (int l = 0; l < ns; ++l) {
-      FNL_CUDA(cudaStreamCreateWithFlags(&b->streams[l], cudaStreamNonBlocking));
-      FNL_CUDA(cudaEventCreateWithFlags(&b->joins[l], cudaEventDisableTiming));
-    }
+    b->multi = n <= kTcMaxInst;
+    for (int i = 0; i < n && b->multi; ++i)
+      b->multi = b->run[i]->nterms == b->run[0]->nterms && b->run[i]->tc_split == b->run[0]->tc_split &&
+                 ring_square_group(b->run[i]) > 0;
     FNL_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    if (b->multi) {
+      b->streams.assign(1, nullptr);
+      FNL_CUDA(cudaStreamCreateWithFlags(&b->streams[0], cudaStreamNonBlocking));
+      b->lane.assign(n, 0);
+      autotune_multi(b);
+    } else {
+      // instances dealt, largest first, to the least-loaded stream; instances that share
+      // scratch (one object) go together
+      std::vector<fnl_shells*> distinct;
+      for (fnl_shells* r : b->run)
+        if (std::find(distinct.begin(), distinct.end(), r) == distinct.end()) distinct.push_back(r);
+      std::vector<double> load_of(distinct.size(), 0.0);
+      for (int i = 0; i < n; ++i)
+        load_of[std::find(distinct.begin(), distinct.end(), b->run[i]) - distinct.begin()] += work_of(b->run[i]);
+      std::vector<int> idx(distinct.size());
+      std::iota(idx.begin(), idx.end(), 0);
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return load_of[a] > load_of[c]; });
+      const int ns = std::max(1, std::min<int>(nstreams ? nstreams : 4, (int)distinct.size()));
+      std::vector<double> lane_load(ns, 0.0);
+      std::vector<int> lane_of(distinct.size(), 0);
+      for (int k : idx) {
+        const int l = (int)(std::min_element(lane_load.begin(), lane_load.end()) - lane_load.begin());
+        lane_of[k] = l;
+        lane_load[l] += load_of[k];
+      }
+      b->lane.resize(n);
+      b->order.assign(ns, {});
+      for (int i = 0; i < n; ++i) {
+        b->lane[i] = lane_of[std::find(distinct.begin(), distinct.end(), b->run[i]) - distinct.begin()];
+        b->order[b->lane[i]].push_back(i);
+      }
+      b->streams.assign(ns, nullptr);
+      b->joins.assign(ns, nullptr);
+      for (int l = 0; l < ns; ++l) {
+        FNL_CUDA(cudaStreamCreateWithFlags(&b->streams[l], cudaStreamNonBlocking));
+        FNL_CUDA(cudaEventCreateWithFlags(&b->joins[l], cudaEventDisableTiming));
+      }
+    }
     *out = b;
   });
   if (st != FNL_OK && b) free_batch(b);
@@ -108,8 +420,7 @@ void fnl_batch_destroy(fnl_batch* b) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
-  for (cudaStream_t s : b->streams)
-    if (s) cudaStreamSynchronize(s);
+  cudaDeviceSynchronize();
   free_batch(b);
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -118,9 +429,17 @@ fnl_status fnl_batch_info(const fnl_batch* b, int* n, int* nstreams, int* lanes)
   return guard([&] {
     FNL_REQUIRE(b, "batch is NULL");
     if (n) *n = b->n;
-    if (nstreams) *nstreams = (int)b->streams.size();
+    if (nstreams) *nstreams = b->multi ? 0 : (int)b->streams.size();
     if (lanes)
       for (int i = 0; i < b->n; ++i) lanes[i] = b->lane[i];
+  });
+}
+
+fnl_status fnl_batch_tiles(const fnl_batch* b, int* nsyn, int* nana) {
+  return guard([&] {
+    FNL_REQUIRE(b, "batch is NULL");
+    if (nsyn) *nsyn = b->multi ? b->syn_w : 0;
+    if (nana) *nana = b->multi ? b->ana_w : 0;
   });
 }
 
@@ -134,49 +453,23 @@ fnl_status fnl_generate_batch(fnl_batch* b, const uint64_t* seeds, const uint64_
       check_dev_ptr(aT[i], "aT[i]", false);
       check_dev_ptr(aE[i], "aE[i]", false);
     }
-    cudaStream_t cap = b->streams[0];
-    cudaGraph_t graph = nullptr;
-    FNL_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    try {
-      FNL_CUDA(cudaEventRecord(b->fork, cap));
-      for (size_t l = 1; l < b->streams.size(); ++l) FNL_CUDA(cudaStreamWaitEvent(b->streams[l], b->fork, 0));
-      for (size_t l = 0; l < b->streams.size(); ++l) {
-        for (int i : b->order[l])
-          run_generate(b->sh[i], seeds[i], realisations[i], fnl[i], nullptr, aT[i], aE[i], nullptr, nullptr, nullptr,
-                       nullptr, b->streams[l], false);
-        if (l) {
-          FNL_CUDA(cudaEventRecord(b->joins[l], b->streams[l]));
-          FNL_CUDA(cudaStreamWaitEvent(cap, b->joins[l], 0));
-        }
-      }
-    } catch (...) {
-      cudaStreamEndCapture(cap, &graph);
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      throw;
+    if (b->multi) {
+      // an owner's tile shape changed since the launch arrays were built: rebuild them
+      bool stale = false;
+      for (int i = 0; i < b->n; ++i) stale |= owner_of(b->run[i])->tiles_version != b->versions[i];
+      if (stale) build_multi(b, b->syn_w, b->ana_w);
+    } else {
+      for (fnl_shells* c : b->clones)
+        if (c->tiles_version != c->owner->tiles_version) refresh_clone(c, c->owner);
     }
-    FNL_CUDA(cudaStreamEndCapture(cap, &graph));
-    bool ok = false;
-    if (b->exec) {
-      cudaGraphExecUpdateResultInfo info;
-      ok = cudaGraphExecUpdate(b->exec, graph, &info) == cudaSuccess;
-      if (!ok) {
-        cudaGetLastError();
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-      }
-    }
-    cudaError_t e = cudaSuccess;
-    if (!ok) e = cudaGraphInstantiate(&b->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    FNL_CUDA(e);
-    FNL_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    run_batch(b, seeds, realisations, fnl, aT, aE, (cudaStream_t)stream);
   });
 }
 
 fnl_status fnl_shells_autotune(fnl_shells* sh, void* stream, int* nsyn, int* nana) {
   return guard([&] {
     check_shells(sh);
+    FNL_REQUIRE(!sh->owner, "tile shapes are set on the objects fnl_make_shells made");
     DeviceScope scope(sh->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (sh->nterms) {
@@ -227,6 +520,7 @@ fnl_status fnl_shells_set_tiles(fnl_shells* sh, int syn_cap, int ana_cap) {
   return guard([&] {
     check_shells(sh);
     FNL_REQUIRE(sh->nterms, "tile shapes are fixed in the FNL_FP64 and FNL_FP32 forms");
+    FNL_REQUIRE(!sh->owner, "tile shapes are set on the objects fnl_make_shells made");
     DeviceScope scope(sh->device);
     FNL_CUDA(cudaDeviceSynchronize());
     configure_tc(sh, syn_cap, ana_cap);

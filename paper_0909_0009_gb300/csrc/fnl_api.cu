@@ -178,9 +178,32 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
     sh->d_tc_syn = dalloc<TcTile>(sh, (size_t)cap_syn);
     sh->d_tc_ana = dalloc<TcTile>(sh, (size_t)cap_ana);
   }
-  // tensor maps of the A operands (BF16, MN-major, 128B swizzle): boxes of 64 columns x 64 k x
-  // both 64-column halves of a 128-column tile, through a view whose last dimension steps over
-  // the halves (128 B apart).  The B maps depend on the tile width: configure_tc builds them.
+  sh->d_tci = dalloc<TcInst>(sh, 2);
+  build_tc_inst_a(sh);
+  for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
+    a->nterms = T;
+    a->split = sh->tc_split;
+    a->alm_out = nullptr;
+    a->err = sh->d_err;
+  }
+  sh->tc_syn.insts = sh->d_tci;
+  sh->tc_ana.insts = sh->d_tci + 1;
+  sh->tc_syn.mode = TC_SYNTH;
+  sh->tc_ana.mode = TC_ANA_QUAD;
+  configure_tc(sh, 256, 256);
+}
+
+}  // namespace
+
+// The per-configuration part of the tensor-core GEMMs' arguments that does not depend on
+// the tile shape: the A tensor maps (BF16, MN-major, 128B swizzle; boxes of 64 columns x 64 k
+// x both 64-column halves of a 128-column tile, through a view whose last dimension steps over
+// the halves, 128 B apart) and the scratch and table pointers.  Entry 0 is the synthesis,
+// entry 1 the analysis.
+void build_tc_inst_a(fnl_shells* sh) {
+  typedef unsigned short bf16_t;
+  const int L = sh->lmax, nr = sh->nr, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms, Cpad = sh->Cpad;
+  const int64_t rows32 = sh->row32[nmp];
   for (int t = 0; t < T; ++t) {
     const bf16_t* phi = (const bf16_t*)sh->d_phiT + (size_t)t * sh->phiT_stride;
     const bf16_t* gt = (const bf16_t*)sh->d_GT + (size_t)t * sh->gt_stride;
@@ -188,37 +211,60 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
       const uint64_t dims[3] = {64, (uint64_t)rows32, (uint64_t)Cpad / 64};
       const uint64_t str[2] = {(uint64_t)Cpad * 2, 128};
       const uint32_t box[3] = {64, (uint32_t)kTcStageK, 2};
-      sh->tc_syn.tmA[t] = make_tensor_map_bf16(phi, 3, dims, str, box, 128);
+      sh->tci[0].tmA[t] = make_tensor_map_bf16(phi, 3, dims, str, box, 128);
     }
     {
       // G is ring-pair-major, [jp][mp][Cpad]: box of 64 columns x 1 problem x 64 ring pairs x 2 halves
       const uint64_t dims[4] = {64, (uint64_t)nmp, (uint64_t)np, (uint64_t)Cpad / 64};
       const uint64_t str[3] = {(uint64_t)Cpad * 2, (uint64_t)nmp * Cpad * 2, 128};
       const uint32_t box[4] = {64, 1, (uint32_t)kTcStageK, 2};
-      sh->tc_ana.tmA[t] = make_tensor_map_bf16(gt, 4, dims, str, box, 128);
+      sh->tci[1].tmA[t] = make_tensor_map_bf16(gt, 4, dims, str, box, 128);
     }
   }
-  for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
-    a->nterms = T;
-    a->split = sh->tc_split;
-    a->L = L;
-    a->nr = nr;
-    a->npairs = np;
-    a->Cpad = Cpad;
-    a->nalm = sh->nalm;
-    a->F = (float*)sh->d_F;
-    a->part = (float4*)sh->d_part;
-    a->alm_out = nullptr;
-    a->qT = sh->d_q32;
-    a->qE = sh->d_q32 + (size_t)(L + 1) * nr;
-    a->err = sh->d_err;
+  for (TcInst& I : sh->tci) {
+    I.F = (float*)sh->d_F;
+    I.part = (float4*)sh->d_part;
+    I.qT = sh->d_q32;
+    I.qE = sh->d_q32 + (size_t)(L + 1) * nr;
+    I.L = L;
+    I.nr = nr;
+    I.npairs = np;
+    I.Cpad = Cpad;
+    I.nalm = sh->nalm;
   }
-  sh->tc_syn.mode = TC_SYNTH;
-  sh->tc_ana.mode = TC_ANA_QUAD;
-  configure_tc(sh, 256, 256);
 }
 
-}  // namespace
+// Tensor maps of the B operands (BF16, K-major, 64B swizzle): boxes of nmax rows x two 32-deep
+// slabs (64 k per stage); rows past the table are zero-filled.  Then the two entries go to
+// the device.
+void build_tc_inst_b(fnl_shells* sh) {
+  typedef unsigned short bf16_t;
+  const int L = sh->lmax, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms;
+  const int64_t nslab = sh->row32[nmp] / 32, rows16 = sh->rows_total;
+  for (int t = 0; t < T; ++t) {
+    const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
+    const bf16_t* lana = (const bf16_t*)sh->d_lana + (size_t)t * sh->lana_stride;
+    {
+      // Lambda_syn [slab][jp][32 k]
+      const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
+      const uint64_t str[2] = {64, (uint64_t)np * 64};
+      const uint32_t box[3] = {32, (uint32_t)sh->tc_syn.nmax, 2};
+      sh->tci[0].tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
+    }
+    {
+      // Lambda_ana [row16][npj]: 32 ring pairs x rows x blocks of 32 ring pairs (64 B apart;
+      // npj is a multiple of 32, so every block stays inside its row)
+      const uint64_t dims[3] = {32, (uint64_t)rows16, (uint64_t)sh->npj / 32};
+      const uint64_t str[2] = {(uint64_t)sh->npj * 2, 64};
+      const uint32_t box[3] = {32, (uint32_t)sh->tc_ana.nmax, 2};
+      sh->tci[1].tmB[t] = make_tensor_map_bf16(lana, 3, dims, str, box, 64);
+    }
+  }
+  FNL_CUDA(cudaMemcpy(sh->d_tci, sh->tci, sizeof(sh->tci), cudaMemcpyHostToDevice));
+  sh->tc_syn.one = sh->tci[0];
+  sh->tc_ana.one = sh->tci[1];
+  sh->tc_syn.multi = sh->tc_ana.multi = 0;
+}
 
 // Tile shapes of the two tensor-core GEMMs.  Synthesis tiles are `nsyn` ring pairs wide, the
 // width <= syn_cap that wastes the fewest ring pairs (each tile charged 16 columns of
@@ -228,13 +274,13 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
 // columns (at most 2) rotate over tiles, so 128-wide tiles double-buffer the epilogue and
 // 256-wide tiles issue half as many, wider MMAs.  The shape changes no result: every output
 // element sums its k blocks in the same order whatever the tiling.
-void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap) {
+void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap, bool exact) {
   FNL_REQUIRE(syn_cap >= kTcMinWidth && syn_cap <= 256 && syn_cap % 16 == 0 && ana_cap >= kTcMinWidth &&
                   ana_cap <= 256 && ana_cap % 16 == 0,
               "tile widths must be multiples of 16 in [64, 256]");
   const int L = sh->lmax, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms;
   int best = syn_cap, bestc = 1 << 30;
-  for (int n = syn_cap; n >= kTcMinWidth; n -= 16) {
+  for (int n = syn_cap; n >= kTcMinWidth && !exact; n -= 16) {
     const int tiles = (np + n - 1) / n, cost = tiles * (n + 16);
     if (cost < bestc) {
       bestc = cost;
@@ -280,6 +326,10 @@ void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap) {
   FNL_CUDA(cudaMemcpy(sh->d_tc_ana, ta.data(), sizeof(TcTile) * ta.size(), cudaMemcpyHostToDevice));
   int widest_ana = 16;
   for (const TcTile& t : ta) widest_ana = std::max(widest_ana, t.nsize);
+  if (exact) widest_ana = ana_cap;  // every configuration of a multi-instance launch: the same box
+  sh->tiles_syn_h = ts;
+  sh->tiles_ana_h = ta;
+  ++sh->tiles_version;
   for (TcArgs* a : {&sh->tc_syn, &sh->tc_ana}) {
     const bool syn = a == &sh->tc_syn;
     const int nm = syn ? sh->nsyn : widest_ana;
@@ -290,29 +340,65 @@ void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap) {
     a->tiles = syn ? sh->d_tc_syn : sh->d_tc_ana;
     a->ntiles = (int)(syn ? ts.size() : ta.size());
   }
-  // tensor maps of the B operands (BF16, K-major, 64B swizzle): boxes of nmax rows x two
-  // 32-deep slabs (64 k per stage); rows past the table are zero-filled
-  typedef unsigned short bf16_t;
-  const int64_t nslab = sh->row32[nmp] / 32, rows16 = sh->rows_total;
-  for (int t = 0; t < T; ++t) {
-    const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
-    const bf16_t* lana = (const bf16_t*)sh->d_lana + (size_t)t * sh->lana_stride;
-    {
-      // Lambda_syn [slab][jp][32 k]
-      const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
-      const uint64_t str[2] = {64, (uint64_t)np * 64};
-      const uint32_t box[3] = {32, (uint32_t)sh->tc_syn.nmax, 2};
-      sh->tc_syn.tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
-    }
-    {
-      // Lambda_ana [row16][npj]: 32 ring pairs x rows x blocks of 32 ring pairs (64 B apart;
-      // npj is a multiple of 32, so every block stays inside its row)
-      const uint64_t dims[3] = {32, (uint64_t)rows16, (uint64_t)sh->npj / 32};
-      const uint64_t str[2] = {(uint64_t)sh->npj * 2, 64};
-      const uint32_t box[3] = {32, (uint32_t)sh->tc_ana.nmax, 2};
-      sh->tc_ana.tmB[t] = make_tensor_map_bf16(lana, 3, dims, str, box, 64);
-    }
+  build_tc_inst_b(sh);
+}
+
+fnl_shells* clone_scratch(const fnl_shells* src) {
+  FNL_REQUIRE(src->nterms, "scratch clones are made for the tensor-core forms");
+  DeviceScope scope(src->device);
+  fnl_shells* c = new fnl_shells(*src);
+  c->allocations.clear();
+  c->device_bytes = 0;
+  c->ring.clear();
+  c->ring_slots = c->ring_head = c->ring_count = 0;
+  c->owner = src->owner ? src->owner : src;
+  try {
+    typedef unsigned short bf16_t;
+    const int L = c->lmax, nr = c->nr, np = c->npairs, nmp = 2 * (L + 1), T = c->nterms, Cpad = c->Cpad;
+    c->d_phiT = dalloc<bf16_t>(c, (size_t)T * c->phiT_stride);
+    c->d_GT = dalloc<bf16_t>(c, (size_t)T * c->gt_stride);
+    c->d_F = dalloc<float>(c, (size_t)nmp * np * Cpad);
+    c->d_part = dalloc<float>(c, 4 * (size_t)(Cpad / 128) * c->nalm);
+    c->d_err = dalloc<int>(c, 1);
+    c->d_psum = dalloc<double>(c, nr);
+    c->d_psum_part = dalloc<double>(c, (size_t)(L + 1) * 2 * nr);
+    c->d_aL = dalloc<double>(c, 4 * (size_t)c->nalm);
+    c->d_aNL = dalloc<double>(c, 4 * (size_t)c->nalm);
+    c->d_aOut = dalloc<double>(c, 4 * (size_t)c->nalm);
+    c->d_tci = dalloc<TcInst>(c, 2);
+    FNL_CUDA(cudaMemset(c->d_phiT, 0, sizeof(bf16_t) * (size_t)T * c->phiT_stride));
+    FNL_CUDA(cudaMemset(c->d_GT, 0, sizeof(bf16_t) * (size_t)T * c->gt_stride));
+    FNL_CUDA(cudaMemset(c->d_F, 0, sizeof(float) * (size_t)nmp * np * Cpad));
+    FNL_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    build_tc_inst_a(c);
+    refresh_clone(c, src);
+  } catch (...) {
+    free_shells(c);
+    throw;
   }
+  return c;
+}
+
+void refresh_clone(fnl_shells* c, const fnl_shells* src) {
+  for (int k = 0; k < 2; ++k)
+    for (int t = 0; t < 3; ++t) c->tci[k].tmB[t] = src->tci[k].tmB[t];
+  FNL_CUDA(cudaMemcpy(c->d_tci, c->tci, sizeof(c->tci), cudaMemcpyHostToDevice));
+  c->tc_syn = src->tc_syn;
+  c->tc_ana = src->tc_ana;
+  c->tc_syn.one = c->tci[0];
+  c->tc_ana.one = c->tci[1];
+  c->tc_syn.insts = c->d_tci;
+  c->tc_ana.insts = c->d_tci + 1;
+  c->tc_syn.err = c->tc_ana.err = c->d_err;
+  c->nsyn = src->nsyn;
+  c->nana = src->nana;
+  c->tiles_syn_h = src->tiles_syn_h;
+  c->tiles_ana_h = src->tiles_ana_h;
+  c->tiles_version = src->tiles_version;
+}
+
+void destroy_clone(fnl_shells* c) {
+  if (c) free_shells(c);
 }
 
 namespace {

@@ -10,6 +10,7 @@
 //   contractions per m: even (p = 0) and odd (p = 1) degrees over the northern rings.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -167,6 +168,11 @@ struct fnl_shells {
   fnl::TcTile* d_tc_syn = nullptr;
   fnl::TcTile* d_tc_ana = nullptr;
   fnl::TcArgs tc_syn{}, tc_ana{};
+  fnl::TcInst tci[2] = {};         // per-configuration GEMM arguments: synthesis, analysis
+  fnl::TcInst* d_tci = nullptr;    // their device copy (TcArgs::insts)
+  std::vector<fnl::TcTile> tiles_syn_h, tiles_ana_h;  // host copies of the tile lists
+  int tiles_version = 0;           // incremented whenever the tile shape changes
+  const fnl_shells* owner = nullptr;  // set on scratch clones: the object whose tables they use
 
   // SIMT tile lists
   fnl::Tile* d_tiles_syn = nullptr;
@@ -196,7 +202,15 @@ void run_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisation, dou
 // Tile shapes of the tensor-core GEMMs (mixed forms): widths capped at syn_cap ring pairs and
 // ana_cap degrees, multiples of 16 in [kTcMinWidth, 256].
 constexpr int kTcMinWidth = 64;
-void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap);
+void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap, bool exact = false);
+// A shells object of the tensor-core forms that shares src's tables and tile lists but owns
+// its scratch (so that several realisations of one configuration can run at once), and the
+// step that copies src's current tile shape into it.  Freed with destroy_clone.
+fnl_shells* clone_scratch(const fnl_shells* src);
+void refresh_clone(fnl_shells* c, const fnl_shells* src);
+void destroy_clone(fnl_shells* c);
+void build_tc_inst_a(fnl_shells* sh);
+void build_tc_inst_b(fnl_shells* sh);
 
 // ---- host set-up (setup_host.cpp) -------------------------------------------------------
 void gauss_legendre(int n, double* x, double* w);
@@ -235,6 +249,57 @@ void launch_adjoint_filter(const fnl_shells* sh, const double* gT, const double*
                            cudaStream_t st);
 void launch_dot_fnl(const fnl_shells* sh, const double* gT, const double* gE, const double* aNLT,
                     const double* aNLE, double* out, cudaStream_t st);
+
+// ---- several instances (configurations or realisations) in one launch (batch.cu) ----------
+
+// Per-launch keys and outputs of up to kTcMaxInst instances (kernel parameters).
+struct MultiKeys {
+  uint64_t seed[kTcMaxInst];
+  uint64_t real[kTcMaxInst];
+};
+struct MultiOut {
+  double fnl[kTcMaxInst];
+  double2* aT[kTcMaxInst];
+  double2* aE[kTcMaxInst];
+};
+// Step (i) of one instance: its tables and scratch (device array entry).
+struct FilterInst {
+  int L, nr, Cpad, nterms;
+  int64_t term_stride;
+  const float* Kf;
+  const double* vT;
+  const double* vE;
+  const int64_t* row32;
+  __nv_bfloat16* phiT;
+  double* aLT;
+  double* aLE;
+  double* psum_part;
+  double* psum;
+};
+// Step (v) of one instance.
+struct CombineInst {
+  int64_t nalm;
+  int nct, nr;
+  const float4* part;
+  const double* psum;
+  const double* mu;
+  const double* qT;
+  const double* qE;
+  const double2* aLT;
+  const double2* aLE;
+  double2* aNLT;
+  double2* aNLE;
+};
+// Specialised ring kernel (ring_square.cu): shell-group size if this configuration has one
+// (else 0), the size and contents of its argument block, and one launch over instances.
+int ring_square_group(const fnl_shells* sh);
+size_t ring_square_args_size();
+void ring_square_args(const fnl_shells* sh, void* out);
+void launch_ring_square_multi(const fnl_shells* proto, const void* d_inst, const int* d_item0, int ninst, int maxL,
+                              int items, cudaStream_t st);
+void launch_filter_multi(const FilterInst* inst, const int2* blocks, int nblocks, const MultiKeys& keys, int max_nr,
+                         int ninst, cudaStream_t st);
+void launch_combine_multi(const CombineInst* inst, int64_t max_nalm, int ninst, const MultiOut& out, cudaStream_t st);
 
 // ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
 void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st);

@@ -76,7 +76,7 @@ constexpr int kFCols = 64;
 // that the float4 stores of 8 lanes (consecutive column blocks) hit distinct bank quads.
 __host__ __device__ inline int out_stride(int nrp) { return nrp + 4; }
 
-__global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
+__device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int nterms, int64_t term_stride,
                                                              const float* __restrict__ Kf,
                                                              const double* __restrict__ vT,
                                                              const double* __restrict__ vE, uint64_t seed,
@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
                                                              double* __restrict__ phi_api, double* __restrict__ aLT,
                                                              double* __restrict__ aLE, double* __restrict__ psum) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int l = L - blockIdx.x;
   const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
   float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
   // output tile [col][i], row stride os (see out_stride)
@@ -253,15 +252,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
   }
   // one partial per (l, half of the orders, shell): summed in a fixed order by k_psum_reduce,
   // so the monopole (and every result) is reproducible bit for bit
-  if (psum && ws < nr) psum[((size_t)blockIdx.x * (kThreads / 128) + wh) * nr + ws] = (double)ph + (double)pl;
+  if (psum && ws < nr) psum[((size_t)(L - l) * (kThreads / 128) + wh) * nr + ws] = (double)ph + (double)pl;
 }
 
-// psum[s] = sum over the filter's partials of shell s = blockIdx.x: strided per-thread sums,
-// then a tree over the block, both in a fixed order (the result does not depend on timing).
-__global__ void __launch_bounds__(256) k_psum_reduce(int nparts, int nr, const double* __restrict__ part,
-                                                     double* __restrict__ psum) {
+// One configuration: block b takes degree l = L - b (largest first).
+__global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
+                                                             const float* __restrict__ Kf,
+                                                             const double* __restrict__ vT,
+                                                             const double* __restrict__ vE, uint64_t seed,
+                                                             uint64_t real, const double* __restrict__ noise,
+                                                             const int64_t* __restrict__ row32,
+                                                             __nv_bfloat16* __restrict__ phiT,
+                                                             double* __restrict__ phi_api, double* __restrict__ aLT,
+                                                             double* __restrict__ aLE, double* __restrict__ psum) {
+  filter_body(L - (int)blockIdx.x, L, nr, Cpad, nterms, term_stride, Kf, vT, vE, seed, real, noise, row32, phiT,
+              phi_api, aLT, aLE, psum);
+}
+
+// Several instances in one launch: block b takes (instance, degree) = blocks[b] (ordered by
+// descending degree across instances); the noise keys come with the launch.
+__global__ void __launch_bounds__(kThreads, 2) k_filter_multi(const FilterInst* __restrict__ inst,
+                                                              const int2* __restrict__ blocks, const MultiKeys keys) {
+  const int2 b = blocks[blockIdx.x];
+  const FilterInst f = inst[b.x];
+  filter_body(b.y, f.L, f.nr, f.Cpad, f.nterms, f.term_stride, f.Kf, f.vT, f.vE, keys.seed[b.x], keys.real[b.x],
+              nullptr, f.row32, f.phiT, nullptr, f.aLT, f.aLE, f.psum_part);
+}
+
+// psum[s] = sum over the filter's partials of shell s: strided per-thread sums, then a tree
+// over the block, both in a fixed order (the result does not depend on timing).
+__device__ __forceinline__ void psum_body(int s, int nparts, int nr, const double* __restrict__ part,
+                                          double* __restrict__ psum) {
   __shared__ double red[256];
-  const int s = blockIdx.x;
   double acc = 0.0;
   for (int e = threadIdx.x; e < nparts; e += 256) acc += part[(size_t)e * nr + s];
   red[threadIdx.x] = acc;
@@ -271,6 +293,18 @@ __global__ void __launch_bounds__(256) k_psum_reduce(int nparts, int nr, const d
     __syncthreads();
   }
   if (threadIdx.x == 0) psum[s] = red[0];
+}
+
+__global__ void __launch_bounds__(256) k_psum_reduce(int nparts, int nr, const double* __restrict__ part,
+                                                     double* __restrict__ psum) {
+  psum_body(blockIdx.x, nparts, nr, part, psum);
+}
+
+// Several instances: block (s, i) sums shell s of instance i.
+__global__ void __launch_bounds__(256) k_psum_multi(const FilterInst* __restrict__ inst) {
+  const FilterInst& f = inst[blockIdx.y];
+  if ((int)blockIdx.x >= f.nr) return;
+  psum_body(blockIdx.x, (f.L + 1) * (kThreads / 128), f.nr, f.psum_part, f.psum);
 }
 
 __device__ __forceinline__ double flushed(double v) { return fabs(v) < 1e-290 ? 0.0 : v; }
@@ -334,13 +368,13 @@ __global__ void k_alm_to_terms(int L, int nr, int Cpad, int64_t nalm, int nterms
 // monopole comes from Parseval's identity instead (exact on this grid):
 //   Phi_NL,00(r_i) = (sum_lm w_m |Phi_L,lm(r_i)|^2 - 4 pi mu_i) / sqrt(4 pi),  w_0 = 1, w_m>0 = 2,
 // a difference of two nearly equal numbers that FP32 grid sums would resolve poorly.
-__global__ void k_combine_mixed(int64_t nalm, int nct, int nr, double fnl, const float4* __restrict__ part,
-                                const double* __restrict__ psum, const double* __restrict__ mu,
-                                const double* __restrict__ qT, const double* __restrict__ qE,
-                                const double2* __restrict__ aLT, const double2* __restrict__ aLE,
-                                double2* __restrict__ aNLT, double2* __restrict__ aNLE, double2* __restrict__ aT,
-                                double2* __restrict__ aE) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void combine_body(int64_t i, int64_t nalm, int nct, int nr, double fnl,
+                                             const float4* __restrict__ part, const double* __restrict__ psum,
+                                             const double* __restrict__ mu, const double* __restrict__ qT,
+                                             const double* __restrict__ qE, const double2* __restrict__ aLT,
+                                             const double2* __restrict__ aLE, double2* __restrict__ aNLT,
+                                             double2* __restrict__ aNLE, double2* __restrict__ aT,
+                                             double2* __restrict__ aE) {
   if (i >= nalm) return;
   double tr = 0, ti = 0, er = 0, ei = 0;
   if (i == 0 && psum) {
@@ -370,7 +404,43 @@ __global__ void k_combine_mixed(int64_t nalm, int nct, int nr, double fnl, const
   }
 }
 
+__global__ void k_combine_mixed(int64_t nalm, int nct, int nr, double fnl, const float4* __restrict__ part,
+                                const double* __restrict__ psum, const double* __restrict__ mu,
+                                const double* __restrict__ qT, const double* __restrict__ qE,
+                                const double2* __restrict__ aLT, const double2* __restrict__ aLE,
+                                double2* __restrict__ aNLT, double2* __restrict__ aNLE, double2* __restrict__ aT,
+                                double2* __restrict__ aE) {
+  combine_body((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nalm, nct, nr, fnl, part, psum, mu, qT, qE, aLT, aLE,
+               aNLT, aNLE, aT, aE);
+}
+
+// Several instances: block row blockIdx.y is instance i; f_NL and the outputs come with the launch.
+__global__ void k_combine_multi(const CombineInst* __restrict__ inst, const MultiOut out) {
+  const int n = blockIdx.y;
+  const CombineInst& c = inst[n];
+  combine_body((int64_t)blockIdx.x * blockDim.x + threadIdx.x, c.nalm, c.nct, c.nr, out.fnl[n], c.part, c.psum, c.mu,
+               c.qT, c.qE, c.aLT, c.aLE, c.aNLT, c.aNLE, out.aT[n], out.aE[n]);
+}
+
 }  // namespace
+
+void launch_filter_multi(const FilterInst* inst, const int2* blocks, int nblocks, const MultiKeys& keys, int max_nr,
+                         int ninst, cudaStream_t st) {
+  const int nrp = (max_nr + 7) / 8 * 8;
+  const size_t smem = sizeof(float) * ((size_t)max_nr * nrp +
+                                       (size_t)std::max(max_nr * kFCols, kFCols * out_stride(nrp)) + 4 * max_nr +
+                                       4 * kFCols);
+  FNL_CUDA(cudaFuncSetAttribute(k_filter_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_filter_multi<<<nblocks, kThreads, smem, st>>>(inst, blocks, keys);
+  FNL_CUDA(cudaGetLastError());
+  k_psum_multi<<<dim3(max_nr, ninst), 256, 0, st>>>(inst);
+  FNL_CUDA(cudaGetLastError());
+}
+
+void launch_combine_multi(const CombineInst* inst, int64_t max_nalm, int ninst, const MultiOut& out, cudaStream_t st) {
+  k_combine_multi<<<dim3((unsigned)((max_nalm + 255) / 256), ninst), 256, 0, st>>>(inst, out);
+  FNL_CUDA(cudaGetLastError());
+}
 
 void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
   const int L = sh->lmax, np = sh->npairs;

@@ -9,8 +9,8 @@
 // G_S,m = (W_m - conj W_{N-m}) / (2 i)), scaled by (2 pi / N) times the GL weight, as BF16 terms.
 //
 // Factorisation N = N1 * P * Q (N1 = 25 = 5 x 5; (P, Q) = (16, 8) for 3200, (25, 5) for 3125 =
-// 5^5, (8, 8) for 1600, (8, 4) for 800); a shell's group is P Q threads rounded up to whole
-// warps (the extra threads sit out phase 2).  With
+// 5^5, (8, 8) for 1600, (8, 4) for 800, (4, 4) for 400); a shell's group is P Q threads
+// rounded up to whole warps (the extra threads sit out phase 2).  With
 // k = k1 + N1 (a + P b) and n = (c + Q d) + P Q n1 the inverse DFT runs as
 //   phase 1a  DFT_Q over b              (thread per (k1, a))
 //   phase 1b  x w_PQ^{a c}, DFT_P over a (thread per (k1, c))
@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "fnl_internal.cuh"
 
@@ -252,8 +253,17 @@ __device__ __forceinline__ void store_pair_terms(__nv_bfloat16* p, int64_t strid
   if (nterms > 2) *(__nv_bfloat162*)(p + 2 * stride) = __floats2bfloat162_rn(rx - __low2float(h1), ry - __high2float(h1));
 }
 
-template <int N1, int P, int Q, int PAD, int G>
-__global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_square(const SqArgs a) {
+// Several instances of one ring length in one launch: instance n owns the work items
+// [item0[n], item0[n + 1]); its arguments are inst[n].
+struct SqMulti {
+  const SqArgs* inst;
+  const int* item0;  // [ninst + 1]
+  int ninst, maxL;
+};
+
+template <int N1, int P, int Q, int PAD, int G, bool MULTI>
+__global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1)
+    k_ring_square(const __grid_constant__ SqArgs a, const __grid_constant__ SqMulti mi) {
   constexpr int T = P * Q;             // tasks of phase 2 (one (c, d) each)
   constexpr int TG = (T + 31) / 32 * 32;  // threads of one shell group (whole warps)
   constexpr int N = N1 * P * Q;
@@ -263,32 +273,62 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_square
   extern __shared__ __align__(16) unsigned char smem[];
   float2* buf = (float2*)smem;                  // [G][NB]
   float2* stg = buf + (size_t)G * NB;           // [2 L + 1][G]: staged F rows of the item
-  const int L = a.L;
-  float2* tw2 = stg + (size_t)(2 * L + 1) * G;  // [N1][Q][P]
-  float2* tw1 = tw2 + (size_t)N1 * T;           // [P][Q]
+  const int Lmax = MULTI ? mi.maxL : a.L;
+  float2* tw2 = stg + (size_t)(2 * Lmax + 1) * G;  // [N1][Q][P]
+  float2* tw1 = tw2 + (size_t)N1 * T;              // [P][Q]
   for (int i = threadIdx.x; i < N1 * T; i += blockDim.x) tw2[i] = a.tw2[i];
   for (int i = threadIdx.x; i < T; i += blockDim.x) tw1[i] = a.tw1[i];
 
-  const int groups = a.nr / G;
-  const int items = groups * a.npairs;
+  const int items = MULTI ? mi.item0[mi.ninst] : (a.nr / G) * a.npairs;
   const int g = threadIdx.x / TG, u = threadIdx.x % TG;
   float2* B = buf + (size_t)g * NB;
-  const int nrows = 2 * L + 1;  // problem (m = L, p = 1) is empty
+  // instance of a work item (binary search over the item offsets)
+  auto inst_of = [&](int item) -> int {
+    int lo = 0, hi = mi.ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mi.item0[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  };
 
   auto prefetch = [&](int item) {
-    const int jp = item / groups, s0 = (item % groups) * G;
-    const float* src = a.F + (size_t)jp * a.sj + 2 * s0;
+    int li = item, groups, nrows;  // nrows: problem (m = L, p = 1) is empty
+    const float* Fp;
+    int64_t sp, sj;
+    if constexpr (MULTI) {
+      const int n = inst_of(item);
+      const SqArgs& pa = mi.inst[n];
+      li = item - mi.item0[n];
+      groups = pa.nr / G, nrows = 2 * pa.L + 1, Fp = pa.F, sp = pa.sp, sj = pa.sj;
+    } else {
+      groups = a.nr / G, nrows = 2 * a.L + 1, Fp = a.F, sp = a.sp, sj = a.sj;
+    }
+    const int jp = li / groups, s0 = (li % groups) * G;
+    const float* src = Fp + (size_t)jp * sj + 2 * s0;
     for (int q = threadIdx.x; q < nrows * (G / 2); q += blockDim.x) {
       const int mp = q / (G / 2), h = q % (G / 2);
-      cp_async16(stg + (size_t)mp * G + 2 * h, src + (size_t)mp * a.sp + 4 * h);
+      cp_async16(stg + (size_t)mp * G + 2 * h, src + (size_t)mp * sp + 4 * h);
     }
     cp_async_commit();
   };
 
   int item = blockIdx.x;
   if (item < items) prefetch(item);
+  SqArgs cur;
   for (; item < items; item += gridDim.x) {
-    const int jp = item / groups, s0 = (item % groups) * G;
+    // this item's instance: the kernel parameters themselves when there is one
+    int li = item;
+    if constexpr (MULTI) {
+      const int n = inst_of(item);
+      cur = mi.inst[n];
+      li = item - mi.item0[n];
+    }
+    const SqArgs& A = MULTI ? cur : a;
+    const int L = A.L;
+    const int groups = A.nr / G;
+    const int jp = li / groups, s0 = (li % groups) * G;
     cp_async_wait_all();
     __syncthreads();  // staged rows visible; the previous item's buffers are free
     // spectrum Z of every shell of the item, natural order at k + PAD (k / (N1 P))
@@ -345,7 +385,7 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_square
     if (u < T) {
       const int d = u % P, c = u / P;
       const int base = N1 * d + S * c;
-      const float mu = (float)a.mu[s0 + g];
+      const float mu = (float)A.mu[s0 + g];
       const float2* w = tw2 + c * P + d;
       float2 v[N1];
 #pragma unroll
@@ -391,10 +431,10 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_square
     }
     __syncthreads();
     // S and D of every shell, as BF16 terms
-    const int south = a.ntheta - 1 - jp;
+    const int south = A.ntheta - 1 - jp;
     const bool equator = (south == jp);
-    const float scale = (float)(6.28318530717958647692 / N * a.wgl[jp]);
-    __nv_bfloat16* out = a.GT + (size_t)jp * a.sj + 2 * s0;
+    const float scale = (float)(6.28318530717958647692 / N * A.wgl[jp]);
+    __nv_bfloat16* out = A.GT + (size_t)jp * A.sj + 2 * s0;
     for (int t = threadIdx.x; t < (L + 1) * G; t += blockDim.x) {
       const int gg = t % G, m = t / G;
       const float2* Bg = buf + (size_t)gg * NB;
@@ -413,9 +453,9 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_square
         Dx = (gnx - gsx) * scale;
         Dy = (gny - gsy) * scale;
       }
-      __nv_bfloat16* o = out + (size_t)(2 * m) * a.sp + 2 * gg;
-      store_pair_terms(o, a.gt_stride, a.nterms, Sx, Sy);
-      if (m < L) store_pair_terms(o + a.sp, a.gt_stride, a.nterms, Dx, Dy);
+      __nv_bfloat16* o = out + (size_t)(2 * m) * A.sp + 2 * gg;
+      store_pair_terms(o, A.gt_stride, A.nterms, Sx, Sy);
+      if (m < L) store_pair_terms(o + A.sp, A.gt_stride, A.nterms, Dx, Dy);
     }
   }
   cp_async_wait_all();
@@ -426,22 +466,26 @@ struct SqConfig {
 };
 
 // Sizes with a specialised kernel: N = 25 P Q.
-constexpr SqConfig kSqConfigs[] = {{3200, 25, 16, 8, 4}, {3125, 25, 25, 5, 4}, {1600, 25, 8, 8, 8}, {800, 25, 8, 4, 8}};
+constexpr SqConfig kSqConfigs[] = {{3200, 25, 16, 8, 4}, {3125, 25, 25, 5, 4}, {1600, 25, 8, 8, 8}, {800, 25, 8, 4, 8},
+                                   {400, 25, 4, 4, 8}};
 
 template <int N1, int P, int Q, int PAD, int G>
-void launch_sq(const SqArgs& a, int sms, cudaStream_t st) {
+void launch_sq(const SqArgs& a, int sms, cudaStream_t st, const SqMulti* multi = nullptr, int items_multi = 0) {
   constexpr int T = P * Q, TG = (T + 31) / 32 * 32, N = N1 * P * Q, S = N1 * P + PAD, NB = N1 * P + S * (Q - 1);
-  const size_t smem = sizeof(float2) * ((size_t)G * NB + (size_t)(2 * a.L + 1) * G + (size_t)N1 * T + T);
+  const int Lmax = multi ? multi->maxL : a.L;
+  const size_t smem = sizeof(float2) * ((size_t)G * NB + (size_t)(2 * Lmax + 1) * G + (size_t)N1 * T + T);
   if (smem > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "ring square staging exceeds shared memory");
   (void)N;
-  auto kern = k_ring_square<N1, P, Q, PAD, G>;
-  FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * TG, smem));
-  const int items = (a.nr / G) * a.npairs;
-  const int grid = std::max(1, std::min(items, sms * std::max(per_sm, 1)));
-  kern<<<grid, G * TG, smem, st>>>(a);
-  FNL_CUDA(cudaGetLastError());
+  auto run = [&](auto kern, int items) {
+    FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * TG, smem));
+    const int grid = std::max(1, std::min(items, sms * std::max(per_sm, 1)));
+    kern<<<grid, G * TG, smem, st>>>(a, multi ? *multi : SqMulti{});
+    FNL_CUDA(cudaGetLastError());
+  };
+  if (multi) run(k_ring_square<N1, P, Q, PAD, G, true>, items_multi);
+  else run(k_ring_square<N1, P, Q, PAD, G, false>, (a.nr / G) * a.npairs);
 }
 
 }  // namespace
@@ -472,10 +516,9 @@ void ring_square_tables(int nphi, std::vector<float>& tw2, std::vector<float>& t
   }
 }
 
-// Specialised steps (ii)-(iv) ring kernel of the tensor-core forms; false if this
-// configuration has none (the caller then runs the general kernel).
-bool launch_ring_square(const fnl_shells* sh, cudaStream_t st) {
-  if (!sh->nterms || !sh->d_sqtw2) return false;
+namespace {
+
+SqArgs sq_args_of(const fnl_shells* sh) {
   SqArgs a;
   a.L = sh->lmax;
   a.nr = sh->nr;
@@ -492,25 +535,53 @@ bool launch_ring_square(const fnl_shells* sh, cudaStream_t st) {
   a.tw1 = (const float2*)sh->d_sqtw1;
   a.mu = sh->d_mu;
   a.wgl = sh->d_wgl;
+  return a;
+}
+
+}  // namespace
+
+int ring_square_group(const fnl_shells* sh) {
+  if (!sh->nterms || !sh->d_sqtw2) return 0;
+  for (const SqConfig& c : kSqConfigs)
+    if (c.N == sh->nphi) return (sh->nr % c.G || 2 * sh->lmax + 2 > c.N) ? 0 : c.G;
+  return 0;
+}
+
+size_t ring_square_args_size() { return sizeof(SqArgs); }
+
+void ring_square_args(const fnl_shells* sh, void* out) {
+  const SqArgs a = sq_args_of(sh);
+  std::memcpy(out, &a, sizeof(a));
+}
+
+// Specialised steps (ii)-(iv) ring kernel of the tensor-core forms; false if this
+// configuration has none (the caller then runs the general kernel).
+bool launch_ring_square(const fnl_shells* sh, cudaStream_t st) {
+  if (!ring_square_group(sh)) return false;
+  const SqArgs a = sq_args_of(sh);
   switch (sh->nphi) {
-    case 3200:
-      if (sh->nr % 4 || 2 * sh->lmax + 2 > 3200) return false;
-      launch_sq<25, 16, 8, 2, 4>(a, sh->sms, st);
-      return true;
-    case 3125:
-      if (sh->nr % 4 || 2 * sh->lmax + 2 > 3125) return false;
-      launch_sq<25, 25, 5, 2, 4>(a, sh->sms, st);
-      return true;
-    case 1600:
-      if (sh->nr % 8 || 2 * sh->lmax + 2 > 1600) return false;
-      launch_sq<25, 8, 8, 2, 8>(a, sh->sms, st);
-      return true;
-    case 800:
-      if (sh->nr % 8 || 2 * sh->lmax + 2 > 800) return false;
-      launch_sq<25, 8, 4, 4, 8>(a, sh->sms, st);
-      return true;
-    default:
-      return false;
+    case 3200: launch_sq<25, 16, 8, 2, 4>(a, sh->sms, st); return true;
+    case 3125: launch_sq<25, 25, 5, 2, 4>(a, sh->sms, st); return true;
+    case 1600: launch_sq<25, 8, 8, 2, 8>(a, sh->sms, st); return true;
+    case 800: launch_sq<25, 8, 4, 4, 8>(a, sh->sms, st); return true;
+    case 400: launch_sq<25, 4, 4, 2, 8>(a, sh->sms, st); return true;
+    default: return false;
+  }
+}
+
+// One launch over several instances of the ring length of `proto` (whose twiddle tables
+// serve all of them): d_inst holds their ring_square_args, d_item0 the item offsets.
+void launch_ring_square_multi(const fnl_shells* proto, const void* d_inst, const int* d_item0, int ninst, int maxL,
+                              int items, cudaStream_t st) {
+  const SqArgs a = sq_args_of(proto);
+  const SqMulti m{(const SqArgs*)d_inst, d_item0, ninst, maxL};
+  switch (proto->nphi) {
+    case 3200: launch_sq<25, 16, 8, 2, 4>(a, proto->sms, st, &m, items); return;
+    case 3125: launch_sq<25, 25, 5, 2, 4>(a, proto->sms, st, &m, items); return;
+    case 1600: launch_sq<25, 8, 8, 2, 8>(a, proto->sms, st, &m, items); return;
+    case 800: launch_sq<25, 8, 4, 4, 8>(a, proto->sms, st, &m, items); return;
+    case 400: launch_sq<25, 4, 4, 2, 8>(a, proto->sms, st, &m, items); return;
+    default: throw Error(FNL_EUNSUPPORTED, "no specialised ring kernel for this ring length");
   }
 }
 

@@ -39,6 +39,9 @@ namespace fnl {
 
 namespace {
 
+// Tensor maps of the instances of a multi-instance launch (see TcArgs::multi).
+__constant__ CUtensorMap c_tc_maps[kTcMaxInst * 6];
+
 constexpr int kEpiWarps = 4;
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr uint32_t kWaitLimit = 1u << 26;
@@ -194,6 +197,7 @@ __device__ __forceinline__ void issue_stage(uint64_t da, uint64_t db, uint32_t b
   }
 }
 
+template <bool MULTI>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -244,8 +248,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       uint32_t phase = 0;
       bool ok = true;
       uint32_t armed = 0, armed_par = 0;  // stages with copies issued, and the parity armed
+      int prev_inst = -1;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
+        const CUtensorMap* mA = MULTI ? c_tc_maps + 6 * tl.inst : a.one.tmA;
+        const CUtensorMap* mB = MULTI ? c_tc_maps + 6 * tl.inst + 3 : a.one.tmB;
+        if (MULTI && tl.inst != prev_inst && lane == 0) {
+          // bring this instance's tensor maps into the copy engine's descriptor cache
+          for (int tm = 0; tm < a.nterms; ++tm) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mA[tm]) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mB[tm]) : "memory");
+          }
+        }
+        prev_inst = tl.inst;
         const int nst = (tl.nkb + 1) / 2;
         for (int sg = 0; sg < nst; ++sg) {
           int good = 1;
@@ -267,14 +282,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               const uint32_t sb = st + (uint32_t)a.nterms * kTcABytes + (uint32_t)tm * bBytes;
               if (a.mode == TC_SYNTH) {
                 // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
-                tma_load_3d(sa, &a.tmA[tm], 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, &full[stage]);
+                tma_load_3d(sa, &mA[tm], 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, &full[stage]);
                 // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
-                tma_load_3d(sb, &a.tmB[tm], 0, tl.n0, tl.r0 / 32 + 2 * sg, &full[stage]);
+                tma_load_3d(sb, &mB[tm], 0, tl.n0, tl.r0 / 32 + 2 * sg, &full[stage]);
               } else {
                 // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
-                tma_load_4d(sa, &a.tmA[tm], 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, &full[stage]);
+                tma_load_4d(sa, &mA[tm], 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, &full[stage]);
                 // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
-                tma_load_3d(sb, &a.tmB[tm], 0, tl.r0 + tl.n0, 2 * sg, &full[stage]);
+                tma_load_3d(sb, &mB[tm], 0, tl.r0 + tl.n0, 2 * sg, &full[stage]);
               }
             }
           }  // lane 0
@@ -373,11 +388,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     uint32_t aphase = 0, ephase = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
       const TcTile tl = a.tiles[t];
+      // this tile's instance, copied into registers (stores through F or part could alias it)
       if (!mbar_wait(&tfull[acc], aphase, a.err, 4)) break;
       tc_fence_after();
+      // this tile's instance: with one instance its fields are read from the kernel
+      // parameters where they are used (constant-bank operands: measurably faster in the
+      // store loop than register copies); with several they are copied into registers
+      // once per tile (stores through F or part could alias the array)
+      TcInst mi;
+      if constexpr (MULTI) {
+        const TcInst* Ip = a.insts + tl.inst;
+        mi.F = Ip->F, mi.part = Ip->part, mi.qT = Ip->qT, mi.qE = Ip->qE;
+        mi.L = Ip->L, mi.nr = Ip->nr, mi.npairs = Ip->npairs, mi.Cpad = Ip->Cpad, mi.nalm = Ip->nalm;
+      }
+      const TcInst& I = MULTI ? mi : a.one;
+      const int L = I.L, nr = I.nr;
       const int m = tl.mp >> 1, p = tl.mp & 1;
       const int c = tl.c0 + 32 * q + lane;
-      const bool cvalid = c < 2 * a.nr;
+      const bool cvalid = c < 2 * nr;
       const int nch = (tl.nsize + 31) / 32;
       for (int ch = 0; ch < nch; ++ch) {
         float v[32];
@@ -398,12 +426,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         if (a.mode == TC_SYNTH) {
           if (cvalid) {
             // F is ring-pair-major: F[jp][mp][Cpad]
-            float* out = a.F + (size_t)tl.mp * a.Cpad + c;
-            const size_t sj = (size_t)2 * (a.L + 1) * a.Cpad;
+            float* out = I.F + (size_t)tl.mp * I.Cpad + c;
+            const size_t sj = (size_t)2 * (L + 1) * I.Cpad;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int jr = tl.n0 + ch * 32 + j;
-              if (ch * 32 + j < tl.nsize && jr < a.npairs) out[(size_t)jr * sj] = v[j];
+              if (ch * 32 + j < tl.nsize && jr < I.npairs) out[(size_t)jr * sj] = v[j];
             }
           }
         } else if (a.mode == TC_ANA_STORE) {
@@ -413,7 +441,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               const int k = tl.n0 + ch * 32 + j;
               if (ch * 32 + j < tl.nsize && k < tl.kvalid) {
                 const int l = m + p + 2 * k;
-                a.alm_out[alm_idx(l, m, a.L) * (2 * a.nr) + c] = (double)v[j];
+                a.alm_out[alm_idx(l, m, L) * (2 * nr) + c] = (double)v[j];
               }
             }
           }
@@ -427,8 +455,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             float qt = 0.f, qe = 0.f;
             if (cvalid && ch * 32 + j < tl.nsize && k < tl.kvalid) {
               const int l = m + p + 2 * k;
-              qt = a.qT[(size_t)l * a.nr + i];
-              qe = a.qE[(size_t)l * a.nr + i];
+              qt = I.qT[(size_t)l * nr + i];
+              qe = I.qE[(size_t)l * nr + i];
             }
             tx[j] = v[j] * qt;
             ex[j] = v[j] * qe;
@@ -460,7 +488,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             s.w += rw[3];
           }
           const int l = m + p + 2 * k;
-          a.part[(size_t)(tl.c0 >> 7) * a.nalm + alm_idx(l, m, a.L)] = s;
+          I.part[(size_t)(tl.c0 >> 7) * I.nalm + alm_idx(l, m, L)] = s;
         }
         if (!epi_sync(&epib[1], ephase, lane, a.err)) break;
         ephase ^= 1;
@@ -521,12 +549,23 @@ int tc_stages(int nterms, int nmax, int mode) {
   return s;
 }
 
+void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st) {
+  if (n < 1 || n > kTcMaxInst) throw Error(FNL_EINVAL, "too many instances for one tensor-core launch");
+  FNL_CUDA(cudaMemcpyToSymbolAsync(c_tc_maps, host, sizeof(CUtensorMap) * 6 * (size_t)n, 0,
+                                   cudaMemcpyHostToDevice, st));
+}
+
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(args.nterms, args.nmax, args.stages, args.mode);
   if (smem > 227 * 1024 || args.stages < 1) throw Error(FNL_EUNSUPPORTED, "tensor-core tile does not fit shared memory");
-  FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::max(1, std::min(args.ntiles, sms));
-  k_tc_gemm<<<grid, kThreadsTc, smem, st>>>(args);
+  if (args.multi) {
+    FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_gemm<true><<<grid, kThreadsTc, smem, st>>>(args);
+  } else {
+    FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_gemm<false><<<grid, kThreadsTc, smem, st>>>(args);
+  }
   FNL_CUDA(cudaGetLastError());
 }
 

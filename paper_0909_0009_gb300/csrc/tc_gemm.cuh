@@ -11,9 +11,10 @@ enum TcMode { TC_SYNTH = 0, TC_ANA_QUAD = 1, TC_ANA_STORE = 2 };
 
 // One output tile: problem mp = 2 m + p, column tile c0 (multiple of 128), N range
 // [n0, n0 + nsize) (ring pairs for the synthesis, degrees k for the analysis), nkb
-// 32-deep k blocks, r0 = first row of the problem in the packed operand, kvalid = K_mp.
+// 32-deep k blocks, r0 = first row of the problem in the packed operand, kvalid = K_mp,
+// inst = the configuration (TcInst) the tile belongs to.
 struct TcTile {
-  int mp, c0, n0, nsize, nkb, r0, kvalid, pad;
+  int mp, c0, n0, nsize, nkb, r0, kvalid, inst;
 };
 
 // Operands arrive in stages 64 deep in k: per BF16 term one TMA box of A (128 columns x 64 k,
@@ -22,9 +23,29 @@ struct TcTile {
 constexpr int kTcStageK = 64;
 constexpr uint32_t kTcABytes = 128u * kTcStageK * 2u;  // A bytes per term and stage
 
-struct TcArgs {
+// Instances (configurations or realisations) in one multi-instance launch, at most.
+constexpr int kTcMaxInst = 64;
+
+// What differs between the instances that share one launch; an array of these lives in
+// device memory and every tile names its entry.  The tensor maps are kept apart (kernel
+// parameters for one instance, a constant-memory table for several): the copy engine reads
+// a map from global memory far more slowly than from those two spaces.
+struct alignas(64) TcInst {
   CUtensorMap tmA[3];   // per BF16 term: Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves}
   CUtensorMap tmB[3];   // per BF16 term: Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs}
+  float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
+  float4* part;         // TC_ANA_QUAD: [Cpad / 128][nalm] (T re, T im, E re, E im)
+  const float* qT;      // [L+1][nr]
+  const float* qE;
+  int L, nr, npairs, Cpad;
+  int64_t nalm;
+};
+
+struct TcArgs {
+  TcInst one;           // the single instance (multi == 0), maps and fields in parameter space
+  int multi;            // 1: maps of instance i at c_tc_maps[6 i .. 6 i + 5] (A terms, B terms),
+                        //    its other fields at insts[i]
+  const TcInst* insts;  // device array indexed by TcTile::inst (multi == 1)
   const TcTile* tiles;
   int ntiles;
   int mode;
@@ -35,13 +56,7 @@ struct TcArgs {
   int cols;             // TMEM columns between the leading and the correction accumulator
   int nbuf;             // accumulator sets in TMEM (double buffering when 2)
   int stages;
-  int L, nr, npairs, Cpad;
-  int64_t nalm;
-  float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
-  float4* part;         // TC_ANA_QUAD: [Cpad / 128][nalm] (T re, T im, E re, E im)
-  double* alm_out;      // TC_ANA_STORE: [nalm][nr][2]
-  const float* qT;      // [L+1][nr]
-  const float* qE;
+  double* alm_out;      // TC_ANA_STORE (one configuration per launch): [nalm][nr][2]
   int* err;             // device error word (0 = ok)
 };
 
@@ -50,5 +65,8 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode);
 int tc_stages(int nterms, int nmax, int mode);
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st);
+// Copy n instances' maps (A0..A2, B0..B2 each) into the constant table, on `st` from pinned
+// host memory that stays unchanged until the copy has run.
+void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st);
 
 }  // namespace fnl

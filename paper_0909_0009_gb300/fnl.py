@@ -27,7 +27,7 @@ EXPORTS = [
     "fnl_accumulate", "fnl_gauss_legendre", "fnl_covariance", "fnl_cholesky_filters",
     "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
     "fnl_accumulate_noalloc", "fnl_generate_backward", "fnl_batch_create", "fnl_batch_destroy",
-    "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles",
+    "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(vp), vp]
     lib.fnl_shells_autotune.argtypes = [vp, vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.fnl_shells_set_tiles.argtypes = [vp, i, i]
+    lib.fnl_batch_tiles.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -348,6 +349,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    @property
+    def multi(self) -> bool:
+        """True when every stage runs as one launch over all instances."""
+        n, ns = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fnl_batch_info(self.handle, ctypes.byref(n), ctypes.byref(ns), None))
+        return ns.value == 0
+
+    def tiles(self) -> tuple[int, int]:
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fnl_batch_tiles(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def lanes(self) -> list:
         n, ns = ctypes.c_int(), ctypes.c_int()

@@ -53,19 +53,48 @@ def assert_same(batch_out, ref):
 
 @pytest.mark.parametrize("prec,nstreams", [("bf16x2", 0), ("bf16x2", 1), ("bf16x3", 3), ("fp64", 2), ("fp32", 0)])
 def test_batch_matches_single_calls(F, prec, nstreams):
+    """Stream mode (ring lengths 50, 100, 150 have no specialised ring kernel)."""
     A, B, C = make(F, 16, 8, prec), make(F, 32, 16, prec), make(F, 48, 24, prec)
     inst = [A, B, A, C, B, C, A]
     b = F.Batch(inst, nstreams=nstreams)
+    assert not b.multi
     lanes = b.lanes()
-    # instances of one object share its scratch: they must sit on one stream
-    for s in (A, B, C):
-        assert len({lanes[i] for i, x in enumerate(inst) if x is s}) == 1
+    if prec in ("fp64", "fp32"):
+        # repeated objects of the SIMT forms share their scratch: one stream each
+        for s in (A, B, C):
+            assert len({lanes[i] for i, x in enumerate(inst) if x is s}) == 1
     for call in range(2):  # the second call updates the instantiated graph in place
         seeds = [11 + 7 * i + call for i in range(len(inst))]
         reals = [i % 3 for i in range(len(inst))]
         fnls = [-40.0 + 13.0 * i + call for i in range(len(inst))]
         out = b.generate(seeds, reals, fnls)
         assert_same(out, singles(inst, seeds, reals, fnls))
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
+def test_multi_instance_batch_matches_single_calls(F, prec):
+    """Multi-instance mode: ring lengths 800, 1600 and 3125 (specialised kernels), repeated
+    objects (scratch clones), two calls (the second updates the graph); every instance bit
+    for bit equal to a single call on its object with the tile shape the batch picked."""
+    A = make(F, 100, 8, prec, grid=(151, 800))
+    B = make(F, 200, 16, prec, grid=(301, 1600))
+    C = make(F, 150, 8, prec, grid=(226, 800))
+    D = make(F, 300, 12, prec, grid=(451, 3125))
+    inst = [A, B, A, C, D, B, A, D]
+    b = F.Batch(inst)
+    assert b.multi
+    syn, ana = b.tiles()
+    assert syn in (96, 112, 128) and ana in (128, 256)
+    for call in range(2):
+        seeds = [5 + 3 * i + call for i in range(len(inst))]
+        reals = [i % 2 for i in range(len(inst))]
+        fnls = [-25.0 + 9.0 * i - call for i in range(len(inst))]
+        out = b.generate(seeds, reals, fnls)
+        assert_same(out, singles(inst, seeds, reals, fnls))
+    # and against the FP64 GPU path, within the mixed forms' bound
+    d64 = make(F, 300, 12, "fp64", grid=(451, 3125))
+    ref = d64.generate(seeds[4], reals[4], fnls[4], parts=False)
+    assert rel_l2(host(out[4][0]), host(ref["aT"])) < 1e-5
 
 
 def test_batch_rejects_bad_arguments(F):
@@ -109,6 +138,7 @@ def test_uneven_batch_of_64(F):
     tuned = {k: s.autotune() for k, s in objs.items()}
     shells = [objs[(x.lmax, x.nr)] for x in insts]
     b = F.Batch(shells)
+    assert b.multi
     seeds = [x.seed for x in insts]
     reals = [x.realisation for x in insts]
     fnls = [x.fnl for x in insts]

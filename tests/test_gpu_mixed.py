@@ -78,11 +78,13 @@ def test_stages_match_oracle(F, prec, lmax, nr, ntheta, nphi):
 @pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
 @pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(256, 8, 385, 800), (300, 16, 452, 800), (512, 8, 769, 1600),
                                                   (1024, 8, 1537, 3200), (700, 24, 1051, 3200),
-                                                  (1024, 4, 1537, 3125), (600, 12, 902, 3125)])
+                                                  (1024, 4, 1537, 3125), (600, 12, 902, 3125),
+                                                  (128, 8, 193, 400), (150, 16, 226, 400)])
 def test_ring_square_specialised_sizes(F, prec, lmax, nr, ntheta, nphi):
-    """n_phi = 800, 1600, 3125 and 3200 have a specialised ring kernel (25 P Q factorisation,
-    fused square; 3125 = 25 x 25 x 5 with 125-thread shell groups): its square against the
-    FP64 path's on the same Phi_L, odd and even n_theta, full and partial band limits."""
+    """n_phi = 400, 800, 1600, 3125 and 3200 have a specialised ring kernel (25 P Q
+    factorisation, fused square; 3125 = 25 x 25 x 5 with 125-thread shell groups, 400 with
+    16-thread groups in one warp): its square against the FP64 path's on the same Phi_L, odd
+    and even n_theta, full and partial band limits."""
     c = Pair(F, lmax, nr, ntheta, nphi, prec, store=False)
     phiL = O.phi_linear(c.K, O.philox_noise(lmax, nr, 5, 0))
     got = host(c.mx.square(cuda(phiL)))
