@@ -22,6 +22,11 @@ numpy matmul, numpy.fft.rfft/irfft (a DFT of a Hermitian-symmetric spectrum),
 numpy.linalg.cholesky.  Nothing is blocked, fused or reordered beyond the
 definitions written in each docstring.
 
+The output maps (``maps_iqu``: Stokes I, Q, U from a^T, a^E, a^B) use spin-2 functions
+written from the spin raising and lowering operators (``spin2_functions``); their pins are the
+operators evaluated by finite differences of scipy's Y_lm, the closed form of 2Y_20,
+orthonormality on the grid, the spin-2 analysis round trip, Parseval and the E/B rotation.
+
 The adjoint (``generate_backward`` and the transposes it chains) is the chain rule
 through these steps; its pins are the dot-product test of every transpose against its
 pinned forward map and central finite differences of a loss through ``generate``.
@@ -591,10 +596,92 @@ def generate_backward(K, noise, grid: Grid, r, w, alphaT, alphaE, fnl: float, gT
     return phi_linear_adjoint(K, phibar), dfnl
 
 
+# ---------------------------------------------------------------------------
+# Output maps: Stokes I, Q, U on the ring grid from a^T, a^E, a^B.  The paper's deliverable is
+# temperature and polarization maps, the three Stokes maps I, Q, U (Sect. 4; its Fig. 2 shows
+# I and the polarization intensity sqrt(Q^2 + U^2)).
+# ---------------------------------------------------------------------------
+
+def spin2_functions(m: int, grid: Grid) -> tuple[np.ndarray, np.ndarray]:
+    """W_lm(x_j) and X_lm(x_j) for l = m..lmax, shape [lmax - m + 1, n_theta] each, with
+    W = (2lam + (-2)lam) / 2 and X = (2lam - (-2)lam) / 2, where sY_lm = slam_lm(theta) e^{i m phi}.
+
+    Definition: the spin-weighted harmonics come from Y_lm by the spin raising and lowering
+    operators, 2Y_lm = N_l edth^2 Y_lm and -2Y_lm = N_l edthbar^2 Y_lm, N_l = ((l-1) l (l+1) (l+2))^(-1/2),
+    with edth eta = -(sin th)^s (d_th + i / sin th d_phi)[(sin th)^(-s) eta] on spin weight s and
+    edthbar eta = -(sin th)^(-s) (d_th - i / sin th d_phi)[(sin th)^s eta].  Applied twice to
+    lam_lm e^{i m phi}, with the Legendre equation for lam'' and
+    sin th lam'_lm = l x lam_lm - c_lm lam_{l-1,m}, c_lm = sqrt((2l+1)(l^2 - m^2) / (2l-1)):
+       W = N_l [((2 m^2 - 2 l x^2) lam_lm + 2 x c_lm lam_{l-1,m}) / sin^2 th - l (l+1) lam_lm]
+       X = N_l 2 m [(1 - l) x lam_lm + c_lm lam_{l-1,m}] / sin^2 th,
+    both 0 for l < 2."""
+    L = grid.lmax
+    x = grid.x
+    lam = grid.lam(m)                                       # [L - m + 1, ntheta], l = m..L
+    prev = np.vstack([np.zeros((1, x.size)), lam[:-1]])     # lam_{l-1,m} (zero at l = m)
+    ls = np.arange(m, L + 1, dtype=np.float64)[:, None]
+    c = np.sqrt((2 * ls + 1) * (ls * ls - m * m) / np.maximum(2 * ls - 1, 1.0))
+    s2 = (1.0 - x) * (1.0 + x)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        nl = np.where(ls >= 2, 1.0 / np.sqrt(np.maximum((ls - 1) * ls * (ls + 1) * (ls + 2), 1.0)), 0.0)
+    W = nl * (((2.0 * m * m - 2.0 * ls * x * x) * lam + 2.0 * x * c * prev) / s2 - ls * (ls + 1) * lam)
+    X = nl * 2.0 * m * ((1.0 - ls) * x * lam + c * prev) / s2
+    return W, X
+
+
+def maps_iqu(aT, aE, aB, grid: Grid) -> np.ndarray:
+    """Stokes maps [3, n_theta, n_phi] = (I, Q, U) of one realisation.
+
+    I = sum_lm a^T_lm Y_lm (the spin-0 synthesis); Q + iU = sum_lm a_{2,lm} 2Y_lm and
+    Q - iU = sum_lm a_{-2,lm} -2Y_lm with a_{+-2,lm} = -(a^E_lm +- i a^B_lm) (the convention of
+    HEALPix, whose maps the paper makes).  With a_{l,-m} = (-1)^m conj(a_lm) for E and B,
+    W_{l,-m} = (-1)^m W_lm and X_{l,-m} = -(-1)^m X_lm, every ring reduces to m >= 0:
+       Q_m = -sum_l (E_lm W_lm + i B_lm X_lm),   U_m = sum_l (i E_lm X_lm - B_lm W_lm),
+       Q = Q_0 + 2 Re sum_{m>0} Q_m e^{i m phi},  likewise U (X_l0 = 0).
+    aB may be None (zero)."""
+    L = grid.lmax
+    aT = np.asarray(aT, dtype=np.complex128)
+    aE = np.asarray(aE, dtype=np.complex128)
+    aB = np.zeros_like(aE) if aB is None else np.asarray(aB, dtype=np.complex128)
+    half = grid.nphi // 2 + 1
+    Qm = np.zeros((grid.ntheta, half), dtype=np.complex128)
+    Um = np.zeros_like(Qm)
+    for m in range(L + 1):
+        rows = alm_index(np.arange(m, L + 1), m, L)
+        W, X = spin2_functions(m, grid)
+        E, B = aE[rows], aB[rows]
+        Qm[:, m] = -(W.T @ E + 1j * (X.T @ B))
+        Um[:, m] = 1j * (X.T @ E) - W.T @ B
+    I = synthesis(aT[:, None], grid)[0]
+    Q = np.fft.irfft(Qm, n=grid.nphi, axis=-1) * grid.nphi
+    U = np.fft.irfft(Um, n=grid.nphi, axis=-1) * grid.nphi
+    return np.stack([I, Q, U])
+
+
+def analysis_spin2(Q: np.ndarray, U: np.ndarray, grid: Grid) -> tuple[np.ndarray, np.ndarray]:
+    """(a^E, a^B) from Q, U maps [n_theta, n_phi]: a_{+-2,lm} = int (Q +- iU) +-2Y*_lm dOmega by GL
+    quadrature and the rectangle rule, then a^E = -(a_2 + a_-2) / 2, a^B = i (a_2 - a_-2) / 2, i.e.
+       a^E_lm = -sum_j w_j (W_lm Q^_m + i X_lm U^_m),  a^B_lm = sum_j w_j (i X_lm Q^_m - W_lm U^_m),
+    Q^_m = (2 pi / n_phi) sum_k Q_jk e^{-i m phi_k}.  Exact for band-limited maps on this grid."""
+    L = grid.lmax
+    Qh = np.fft.rfft(np.asarray(Q, dtype=np.float64), axis=-1) * (2.0 * math.pi / grid.nphi)
+    Uh = np.fft.rfft(np.asarray(U, dtype=np.float64), axis=-1) * (2.0 * math.pi / grid.nphi)
+    aE = np.zeros(n_alm(L), dtype=np.complex128)
+    aB = np.zeros_like(aE)
+    for m in range(L + 1):
+        rows = alm_index(np.arange(m, L + 1), m, L)
+        W, X = spin2_functions(m, grid)
+        q, u = grid.w * Qh[:, m], grid.w * Uh[:, m]
+        aE[rows] = -(W @ q + 1j * (X @ u))
+        aB[rows] = 1j * (X @ q) - W @ u
+    return aE, aB
+
+
 __all__ = [
     "FOUR_PI", "FLUSH", "gauss_legendre", "lambda_mm", "lambda_column", "lambda_table", "Grid",
     "synthesis", "analysis", "spherical_jn_table", "k_rule", "covariance", "filters",
     "mu_ensemble", "philox4x64", "philox_noise", "phi_linear", "phi_nonlinear",
     "quadrature_weights", "radial_quadrature", "generate", "synthesis_adjoint", "analysis_adjoint",
-    "phi_linear_adjoint", "radial_quadrature_adjoint", "generate_backward",
+    "phi_linear_adjoint", "radial_quadrature_adjoint", "generate_backward", "spin2_functions", "maps_iqu",
+    "analysis_spin2",
 ]

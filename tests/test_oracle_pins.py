@@ -553,3 +553,159 @@ def test_planted_adjoint_mistakes_fail_central_differences():
     undoubled = O.phi_linear_adjoint(K, O.synthesis_adjoint(2.0 * f * gbar, grid) * 0.5 + lin)
     for bad in (no_lin, undoubled):
         assert np.linalg.norm(bad - good) > 1e-3 * np.linalg.norm(good)
+
+
+# ---------------------------------------------------------------------------
+# Output maps: spin-2 functions and the Stokes I, Q, U synthesis
+# ---------------------------------------------------------------------------
+
+def _edth_numeric(f, s, m, h=1e-4):
+    """The spin raising operator on eta(theta) e^{i m phi} of spin weight s, by central
+    differences in theta: edth eta = -(sin th)^s (d_th - m / sin th)[(sin th)^(-s) eta]."""
+    def g(th):
+        u = lambda t: np.sin(t) ** (-s) * f(t)
+        d = (u(th + h) - u(th - h)) / (2 * h)
+        return -np.sin(th) ** s * (d - m / np.sin(th) * u(th))
+    return g
+
+
+def _edthbar_numeric(f, s, m, h=1e-4):
+    """The spin lowering operator: edthbar eta = -(sin th)^(-s) (d_th + m / sin th)[(sin th)^s eta]."""
+    def g(th):
+        u = lambda t: np.sin(t) ** s * f(t)
+        d = (u(th + h) - u(th - h)) / (2 * h)
+        return -np.sin(th) ** (-s) * (d + m / np.sin(th) * u(th))
+    return g
+
+
+def test_spin2_functions_follow_the_spin_operators():
+    """W +- X = +-2lam against N_l edth^2 Y and N_l edthbar^2 Y evaluated by finite differences
+    of scipy's Y_lm: pins the closed forms (signs, c_lm, the 1 / sin^2 terms) to the definition."""
+    sp = pytest.importorskip("scipy.special")
+    L = 7
+    g = O.Grid(L, 9, 16)
+    th = np.arccos(g.x)
+    for m in range(L + 1):
+        W, X = O.spin2_functions(m, g)
+        for l in range(max(m, 2), L + 1):
+            y = lambda t, l=l, m=m: sp.sph_harm_y(l, m, t, 0.0).real
+            nl = 1.0 / math.sqrt((l - 1) * l * (l + 1) * (l + 2))
+            p2 = nl * _edth_numeric(_edth_numeric(y, 0, m), 1, m)(th)
+            m2 = nl * _edthbar_numeric(_edthbar_numeric(y, 0, m), -1, m)(th)
+            scale = max(np.max(np.abs(p2)), np.max(np.abs(m2)), 1e-3)
+            assert np.max(np.abs(W[l - m] + X[l - m] - p2)) < 2e-6 * scale, (l, m)
+            assert np.max(np.abs(W[l - m] - X[l - m] - m2)) < 2e-6 * scale, (l, m)
+        assert np.all(W[: max(0, 2 - m)] == 0) and np.all(X[: max(0, 2 - m)] == 0)
+
+
+def test_spin2_y20_closed_form():
+    """2Y_20 = -2Y_20 = (1/4) sqrt(15 / (2 pi)) sin^2 theta (tabulated closed form)."""
+    g = O.Grid(4, 7, 13)
+    W, X = O.spin2_functions(0, g)
+    ref = 0.25 * math.sqrt(15 / (2 * math.pi)) * (1 - g.x ** 2)
+    assert np.max(np.abs(W[2] - ref)) < 1e-15 and np.max(np.abs(X[2])) == 0.0
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 5, 31])
+def test_spin2_functions_orthonormal_on_gl_grid(m):
+    """sum_j w_j 2 pi (+-2lam_l)(+-2lam_l') = delta_ll' for l, l' >= 2 (exact GL quadrature)."""
+    L = 40
+    g = O.Grid(L, L + 2, 2 * L + 2)
+    W, X = O.spin2_functions(m, g)
+    lo = max(0, 2 - m)
+    for F in (W + X, W - X):
+        F = F[lo:]
+        gram = 2 * math.pi * (F * g.w) @ F.T
+        assert np.max(np.abs(gram - np.eye(F.shape[0]))) < 1e-12
+
+
+def _random_eb(L, seed):
+    rng = np.random.default_rng(seed)
+    na = W.n_alm(L)
+    out = []
+    for _ in range(3):
+        a = rng.standard_normal(na) + 1j * rng.standard_normal(na)
+        a[: L + 1] = a[: L + 1].real
+        out.append(a)
+    ls, _ = W.alm_lm(L)
+    out[1][ls < 2] = 0.0  # E and B start at l = 2
+    out[2][ls < 2] = 0.0
+    return out
+
+
+@pytest.mark.parametrize("L,nt,nph", [(8, 13, 25), (24, 37, 75), (40, 41, 90)])
+def test_spin2_analysis_of_synthesis_is_identity(L, nt, nph):
+    aT, aE, aB = _random_eb(L, 5 + L)
+    g = O.Grid(L, nt, nph)
+    I, Q, U = O.maps_iqu(aT, aE, aB, g)
+    e, b = O.analysis_spin2(Q, U, g)
+    assert np.max(np.abs(e - aE)) < 1e-12 * np.max(np.abs(aE))
+    assert np.max(np.abs(b - aB)) < 1e-12 * np.max(np.abs(aB))
+    assert np.max(np.abs(I - O.synthesis(aT[:, None], g)[0])) == 0.0
+
+
+def test_spin2_parseval_and_eb_rotation():
+    """int (Q^2 + U^2) dOmega = sum over all m of |E|^2 + |B|^2 (from |a_{+-2}|^2), and the
+    exchange E -> -B, B -> E turns (Q, U) into (-U, Q) (a 45-degree rotation of the frame)."""
+    L = 24
+    aT, aE, aB = _random_eb(L, 2)
+    g = O.Grid(L, 40, 80)
+    I, Q, U = O.maps_iqu(aT, aE, aB, g)
+    integral = 2 * math.pi / g.nphi * np.sum(g.w[:, None] * (Q ** 2 + U ** 2))
+    _, ms = W.alm_lm(L)
+    wm = np.where(ms == 0, 1.0, 2.0)
+    assert abs(integral - np.sum(wm * (np.abs(aE) ** 2 + np.abs(aB) ** 2))) < 1e-11 * integral
+    I2, Q2, U2 = O.maps_iqu(aT, -aB, aE, g)
+    assert np.max(np.abs(Q2 + U)) < 1e-12 * np.max(np.abs(U)) and np.max(np.abs(U2 - Q)) < 1e-12 * np.max(np.abs(Q))
+
+
+def test_pure_e_monopole_like_mode_has_no_u():
+    """a^E_20 = 1 alone: Q = -(1/4) sqrt(15 / (2 pi)) sin^2 theta on every ring and U = 0."""
+    L = 6
+    g = O.Grid(L, 10, 19)
+    aE = np.zeros(W.n_alm(L), complex)
+    aE[W.alm_index(2, 0, L)] = 1.0
+    I, Q, U = O.maps_iqu(np.zeros_like(aE), aE, None, g)
+    ref = -0.25 * math.sqrt(15 / (2 * math.pi)) * (1 - g.x ** 2)
+    assert np.max(np.abs(Q - ref[:, None])) < 1e-15 and np.max(np.abs(U)) < 1e-15 and np.max(np.abs(I)) == 0
+
+
+def test_planted_spin2_mistakes_are_caught():
+    """A flipped X, a dropped lam_{l-1} term or a swapped E/B convention in the maps each fail
+    the pins above (checked here on the CPU by recomputing them with the mistake planted)."""
+    sp = pytest.importorskip("scipy.special")
+    g = O.Grid(6, 8, 15)
+    th = np.arccos(g.x)
+    good = O.spin2_functions
+
+    def flipped_x(m, grid):
+        Wm, Xm = good(m, grid)
+        return Wm, -Xm
+
+    def dropped_prev(m, grid):
+        Wm, Xm = good(m, grid)
+        lam = grid.lam(m)
+        ls = np.arange(m, grid.lmax + 1, dtype=float)[:, None]
+        nl = np.where(ls >= 2, 1 / np.sqrt(np.maximum((ls - 1) * ls * (ls + 1) * (ls + 2), 1)), 0)
+        s2 = 1 - grid.x ** 2
+        return nl * ((2.0 * m * m - 2 * ls * grid.x ** 2) * lam / s2 - ls * (ls + 1) * lam), Xm
+
+    def edth_error(fn):
+        err = 0.0
+        for m in range(1, 4):
+            Wm, Xm = fn(m, g)
+            for l in range(max(m, 2), 7):
+                y = lambda t, l=l, m=m: sp.sph_harm_y(l, m, t, 0.0).real
+                nl = 1.0 / math.sqrt((l - 1) * l * (l + 1) * (l + 2))
+                p2 = nl * _edth_numeric(_edth_numeric(y, 0, m), 1, m)(th)
+                err = max(err, np.max(np.abs(Wm[l - m] + Xm[l - m] - p2)))
+        return err
+
+    assert edth_error(good) < 1e-6
+    assert edth_error(flipped_x) > 1e-3
+    assert edth_error(dropped_prev) > 1e-3
+    # swapping the E/B convention (Q + iU = +sum (E + iB) 2Y) breaks the closed form of 2Y_20's Q
+    aE = np.zeros(W.n_alm(6), complex)
+    aE[W.alm_index(2, 0, 6)] = 1.0
+    Q = O.maps_iqu(np.zeros_like(aE), -aE, None, g)[1]
+    assert np.max(np.abs(Q + 0.25 * math.sqrt(15 / (2 * math.pi)) * (1 - g.x ** 2)[:, None])) > 1e-2
