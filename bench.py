@@ -318,6 +318,35 @@ def measure_adjoint(F, device: int, reps: int = 3) -> dict:
     return res
 
 
+def measure_maps(F, sh, out, device: int, reps: int = 5) -> dict:
+    """Stokes I, Q, U maps (fnl_maps) of the timed object's last a^T, a^E (zero B modes, as
+    the paper's maps): tables prepared once (untimed), then `reps` calls timed with events.
+    The bound is HBM: one pass over the lambda, W and X tables (nalm x npj entries each in the
+    object's real type) per call; the three ring FFTs are a few per cent of the call."""
+    import torch
+    t0 = time.perf_counter()
+    sh.maps_prepare()
+    prep = time.perf_counter() - t0
+    maps = sh.maps(out["aT"], out["aE"])
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sh.maps(out["aT"], out["aE"], out=maps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    real_bytes = 8 if sh.prec == F.FNL_FP64 else 4
+    npj = ((sh.ntheta + 1) // 2 + 31) // 32 * 32
+    table_bytes = 3 * sh.nalm * npj * real_bytes
+    pk, pk_kind = peaks()
+    return {"ms": ms, "prepare_s": prep, "table_bytes": table_bytes, "maps_per_s": 1e3 / ms,
+            "roofline": {"bound": "hbm", "achieved": table_bytes / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": table_bytes / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                         "peak_source": f"HBM copy ({pk_kind}); whole fnl_maps call timed"}}
+
+
 # ---------------------------------------------------------------------------------------
 # replicas over realisations (one process per GPU): the only cross-rank logic of the path
 # ---------------------------------------------------------------------------------------
@@ -367,6 +396,7 @@ def main():
                     help="timed steps of the FP64 comparator beside a mixed run (0: skip it)")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-maps", action="store_true", help="skip the Stokes-maps measurement")
     ap.add_argument("--tiles", default="auto",
                     help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
@@ -475,6 +505,7 @@ def main():
         d64.close()
         del d64, out64, ref, b
 
+    maps = None if args.no_maps else measure_maps(F, sh, out, local)
     batch = None if args.no_batch or args.prec not in ("bf16x2", "bf16x3") else measure_batch(F, args.prec, local)
     adjoint = None if args.no_adjoint else measure_adjoint(F, local)
 
@@ -557,6 +588,8 @@ def main():
         line["batch"] = batch
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if maps is not None:
+        line["maps"] = maps
     if fp64 is not None:
         line["fp64"] = fp64
         line["speedup_vs_fp64"] = value / fp64["value"]

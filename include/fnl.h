@@ -176,6 +176,29 @@ fnl_status fnl_accumulate(const fnl_shells* sh, const double* phiL, const double
                           double fnl, double* aT, double* aE, double* aLT, double* aLE,
                           double* aNLT, double* aNLE, void* stream);
 
+/* ---- output maps: Stokes I, Q, U of one realisation (Sect. 4) ----------------------- */
+
+/* Tables of the map synthesis: lambda_lm, W_lm and X_lm on the northern rings of the
+ * object's grid, in the object's real type (FP64 for FNL_FP64, FP32 otherwise), computed
+ * in FP64 on the device; W = (2lam + (-2)lam) / 2 and X = (2lam - (-2)lam) / 2, where
+ * +-2Y_lm = +-2lam_lm(theta) e^{i m phi} are the spin-2 harmonics obtained from Y_lm with the
+ * spin raising and lowering operators.  Allocates three tables of the size of the SIMT
+ * Legendre table plus a [2 (lmax+1)][npairs][6] scratch (owned by the object, freed with
+ * it), and synchronises the device.  Idempotent. */
+fnl_status fnl_maps_prepare(fnl_shells* sh);
+
+/* Stokes maps of one set of coefficients (needs fnl_maps_prepare; no allocation):
+ *   I = sum_lm aT_lm Y_lm,   Q +- iU = sum_lm a_{+-2,lm} +-2Y_lm,   a_{+-2,lm} = -(aE_lm +- i aB_lm)
+ * (the sign convention of HEALPix, whose I, Q, U maps the paper produces).
+ *  aT, aE: device [nalm][2]; aB: device [nalm][2] or NULL (zero B modes, as the paper's
+ *      maps have); the imaginary part of every m = 0 entry is ignored.
+ *  maps: device [3][ntheta][nphi] double, (I, Q, U) on the object's ring grid.
+ * One pass over the tables per call (one thread per ring pair and m, sums in the real type),
+ * then one ring FFT per field.  FNL_EINVAL before fnl_maps_prepare or for a NULL aT, aE or
+ * maps. */
+fnl_status fnl_maps(const fnl_shells* sh, const double* aT, const double* aE, const double* aB, double* maps,
+                    void* stream);
+
 /* Wait for all work on the object's device, then report FNL_ETIMEOUT if a bounded wait
  * inside a tensor-core kernel expired since the last call (the kernels record it in a
  * device word instead of hanging), else FNL_OK.  Clears the word. */

@@ -352,6 +352,8 @@ fnl_shells* clone_scratch(const fnl_shells* src) {
   c->ring.clear();
   c->ring_slots = c->ring_head = c->ring_count = 0;
   c->owner = src->owner ? src->owner : src;
+  c->maps_ready = false;
+  c->d_mapL = c->d_mapW = c->d_mapX = c->d_Fiqu = nullptr;
   try {
     typedef unsigned short bf16_t;
     const int L = c->lmax, nr = c->nr, np = c->npairs, nmp = 2 * (L + 1), T = c->nterms, Cpad = c->Cpad;
@@ -707,6 +709,29 @@ fnl_status fnl_synth(const fnl_shells* sh, const double* alm, double* maps, void
       launch_synth_gemm(sh, st);
     }
     launch_ring_fft(sh, FFT_SYNTH_MAP, nullptr, maps, st);
+  });
+}
+
+fnl_status fnl_maps_prepare(fnl_shells* sh) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(!sh->owner, "fnl_maps_prepare: not on a scratch clone");
+    DeviceScope scope(sh->device);
+    maps_prepare(sh);
+  });
+}
+
+fnl_status fnl_maps(const fnl_shells* sh, const double* aT, const double* aE, const double* aB, double* maps,
+                    void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(sh->maps_ready, "fnl_maps: call fnl_maps_prepare first");
+    DeviceScope scope(sh->device);
+    check_dev_ptr(aT, "aT", false);
+    check_dev_ptr(aE, "aE", false);
+    check_dev_ptr(aB, "aB", true);
+    check_dev_ptr(maps, "maps", false);
+    launch_maps(sh, aT, aE, aB, maps, (cudaStream_t)stream);
   });
 }
 

@@ -174,6 +174,14 @@ struct fnl_shells {
   int tiles_version = 0;           // incremented whenever the tile shape changes
   const fnl_shells* owner = nullptr;  // set on scratch clones: the object whose tables they use
 
+  // Stokes maps (fnl_maps): lambda, W, X in the SIMT table layout (real type) and the ring
+  // sums F [2(L+1)][npairs][6] of I, Q, U; allocated by fnl_maps_prepare
+  bool maps_ready = false;
+  void* d_mapL = nullptr;
+  void* d_mapW = nullptr;
+  void* d_mapX = nullptr;
+  void* d_Fiqu = nullptr;
+
   // SIMT tile lists
   fnl::Tile* d_tiles_syn = nullptr;
   int n_tiles_syn = 0;
@@ -239,6 +247,13 @@ void launch_quadrature(const fnl_shells* sh, const double* phi_api, int from_int
 void launch_combine(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE,
                     const double* aNLT, const double* aNLE, double* aT, double* aE,
                     cudaStream_t st);
+// Ring synthesis of nf complex fields F [2(L+1)][npairs][2 nf] (problem 2 m + parity; the
+// odd problem of m = L included) into maps [nf][ntheta][nphi].
+void launch_ring_synth_fields(const fnl_shells* sh, const void* F, int nf, double* maps, cudaStream_t st);
+// Stokes maps (maps.cu): tables once, then I, Q, U of one set of a_lm.
+void maps_prepare(fnl_shells* sh);
+void launch_maps(const fnl_shells* sh, const double* aT, const double* aE, const double* aB, double* maps,
+                 cudaStream_t st);
 void launch_lambda_mm(const double* x, const double* fac, int npairs, int L, double* mant, int* expo,
                       cudaStream_t st);
 

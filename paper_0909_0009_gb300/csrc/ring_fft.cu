@@ -259,6 +259,7 @@ struct FftArgs {
   int L, nr, ntheta, npairs, C;  // C: column count of a row of F and G
   int64_t sp, sj;                // element strides of F and G between problems mp and ring pairs jp
   int nterms;                    // 0: G in the real type T; 2 or 3: G as BF16 terms in GT
+  int odd_top;                   // 1: problem 2 L + 1 holds data (field synthesis); 0: it is empty
   int64_t gt_stride;             // elements between BF16 terms
   __nv_bfloat16* GT;
   FftPlan plan;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
       const T* e = a.F + (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
       const T* o = a.F + (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
       const cplx<T> E = {e[0], e[1]};
-      const cplx<T> O = (m < L) ? cplx<T>{o[0], o[1]} : cplx<T>{(T)0, (T)0};
+      const cplx<T> O = (m < L || a.odd_top) ? cplx<T>{o[0], o[1]} : cplx<T>{(T)0, (T)0};
       const cplx<T> FN = cadd(E, O), FS = csub(E, O);
       if (m == 0) {
         b0[0] = {FN.x, FS.x};
@@ -585,7 +586,7 @@ bool plan_fits_group(const FftPlan&, int) { return true; }
 template <typename T>
 void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
   if (std::is_same<T, float>::value && mode == FFT_SQUARE && launch_ring_square(sh, st)) return;
-  FftArgs<T> a;
+  FftArgs<T> a{};
   a.L = sh->lmax;
   a.nr = sh->nr;
   a.ntheta = sh->ntheta;
@@ -695,6 +696,36 @@ void launch_ring_product(const fnl_shells* sh, cudaStream_t st) {
 void launch_ring_fft(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
   if (sh->real_is_double) fft_impl<double>(sh, mode, maps_in, maps_out, st);
   else fft_impl<float>(sh, mode, maps_in, maps_out, st);
+}
+
+template <typename T>
+void synth_fields_impl(const fnl_shells* sh, const void* F, int nf, double* maps, cudaStream_t st) {
+  FftArgs<T> a{};
+  a.L = sh->lmax;
+  a.nr = nf;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.C = 2 * nf;
+  a.sp = (int64_t)sh->npairs * a.C;
+  a.sj = a.C;
+  a.odd_top = 1;
+  a.plan = sh->fft;
+  a.tw = (const cplx<T>*)sh->d_tw;
+  a.twp = (const cplx<T>*)sh->d_twp;
+  a.F = (const T*)F;
+  a.mu = sh->d_mu;
+  a.wgl = sh->d_wgl;
+  a.maps_out = maps;
+  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)sh->nphi;
+  if (smem > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "nphi too large for the field synthesis");
+  FNL_CUDA(cudaFuncSetAttribute(k_ring_fft<T, FFT_SYNTH_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_ring_fft<T, FFT_SYNTH_MAP><<<dim3(nf, sh->npairs), sh->nphi >= 1024 ? 256 : 128, smem, st>>>(a);
+  FNL_CUDA(cudaGetLastError());
+}
+
+void launch_ring_synth_fields(const fnl_shells* sh, const void* F, int nf, double* maps, cudaStream_t st) {
+  if (sh->real_is_double) synth_fields_impl<double>(sh, F, nf, maps, st);
+  else synth_fields_impl<float>(sh, F, nf, maps, st);
 }
 
 }  // namespace fnl

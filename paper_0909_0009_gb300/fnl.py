@@ -28,6 +28,7 @@ EXPORTS = [
     "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
     "fnl_accumulate_noalloc", "fnl_generate_backward", "fnl_batch_create", "fnl_batch_destroy",
     "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
+    "fnl_maps_prepare", "fnl_maps",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -94,6 +95,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_shells_autotune.argtypes = [vp, vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.fnl_shells_set_tiles.argtypes = [vp, i, i]
     lib.fnl_batch_tiles.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.fnl_maps_prepare.argtypes = [vp]
+    lib.fnl_maps.argtypes = [vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -317,6 +320,22 @@ class Shells:
         assert phiL.dtype == torch.complex128 and phiL.is_contiguous() and phiL.shape == (self.nalm, self.nr)
         out = self._alm(self.nr)
         _check(_lib.fnl_square(self.handle, _ptr(phiL), _ptr(out), _stream(stream)))
+        return out
+
+    def maps_prepare(self):
+        """Spin-0 and spin-2 tables of the Stokes maps (fnl_maps_prepare; synchronous, allocates)."""
+        _check(_lib.fnl_maps_prepare(self.handle))
+
+    def maps(self, aT, aE, aB=None, out=None, stream=None):
+        """Stokes maps [3, ntheta, nphi] = (I, Q, U) of aT, aE and aB (complex128 [nalm] on the
+        device; aB None for zero B modes) on the object's grid (fnl_maps)."""
+        torch = _torch()
+        for a in (aT, aE) + ((aB,) if aB is not None else ()):
+            assert a.dtype == torch.complex128 and a.is_contiguous() and a.shape == (self.nalm,)
+        if out is None:
+            out = torch.empty((3, self.ntheta, self.nphi), dtype=torch.float64, device=aT.device)
+        assert out.dtype == torch.float64 and out.is_contiguous() and out.shape == (3, self.ntheta, self.nphi)
+        _check(_lib.fnl_maps(self.handle, _ptr(aT), _ptr(aE), _ptr(aB), _ptr(out), _stream(stream)))
         return out
 
     def accumulate(self, phiL=None, phiNL=None, fnl: float = 0.0, stream=None) -> dict:
