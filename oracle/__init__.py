@@ -4,6 +4,8 @@ This package is test infrastructure, not part of the product: only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and reference legs
 may import it.  It shares no code with the CUDA library and never imports it.
 
-Parity status of each function is stated in ``oracle/fnl_oracle.py``.
+Parity status of each function is stated in ``oracle/fnl_oracle.py`` (the generator, its
+adjoint and the output maps) and ``oracle/ksw_oracle.py`` (the cubic estimator).
 """
 from .fnl_oracle import *  # noqa: F401,F403
+from .ksw_oracle import *  # noqa: F401,F403
