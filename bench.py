@@ -347,6 +347,32 @@ def measure_maps(F, sh, out, device: int, reps: int = 5) -> dict:
                          "peak_source": f"HBM copy ({pk_kind}); whole fnl_maps call timed"}}
 
 
+def measure_ksw(F, sh, out, device: int, reps: int = 5) -> dict:
+    """The cubic estimator (Sect. 5) on the timed configuration: set-up (weights, FP64
+    normalisation summed over l1 <= l2 <= l3), then `reps` calls of fnl_ksw_statistic on the
+    last generated sky timed with events, and its f_NL estimate against the input."""
+    import torch
+    t0 = time.perf_counter()
+    k = F.Ksw(sh)
+    setup_s = time.perf_counter() - t0
+    s = k.statistic(out["aT"], out["aE"])
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        k.statistic(out["aT"], out["aE"], out=s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res = {"ms": ms, "estimates_per_s": 1e3 / ms, "setup_s": setup_s, "norm_s": k.norm_seconds,
+           "norm": k.norm, "sigma_fnl": 1.0 / math.sqrt(k.norm) if k.norm > 0 else None,
+           "fnl_estimate": float(s.item()) / k.norm if k.norm > 0 else None,
+           "note": "one sky: synthesis of A and B on every shell (2 N_r fields), ring cubic sums, reduction"}
+    k.close()
+    return res
+
+
 # ---------------------------------------------------------------------------------------
 # replicas over realisations (one process per GPU): the only cross-rank logic of the path
 # ---------------------------------------------------------------------------------------
@@ -397,6 +423,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-maps", action="store_true", help="skip the Stokes-maps measurement")
+    ap.add_argument("--no-ksw", action="store_true", help="skip the cubic-estimator measurement")
     ap.add_argument("--tiles", default="auto",
                     help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
@@ -506,6 +533,7 @@ def main():
         del d64, out64, ref, b
 
     maps = None if args.no_maps else measure_maps(F, sh, out, local)
+    ksw = None if args.no_ksw else measure_ksw(F, sh, out, local)
     batch = None if args.no_batch or args.prec not in ("bf16x2", "bf16x3") else measure_batch(F, args.prec, local)
     adjoint = None if args.no_adjoint else measure_adjoint(F, local)
 
@@ -590,6 +618,9 @@ def main():
         line["adjoint"] = adjoint
     if maps is not None:
         line["maps"] = maps
+    if ksw is not None:
+        ksw["fnl_input"] = fnl
+        line["ksw"] = ksw
     if fp64 is not None:
         line["fp64"] = fp64
         line["speedup_vs_fp64"] = value / fp64["value"]

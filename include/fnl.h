@@ -199,6 +199,39 @@ fnl_status fnl_maps_prepare(fnl_shells* sh);
 fnl_status fnl_maps(const fnl_shells* sh, const double* aT, const double* aE, const double* aB, double* maps,
                     void* stream);
 
+/* ---- the fast cubic f_NL estimator (Sect. 5) ------------------------------------------ */
+
+typedef struct fnl_ksw fnl_ksw; /* opaque: weights, normalisation, a synthesis object of 2 nr fields */
+
+/* Estimator for the configuration of `sh` (its l_max, ring grid, radial nodes r_i, weights
+ * w_i, transfer kernels alpha^X_l and filters K_l; same precision form).  Sect. 5 defines
+ *   A(r, n) = sum_{i,j in T,E} sum_lm (C^-1)^{ij}_l alpha^i_l(r) a^j_lm Y_lm(n),  B likewise with beta,
+ *   S_prim  = int dr r^2 int d^2n A B^2,  and f_NL = S_prim / N with
+ *   N = sum_{l1<=l2<=l3} (1/Delta) B^{ijk} (C^-1)^{io}_l1 (C^-1)^{jp}_l2 (C^-1)^{kq}_l3 B^{opq},
+ *   B^{ijk} = 2 I_{l1l2l3} int dr r^2 [beta^i_l1 beta^j_l2 alpha^k_l3 + 2 more terms, alpha on each leg],
+ *   I_{l1l2l3} = sqrt((2l1+1)(2l2+1)(2l3+1)/(4 pi)) (l1 l2 l3; 0 0 0),  Delta = 6, 2 or 1.
+ * On the shells: int dr r^2 = sum_i w_i r_i^2; beta^X_l(r_i) = (K_l K_l^T q^X_l)_i with
+ * q^X_l[i] = w_i r_i^2 alpha^X_l(r_i) (the covariance of Phi_L(r_i) and a^X_L, the discrete form of
+ * the paper's beta); C^XY_l = (K_l^T q^X_l).(K_l^T q^Y_l), the covariance of a^T_L, a^E_L;
+ * C^-1 the Moore-Penrose inverse (full inverse if the smaller eigenvalue exceeds 1e-10 of the
+ * larger, else v v^T / lambda of the leading eigenpair); degrees l < 2 left out.
+ * N is summed here in FP64 over all l1 <= l2 <= l3 (synchronous; a fraction of a second at
+ * l_max 1024).  Needs 3 n_phi complex values of the object's real type in shared memory
+ * (FNL_EINVAL above 227 KB).  Allocates device memory (a second set of synthesis scratch for
+ * 2 nr fields); `sh` must outlive the estimator. */
+fnl_status fnl_ksw_create(const fnl_shells* sh, fnl_ksw** out);
+void fnl_ksw_destroy(fnl_ksw* k);
+
+/* norm: N (host double, may be NULL); norm_seconds: device time of its sum (may be NULL);
+ * rank: host [lmax+1] rank of C_l used, 0 for l < 2 (may be NULL). */
+fnl_status fnl_ksw_info(const fnl_ksw* k, double* norm, double* norm_seconds, int* rank);
+
+/* S_prim of one sky (no allocation, asynchronous on `stream`): aT, aE device [nalm][2]
+ * (imaginary part of m = 0 ignored); S device double.  The sphere integral is the grid's
+ * Gauss-Legendre x rectangle rule, exact for the cubic when ntheta >= (3 lmax + 2) / 2 and
+ * nphi >= 3 lmax + 1.  The f_NL estimate is S / N. */
+fnl_status fnl_ksw_statistic(const fnl_ksw* k, const double* aT, const double* aE, double* S, void* stream);
+
 /* Wait for all work on the object's device, then report FNL_ETIMEOUT if a bounded wait
  * inside a tensor-core kernel expired since the last call (the kernels record it in a
  * device word instead of hanging), else FNL_OK.  Clears the word. */

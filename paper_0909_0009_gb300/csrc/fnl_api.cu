@@ -103,17 +103,17 @@ void free_shells(fnl_shells* sh) {
   delete sh;
 }
 
-void validate_desc(const fnl_shell_desc* d) {
+void validate_desc(const fnl_shell_desc* d, bool synth_only = false) {
   FNL_REQUIRE(d, "desc is NULL");
   FNL_REQUIRE(d->lmax >= 1 && d->lmax <= 4096, "lmax must be in [1, 4096]");
-  FNL_REQUIRE(d->nr >= 1 && d->nr <= 128, "nr must be in [1, 128]");
+  FNL_REQUIRE(d->nr >= 1 && d->nr <= (synth_only ? 256 : 128), "nr must be in [1, 128]");
   FNL_REQUIRE(d->ntheta >= d->lmax + 1, "ntheta must be >= lmax + 1");
   FNL_REQUIRE(d->nphi >= 2 * d->lmax + 2, "nphi must be >= 2 lmax + 2");
   FNL_REQUIRE(smooth235(d->nphi), "nphi must be 2/3/5-smooth");
   FNL_REQUIRE(d->r && d->w, "r and w must not be NULL");
   FNL_REQUIRE(d->alphaT && d->alphaE, "alphaT and alphaE must not be NULL");
   FNL_REQUIRE(d->prec >= FNL_FP64 && d->prec <= FNL_BF16X3, "unknown precision");
-  if (!d->K) {
+  if (!d->K && !synth_only) {
     FNL_REQUIRE(d->nk >= 2, "nk must be >= 2");
     FNL_REQUIRE(d->kmin > 0 && d->kmax > d->kmin, "need 0 < kmin < kmax");
     FNL_REQUIRE(d->A > 0 && std::isfinite(d->ns), "need A > 0 and finite ns");
@@ -403,6 +403,10 @@ void destroy_clone(fnl_shells* c) {
   if (c) free_shells(c);
 }
 
+void release_shells(fnl_shells* sh) {
+  if (sh) free_shells(sh);
+}
+
 namespace {
 
 void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st) {
@@ -413,6 +417,11 @@ void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_o
 }
 
 }  // namespace
+
+void launch_synthesis_gemm(const fnl_shells* sh, cudaStream_t st) {
+  if (sh->nterms) launch_tc(sh, sh->tc_syn, TC_SYNTH, nullptr, st);
+  else launch_synth_gemm(sh, st);
+}
 }  // namespace fnl
 
 using namespace fnl;
@@ -454,7 +463,20 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
   fnl_status st = guard([&] {
     FNL_REQUIRE(out, "out must not be NULL");
     *out = nullptr;
-    validate_desc(d);
+    sh = make_shells_core(d, device, false);
+    *out = sh;
+  });
+  return st;
+}
+
+}  // extern "C"
+
+namespace fnl {
+
+fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only) {
+  fnl_shells* sh = nullptr;
+  try {
+    validate_desc(d, synth_only);
     const bool mixed = (d->prec == FNL_BF16X2 || d->prec == FNL_BF16X3);
     int ndev = 0;
     FNL_CUDA(cudaGetDeviceCount(&ndev));
@@ -524,9 +546,11 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
     sh->wgl.assign(wg.begin(), wg.begin() + np);
 
     // ---- filters K_l (Eq. 9)
-    const size_t kk = (size_t)(L + 1) * nr * nr;
+    const size_t kk = synth_only ? 0 : (size_t)(L + 1) * nr * nr;
     std::vector<double> Kf(kk);
-    if (d->K) {
+    if (synth_only) {
+      // a synthesis-only object (internal): no filters, mu, q or v
+    } else if (d->K) {
       for (int l = 0; l <= L; ++l)
         for (int i = 0; i < nr; ++i)
           for (int j = 0; j < nr; ++j)
@@ -540,7 +564,8 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
 
     // ---- mu (Eq. 2), q^X and v^X (Eq. 5)
     sh->mu.assign(nr, 0.0);
-    if (d->mu) {
+    if (synth_only) {
+    } else if (d->mu) {
       for (int i = 0; i < nr; ++i) sh->mu[i] = d->mu[i];
     } else {
       for (int l = 0; l <= L; ++l)
@@ -557,7 +582,7 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
         qT[(size_t)l * nr + i] = f * d->alphaT[(size_t)l * nr + i];
         qE[(size_t)l * nr + i] = f * d->alphaE[(size_t)l * nr + i];
       }
-    for (int l = 0; l <= L; ++l)
+    for (int l = 0; l <= (synth_only ? -1 : L); ++l)
       for (int i = 0; i < nr; ++i)
         for (int j = 0; j <= i; ++j) {
           const double k = Kf[((size_t)l * nr + i) * nr + j];
@@ -643,11 +668,26 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
       setup_mixed(sh, qT, qE);
     }
     FNL_CUDA(cudaDeviceSynchronize());
-    *out = sh;
-  });
-  if (st != FNL_OK && sh) free_shells(sh);
-  return st;
+    auto hs = std::make_shared<HostSetup>();
+    hs->K = std::move(Kf);
+    hs->r.assign(d->r, d->r + nr);
+    hs->w.assign(d->w, d->w + nr);
+    hs->alphaT.assign(d->alphaT, d->alphaT + (size_t)(L + 1) * nr);
+    hs->alphaE.assign(d->alphaE, d->alphaE + (size_t)(L + 1) * nr);
+    hs->vT = std::move(vT);
+    hs->vE = std::move(vE);
+    sh->host = hs;
+    sh->synth_only = synth_only;
+  } catch (...) {
+    if (sh) free_shells(sh);
+    throw;
+  }
+  return sh;
 }
+
+}  // namespace fnl
+
+extern "C" {
 
 void fnl_shells_destroy(fnl_shells* sh) {
   if (!sh) return;

@@ -16,6 +16,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <functional>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -83,6 +84,13 @@ struct Tile {
 
 // ---- the shells object ---------------------------------------------------------------
 
+// Host copies of a shells object's set-up data in FP64 (shared by its scratch clones):
+// K_l [L+1][nr][nr] (lower; empty for a synthesis-only object), r, w [nr], alpha^T, alpha^E
+// [L+1][nr] and v^X_l = K_l^T q^X_l [L+1][nr].
+struct HostSetup {
+  std::vector<double> K, r, w, alphaT, alphaE, vT, vE;
+};
+
 struct DeviceBuffer {
   void* p = nullptr;
   size_t bytes = 0;
@@ -98,6 +106,9 @@ struct fnl_shells {
   bool real_is_double = true;  // SIMT real type: double (FP64) or float (FP32 and mixed)
   size_t device_bytes = 0;
   std::vector<void*> allocations;
+
+  std::shared_ptr<const fnl::HostSetup> host;
+  bool synth_only = false;     // internal object without filters (the estimator's synthesis)
 
   // problem geometry
   std::vector<int> K;          // [2(L+1)]
@@ -218,6 +229,13 @@ fnl_shells* clone_scratch(const fnl_shells* src);
 void refresh_clone(fnl_shells* c, const fnl_shells* src);
 void destroy_clone(fnl_shells* c);
 void build_tc_inst_a(fnl_shells* sh);
+// fnl_make_shells; with synth_only, an object without filters (K, mu, q and v zero) of up to
+// 256 fields, used for the synthesis of other fields (the estimator's A and B maps).
+fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only);
+// Frees an object made by make_shells_core (its device memory and the object).
+void release_shells(fnl_shells* sh);
+// Step (ii) Legendre GEMM of the object's own Phi rows (tensor-core or SIMT form) into F.
+void launch_synthesis_gemm(const fnl_shells* sh, cudaStream_t st);
 void build_tc_inst_b(fnl_shells* sh);
 
 // ---- host set-up (setup_host.cpp) -------------------------------------------------------
@@ -250,6 +268,12 @@ void launch_combine(const fnl_shells* sh, double fnl, const double* aLT, const d
 // Ring synthesis of nf complex fields F [2(L+1)][npairs][2 nf] (problem 2 m + parity; the
 // odd problem of m = L included) into maps [nf][ntheta][nphi].
 void launch_ring_synth_fields(const fnl_shells* sh, const void* F, int nf, double* maps, cudaStream_t st);
+// Estimator rings (ring_fft.cu): fields 0..nsh-1 (A) and nsh..2nsh-1 (B) of the object's F;
+// part [nsh][npairs] = w^GL_j sum_k A B^2 on ring pair j (both rings).
+void launch_ring_cubic(const fnl_shells* sh, int nsh, double* part, cudaStream_t st);
+// The same with the specialised ring kernel of the tensor-core forms (ring_square.cu); false if
+// the object's ring length has none.
+bool launch_ring_cubic_sq(const fnl_shells* sh, int nsh, double* part, cudaStream_t st);
 // Stokes maps (maps.cu): tables once, then I, Q, U of one set of a_lm.
 void maps_prepare(fnl_shells* sh);
 void launch_maps(const fnl_shells* sh, const double* aT, const double* aE, const double* aB, double* maps,

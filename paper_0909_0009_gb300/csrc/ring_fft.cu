@@ -433,6 +433,62 @@ __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
   }
 }
 
+// Estimator rings: per (shell s, ring pair jp) the maps A (columns 2s, 2s + 1 of F) and B
+// (columns 2 (nsh + s), + 1) on the north and south rings (inverse DFTs as in the square), then
+// sum_k A B^2 on each ring (the equator once), times the ring's Gauss-Legendre weight, into
+// part[s][jp] (FP64 sums).
+template <typename T>
+__device__ __forceinline__ void pack_rings(const FftArgs<T>& a, int jp, int col, cplx<T>* b) {
+  const int N = a.plan.n, L = a.L;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) b[k] = {(T)0, (T)0};
+  __syncthreads();
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const T* e = a.F + (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + col;
+    const T* o = a.F + (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + col;
+    const cplx<T> E = {e[0], e[1]};
+    const cplx<T> O = (m < L) ? cplx<T>{o[0], o[1]} : cplx<T>{(T)0, (T)0};
+    const cplx<T> FN = cadd(E, O), FS = csub(E, O);
+    if (m == 0) {
+      b[0] = {FN.x, FS.x};
+    } else {
+      b[m] = {FN.x - FS.y, FN.y + FS.x};
+      b[N - m] = {FN.x + FS.y, FS.x - FN.y};
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ring_cubic(const FftArgs<T> a, int nsh, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  const int N = a.plan.n;
+  cplx<T>* b0 = (cplx<T>*)smem;
+  cplx<T>* b1 = b0 + N;
+  cplx<T>* b2 = b1 + N;
+  const int s = blockIdx.x, jp = blockIdx.y;
+  const bool equator = (a.ntheta - 1 - jp == jp);
+  pack_rings(a, jp, 2 * s, b0);
+  const cplx<T>* A = stockham(b0, b1, a.plan, a.tw, (T)1);
+  cplx<T>* x = (A == b0) ? b1 : b0;
+  pack_rings(a, jp, 2 * (nsh + s), x);
+  const cplx<T>* B = stockham(x, b2, a.plan, a.tw, (T)1);
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const cplx<T> av = A[k], bv = B[k];
+    acc += (double)av.x * (double)bv.x * (double)bv.x;
+    if (!equator) acc += (double)av.y * (double)bv.y * (double)bv.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[(size_t)s * a.npairs + jp] = t * a.wgl[jp];
+  }
+}
+
 // Group variant: block (group of shells, ring pair); the group's rows of F are staged in
 // shared memory with vector loads, every shell then runs through one in-place N-point
 // buffer, its results (S, D per order m) overwrite its staged F values, and the group's
@@ -726,6 +782,38 @@ void synth_fields_impl(const fnl_shells* sh, const void* F, int nf, double* maps
 void launch_ring_synth_fields(const fnl_shells* sh, const void* F, int nf, double* maps, cudaStream_t st) {
   if (sh->real_is_double) synth_fields_impl<double>(sh, F, nf, maps, st);
   else synth_fields_impl<float>(sh, F, nf, maps, st);
+}
+
+template <typename T>
+void ring_cubic_impl(const fnl_shells* sh, int nsh, double* part, cudaStream_t st) {
+  FftArgs<T> a{};
+  a.L = sh->lmax;
+  a.nr = sh->nr;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.C = sh->nterms ? sh->Cpad : sh->C;
+  if (sh->nterms) {
+    a.sp = sh->Cpad;
+    a.sj = (int64_t)2 * (sh->lmax + 1) * sh->Cpad;
+  } else {
+    a.sp = (int64_t)sh->npairs * sh->C;
+    a.sj = sh->C;
+  }
+  a.plan = sh->fft;
+  a.tw = (const cplx<T>*)sh->d_tw;
+  a.twp = (const cplx<T>*)sh->d_twp;
+  a.F = (const T*)sh->d_F;
+  a.wgl = sh->d_wgl;
+  const size_t smem = 3 * sizeof(cplx<T>) * (size_t)sh->nphi;
+  if (smem > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "nphi too large for the estimator's ring kernel");
+  FNL_CUDA(cudaFuncSetAttribute(k_ring_cubic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_ring_cubic<T><<<dim3(nsh, sh->npairs), 256, smem, st>>>(a, nsh, part);
+  FNL_CUDA(cudaGetLastError());
+}
+
+void launch_ring_cubic(const fnl_shells* sh, int nsh, double* part, cudaStream_t st) {
+  if (sh->real_is_double) ring_cubic_impl<double>(sh, nsh, part, st);
+  else ring_cubic_impl<float>(sh, nsh, part, st);
 }
 
 }  // namespace fnl

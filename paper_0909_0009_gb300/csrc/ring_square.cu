@@ -461,6 +461,156 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1)
   cp_async_wait_all();
 }
 
+// Rings of the cubic estimator (Sect. 5): work item = (ring pair, G / 2 shells).  Groups
+// 0 .. G/2 - 1 hold the A spectra of the item's shells (columns 2 s of F), groups G/2 .. G - 1
+// their B spectra (columns 2 (nsh + s)).  Phases 1a, 1b and the inverse half of phase 2 run as
+// in the square and leave every field's ring values in its buffer, in the same permuted order;
+// then the A group of each shell sums A B^2 over the ring pair (north rings in x, south in y,
+// the equator once; FP32 products, FP64 sums) and writes the GL weight times the sum to
+// part[s][jp].
+struct CubeArgs {
+  int L, nsh, ntheta, npairs;
+  int64_t sp, sj;      // F strides between problems mp and ring pairs jp (floats)
+  const float* F;      // [jp][mp][Cpad]
+  const float2* tw2;   // as SqArgs
+  const float2* tw1;
+  const double* wgl;   // [npairs]
+  double* part;        // [nsh][npairs]
+};
+
+template <int N1, int P, int Q, int PAD, int G>
+__global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_cubic_sq(const __grid_constant__ CubeArgs a) {
+  constexpr int T = P * Q;
+  constexpr int TG = (T + 31) / 32 * 32;
+  constexpr int N = N1 * P * Q;
+  constexpr int S = N1 * P + PAD;
+  constexpr int NB = N1 * P + S * (Q - 1);
+  constexpr int H = G / 2;  // shells of an item
+  static_assert(NB >= N && H % 2 == 0, "layout");
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[G][TG / 32];
+  float2* buf = (float2*)smem;                       // [G][NB]
+  float2* stg = buf + (size_t)G * NB;                // [2 L + 1][G]: A fields, then B fields
+  float2* tw2 = stg + (size_t)(2 * a.L + 1) * G;     // [N1][Q][P]
+  float2* tw1 = tw2 + (size_t)N1 * T;                // [P][Q]
+  for (int i = threadIdx.x; i < N1 * T; i += blockDim.x) tw2[i] = a.tw2[i];
+  for (int i = threadIdx.x; i < T; i += blockDim.x) tw1[i] = a.tw1[i];
+  const int groups = a.nsh / H;
+  const int items = groups * a.npairs;
+  const int g = threadIdx.x / TG, u = threadIdx.x % TG;
+  float2* B = buf + (size_t)g * NB;
+  const int L = a.L;
+
+  auto prefetch = [&](int item) {
+    const int jp = item / groups, s0 = (item % groups) * H;
+    const float* srcA = a.F + (size_t)jp * a.sj + 2 * s0;
+    const float* srcB = a.F + (size_t)jp * a.sj + 2 * (a.nsh + s0);
+    constexpr int Q4 = H / 2;  // 16-byte copies per row and field
+    for (int q = threadIdx.x; q < (2 * L + 1) * 2 * Q4; q += blockDim.x) {
+      const int mp = q / (2 * Q4), h = q % (2 * Q4);
+      const bool isB = h >= Q4;
+      const int hh = isB ? h - Q4 : h;
+      cp_async16(stg + (size_t)mp * G + (isB ? H : 0) + 2 * hh, (isB ? srcB : srcA) + (size_t)mp * a.sp + 4 * hh);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  if (item < items) prefetch(item);
+  for (; item < items; item += gridDim.x) {
+    const int jp = item / groups, s0 = (item % groups) * H;
+    cp_async_wait_all();
+    __syncthreads();  // staged rows visible; the previous item's buffers are free
+    for (int t = threadIdx.x; t < (L + 1) * G; t += blockDim.x) {
+      const int gg = t % G, m = t / G;
+      const float2 E = stg[(size_t)(2 * m) * G + gg];
+      const float2 O = m < L ? stg[(size_t)(2 * m + 1) * G + gg] : make_float2(0.f, 0.f);
+      const float2 FN = cadd(E, O), FS = csub(E, O);
+      float2* Bg = buf + (size_t)gg * NB;
+      if (m == 0) {
+        Bg[0] = make_float2(FN.x, FS.x);
+      } else {
+        Bg[m + PAD * (m / (N1 * P))] = make_float2(FN.x - FS.y, FN.y + FS.x);
+        const int k = N - m;
+        Bg[k + PAD * (k / (N1 * P))] = make_float2(FN.x + FS.y, FS.x - FN.y);
+      }
+    }
+    __syncthreads();
+    if (item + (int)gridDim.x < items) prefetch(item + gridDim.x);
+    // phase 1a: DFT_Q over b (inverse)
+#pragma unroll 1
+    for (int t = u; t < N1 * P; t += TG) {
+      const int base = t;
+      float2 v[Q];
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        const int k = base + N1 * P * b;
+        v[b] = (k > L && k < N - L) ? make_float2(0.f, 0.f) : B[base + S * b];
+      }
+      Dft<Q, 1>::run(v);
+#pragma unroll
+      for (int c = 0; c < Q; ++c) B[base + S * c] = v[c];
+    }
+    group_sync<TG>(g);
+    // phase 1b: twiddle w_PQ^(a c), DFT_P over a (inverse)
+#pragma unroll 1
+    for (int t = u; t < N1 * Q; t += TG) {
+      const int c = t % Q, k1 = t / Q;
+      const int base = k1 + S * c;
+      float2 v[P];
+#pragma unroll
+      for (int aa = 0; aa < P; ++aa) {
+        const float2 x = B[base + N1 * aa];
+        v[aa] = aa ? cmul(x, tw1[aa * Q + c]) : x;
+      }
+      Dft<P, 1>::run(v);
+#pragma unroll
+      for (int d = 0; d < P; ++d) B[base + N1 * d] = v[d];
+    }
+    group_sync<TG>(g);
+    // phase 2 (inverse half): twiddle w_N^(k1 n2), DFT_N1 -> ring values, back in place
+    if (u < T) {
+      const int d = u % P, c = u / P;
+      const int base = N1 * d + S * c;
+      const float2* w = tw2 + c * P + d;
+      float2 v[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const float2 x = B[base + k1];
+        v[k1] = k1 ? cmul(x, w[k1 * T]) : x;
+      }
+      Dft<N1, 1>::run(v);
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) B[base + n1] = v[n1];
+    }
+    __syncthreads();  // A and B ring values of every shell in place
+    if (g < H) {
+      const float2* BA = buf + (size_t)g * NB;
+      const float2* BB = buf + (size_t)(g + H) * NB;
+      const bool equator = (a.ntheta - 1 - jp == jp);
+      double acc = 0.0;
+      for (int t = u; t < N; t += TG) {
+        const int n1 = t % N1, r = t / N1, d = r % P, c = r / P;
+        const int pos = N1 * d + S * c + n1;
+        const float2 x = BA[pos], y = BB[pos];
+        float s = x.x * y.x * y.x;
+        if (!equator) s += x.y * y.y * y.y;
+        acc += (double)s;
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if ((u & 31) == 0) red[g][u >> 5] = acc;
+      group_sync<TG>(g);
+      if (u == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < TG / 32; ++w) t += red[g][w];
+        a.part[(size_t)(s0 + g) * a.npairs + jp] = t * a.wgl[jp];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
 struct SqConfig {
   int N, N1, P, Q, G;
 };
@@ -486,6 +636,22 @@ void launch_sq(const SqArgs& a, int sms, cudaStream_t st, const SqMulti* multi =
   };
   if (multi) run(k_ring_square<N1, P, Q, PAD, G, true>, items_multi);
   else run(k_ring_square<N1, P, Q, PAD, G, false>, (a.nr / G) * a.npairs);
+}
+
+template <int N1, int P, int Q, int PAD, int G>
+void launch_cube(const CubeArgs& a, int sms, cudaStream_t st) {
+  constexpr int T = P * Q, TG = (T + 31) / 32 * 32, S = N1 * P + PAD, NB = N1 * P + S * (Q - 1);
+  const size_t smem = sizeof(float2) * ((size_t)G * NB + (size_t)(2 * a.L + 1) * G + (size_t)N1 * T + T);
+  if (smem > 227 * 1024 - sizeof(double) * G * (TG / 32))
+    throw Error(FNL_EUNSUPPORTED, "estimator ring staging exceeds shared memory");
+  auto kern = k_ring_cubic_sq<N1, P, Q, PAD, G>;
+  FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * TG, smem));
+  const int items = (a.nsh / (G / 2)) * a.npairs;
+  const int grid = std::max(1, std::min(items, sms * std::max(per_sm, 1)));
+  kern<<<grid, G * TG, smem, st>>>(a);
+  FNL_CUDA(cudaGetLastError());
 }
 
 }  // namespace
@@ -582,6 +748,33 @@ void launch_ring_square_multi(const fnl_shells* proto, const void* d_inst, const
     case 800: launch_sq<25, 8, 4, 4, 8>(a, proto->sms, st, &m, items); return;
     case 400: launch_sq<25, 4, 4, 2, 8>(a, proto->sms, st, &m, items); return;
     default: throw Error(FNL_EUNSUPPORTED, "no specialised ring kernel for this ring length");
+  }
+}
+
+// Specialised rings of the estimator for an object of 2 nsh fields (A, then B); false if this
+// configuration has none (the caller then runs the general kernel).
+bool launch_ring_cubic_sq(const fnl_shells* sh, int nsh, double* part, cudaStream_t st) {
+  const int G = ring_square_group(sh);
+  if (!G || sh->nr != 2 * nsh || nsh % (G / 2) || nsh % 2) return false;
+  CubeArgs a;
+  a.L = sh->lmax;
+  a.nsh = nsh;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.sp = sh->Cpad;
+  a.sj = (int64_t)2 * (sh->lmax + 1) * sh->Cpad;
+  a.F = (const float*)sh->d_F;
+  a.tw2 = (const float2*)sh->d_sqtw2;
+  a.tw1 = (const float2*)sh->d_sqtw1;
+  a.wgl = sh->d_wgl;
+  a.part = part;
+  switch (sh->nphi) {
+    case 3200: launch_cube<25, 16, 8, 2, 4>(a, sh->sms, st); return true;
+    case 3125: launch_cube<25, 25, 5, 2, 4>(a, sh->sms, st); return true;
+    case 1600: launch_cube<25, 8, 8, 2, 8>(a, sh->sms, st); return true;
+    case 800: launch_cube<25, 8, 4, 4, 8>(a, sh->sms, st); return true;
+    case 400: launch_cube<25, 4, 4, 2, 8>(a, sh->sms, st); return true;
+    default: return false;
   }
 }
 

@@ -28,7 +28,7 @@ EXPORTS = [
     "fnl_profile_enable", "fnl_profile_read", "fnl_generate_host", "fnl_device_status",
     "fnl_accumulate_noalloc", "fnl_generate_backward", "fnl_batch_create", "fnl_batch_destroy",
     "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
-    "fnl_maps_prepare", "fnl_maps",
+    "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -97,8 +97,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_batch_tiles.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.fnl_maps_prepare.argtypes = [vp]
     lib.fnl_maps.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.fnl_ksw_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.fnl_ksw_destroy.argtypes = [vp]
+    lib.fnl_ksw_destroy.restype = None
+    lib.fnl_ksw_info.argtypes = [vp, dp, dp, ctypes.POINTER(i)]
+    lib.fnl_ksw_statistic.argtypes = [vp, vp, vp, vp, vp]
     for name in EXPORTS:
-        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy"):
+        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -343,6 +348,49 @@ class Shells:
         ptrs = [_ptr(out[k]) for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]]
         _check(_lib.fnl_accumulate(self.handle, _ptr(phiL), _ptr(phiNL), float(fnl), *ptrs, _stream(stream)))
         return out
+
+
+class Ksw:
+    """The fast cubic f_NL estimator of Sect. 5 (fnl_ksw_*) for the configuration of a shells
+    object: S_prim of a sky (a^T, a^E) and the normalisation N, f_NL = S_prim / N."""
+
+    def __init__(self, shells: "Shells"):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.fnl_ksw_create(shells.handle, ctypes.byref(h)))
+        self.handle = h
+        self.shells = shells  # the estimator keeps pointers into it
+        norm, secs = ctypes.c_double(), ctypes.c_double()
+        rank = (ctypes.c_int * (shells.lmax + 1))()
+        _check(lib.fnl_ksw_info(h, ctypes.byref(norm), ctypes.byref(secs), rank))
+        self.norm = norm.value
+        self.norm_seconds = secs.value
+        self.rank = np.array(rank[:], dtype=int)
+
+    def statistic(self, aT, aE, out=None, stream=None):
+        """S_prim as a 0-d float64 device tensor (asynchronous)."""
+        torch = _torch()
+        for a in (aT, aE):
+            assert a.dtype == torch.complex128 and a.is_contiguous() and a.shape == (self.shells.nalm,)
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=aT.device)
+        _check(_lib.fnl_ksw_statistic(self.handle, _ptr(aT), _ptr(aE), _ptr(out), _stream(stream)))
+        return out
+
+    def fnl(self, aT, aE, stream=None) -> float:
+        """The estimate S_prim / N (synchronises)."""
+        return float(self.statistic(aT, aE, stream=stream).item()) / self.norm
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.fnl_ksw_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -5,6 +5,7 @@ For profilers and quick timing of a configuration that is not one of the named w
   python -m paper_0909_0009_gb300.run_case --lmax 512 --nr 128 --ntheta 769 --nphi 3200 \
       --prec bf16x2 --tiles 112,128 --reps 3
   python -m paper_0909_0009_gb300.run_case --lmax 512 --nr 8 --ntheta 769 --nphi 1600 --maps --reps 3
+  python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --ntheta 1537 --nphi 3200 --ksw --reps 3
 
 Filters are seeded lower-triangular matrices of the covariance's amplitude (the cost of the
 path does not depend on their values); noise is the Philox draw of (seed 1, realisation i).
@@ -30,6 +31,8 @@ def main(argv=None) -> int:
     ap.add_argument("--tiles", default="", help="'synthesis,analysis' tile widths of the tensor-core forms")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--fnl", type=float, default=20.0)
+    ap.add_argument("--ksw", action="store_true",
+                    help="also run the cubic f_NL estimator (fnl_ksw_statistic) on each realisation and time it")
     ap.add_argument("--maps", action="store_true",
                     help="also make the Stokes I, Q, U maps of each realisation (fnl_maps) and time them")
     args = ap.parse_args(argv)
@@ -61,6 +64,19 @@ def main(argv=None) -> int:
         e1.record()
         torch.cuda.synchronize()
         print(f"maps: {e0.elapsed_time(e1) / max(args.reps, 1):.4f} ms per call")
+    if args.ksw:
+        k = F.Ksw(sh)
+        o = sh.generate(1, 0, args.fnl, parts=False)
+        s = k.statistic(o["aT"], o["aE"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(max(args.reps, 1)):
+            k.statistic(o["aT"], o["aE"], out=s)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"ksw: {e0.elapsed_time(e1) / max(args.reps, 1):.4f} ms per sky, normalisation {k.norm:.6g} "
+              f"({k.norm_seconds:.3f} s), f_NL estimate {float(s.item()) / k.norm:.4g}")
+        k.close()
     sh.device_status()
     ms, calls = sh.stage_ms()
     per = {k: round(v / max(calls, 1), 4) for k, v in ms.items()}
