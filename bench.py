@@ -373,6 +373,29 @@ def measure_ksw(F, sh, out, device: int, reps: int = 5) -> dict:
     return res
 
 
+def measure_quadrature(F, device: int, nsel: int = 64) -> dict:
+    """Optimal radial quadrature (Sect. 3) for l_max 1024 on 384 fine shells over the workload's
+    radial range (the 128 midpoints of the generator are fine nodes 3 i + 1): the fine covariance
+    on the device (Eq. 7, FP64), the greedy choice of nsel nodes with their optimal weights, and
+    the relative errors of that rule and of the generator's 128-node midpoint rule."""
+    L, ntot = W.FULL.lmax, 384
+    r, w = W.radial_grid(ntot)
+    aT, aE = W.transfer_kernels(L, r)
+    qd = F.Quadrature(L, r, w, aT, aE, device=device)
+    g = qd.greedy(nsel)
+    rm, wm = W.radial_grid(128)
+    mT, mE = W.transfer_kernels(L, rm)
+    mid = [3 * i + 1 for i in range(128)]
+    rel_mid = qd.error(mid, np.stack([mT, mE]) * (wm * rm * rm)[None, None, :])
+    live = qd.I2 > 0
+    res = {"lmax": L, "ntot": ntot, "nsel": nsel, "covariance_s": qd.create_seconds, "greedy_s": g["seconds"],
+           "rel_err_mean": float(g["rel_err"][live].mean()), "rel_err_max": float(g["rel_err"][live].max()),
+           "midpoint128_rel_err_mean": float(rel_mid[live].mean()),
+           "midpoint128_rel_err_max": float(rel_mid[live].max())}
+    qd.close()
+    return res
+
+
 # ---------------------------------------------------------------------------------------
 # replicas over realisations (one process per GPU): the only cross-rank logic of the path
 # ---------------------------------------------------------------------------------------
@@ -424,6 +447,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-maps", action="store_true", help="skip the Stokes-maps measurement")
     ap.add_argument("--no-ksw", action="store_true", help="skip the cubic-estimator measurement")
+    ap.add_argument("--no-quad", action="store_true", help="skip the optimal-quadrature measurement")
     ap.add_argument("--tiles", default="auto",
                     help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
@@ -534,6 +558,7 @@ def main():
 
     maps = None if args.no_maps else measure_maps(F, sh, out, local)
     ksw = None if args.no_ksw else measure_ksw(F, sh, out, local)
+    quad = None if args.no_quad else measure_quadrature(F, local)
     batch = None if args.no_batch or args.prec not in ("bf16x2", "bf16x3") else measure_batch(F, args.prec, local)
     adjoint = None if args.no_adjoint else measure_adjoint(F, local)
 
@@ -621,6 +646,8 @@ def main():
     if ksw is not None:
         ksw["fnl_input"] = fnl
         line["ksw"] = ksw
+    if quad is not None:
+        line["quadrature"] = quad
     if fp64 is not None:
         line["fp64"] = fp64
         line["speedup_vs_fp64"] = value / fp64["value"]

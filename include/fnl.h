@@ -232,6 +232,55 @@ fnl_status fnl_ksw_info(const fnl_ksw* k, double* norm, double* norm_seconds, in
  * nphi >= 3 lmax + 1.  The f_NL estimate is S / N. */
 fnl_status fnl_ksw_statistic(const fnl_ksw* k, const double* aT, const double* aE, double* S, void* stream);
 
+/* ---- optimal radial quadrature (Sect. 3) -------------------------------------------------- */
+
+/* The design problem: degrees 0..lmax, a fine grid of ntot shells with nodes r and weights w
+ * (the fine line-of-sight rule I = sum_k w_k r_k^2 alpha^X_l(r_k) Phi(r_k)), the transfer kernels
+ * on it, and the covariance P_l of Phi on the fine nodes: given (host [lmax+1][ntot][ntot]), or
+ * NULL and then built on the device as Eq. 7, C_l(r_i, r_j) = (2/pi) sum_k wk k^2 A k^(ns-4)
+ * j_l(k r_i) j_l(k r_j) on the nk-point trapezoid rule over [kmin, kmax].  In both cases
+ * eps_l = jitter_rel * mean(diag) is added to the diagonal (the covariance the filters realise). */
+typedef struct {
+  int lmax;                       /* 0 <= lmax <= 4096 */
+  int ntot;                       /* fine shells, 1 <= ntot <= 4096 */
+  const double* r;                /* host [ntot] fine nodes */
+  const double* w;                /* host [ntot] fine weights */
+  const double* alphaT;           /* host [lmax+1][ntot] */
+  const double* alphaE;           /* host [lmax+1][ntot] */
+  const double* P;                /* host [lmax+1][ntot][ntot] covariance, or NULL (Eq. 7 below) */
+  double A, ns, kmin, kmax;       /* P(k) = A k^(ns - 4) and the k range */
+  int nk;                         /* k points (>= 2) */
+  double jitter_rel;              /* >= 0 */
+} fnl_quad_desc;
+
+typedef struct fnl_quad fnl_quad; /* opaque: the fine covariance, c = P q and <I^2> on the device */
+
+/* Builds P_l (FP64, on the device when desc->P is NULL), c^X_l = P_l q^X_l and <I^2>^X_l = q.c,
+ * q^X_l[k] = w_k r_k^2 alpha^X_l(r_k).  Synchronous; allocates (lmax+1) ntot^2 doubles. */
+fnl_status fnl_quad_create(const fnl_quad_desc* desc, int device, fnl_quad** out);
+void fnl_quad_destroy(fnl_quad* q);
+
+/* I2: host [2][lmax+1] <I^2> of T and E (may be NULL); seconds: wall time of fnl_quad_create. */
+fnl_status fnl_quad_moments(const fnl_quad* q, double* I2, double* seconds);
+
+/* The paper's greedy: nsel fine nodes, each step adding the node that lowers the summed relative
+ * error sum_{l, X: <I^2> > 0} <(I^ - I)^2> / <I^2> most (ties: smallest index), with the optimal
+ * weights P_SS w = c_S.  Outputs (host): nodes [nsel] in selection order; weights [2][lmax+1][nsel]
+ * (w^X_l on those nodes, to multiply Phi(r_i) directly) or NULL; objective [nsel] after each step
+ * or NULL; rel_err [2][lmax+1] at the end or NULL; seconds: wall time, or NULL.
+ * Expected error: <I^2> - c_S^T P_SS^-1 c_S, by the pivoted Cholesky factor of P_l. */
+fnl_status fnl_quad_greedy(const fnl_quad* q, int nsel, int* nodes, double* weights, double* objective,
+                           double* rel_err, double* seconds);
+
+/* Optimal weights on given distinct fine nodes (host [n]): P_SS w = c_S by the same pivoted
+ * Cholesky steps; weights host [2][lmax+1][n] (node order as given) or NULL; rel_err host
+ * [2][lmax+1] or NULL. */
+fnl_status fnl_quad_fit(const fnl_quad* q, int n, const int* nodes, double* weights, double* rel_err);
+
+/* Relative expected error (<I^2> - 2 w.c_S + w^T P_SS w) / <I^2> of any rule: n fine nodes
+ * (host [n]) with weights (host [2][lmax+1][n]); rel_err host [2][lmax+1] (0 where <I^2> = 0). */
+fnl_status fnl_quad_error(const fnl_quad* q, int n, const int* nodes, const double* weights, double* rel_err);
+
 /* Wait for all work on the object's device, then report FNL_ETIMEOUT if a bounded wait
  * inside a tensor-core kernel expired since the last call (the kernels record it in a
  * device word instead of hanging), else FNL_OK.  Clears the word. */

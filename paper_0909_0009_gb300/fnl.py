@@ -29,6 +29,7 @@ EXPORTS = [
     "fnl_accumulate_noalloc", "fnl_generate_backward", "fnl_batch_create", "fnl_batch_destroy",
     "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
+    "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -48,6 +49,17 @@ class ShellDesc(ctypes.Structure):
         ("nk", ctypes.c_int), ("jitter_rel", ctypes.c_double),
         ("alphaT", ctypes.POINTER(ctypes.c_double)), ("alphaE", ctypes.POINTER(ctypes.c_double)),
         ("mu", ctypes.POINTER(ctypes.c_double)), ("prec", ctypes.c_int),
+    ]
+
+
+class QuadDesc(ctypes.Structure):
+    _fields_ = [
+        ("lmax", ctypes.c_int), ("ntot", ctypes.c_int),
+        ("r", ctypes.POINTER(ctypes.c_double)), ("w", ctypes.POINTER(ctypes.c_double)),
+        ("alphaT", ctypes.POINTER(ctypes.c_double)), ("alphaE", ctypes.POINTER(ctypes.c_double)),
+        ("P", ctypes.POINTER(ctypes.c_double)),
+        ("A", ctypes.c_double), ("ns", ctypes.c_double), ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
+        ("nk", ctypes.c_int), ("jitter_rel", ctypes.c_double),
     ]
 
 
@@ -102,8 +114,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_ksw_destroy.restype = None
     lib.fnl_ksw_info.argtypes = [vp, dp, dp, ctypes.POINTER(i)]
     lib.fnl_ksw_statistic.argtypes = [vp, vp, vp, vp, vp]
+    lib.fnl_quad_create.argtypes = [ctypes.POINTER(QuadDesc), i, ctypes.POINTER(vp)]
+    lib.fnl_quad_destroy.argtypes = [vp]
+    lib.fnl_quad_destroy.restype = None
+    lib.fnl_quad_moments.argtypes = [vp, dp, dp]
+    lib.fnl_quad_greedy.argtypes = [vp, i, ctypes.POINTER(i), dp, dp, dp, dp]
+    lib.fnl_quad_error.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
+    lib.fnl_quad_fit.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
     for name in EXPORTS:
-        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy"):
+        if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy",
+                        "fnl_quad_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -384,6 +404,76 @@ class Ksw:
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
             _lib.fnl_ksw_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Quadrature:
+    """Optimal radial quadrature of Sect. 3 (fnl_quad_*): the fine-grid covariance and moments
+    are built at construction (on the device unless P is given); greedy() selects nodes and
+    optimal weights, error() evaluates any rule."""
+
+    def __init__(self, lmax: int, r, w, alphaT, alphaE, P=None, cov: "Cov" = None, device: int = 0):
+        lib = load_library()
+        cov = cov or Cov()
+        self.lmax, self.ntot = lmax, len(r)
+        keep = []
+
+        def arr(a, shape):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+            keep.append(a)
+            return _dptr(a)
+
+        d = QuadDesc()
+        d.lmax, d.ntot = lmax, self.ntot
+        d.r, d.w = arr(r, (self.ntot,)), arr(w, (self.ntot,))
+        d.alphaT, d.alphaE = arr(alphaT, (lmax + 1, self.ntot)), arr(alphaE, (lmax + 1, self.ntot))
+        d.P = arr(P, (lmax + 1, self.ntot, self.ntot))
+        d.A, d.ns, d.kmin, d.kmax, d.nk, d.jitter_rel = cov.A, cov.ns, cov.kmin, cov.kmax, cov.nk, cov.jitter_rel
+        h = ctypes.c_void_p()
+        _check(lib.fnl_quad_create(ctypes.byref(d), device, ctypes.byref(h)))
+        self.handle = h
+        I2 = np.zeros((2, lmax + 1))
+        sec = ctypes.c_double()
+        _check(lib.fnl_quad_moments(h, _dptr(I2), ctypes.byref(sec)))
+        self.I2, self.create_seconds = I2, sec.value
+
+    def greedy(self, nsel: int) -> dict:
+        nodes = (ctypes.c_int * nsel)()
+        W = np.zeros((2, self.lmax + 1, nsel))
+        obj = np.zeros(nsel)
+        rel = np.zeros((2, self.lmax + 1))
+        sec = ctypes.c_double()
+        _check(_lib.fnl_quad_greedy(self.handle, nsel, nodes, _dptr(W), _dptr(obj), _dptr(rel), ctypes.byref(sec)))
+        return {"nodes": list(nodes), "weights": W, "objective": obj, "rel_err": rel, "seconds": sec.value}
+
+    def fit(self, nodes) -> dict:
+        """Optimal weights and relative errors of the given distinct fine nodes."""
+        n = len(nodes)
+        nd = (ctypes.c_int * n)(*[int(x) for x in nodes])
+        W = np.zeros((2, self.lmax + 1, n))
+        rel = np.zeros((2, self.lmax + 1))
+        _check(_lib.fnl_quad_fit(self.handle, n, nd, _dptr(W), _dptr(rel)))
+        return {"weights": W, "rel_err": rel}
+
+    def error(self, nodes, weights) -> np.ndarray:
+        n = len(nodes)
+        nd = (ctypes.c_int * n)(*[int(x) for x in nodes])
+        W = np.ascontiguousarray(weights, dtype=np.float64).reshape(2, self.lmax + 1, n)
+        rel = np.zeros((2, self.lmax + 1))
+        _check(_lib.fnl_quad_error(self.handle, n, nd, _dptr(W), _dptr(rel)))
+        return rel
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.fnl_quad_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):
