@@ -396,6 +396,36 @@ def measure_quadrature(F, device: int, nsel: int = 64) -> dict:
     return res
 
 
+def measure_healpix(F, K, device: int, steps: int = 3) -> dict:
+    """The paper's grid: HEALPix nside 512 at l_max 1024, N_r 128, FP32 form, against the FP32
+    form on the 1537 x 3200 Gauss-Legendre grid with the same filters: realisations/s of each
+    (events over `steps` calls after one warm-up) and the relative difference of a^T, a^E
+    (the HEALPix rule is approximate, the Gauss-Legendre one exact)."""
+    import torch
+    wl = W.FULL
+    r, w = W.radial_grid(wl.nr)
+    aT, aE = W.transfer_kernels(wl.lmax, r)
+    res = {"lmax": wl.lmax, "nr": wl.nr, "nside": 512, "precision": "fp32"}
+    outs = {}
+    for name, kw in (("healpix", {"nside": 512}), ("gauss_legendre", {})):
+        sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec="fp32", device=device, **kw)
+        o = sh.generate(1, 0, wl.fnl[0], parts=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            sh.generate(1, i, wl.fnl[0], parts=False)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_realisations_per_s"] = steps * 1e3 / e0.elapsed_time(e1)
+        outs[name] = {k: v.cpu().numpy() for k, v in o.items()}
+        sh.close()
+    for X in ("aT", "aE"):
+        a, b = outs["healpix"][X], outs["gauss_legendre"][X]
+        res["rel_diff_" + X] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return res
+
+
 # ---------------------------------------------------------------------------------------
 # replicas over realisations (one process per GPU): the only cross-rank logic of the path
 # ---------------------------------------------------------------------------------------
@@ -448,6 +478,7 @@ def main():
     ap.add_argument("--no-maps", action="store_true", help="skip the Stokes-maps measurement")
     ap.add_argument("--no-ksw", action="store_true", help="skip the cubic-estimator measurement")
     ap.add_argument("--no-quad", action="store_true", help="skip the optimal-quadrature measurement")
+    ap.add_argument("--no-healpix", action="store_true", help="skip the HEALPix-grid measurement")
     ap.add_argument("--tiles", default="auto",
                     help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
@@ -559,6 +590,7 @@ def main():
     maps = None if args.no_maps else measure_maps(F, sh, out, local)
     ksw = None if args.no_ksw else measure_ksw(F, sh, out, local)
     quad = None if args.no_quad else measure_quadrature(F, local)
+    hp = None if args.no_healpix or wl is not W.FULL else measure_healpix(F, K, local)
     batch = None if args.no_batch or args.prec not in ("bf16x2", "bf16x3") else measure_batch(F, args.prec, local)
     adjoint = None if args.no_adjoint else measure_adjoint(F, local)
 
@@ -648,6 +680,8 @@ def main():
         line["ksw"] = ksw
     if quad is not None:
         line["quadrature"] = quad
+    if hp is not None:
+        line["healpix"] = hp
     if fp64 is not None:
         line["fp64"] = fp64
         line["speedup_vs_fp64"] = value / fp64["value"]

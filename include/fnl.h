@@ -86,6 +86,18 @@ typedef struct {
   int prec;             /* fnl_precision */
 } fnl_shell_desc;
 
+/* The same on the HEALPix grid of the paper's maps (Sect. 3; Gorski et al. 2005): 12 nside^2
+ * equal-area pixels on 4 nside - 1 iso-latitude rings (ring i < nside at z = 1 - i^2/(3 nside^2)
+ * with 4 i pixels, belt rings at z = 4/3 - 2 i/(3 nside) with 4 nside pixels, pixel k at
+ * phi_0 + 2 pi k / n_i, phi_0 = pi/(4 i) in the caps and alternately pi/(4 nside) and 0 in the
+ * belt), sphere integrals by the equal weight 4 pi / N_pix (approximate: the analysis of a
+ * synthesis returns a_lm up to an error falling as nside^-2).  desc->ntheta and desc->nphi are
+ * ignored; any lmax is allowed (the short polar rings alias m > n_i / 2).  nside a power of two;
+ * FNL_FP64 and FNL_FP32 only (FNL_EINVAL otherwise).  fnl_synth / fnl_analyse maps are
+ * [nr][12 nside^2] in RING order.  The Stokes maps, the estimator and the adjoint run on the
+ * Gauss-Legendre grid only (FNL_EUNSUPPORTED here). */
+fnl_status fnl_make_shells_healpix(const fnl_shell_desc* desc, int nside, int device, fnl_shells** out);
+
 /* Library version string. */
 const char* fnl_version(void);
 

@@ -22,12 +22,11 @@ and steps (ii)-(iv) of the generator on this grid are Phi_NL = analysis((synthes
 Unlike the Gauss-Legendre grid the rule is not exact; the analysis of a synthesis returns a_lm
 up to an error that falls with n_side.
 
-Pins (tests/test_healpix_pins.py, CPU): ring geometry against the published values for
-n_side = 1 and 2 and the counting identities (pixels per ring, N_pix, z symmetry, pixel areas
-equal: the cap above ring i holds the right share of the sphere); synthesis at every pixel
-against a direct sum of scipy's Y_lm at the pixel centre; analysis against a direct pixel sum
-with scipy's Y_lm; the monopole and dipole exactly integrated; the round trip error falling with
-n_side.
+Pins (tests/test_healpix_pins.py, CPU): ring geometry against the published pixel centres of
+n_side = 1 and 2 and the counting identities (N_pix = 12 n_side^2, 4 n_side - 1 rings, z
+antisymmetric, ring sizes and offsets mirrored); synthesis at every pixel against a direct sum of
+scipy's Y_lm at the pixel centre; analysis against a direct pixel sum with scipy's Y_lm; the
+monopole integrated exactly; the round trip error falling with n_side.
 """
 from __future__ import annotations
 
@@ -121,4 +120,20 @@ def healpix_nonlinear(phi_L: np.ndarray, mu: np.ndarray, grid: HealpixGrid) -> n
     return healpix_analysis(f * f - np.asarray(mu, dtype=np.float64)[:, None], grid)
 
 
-__all__ = ["HealpixGrid", "healpix_synthesis", "healpix_analysis", "healpix_nonlinear"]
+def healpix_generate(K, noise, grid: HealpixGrid, r, w, alphaT, alphaE, fnl: float, mu=None) -> dict:
+    """The recipe of ``generate`` with steps (ii)-(iv) on the HEALPix grid."""
+    from .fnl_oracle import mu_ensemble, phi_linear, quadrature_weights, radial_quadrature
+    phiL = phi_linear(K, noise)
+    if mu is None:
+        mu = mu_ensemble(K)
+    qT = quadrature_weights(r, w, alphaT)
+    qE = quadrature_weights(r, w, alphaE)
+    phiNL = healpix_nonlinear(phiL, mu, grid)
+    out = {"aLT": radial_quadrature(phiL, qT), "aLE": radial_quadrature(phiL, qE),
+           "aNLT": radial_quadrature(phiNL, qT), "aNLE": radial_quadrature(phiNL, qE)}
+    out["aT"] = out["aLT"] + fnl * out["aNLT"]
+    out["aE"] = out["aLE"] + fnl * out["aNLE"]
+    return out
+
+
+__all__ = ["HealpixGrid", "healpix_synthesis", "healpix_analysis", "healpix_nonlinear", "healpix_generate"]

@@ -103,12 +103,12 @@ void free_shells(fnl_shells* sh) {
   delete sh;
 }
 
-void validate_desc(const fnl_shell_desc* d, bool synth_only = false) {
+void validate_desc(const fnl_shell_desc* d, bool synth_only = false, bool healpix = false) {
   FNL_REQUIRE(d, "desc is NULL");
   FNL_REQUIRE(d->lmax >= 1 && d->lmax <= 4096, "lmax must be in [1, 4096]");
   FNL_REQUIRE(d->nr >= 1 && d->nr <= (synth_only ? 256 : 128), "nr must be in [1, 128]");
-  FNL_REQUIRE(d->ntheta >= d->lmax + 1, "ntheta must be >= lmax + 1");
-  FNL_REQUIRE(d->nphi >= 2 * d->lmax + 2, "nphi must be >= 2 lmax + 2");
+  FNL_REQUIRE(healpix || d->ntheta >= d->lmax + 1, "ntheta must be >= lmax + 1");
+  FNL_REQUIRE(healpix || d->nphi >= 2 * d->lmax + 2, "nphi must be >= 2 lmax + 2");
   FNL_REQUIRE(smooth235(d->nphi), "nphi must be 2/3/5-smooth");
   FNL_REQUIRE(d->r && d->w, "r and w must not be NULL");
   FNL_REQUIRE(d->alphaT && d->alphaE, "alphaT and alphaE must not be NULL");
@@ -469,14 +469,32 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
   return st;
 }
 
+fnl_status fnl_make_shells_healpix(const fnl_shell_desc* d, int nside, int device, fnl_shells** out) {
+  return guard([&] {
+    FNL_REQUIRE(out, "out must not be NULL");
+    *out = nullptr;
+    FNL_REQUIRE(nside >= 1, "nside must be >= 1");
+    *out = make_shells_core(d, device, false, nside);
+  });
+}
+
 }  // extern "C"
 
 namespace fnl {
 
-fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only) {
+fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_only, int nside) {
   fnl_shells* sh = nullptr;
   try {
-    validate_desc(d, synth_only);
+    FNL_REQUIRE(d_in, "desc is NULL");
+    fnl_shell_desc dd = *d_in;
+    if (nside) {
+      FNL_REQUIRE(nside >= 1 && nside <= 4096 && (nside & (nside - 1)) == 0, "nside must be a power of two <= 4096");
+      FNL_REQUIRE(dd.prec == FNL_FP64 || dd.prec == FNL_FP32, "the HEALPix grid runs in the FNL_FP64 and FNL_FP32 forms");
+      dd.ntheta = 4 * nside - 1;
+      dd.nphi = 4 * nside;
+    }
+    const fnl_shell_desc* d = &dd;
+    validate_desc(d, synth_only, nside > 0);
     const bool mixed = (d->prec == FNL_BF16X2 || d->prec == FNL_BF16X3);
     int ndev = 0;
     FNL_CUDA(cudaGetDeviceCount(&ndev));
@@ -539,11 +557,23 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_onl
     sh->Cpad = round_up(C, 128);
     sh->npj = round_up(np, 32);
 
-    // ---- Gauss-Legendre grid (northern half)
-    std::vector<double> xg(d->ntheta), wg(d->ntheta);
-    gauss_legendre(d->ntheta, xg.data(), wg.data());
-    sh->x.assign(xg.begin(), xg.begin() + np);
-    sh->wgl.assign(wg.begin(), wg.begin() + np);
+    // ---- ring grid (northern half): Gauss-Legendre nodes and weights, or the HEALPix rings with
+    // the equal-area rule's weight 2 n_j / N_pix per ring (so that (2 pi / n_j) w_j = 4 pi / N_pix)
+    sh->nside = nside;
+    if (nside) {
+      std::vector<double> z, phi0;
+      std::vector<int> n;
+      healpix_rings(nside, z, n, phi0);
+      const double npix = 12.0 * nside * nside;
+      sh->x.assign(z.begin(), z.begin() + np);
+      sh->wgl.resize(np);
+      for (int j = 0; j < np; ++j) sh->wgl[j] = 2.0 * n[j] / npix;
+    } else {
+      std::vector<double> xg(d->ntheta), wg(d->ntheta);
+      gauss_legendre(d->ntheta, xg.data(), wg.data());
+      sh->x.assign(xg.begin(), xg.begin() + np);
+      sh->wgl.assign(wg.begin(), wg.begin() + np);
+    }
 
     // ---- filters K_l (Eq. 9)
     const size_t kk = synth_only ? 0 : (size_t)(L + 1) * nr * nr;
@@ -664,6 +694,7 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_onl
       FNL_CUDA(cudaMemset(sh->d_F, 0, fg));
       FNL_CUDA(cudaMemset(sh->d_G, 0, fg));
       build_lambda_tables(sh, 0);
+      if (nside) setup_healpix(sh);
     } else {
       setup_mixed(sh, qT, qE);
     }
@@ -755,6 +786,7 @@ fnl_status fnl_synth(const fnl_shells* sh, const double* alm, double* maps, void
 fnl_status fnl_maps_prepare(fnl_shells* sh) {
   return guard([&] {
     check_shells(sh);
+    if (sh->nside) throw Error(FNL_EUNSUPPORTED, "the Stokes maps run on the Gauss-Legendre grid");
     FNL_REQUIRE(!sh->owner, "fnl_maps_prepare: not on a scratch clone");
     DeviceScope scope(sh->device);
     maps_prepare(sh);
@@ -919,6 +951,7 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
     DeviceScope scope(sh->device);
     if (sh->nterms)
       throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward runs in the FNL_FP64 and FNL_FP32 forms");
+    if (sh->nside) throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward runs on the Gauss-Legendre grid");
     check_dev_ptr(noise, "noise", true);
     check_dev_ptr(gT, "gT", true);
     check_dev_ptr(gE, "gE", true);

@@ -193,6 +193,19 @@ struct fnl_shells {
   void* d_mapX = nullptr;
   void* d_Fiqu = nullptr;
 
+  // HEALPix ring grid (nside > 0; FP64 and FP32 forms): ring pair j = ring j + 1 and its mirror
+  int nside = 0;
+  int hp_M = 0;                    // Bluestein FFT length: a power of two >= 2 (4 nside) - 1
+  int hp_nmax = 0;                 // longest ring, 4 nside
+  int64_t npix = 0;                // 12 nside^2
+  fnl::FftPlan hp_plan;            // of hp_M
+  int* d_hp_n = nullptr;           // [npairs] ring lengths
+  int64_t* d_hp_off = nullptr;     // [ntheta + 1] first pixel of each ring (RING order)
+  void* d_hp_rot = nullptr;        // [npairs][L+1] complex: e^{i m phi_0}
+  void* d_hp_chirp = nullptr;      // [npairs][hp_nmax] complex: e^{-i pi k^2 / n}
+  void* d_hp_bf = nullptr;         // [npairs][hp_M] complex: DFT_M of the chirp filter
+  void* d_hp_tw = nullptr;         // [hp_M] complex: e^{-2 pi i k / hp_M}
+
   // SIMT tile lists
   fnl::Tile* d_tiles_syn = nullptr;
   int n_tiles_syn = 0;
@@ -231,7 +244,11 @@ void destroy_clone(fnl_shells* c);
 void build_tc_inst_a(fnl_shells* sh);
 // fnl_make_shells; with synth_only, an object without filters (K, mu, q and v zero) of up to
 // 256 fields, used for the synthesis of other fields (the estimator's A and B maps).
-fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only);
+fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only, int nside = 0);
+// HEALPix rings (healpix.cu): z, ring length and phi offset of rings 1 .. 4 nside - 1 (north to
+// south); the per-ring-pair tables of the HEALPix ring kernel.
+void healpix_rings(int nside, std::vector<double>& z, std::vector<int>& n, std::vector<double>& phi0);
+void setup_healpix(fnl_shells* sh);
 // Frees an object made by make_shells_core (its device memory and the object).
 void release_shells(fnl_shells* sh);
 // Step (ii) Legendre GEMM of the object's own Phi rows (tensor-core or SIMT form) into F.

@@ -369,6 +369,7 @@ fnl_status fnl_ksw_create(const fnl_shells* sh, fnl_ksw** out) {
     *out = nullptr;
     check_shells(sh);
     FNL_REQUIRE(!sh->synth_only && !sh->owner && sh->host, "fnl_ksw_create: not on an internal object");
+    if (sh->nside) throw Error(FNL_EUNSUPPORTED, "the estimator runs on the Gauss-Legendre grid");
     DeviceScope scope(sh->device);
     const int L = sh->lmax, nr = sh->nr, np = sh->npairs;
     const size_t ts = sh->real_is_double ? 16 : 8;

@@ -433,6 +433,139 @@ __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
   }
 }
 
+// HEALPix rings: per (shell s, ring pair jp) of ring length n and offset phi_0.  The packed
+// spectrum Z_k' = sum_{m = k' mod n, |m| <= L} e^{i m phi_0} (F_N,m + i F_S,m) (F_X,-m = conj F_X,m;
+// the short polar rings fold m above n / 2 onto their bins) goes to the ring values
+// z = f_N + i f_S by an inverse DFT of length n, taken as conj(DFT(conj Z)) with Bluestein's
+// algorithm: a = (x c) zero-padded to M, A = FFT_M(a), y = IFFT_M(A Bf) / M, X_m = c_m y_m.  The
+// square mode then forms w = (Re z)^2 - mu + i ((Im z)^2 - mu), takes W = DFT_n(w) the same way and
+// writes S, D of G_m = e^{-i m phi_0} W_{m mod n} (north / south separated as on the Gauss-Legendre
+// rings) scaled by (2 pi / n) w_j = 4 pi / N_pix.  The map modes write or read the RING-ordered
+// maps [nr][N_pix].
+template <typename T>
+struct HpArgs {
+  int L, ntheta, npairs, M, nmax;
+  int64_t sp, sj, npix;   // F and G strides (SIMT layout), pixels per map
+  FftPlan plan;           // of M
+  const cplx<T>* tw;      // [M]
+  const int* n;           // [npairs]
+  const int64_t* off;     // [ntheta + 1]
+  const cplx<T>* rot;     // [npairs][L+1]
+  const cplx<T>* chirp;   // [npairs][nmax]
+  const cplx<T>* bf;      // [npairs][M]
+  const T* F;
+  T* G;
+  const double* mu;
+  const double* wgl;
+  const double* maps_in;
+  double* maps_out;
+};
+
+// DFT_n of x[0..n) (in buf, capacity M) by Bluestein; returns the buffer whose first n entries
+// hold X_m / M ... times c_m: the caller reads X_m = c_m y_m / M from it.
+template <typename T>
+__device__ cplx<T>* bluestein(cplx<T>* buf, cplx<T>* other, const HpArgs<T>& a, int n, const cplx<T>* c,
+                              const cplx<T>* bf) {
+  for (int k = threadIdx.x; k < a.M; k += blockDim.x) buf[k] = k < n ? cmul(buf[k], c[k]) : cplx<T>{(T)0, (T)0};
+  __syncthreads();
+  cplx<T>* A = stockham(buf, other, a.plan, a.tw, (T)-1);
+  for (int k = threadIdx.x; k < a.M; k += blockDim.x) A[k] = cmul(A[k], bf[k]);
+  __syncthreads();
+  return stockham(A, A == buf ? other : buf, a.plan, a.tw, (T)1);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cplx<T>* b0 = (cplx<T>*)smem;
+  cplx<T>* b1 = b0 + a.M;
+  const int s = blockIdx.x, jp = blockIdx.y;
+  const int south = a.ntheta - 1 - jp;
+  const bool equator = (south == jp);
+  const int L = a.L, n = a.n[jp];
+  const cplx<T>* rot = a.rot + (size_t)jp * (L + 1);
+  const cplx<T>* c = a.chirp + (size_t)jp * a.nmax;
+  const cplx<T>* bf = a.bf + (size_t)jp * a.M;
+  const T invM = (T)1 / (T)a.M;
+  cplx<T>* z;
+  if (MODE == FFT_ANALYSE_MAP) {
+    const double* rn = a.maps_in + (size_t)s * a.npix + a.off[jp];
+    const double* rs = a.maps_in + (size_t)s * a.npix + a.off[south];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) b0[k] = {(T)rn[k], (T)rs[k]};
+    __syncthreads();
+    z = b0;
+  } else {
+    for (int kp = threadIdx.x; kp < n; kp += blockDim.x) {
+      cplx<T> acc = {(T)0, (T)0};
+      for (int m = kp - n * ((kp + L) / n); m <= L; m += n) {
+        if (m < -L) continue;
+        const int am = m < 0 ? -m : m;
+        const T* e = a.F + (size_t)(2 * am) * a.sp + (size_t)jp * a.sj + 2 * s;
+        const T* o = a.F + (size_t)(2 * am + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
+        cplx<T> E = {e[0], am ? e[1] : (T)0};
+        cplx<T> O = (am < L) ? cplx<T>{o[0], am ? o[1] : (T)0} : cplx<T>{(T)0, (T)0};
+        cplx<T> FN = cadd(E, O), FS = csub(E, O), P = rot[am];
+        if (m < 0) {
+          FN.y = -FN.y;
+          FS.y = -FS.y;
+          P.y = -P.y;
+        }
+        acc = cadd(acc, cmul(P, cplx<T>{FN.x - FS.y, FN.y + FS.x}));
+      }
+      b0[kp] = {acc.x, -acc.y};  // conj: the inverse DFT as conj(DFT(conj Z))
+    }
+    __syncthreads();
+    cplx<T>* y = bluestein(b0, b1, a, n, c, bf);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const cplx<T> v = cmul(c[k], y[k]);
+      y[k] = {v.x * invM, -v.y * invM};
+    }
+    __syncthreads();
+    z = y;
+    if (MODE == FFT_SYNTH_MAP) {
+      double* rn = a.maps_out + (size_t)s * a.npix + a.off[jp];
+      double* rs = a.maps_out + (size_t)s * a.npix + a.off[south];
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        rn[k] = (double)z[k].x;
+        if (!equator) rs[k] = (double)z[k].y;
+      }
+      return;
+    }
+    const T mu = (T)a.mu[s];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) z[k] = {z[k].x * z[k].x - mu, z[k].y * z[k].y - mu};
+    __syncthreads();
+  }
+  cplx<T>* y = bluestein(z, z == b0 ? b1 : b0, a, n, c, bf);
+  const T scale = (T)(6.28318530717958647692 / n * a.wgl[jp]);
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    const int kp = m % n, kc = (n - kp) % n;
+    cplx<T> wm = cmul(c[kp], y[kp]), wc = cmul(c[kc], y[kc]);
+    wm = {wm.x * invM, wm.y * invM};
+    wc = {wc.x * invM, wc.y * invM};
+    cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
+    cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
+    const cplx<T> rc = {rot[m].x, -rot[m].y};  // e^{-i m phi_0}
+    gn = cmul(gn, rc);
+    gs = cmul(gs, rc);
+    cplx<T> S, D;
+    if (equator) {
+      S = {gn.x * scale, gn.y * scale};
+      D = S;
+    } else {
+      S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
+      D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
+    }
+    T* ge = a.G + (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
+    T* go = a.G + (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
+    ge[0] = S.x;
+    ge[1] = S.y;
+    if (m < L) {
+      go[0] = D.x;
+      go[1] = D.y;
+    }
+  }
+}
+
 // Estimator rings: per (shell s, ring pair jp) the maps A (columns 2s, 2s + 1 of F) and B
 // (columns 2 (nsh + s), + 1) on the north and south rings (inverse DFTs as in the square), then
 // sum_k A B^2 on each ring (the equator once), times the ring's Gauss-Legendre weight, into
@@ -640,7 +773,54 @@ __global__ void __launch_bounds__(512, 2) k_ring_fft_group(const FftArgs<T> a, i
 bool plan_fits_group(const FftPlan&, int) { return true; }
 
 template <typename T>
+void healpix_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
+  HpArgs<T> a{};
+  a.L = sh->lmax;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.M = sh->hp_M;
+  a.nmax = sh->hp_nmax;
+  a.sp = (int64_t)sh->npairs * sh->C;
+  a.sj = sh->C;
+  a.npix = sh->npix;
+  a.plan = sh->hp_plan;
+  a.tw = (const cplx<T>*)sh->d_hp_tw;
+  a.n = sh->d_hp_n;
+  a.off = sh->d_hp_off;
+  a.rot = (const cplx<T>*)sh->d_hp_rot;
+  a.chirp = (const cplx<T>*)sh->d_hp_chirp;
+  a.bf = (const cplx<T>*)sh->d_hp_bf;
+  a.F = (const T*)sh->d_F;
+  a.G = (T*)sh->d_G;
+  a.mu = sh->d_mu;
+  a.wgl = sh->d_wgl;
+  a.maps_in = maps_in;
+  a.maps_out = maps_out;
+  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)a.M;
+  const dim3 grid(sh->nr, sh->npairs);
+  switch (mode) {
+    case FFT_SQUARE:
+      FNL_CUDA(cudaFuncSetAttribute(k_ring_healpix<T, FFT_SQUARE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      k_ring_healpix<T, FFT_SQUARE><<<grid, 256, smem, st>>>(a);
+      break;
+    case FFT_SYNTH_MAP:
+      FNL_CUDA(cudaFuncSetAttribute(k_ring_healpix<T, FFT_SYNTH_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      k_ring_healpix<T, FFT_SYNTH_MAP><<<grid, 256, smem, st>>>(a);
+      break;
+    default:
+      FNL_CUDA(cudaFuncSetAttribute(k_ring_healpix<T, FFT_ANALYSE_MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+      k_ring_healpix<T, FFT_ANALYSE_MAP><<<grid, 256, smem, st>>>(a);
+      break;
+  }
+  FNL_CUDA(cudaGetLastError());
+}
+
+template <typename T>
 void fft_impl(const fnl_shells* sh, int mode, const double* maps_in, double* maps_out, cudaStream_t st) {
+  if (sh->nside) return healpix_impl<T>(sh, mode, maps_in, maps_out, st);
   if (std::is_same<T, float>::value && mode == FFT_SQUARE && launch_ring_square(sh, st)) return;
   FftArgs<T> a{};
   a.L = sh->lmax;

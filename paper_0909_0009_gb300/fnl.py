@@ -30,6 +30,7 @@ EXPORTS = [
     "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
     "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
+    "fnl_make_shells_healpix",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -121,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_quad_greedy.argtypes = [vp, i, ctypes.POINTER(i), dp, dp, dp, dp]
     lib.fnl_quad_error.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
     lib.fnl_quad_fit.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
+    lib.fnl_make_shells_healpix.argtypes = [ctypes.POINTER(ShellDesc), i, i, ctypes.POINTER(vp)]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy",
                         "fnl_quad_destroy"):
@@ -195,8 +197,13 @@ class Shells:
     """Device tables and scratch for one configuration (wraps fnl_make_shells)."""
 
     def __init__(self, lmax, nr, ntheta, nphi, r, w, alphaT, alphaE, K=None, cov: Cov | None = None,
-                 mu=None, prec="fp64", device=0):
+                 mu=None, prec="fp64", device=0, nside: int | None = None):
+        """Gauss-Legendre ring grid of ntheta x nphi; or, with nside, the HEALPix grid of
+        12 nside^2 pixels (fnl_make_shells_healpix; ntheta and nphi are then ignored and maps are
+        [nr][npix] in RING order)."""
         lib = load_library()
+        if nside:
+            ntheta, nphi = 4 * nside - 1, 4 * nside
         cov = cov or Cov()
         self._keep = []
 
@@ -216,7 +223,12 @@ class Shells:
         d.mu = arr(mu, (nr,))
         d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         h = ctypes.c_void_p()
-        _check(lib.fnl_make_shells(ctypes.byref(d), device, ctypes.byref(h)))
+        if nside:
+            _check(lib.fnl_make_shells_healpix(ctypes.byref(d), int(nside), device, ctypes.byref(h)))
+        else:
+            _check(lib.fnl_make_shells(ctypes.byref(d), device, ctypes.byref(h)))
+        self.nside = nside or 0
+        self.npix = 12 * nside * nside if nside else ntheta * nphi
         self._keep = []
         self.handle = h
         self.lmax, self.nr, self.ntheta, self.nphi = lmax, nr, ntheta, nphi
@@ -329,13 +341,15 @@ class Shells:
     def synth(self, alm, stream=None):
         torch = _torch()
         assert alm.dtype == torch.complex128 and alm.is_contiguous() and alm.shape == (self.nalm, self.nr)
-        maps = torch.empty((self.nr, self.ntheta, self.nphi), dtype=torch.float64, device=alm.device)
+        shape = (self.nr, self.npix) if self.nside else (self.nr, self.ntheta, self.nphi)
+        maps = torch.empty(shape, dtype=torch.float64, device=alm.device)
         _check(_lib.fnl_synth(self.handle, _ptr(alm), _ptr(maps), _stream(stream)))
         return maps
 
     def analyse(self, maps, stream=None):
         torch = _torch()
-        assert maps.dtype == torch.float64 and maps.is_contiguous() and maps.shape == (self.nr, self.ntheta, self.nphi)
+        shape = (self.nr, self.npix) if self.nside else (self.nr, self.ntheta, self.nphi)
+        assert maps.dtype == torch.float64 and maps.is_contiguous() and maps.shape == shape
         alm = self._alm(self.nr)
         _check(_lib.fnl_analyse(self.handle, _ptr(maps), _ptr(alm), _stream(stream)))
         return alm
