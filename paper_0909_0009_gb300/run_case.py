@@ -6,6 +6,8 @@ For profilers and quick timing of a configuration that is not one of the named w
       --prec bf16x2 --tiles 112,128 --reps 3
   python -m paper_0909_0009_gb300.run_case --lmax 512 --nr 8 --ntheta 769 --nphi 1600 --maps --reps 3
   python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --ntheta 1537 --nphi 3200 --ksw --reps 3
+  python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --nside 512 --prec fp32 --reps 2
+  python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --ntheta 1537 --nphi 3200 --quad 64 --reps 0
 
 Filters are seeded lower-triangular matrices of the covariance's amplitude (the cost of the
 path does not depend on their values); noise is the Philox draw of (seed 1, realisation i).
@@ -25,8 +27,11 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--lmax", type=int, required=True)
     ap.add_argument("--nr", type=int, required=True)
-    ap.add_argument("--ntheta", type=int, required=True)
-    ap.add_argument("--nphi", type=int, required=True)
+    ap.add_argument("--ntheta", type=int, default=0)
+    ap.add_argument("--nphi", type=int, default=0)
+    ap.add_argument("--nside", type=int, default=0, help="HEALPix grid of this nside (FP64 / FP32 forms)")
+    ap.add_argument("--quad", type=int, default=0,
+                    help="also design an optimal radial rule of this many nodes on 3 N_r fine shells")
     ap.add_argument("--prec", default="bf16x2", choices=["fp64", "fp32", "bf16x2", "bf16x3"])
     ap.add_argument("--tiles", default="", help="'synthesis,analysis' tile widths of the tensor-core forms")
     ap.add_argument("--reps", type=int, default=3)
@@ -46,7 +51,19 @@ def main(argv=None) -> int:
     r, w = W.radial_grid(args.nr)
     aT, aE = W.transfer_kernels(args.lmax, r)
     K = W.random_lower_filters(args.lmax, args.nr, seed=1, scale=8e-5)
-    sh = F.Shells(args.lmax, args.nr, args.ntheta, args.nphi, r, w, aT, aE, K=K, prec=args.prec)
+    if args.quad:
+        rf, wf = W.radial_grid(3 * args.nr)
+        fT, fE = W.transfer_kernels(args.lmax, rf)
+        qd = F.Quadrature(args.lmax, rf, wf, fT, fE)
+        g = qd.greedy(args.quad)
+        live = qd.I2 > 0
+        print(f"quadrature: covariance {qd.create_seconds:.3f} s, greedy {g['seconds']:.4f} s, "
+              f"mean rel err {g['rel_err'][live].mean():.3g}")
+        qd.close()
+        if args.reps <= 0:
+            return 0
+    sh = F.Shells(args.lmax, args.nr, args.ntheta, args.nphi, r, w, aT, aE, K=K, prec=args.prec,
+                  nside=args.nside or None)
     if args.tiles:
         sh.set_tiles(*(int(x) for x in args.tiles.split(",")))
     sh.profile(max(args.reps, 1))
@@ -80,7 +97,8 @@ def main(argv=None) -> int:
     sh.device_status()
     ms, calls = sh.stage_ms()
     per = {k: round(v / max(calls, 1), 4) for k, v in ms.items()}
-    print(f"l_max={args.lmax} N_r={args.nr} grid {args.ntheta}x{args.nphi} {args.prec}: "
+    grid = f"HEALPix nside {args.nside}" if args.nside else f"grid {args.ntheta}x{args.nphi}"
+    print(f"l_max={args.lmax} N_r={args.nr} {grid} {args.prec}: "
           f"{sh.device_bytes / 1e9:.2f} GB on the device; ms per realisation {per}")
     return 0
 
