@@ -48,7 +48,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------------------
-# algorithmic work of one realisation (per-unit figures; see DESIGN.md)
+# algorithmic work of one realisation (per-unit figures)
 # ---------------------------------------------------------------------------------------
 
 def legendre_flops(lmax: int, ntheta: int, nr: int) -> float:
@@ -587,12 +587,15 @@ def main():
         d64.close()
         del d64, out64, ref, b
 
-    maps = None if args.no_maps else measure_maps(F, sh, out, local)
-    ksw = None if args.no_ksw else measure_ksw(F, sh, out, local)
-    quad = None if args.no_quad else measure_quadrature(F, local)
-    hp = None if args.no_healpix or wl is not W.FULL else measure_healpix(F, K, local)
-    batch = None if args.no_batch or args.prec not in ("bf16x2", "bf16x3") else measure_batch(F, args.prec, local)
-    adjoint = None if args.no_adjoint else measure_adjoint(F, local)
+    # the secondary measurements run once, on rank 0 (the other ranks wait at the final barrier)
+    lead = rank == 0
+    maps = None if args.no_maps or not lead else measure_maps(F, sh, out, local)
+    ksw = None if args.no_ksw or not lead else measure_ksw(F, sh, out, local)
+    quad = None if args.no_quad or not lead else measure_quadrature(F, local)
+    hp = None if args.no_healpix or not lead or wl is not W.FULL else measure_healpix(F, K, local)
+    batch = (None if args.no_batch or not lead or args.prec not in ("bf16x2", "bf16x3")
+             else measure_batch(F, args.prec, local))
+    adjoint = None if args.no_adjoint or not lead else measure_adjoint(F, local)
 
     if rank != 0:
         if world > 1:
@@ -603,7 +606,7 @@ def main():
     # ---- rooflines of every stage from the live stage events; the dominant one is the
     # line's "roofline".  Each stage is measured against what bounds it: the tensor pipe
     # (executed MMA flops) for the Legendre GEMMs, the FP32 pipes for the filter and the
-    # ring FFTs (ALU-issue bound: see the design doc), HBM for the quadrature.
+    # ring FFTs (bound by instruction issue), HBM for the quadrature.
     pk, pk_kind = peaks()
     per_stage = {k: v / max(calls, 1) for k, v in stage_sum.items()}
     mixed = args.prec in ("bf16x2", "bf16x3")

@@ -88,7 +88,8 @@ def test_band_limit_one_has_no_estimator(F):
 def test_reduced_precision_statistic(F, prec, bar, L, nt, nph):
     """FP32 / mixed synthesis of A and B (relative map errors ~1e-7 / ~1e-5 per stage) make
     S_prim, a sum with cancellations, accurate to the bar stated here relative to the scale
-    sqrt(sum over the rings of (A B^2)^2) of its terms; measured margins are in the design doc."""
+    sqrt(sum over the rings of (A B^2)^2) of its terms (measured: 6e-9 FP32, 4e-7 / 9e-7 bf16x3,
+    1.5e-6 bf16x2)."""
     nr = 8
     sh, k, wts = setup(F, L, nr, nt, nph, prec, True)
     aT, aE = sky(L, seed=4)
