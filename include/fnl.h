@@ -293,6 +293,12 @@ fnl_status fnl_quad_fit(const fnl_quad* q, int n, const int* nodes, double* weig
  * (host [n]) with weights (host [2][lmax+1][n]); rel_err host [2][lmax+1] (0 where <I^2> = 0). */
 fnl_status fnl_quad_error(const fnl_quad* q, int n, const int* nodes, const double* weights, double* rel_err);
 
+/* Cap the SMs that the object's persistent kernels occupy: the tensor-core Legendre GEMMs
+ * (gemm_sms) and the specialised ring kernel (ring_sms); 0 = all SMs (the default).  For
+ * running the DRAM-bound GEMMs of one realisation beside the compute-bound stages of another
+ * on disjoint SMs.  FNL_EINVAL outside [0, SM count]. */
+fnl_status fnl_shells_set_sm_limits(fnl_shells* sh, int gemm_sms, int ring_sms);
+
 /* Wait for all work on the object's device, then report FNL_ETIMEOUT if a bounded wait
  * inside a tensor-core kernel expired since the last call (the kernels record it in a
  * device word instead of hanging), else FNL_OK.  Clears the word. */

@@ -413,7 +413,7 @@ void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_o
   TcArgs a = base;
   a.mode = mode;
   a.alm_out = alm_out;
-  launch_tc_gemm(a, sh->sms, st);
+  launch_tc_gemm(a, sh->sms_gemm ? sh->sms_gemm : sh->sms, st);
 }
 
 }  // namespace
@@ -780,6 +780,16 @@ fnl_status fnl_synth(const fnl_shells* sh, const double* alm, double* maps, void
       launch_synth_gemm(sh, st);
     }
     launch_ring_fft(sh, FFT_SYNTH_MAP, nullptr, maps, st);
+  });
+}
+
+fnl_status fnl_shells_set_sm_limits(fnl_shells* sh, int gemm_sms, int ring_sms) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(gemm_sms >= 0 && gemm_sms <= sh->sms && ring_sms >= 0 && ring_sms <= sh->sms,
+                "SM limits must be in [0, the device's SM count]");
+    sh->sms_gemm = gemm_sms;
+    sh->sms_ring = ring_sms;
   });
 }
 

@@ -159,6 +159,7 @@ struct fnl_shells {
   int nana = 0;                    // analysis tile width cap (degrees)
   int tc_split = 1;                // separate accumulators for leading and correction products
   int sms = 0;
+  int sms_gemm = 0, sms_ring = 0;  // SMs the persistent GEMM and ring kernels may occupy (0: all)
   std::vector<int64_t> row32;      // first Phi row of problem mp (rows padded to 32)
   int64_t* d_row32 = nullptr;
   void* d_phiT = nullptr;          // bf16 [nterms][rows32][Cpad]

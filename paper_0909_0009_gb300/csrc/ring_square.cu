@@ -726,11 +726,11 @@ bool launch_ring_square(const fnl_shells* sh, cudaStream_t st) {
   if (!ring_square_group(sh)) return false;
   const SqArgs a = sq_args_of(sh);
   switch (sh->nphi) {
-    case 3200: launch_sq<25, 16, 8, 2, 4>(a, sh->sms, st); return true;
-    case 3125: launch_sq<25, 25, 5, 2, 4>(a, sh->sms, st); return true;
-    case 1600: launch_sq<25, 8, 8, 2, 8>(a, sh->sms, st); return true;
-    case 800: launch_sq<25, 8, 4, 4, 8>(a, sh->sms, st); return true;
-    case 400: launch_sq<25, 4, 4, 2, 8>(a, sh->sms, st); return true;
+    case 3200: launch_sq<25, 16, 8, 2, 4>(a, sh->sms_ring ? sh->sms_ring : sh->sms, st); return true;
+    case 3125: launch_sq<25, 25, 5, 2, 4>(a, sh->sms_ring ? sh->sms_ring : sh->sms, st); return true;
+    case 1600: launch_sq<25, 8, 8, 2, 8>(a, sh->sms_ring ? sh->sms_ring : sh->sms, st); return true;
+    case 800: launch_sq<25, 8, 4, 4, 8>(a, sh->sms_ring ? sh->sms_ring : sh->sms, st); return true;
+    case 400: launch_sq<25, 4, 4, 2, 8>(a, sh->sms_ring ? sh->sms_ring : sh->sms, st); return true;
     default: return false;
   }
 }

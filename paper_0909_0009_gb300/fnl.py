@@ -30,7 +30,7 @@ EXPORTS = [
     "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
     "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
-    "fnl_make_shells_healpix",
+    "fnl_make_shells_healpix", "fnl_shells_set_sm_limits",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_quad_error.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
     lib.fnl_quad_fit.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
     lib.fnl_make_shells_healpix.argtypes = [ctypes.POINTER(ShellDesc), i, i, ctypes.POINTER(vp)]
+    lib.fnl_shells_set_sm_limits.argtypes = [vp, i, i]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy",
                         "fnl_quad_destroy"):
@@ -286,6 +287,10 @@ class Shells:
             return ctypes.c_void_p(a.ctypes.data)
         _check(_lib.fnl_generate_host(self.handle, seed, realisation, float(fnl), hp(aT), hp(aE), hp(aNLT),
                                       hp(aNLE), _stream(stream)))
+
+    def set_sm_limits(self, gemm: int = 0, ring: int = 0):
+        """SMs the persistent GEMM and ring kernels may occupy (0: all)."""
+        _check(_lib.fnl_shells_set_sm_limits(self.handle, int(gemm), int(ring)))
 
     def autotune(self, stream=None) -> tuple[int, int]:
         """fnl_shells_autotune: time the candidate tile shapes, keep the fastest; returns

@@ -143,3 +143,22 @@ def test_full_size_within_precision_target(F, prec):
     for k, e in errs.items():
         assert e < TARGET, errs
     mx.device_status()
+
+
+def test_sm_limits_change_no_result(F):
+    """Capping the SMs of the persistent GEMM and ring kernels changes which CTA takes a tile,
+    not the order of any sum: the realisation is bit-identical."""
+    r, w = W.radial_grid(16)
+    aT, aE = W.transfer_kernels(100, r)
+    K = W.random_lower_filters(100, 16, seed=3, scale=1e-4)
+    sh = F.Shells(100, 16, 151, 800, r, w, aT, aE, K=K, prec="bf16x2")
+    ref = sh.generate(2, 1, 25.0, parts=False)
+    ref = {k: host(v) for k, v in ref.items()}
+    for g, rg in ((30, 0), (0, 40), (7, 9)):
+        sh.set_sm_limits(g, rg)
+        out = sh.generate(2, 1, 25.0, parts=False)
+        for k in ("aT", "aE"):
+            assert np.array_equal(host(out[k]), ref[k]), (g, rg, k)
+    sh.set_sm_limits(0, 0)
+    with pytest.raises(F.FnlError):
+        sh.set_sm_limits(-1, 0)
