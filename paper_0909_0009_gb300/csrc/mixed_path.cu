@@ -24,23 +24,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Noise in FP32 from the same Philox words as the FP64 path: the 53-bit uniforms are
-// rounded to FP32 (relative 2^-24), so draws agree with the FP64 path to ~1e-7.
-__device__ __forceinline__ float2 box_muller_f32(uint64_t wa, uint64_t wb) {
-  const float u1 = __ull2float_rn((wa >> 11) + 1) * 0x1p-53f;
-  const float u2 = __ull2float_rn(wb >> 11) * 0x1p-53f;
-  const float rho = sqrtf(-2.0f * logf(u1));
-  float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  return make_float2(rho * c, rho * s);
-}
-
-__device__ __forceinline__ float2 noise_value_f32(float2 g, int m) {
-  if (m == 0) return make_float2(g.x, 0.f);
-  const float h = 0.70710678118654752f;
-  return make_float2(g.x * h, g.y * h);
-}
-
 // Double-float accumulation (hi + lo, ~48 significant bits from FP32 operations):
 // the exact square of x (product and fmaf residual) is added with a two-sum.
 __device__ __forceinline__ void df_add(float& hi, float& lo, float p, float e) {

@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
 // HEALPix rings: per (shell s, ring pair jp) of ring length n and offset phi_0.  The packed
 // spectrum Z_k' = sum_{m = k' mod n, |m| <= L} e^{i m phi_0} (F_N,m + i F_S,m) (F_X,-m = conj F_X,m;
 // the short polar rings fold m above n / 2 onto their bins) goes to the ring values
-// z = f_N + i f_S by an inverse DFT of length n, taken as conj(DFT(conj Z)) with Bluestein's
+// z = f_N + i f_S by an inverse DFT of length n: on the belt rings (n = 4 nside, a power of two)
+// by the object's own stockham plan, on the polar caps as conj(DFT(conj Z)) with Bluestein's
 // algorithm: a = (x c) zero-padded to M, A = FFT_M(a), y = IFFT_M(A Bf) / M, X_m = c_m y_m.  The
 // square mode then forms w = (Re z)^2 - mu + i ((Im z)^2 - mu), takes W = DFT_n(w) the same way and
 // writes S, D of G_m = e^{-i m phi_0} W_{m mod n} (north / south separated as on the Gauss-Legendre
@@ -448,6 +449,8 @@ struct HpArgs {
   int64_t sp, sj, npix;   // F and G strides (SIMT layout), pixels per map
   FftPlan plan;           // of M
   const cplx<T>* tw;      // [M]
+  FftPlan dplan;          // of nmax = 4 nside: the belt rings' length, transformed directly
+  const cplx<T>* dtw;     // [nmax]
   const int* n;           // [npairs]
   const int64_t* off;     // [ntheta + 1]
   const cplx<T>* rot;     // [npairs][L+1]
@@ -483,6 +486,7 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
   const int L = a.L, n = a.n[jp];
+  const bool direct = (n == a.nmax);
   const cplx<T>* rot = a.rot + (size_t)jp * (L + 1);
   const cplx<T>* c = a.chirp + (size_t)jp * a.nmax;
   const cplx<T>* bf = a.bf + (size_t)jp * a.M;
@@ -512,16 +516,21 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
         }
         acc = cadd(acc, cmul(P, cplx<T>{FN.x - FS.y, FN.y + FS.x}));
       }
-      b0[kp] = {acc.x, -acc.y};  // conj: the inverse DFT as conj(DFT(conj Z))
+        // the belt rings (n = 4 nside) transform directly; the caps by Bluestein as conj(DFT(conj Z))
+      b0[kp] = direct ? acc : cplx<T>{acc.x, -acc.y};
     }
     __syncthreads();
-    cplx<T>* y = bluestein(b0, b1, a, n, c, bf);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const cplx<T> v = cmul(c[k], y[k]);
-      y[k] = {v.x * invM, -v.y * invM};
+    if (direct) {
+      z = stockham(b0, b1, a.dplan, a.dtw, (T)1);
+    } else {
+      cplx<T>* y = bluestein(b0, b1, a, n, c, bf);
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const cplx<T> v = cmul(c[k], y[k]);
+        y[k] = {v.x * invM, -v.y * invM};
+      }
+      __syncthreads();
+      z = y;
     }
-    __syncthreads();
-    z = y;
     if (MODE == FFT_SYNTH_MAP) {
       double* rn = a.maps_out + (size_t)s * a.npix + a.off[jp];
       double* rs = a.maps_out + (size_t)s * a.npix + a.off[south];
@@ -535,13 +544,22 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) z[k] = {z[k].x * z[k].x - mu, z[k].y * z[k].y - mu};
     __syncthreads();
   }
-  cplx<T>* y = bluestein(z, z == b0 ? b1 : b0, a, n, c, bf);
+  // W = DFT_n of the ring values
+  cplx<T>* W;
+  if (direct) {
+    W = stockham(z, z == b0 ? b1 : b0, a.dplan, a.dtw, (T)-1);
+  } else {
+    W = bluestein(z, z == b0 ? b1 : b0, a, n, c, bf);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const cplx<T> v = cmul(c[k], W[k]);
+      W[k] = {v.x * invM, v.y * invM};
+    }
+    __syncthreads();
+  }
   const T scale = (T)(6.28318530717958647692 / n * a.wgl[jp]);
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
     const int kp = m % n, kc = (n - kp) % n;
-    cplx<T> wm = cmul(c[kp], y[kp]), wc = cmul(c[kc], y[kc]);
-    wm = {wm.x * invM, wm.y * invM};
-    wc = {wc.x * invM, wc.y * invM};
+    const cplx<T> wm = W[kp], wc = W[kc];
     cplx<T> gn = {(wm.x + wc.x) * (T)0.5, (wm.y - wc.y) * (T)0.5};
     cplx<T> gs = {(wm.y + wc.y) * (T)0.5, -(wm.x - wc.x) * (T)0.5};
     const cplx<T> rc = {rot[m].x, -rot[m].y};  // e^{-i m phi_0}
@@ -785,6 +803,8 @@ void healpix_impl(const fnl_shells* sh, int mode, const double* maps_in, double*
   a.npix = sh->npix;
   a.plan = sh->hp_plan;
   a.tw = (const cplx<T>*)sh->d_hp_tw;
+  a.dplan = sh->fft;
+  a.dtw = (const cplx<T>*)sh->d_tw;
   a.n = sh->d_hp_n;
   a.off = sh->d_hp_off;
   a.rot = (const cplx<T>*)sh->d_hp_rot;

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
   double* vs = (double*)(ns + nr);                // [2][nr]
   double* red = vs + 2 * nr;                      // [4][kThreads / 32]
   T* Ks = (T*)(red + 4 * (kThreads / 32));        // [nr][nr + 1] (padded rows: no bank conflicts)
+  T* nt = Ks + (size_t)nr * (nr + 1);             // [2][nr] the noise in T (re, then im)
   const int ldk = nr + 1;
   const T* Kl = Kf + (size_t)l * nr * nr;
   for (int e = threadIdx.x; e < nr * nr; e += kThreads) Ks[(e / nr) * ldk + (e % nr)] = Kl[e];
@@ -53,14 +54,29 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
         ns[j] = v;
       }
     } else {
+      // the FP64 form draws in FP64; the FP32 form through the FP32 Box-Muller of the mixed
+      // forms (the FP64 pipe of this part is far too slow for a transcendental per draw)
       for (int jp = threadIdx.x; jp < (nr + 1) / 2; jp += kThreads) {
         uint64_t w[4];
         noise_words(seed, real, idx, jp, w);
-        ns[2 * jp] = noise_value(box_muller(w[0], w[1]), m);
-        if (2 * jp + 1 < nr) ns[2 * jp + 1] = noise_value(box_muller(w[2], w[3]), m);
+        if (sizeof(T) == sizeof(double)) {
+          ns[2 * jp] = noise_value(box_muller(w[0], w[1]), m);
+          if (2 * jp + 1 < nr) ns[2 * jp + 1] = noise_value(box_muller(w[2], w[3]), m);
+        } else {
+          const float2 g0 = noise_value_f32(box_muller_f32(w[0], w[1]), m);
+          ns[2 * jp] = make_double2(g0.x, g0.y);
+          if (2 * jp + 1 < nr) {
+            const float2 g1 = noise_value_f32(box_muller_f32(w[2], w[3]), m);
+            ns[2 * jp + 1] = make_double2(g1.x, g1.y);
+          }
+        }
       }
     }
     __syncthreads();
+    for (int j = threadIdx.x; j < nr; j += kThreads) {
+      nt[j] = (T)ns[j].x;
+      nt[nr + j] = (T)ns[j].y;
+    }
     // a^X_L = sum_j v^X_l[j] n_j  (FP64)
     double tr = 0.0, ti = 0.0, er = 0.0, ei = 0.0;
     for (int j = threadIdx.x; j < nr; j += kThreads) {
@@ -82,6 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
       red[16 + warp] = er;
       red[24 + warp] = ei;
     }
+    __syncthreads();  // nt complete
     // Phi_L,lm(r_i) = sum_{j <= i} K_l[i, j] n_j
     const int p = (l - m) & 1;
     const int64_t row = row0[2 * m + p] + ((l - m) >> 1);
@@ -89,7 +106,8 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
       const int i = c >> 1, r = c & 1;
       T acc = 0;
       const T* Ki = Ks + (size_t)i * ldk;
-      for (int j = 0; j <= i; ++j) acc += Ki[j] * (T)(r ? ns[j].y : ns[j].x);
+      const T* nj = nt + (r ? nr : 0);
+      for (int j = 0; j <= i; ++j) acc += Ki[j] * nj[j];
       phi[row * C + c] = acc;
       if (phi_api) phi_api[((size_t)idx * nr + i) * 2 + r] = (double)acc;
     }
@@ -351,7 +369,7 @@ void filter_impl(const fnl_shells* sh, uint64_t seed, uint64_t real, const doubl
                  double* aLE, double* phi_api, cudaStream_t st) {
   const int nr = sh->nr;
   const size_t smem = sizeof(double2) * nr + sizeof(double) * 2 * nr + sizeof(double) * 4 * (kThreads / 32) +
-                      sizeof(T) * (size_t)nr * (nr + 1);
+                      sizeof(T) * (size_t)nr * (nr + 1) + sizeof(T) * 2 * (size_t)nr;
   FNL_CUDA(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, (const T*)sh->d_Kf, sh->d_vT, sh->d_vE, seed,
                                                     real, noise, sh->d_row0, (T*)sh->d_phi, phi_api, aLT, aLE);
