@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
 // Estimator rings: per (shell s, ring pair jp) the maps A (columns 2s, 2s + 1 of F) and B
 // (columns 2 (nsh + s), + 1) on the north and south rings (inverse DFTs as in the square), then
 // sum_k A B^2 on each ring (the equator once), times the ring's Gauss-Legendre weight, into
-// part[s][jp] (FP64 sums).
+// part[s][jp] (per-thread sums in the real type, FP64 across threads).
 template <typename T>
 __device__ __forceinline__ void pack_rings(const FftArgs<T>& a, int jp, int col, cplx<T>* b) {
   const int N = a.plan.n, L = a.L;
@@ -624,12 +624,13 @@ __global__ void __launch_bounds__(256) k_ring_cubic(const FftArgs<T> a, int nsh,
   cplx<T>* x = (A == b0) ? b1 : b0;
   pack_rings(a, jp, 2 * (nsh + s), x);
   const cplx<T>* B = stockham(x, b2, a.plan, a.tw, (T)1);
-  double acc = 0.0;
+  T acct = (T)0;  // per-thread sums in the real type, FP64 across threads
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const cplx<T> av = A[k], bv = B[k];
-    acc += (double)av.x * (double)bv.x * (double)bv.x;
-    if (!equator) acc += (double)av.y * (double)bv.y * (double)bv.y;
+    acct += av.x * bv.x * bv.x;
+    if (!equator) acct += av.y * bv.y * bv.y;
   }
+  double acc = (double)acct;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();

@@ -466,8 +466,8 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1)
 // their B spectra (columns 2 (nsh + s)).  Phases 1a, 1b and the inverse half of phase 2 run as
 // in the square and leave every field's ring values in its buffer, in the same permuted order;
 // then the A group of each shell sums A B^2 over the ring pair (north rings in x, south in y,
-// the equator once; FP32 products, FP64 sums) and writes the GL weight times the sum to
-// part[s][jp].
+// the equator once; FP32 products and per-thread sums, FP64 across threads) and writes the GL
+// weight times the sum to part[s][jp].
 struct CubeArgs {
   int L, nsh, ntheta, npairs;
   int64_t sp, sj;      // F strides between problems mp and ring pairs jp (floats)
@@ -588,15 +588,15 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_cubic_
       const float2* BA = buf + (size_t)g * NB;
       const float2* BB = buf + (size_t)(g + H) * NB;
       const bool equator = (a.ntheta - 1 - jp == jp);
-      double acc = 0.0;
+      float accf = 0.f;  // N / TG terms per thread in FP32, the block sums in FP64
       for (int t = u; t < N; t += TG) {
         const int n1 = t % N1, r = t / N1, d = r % P, c = r / P;
         const int pos = N1 * d + S * c + n1;
         const float2 x = BA[pos], y = BB[pos];
-        float s = x.x * y.x * y.x;
-        if (!equator) s += x.y * y.y * y.y;
-        acc += (double)s;
+        accf += x.x * y.x * y.x;
+        if (!equator) accf += x.y * y.y * y.y;
       }
+      double acc = (double)accf;
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if ((u & 31) == 0) red[g][u >> 5] = acc;
       group_sync<TG>(g);
