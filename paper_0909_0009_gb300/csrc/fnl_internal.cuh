@@ -196,16 +196,20 @@ struct fnl_shells {
 
   // HEALPix ring grid (nside > 0; FP64 and FP32 forms): ring pair j = ring j + 1 and its mirror
   int nside = 0;
-  int hp_M = 0;                    // Bluestein FFT length: a power of two >= 2 (4 nside) - 1
+  int hp_M = 0;                    // longest Bluestein FFT: a power of two >= 2 (4 nside) - 1
   int hp_nmax = 0;                 // longest ring, 4 nside
   int64_t npix = 0;                // 12 nside^2
-  fnl::FftPlan hp_plan;            // of hp_M
+  static constexpr int kHpPlans = 14;
+  fnl::FftPlan hp_plans[kHpPlans]; // plan of the power-of-two length 2^e
+  int64_t hp_twoff[kHpPlans] = {}; // offset of the twiddles of 2^e in d_hp_tw
   int* d_hp_n = nullptr;           // [npairs] ring lengths
+  int* d_hp_e = nullptr;           // [npairs] log2 of the ring's Bluestein length M_j >= 2 n_j - 1
+  int64_t* d_hp_bfoff = nullptr;   // [npairs] offset of the ring's filter DFT in d_hp_bf
   int64_t* d_hp_off = nullptr;     // [ntheta + 1] first pixel of each ring (RING order)
   void* d_hp_rot = nullptr;        // [npairs][L+1] complex: e^{i m phi_0}
   void* d_hp_chirp = nullptr;      // [npairs][hp_nmax] complex: e^{-i pi k^2 / n}
-  void* d_hp_bf = nullptr;         // [npairs][hp_M] complex: DFT_M of the chirp filter
-  void* d_hp_tw = nullptr;         // [hp_M] complex: e^{-2 pi i k / hp_M}
+  void* d_hp_bf = nullptr;         // per ring pair, M_j complex: DFT_{M_j} of the chirp filter
+  void* d_hp_tw = nullptr;         // per power of two 2^e: e^{-2 pi i k / 2^e}, k < 2^e
 
   // SIMT tile lists
   fnl::Tile* d_tiles_syn = nullptr;

@@ -10,7 +10,8 @@
 //
 // The ring transforms have lengths n = 4 i that need not be 2/3/5-smooth, so the ring kernel
 // takes each ring's DFT by Bluestein's chirp-z algorithm (X_m = c_m sum_k (x_k c_k) conj(c_{m-k}),
-// c_k = e^{-i pi k^2 / n}, a circular convolution of length M, a power of two >= 2 n - 1, by FFTs).
+// c_k = e^{-i pi k^2 / n}, a circular convolution of length M_j, the ring's own power of two
+// >= 2 n - 1, by FFTs); the belt rings (n = 4 nside, a power of two) need none of it.
 // Tables per ring pair: the chirp c_k (k < n), the M-point DFT of the filter b (b_j = conj(c_j) for
 // 0 <= j < n and b_{M-j} = conj(c_j) for 0 < j < n, else 0), and e^{i m phi_0} for m <= l_max; all
 // built in FP64 on the host (k^2 reduced modulo 2 n exactly before the angle is formed).
@@ -72,35 +73,51 @@ V* upload_vec(fnl_shells* sh, const std::vector<V>& v) {
 
 template <typename T>
 void build_tables(fnl_shells* sh) {
-  const int nside = sh->nside, np = sh->npairs, L = sh->lmax, M = sh->hp_M, nmax = sh->hp_nmax;
+  const int nside = sh->nside, np = sh->npairs, L = sh->lmax, nmax = sh->hp_nmax;
   std::vector<double> z, phi0;
   std::vector<int> n;
   healpix_rings(nside, z, n, phi0);
   std::vector<int64_t> off(sh->ntheta + 1, 0);
   for (int i = 0; i < sh->ntheta; ++i) off[i + 1] = off[i] + n[i];
   sh->npix = off[sh->ntheta];
-  std::vector<int> npair(n.begin(), n.begin() + np);
-  std::vector<std::complex<double>> rot((size_t)np * (L + 1)), chirp((size_t)np * nmax), bf((size_t)np * M);
-  std::vector<std::complex<double>> b(M);
+  std::vector<int> npair(n.begin(), n.begin() + np), e(np);
+  std::vector<int64_t> bfoff(np);
+  int64_t bftotal = 0;
   for (int j = 0; j < np; ++j) {
-    const int nj = n[j];
+    int ej = 0;
+    while ((1 << ej) < 2 * n[j] - 1) ++ej;
+    e[j] = ej;
+    bfoff[j] = bftotal;
+    bftotal += (int64_t)1 << ej;
+  }
+  std::vector<std::complex<double>> rot((size_t)np * (L + 1)), chirp((size_t)np * nmax), bf((size_t)bftotal);
+  for (int j = 0; j < np; ++j) {
+    const int nj = n[j], M = 1 << e[j];
     for (int m = 0; m <= L; ++m) rot[(size_t)j * (L + 1) + m] = std::polar(1.0, (double)m * phi0[j]);
     for (int k = 0; k < nj; ++k) {
-      const long long e = ((long long)k * k) % (2LL * nj);
-      chirp[(size_t)j * nmax + k] = std::polar(1.0, -M_PI * (double)e / (double)nj);
+      const long long ee = ((long long)k * k) % (2LL * nj);
+      chirp[(size_t)j * nmax + k] = std::polar(1.0, -M_PI * (double)ee / (double)nj);
     }
-    std::fill(b.begin(), b.end(), std::complex<double>(0.0, 0.0));
+    std::vector<std::complex<double>> b(M, std::complex<double>(0.0, 0.0));
     for (int k = 0; k < nj; ++k) {
       const std::complex<double> c = std::conj(chirp[(size_t)j * nmax + k]);
       b[k] = c;
       if (k) b[M - k] = c;
     }
     host_fft(b);
-    for (int k = 0; k < M; ++k) bf[(size_t)j * M + k] = b[k];
+    for (int k = 0; k < M; ++k) bf[(size_t)bfoff[j] + k] = b[k];
   }
-  std::vector<std::complex<double>> tw(M);
-  for (int k = 0; k < M; ++k) tw[k] = std::polar(1.0, -2.0 * M_PI * (double)k / (double)M);
+  // twiddles of every power of two up to the longest Bluestein length
+  std::vector<std::complex<double>> tw;
+  for (int ee = 0; ee < fnl_shells::kHpPlans && (1 << ee) <= sh->hp_M; ++ee) {
+    const int M = 1 << ee;
+    sh->hp_twoff[ee] = (int64_t)tw.size();
+    if (ee >= 1) sh->hp_plans[ee] = make_fft_plan(M);
+    for (int k = 0; k < M; ++k) tw.push_back(std::polar(1.0, -2.0 * M_PI * (double)k / (double)M));
+  }
   sh->d_hp_n = upload_vec(sh, npair);
+  sh->d_hp_e = upload_vec(sh, e);
+  sh->d_hp_bfoff = upload_vec(sh, bfoff);
   sh->d_hp_off = upload_vec(sh, off);
   sh->d_hp_rot = upload_complex<T>(sh, rot);
   sh->d_hp_chirp = upload_complex<T>(sh, chirp);
@@ -141,7 +158,7 @@ void setup_healpix(fnl_shells* sh) {
   int M = 1;
   while (M < 2 * sh->hp_nmax - 1) M <<= 1;
   sh->hp_M = M;
-  sh->hp_plan = make_fft_plan(M);
+  FNL_REQUIRE(M < (1 << fnl_shells::kHpPlans), "nside too large for the HEALPix ring kernel");
   const size_t ts = sh->real_is_double ? 16 : 8;
   FNL_REQUIRE(2 * ts * (size_t)M <= 227 * 1024, "nside too large for the HEALPix ring kernel's shared memory");
   if (sh->real_is_double) build_tables<double>(sh);

@@ -445,17 +445,20 @@ __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
 // maps [nr][N_pix].
 template <typename T>
 struct HpArgs {
-  int L, ntheta, npairs, M, nmax;
+  int L, ntheta, npairs, nmax, cap;  // cap: complex values per shared-memory buffer
   int64_t sp, sj, npix;   // F and G strides (SIMT layout), pixels per map
-  FftPlan plan;           // of M
-  const cplx<T>* tw;      // [M]
+  FftPlan plans[fnl_shells::kHpPlans];      // plan of the power of two 2^e
+  int64_t twoff[fnl_shells::kHpPlans];      // its twiddles in tw
+  const cplx<T>* tw;      // e^{-2 pi i k / 2^e} for every 2^e
   FftPlan dplan;          // of nmax = 4 nside: the belt rings' length, transformed directly
   const cplx<T>* dtw;     // [nmax]
   const int* n;           // [npairs]
+  const int* e;           // [npairs] log2 of the ring's Bluestein length
+  const int64_t* bfoff;   // [npairs]
   const int64_t* off;     // [ntheta + 1]
   const cplx<T>* rot;     // [npairs][L+1]
   const cplx<T>* chirp;   // [npairs][nmax]
-  const cplx<T>* bf;      // [npairs][M]
+  const cplx<T>* bf;      // per ring pair, M_j
   const T* F;
   T* G;
   const double* mu;
@@ -467,21 +470,21 @@ struct HpArgs {
 // DFT_n of x[0..n) (in buf, capacity M) by Bluestein; returns the buffer whose first n entries
 // hold X_m / M ... times c_m: the caller reads X_m = c_m y_m / M from it.
 template <typename T>
-__device__ cplx<T>* bluestein(cplx<T>* buf, cplx<T>* other, const HpArgs<T>& a, int n, const cplx<T>* c,
-                              const cplx<T>* bf) {
-  for (int k = threadIdx.x; k < a.M; k += blockDim.x) buf[k] = k < n ? cmul(buf[k], c[k]) : cplx<T>{(T)0, (T)0};
+__device__ cplx<T>* bluestein(cplx<T>* buf, cplx<T>* other, int M, const FftPlan& plan, const cplx<T>* tw, int n,
+                              const cplx<T>* c, const cplx<T>* bf) {
+  for (int k = threadIdx.x; k < M; k += blockDim.x) buf[k] = k < n ? cmul(buf[k], c[k]) : cplx<T>{(T)0, (T)0};
   __syncthreads();
-  cplx<T>* A = stockham(buf, other, a.plan, a.tw, (T)-1);
-  for (int k = threadIdx.x; k < a.M; k += blockDim.x) A[k] = cmul(A[k], bf[k]);
+  cplx<T>* A = stockham(buf, other, plan, tw, (T)-1);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) A[k] = cmul(A[k], bf[k]);
   __syncthreads();
-  return stockham(A, A == buf ? other : buf, a.plan, a.tw, (T)1);
+  return stockham(A, A == buf ? other : buf, plan, tw, (T)1);
 }
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   cplx<T>* b0 = (cplx<T>*)smem;
-  cplx<T>* b1 = b0 + a.M;
+  cplx<T>* b1 = b0 + a.cap;
   const int s = blockIdx.x, jp = blockIdx.y;
   const int south = a.ntheta - 1 - jp;
   const bool equator = (south == jp);
@@ -489,8 +492,11 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
   const bool direct = (n == a.nmax);
   const cplx<T>* rot = a.rot + (size_t)jp * (L + 1);
   const cplx<T>* c = a.chirp + (size_t)jp * a.nmax;
-  const cplx<T>* bf = a.bf + (size_t)jp * a.M;
-  const T invM = (T)1 / (T)a.M;
+  const cplx<T>* bf = a.bf + a.bfoff[jp];
+  const int ej = a.e[jp], M = 1 << ej;
+  const FftPlan& plan = a.plans[ej];
+  const cplx<T>* tw = a.tw + a.twoff[ej];
+  const T invM = (T)1 / (T)M;
   cplx<T>* z;
   if (MODE == FFT_ANALYSE_MAP) {
     const double* rn = a.maps_in + (size_t)s * a.npix + a.off[jp];
@@ -523,7 +529,7 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
     if (direct) {
       z = stockham(b0, b1, a.dplan, a.dtw, (T)1);
     } else {
-      cplx<T>* y = bluestein(b0, b1, a, n, c, bf);
+      cplx<T>* y = bluestein(b0, b1, M, plan, tw, n, c, bf);
       for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const cplx<T> v = cmul(c[k], y[k]);
         y[k] = {v.x * invM, -v.y * invM};
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(256) k_ring_healpix(const HpArgs<T> a) {
   if (direct) {
     W = stockham(z, z == b0 ? b1 : b0, a.dplan, a.dtw, (T)-1);
   } else {
-    W = bluestein(z, z == b0 ? b1 : b0, a, n, c, bf);
+    W = bluestein(z, z == b0 ? b1 : b0, M, plan, tw, n, c, bf);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const cplx<T> v = cmul(c[k], W[k]);
       W[k] = {v.x * invM, v.y * invM};
@@ -797,13 +803,18 @@ void healpix_impl(const fnl_shells* sh, int mode, const double* maps_in, double*
   a.L = sh->lmax;
   a.ntheta = sh->ntheta;
   a.npairs = sh->npairs;
-  a.M = sh->hp_M;
   a.nmax = sh->hp_nmax;
+  a.cap = std::max(sh->hp_M, sh->hp_nmax);
   a.sp = (int64_t)sh->npairs * sh->C;
   a.sj = sh->C;
   a.npix = sh->npix;
-  a.plan = sh->hp_plan;
+  for (int e = 0; e < fnl_shells::kHpPlans; ++e) {
+    a.plans[e] = sh->hp_plans[e];
+    a.twoff[e] = sh->hp_twoff[e];
+  }
   a.tw = (const cplx<T>*)sh->d_hp_tw;
+  a.e = sh->d_hp_e;
+  a.bfoff = sh->d_hp_bfoff;
   a.dplan = sh->fft;
   a.dtw = (const cplx<T>*)sh->d_tw;
   a.n = sh->d_hp_n;
@@ -817,7 +828,7 @@ void healpix_impl(const fnl_shells* sh, int mode, const double* maps_in, double*
   a.wgl = sh->d_wgl;
   a.maps_in = maps_in;
   a.maps_out = maps_out;
-  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)a.M;
+  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)a.cap;
   const dim3 grid(sh->nr, sh->npairs);
   switch (mode) {
     case FFT_SQUARE:
