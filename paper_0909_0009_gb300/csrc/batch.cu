@@ -154,20 +154,18 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
 
   // Legendre GEMMs: one tile list over all instances, the tiles of one (instance, problem)
   // adjacent, groups largest first; instance maps for the constant table
-  FNL_CUDA(cudaMallocHost(&b->pinned, sizeof(CUtensorMap) * 12 * (size_t)n));
+  FNL_CUDA(cudaMallocHost(&b->pinned, sizeof(CUtensorMap) * 4 * (size_t)n));
   b->h_maps_syn = (CUtensorMap*)b->pinned;
-  b->h_maps_ana = b->h_maps_syn + 6 * (size_t)n;
+  b->h_maps_ana = b->h_maps_syn + 2 * (size_t)n;
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<TcInst> insts(n);
     std::vector<std::pair<int64_t, std::vector<TcTile>>> groups;
     for (int i = 0; i < n; ++i) {
       const fnl_shells* s = b->run[i];
       insts[i] = s->tci[dir];
-      CUtensorMap* maps = (dir ? b->h_maps_ana : b->h_maps_syn) + 6 * (size_t)i;
-      for (int t = 0; t < 3; ++t) {
-        maps[t] = s->tci[dir].tmA[t];
-        maps[3 + t] = s->tci[dir].tmB[t];
-      }
+      CUtensorMap* maps = (dir ? b->h_maps_ana : b->h_maps_syn) + 2 * (size_t)i;
+      maps[0] = s->tci[dir].tmA;
+      maps[1] = s->tci[dir].tmB;
       const std::vector<TcTile>& tl = dir ? s->tiles_ana_h : s->tiles_syn_h;
       for (size_t k = 0; k < tl.size(); ++k) {
         if (k == 0 || tl[k].mp != tl[k - 1].mp) groups.push_back({0, {}});

@@ -197,29 +197,25 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
 
 // The per-configuration part of the tensor-core GEMMs' arguments that does not depend on
 // the tile shape: the A tensor maps (BF16, MN-major, 128B swizzle; boxes of 64 columns x 64 k
-// x both 64-column halves of a 128-column tile, through a view whose last dimension steps over
-// the halves, 128 B apart) and the scratch and table pointers.  Entry 0 is the synthesis,
-// entry 1 the analysis.
+// x both 64-column halves of a 128-column tile, through a view whose next dimension steps over
+// the halves, 128 B apart, and whose last dimension steps over the BF16 terms) and the scratch
+// and table pointers.  Entry 0 is the synthesis, entry 1 the analysis.
 void build_tc_inst_a(fnl_shells* sh) {
-  typedef unsigned short bf16_t;
   const int L = sh->lmax, nr = sh->nr, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms, Cpad = sh->Cpad;
   const int64_t rows32 = sh->row32[nmp];
-  for (int t = 0; t < T; ++t) {
-    const bf16_t* phi = (const bf16_t*)sh->d_phiT + (size_t)t * sh->phiT_stride;
-    const bf16_t* gt = (const bf16_t*)sh->d_GT + (size_t)t * sh->gt_stride;
-    {
-      const uint64_t dims[3] = {64, (uint64_t)rows32, (uint64_t)Cpad / 64};
-      const uint64_t str[2] = {(uint64_t)Cpad * 2, 128};
-      const uint32_t box[3] = {64, (uint32_t)kTcStageK, 2};
-      sh->tci[0].tmA[t] = make_tensor_map_bf16(phi, 3, dims, str, box, 128);
-    }
-    {
-      // G is ring-pair-major, [jp][mp][Cpad]: box of 64 columns x 1 problem x 64 ring pairs x 2 halves
-      const uint64_t dims[4] = {64, (uint64_t)nmp, (uint64_t)np, (uint64_t)Cpad / 64};
-      const uint64_t str[3] = {(uint64_t)Cpad * 2, (uint64_t)nmp * Cpad * 2, 128};
-      const uint32_t box[4] = {64, 1, (uint32_t)kTcStageK, 2};
-      sh->tci[1].tmA[t] = make_tensor_map_bf16(gt, 4, dims, str, box, 128);
-    }
+  {
+    const uint64_t dims[4] = {64, (uint64_t)rows32, (uint64_t)Cpad / 64, (uint64_t)T};
+    const uint64_t str[3] = {(uint64_t)Cpad * 2, 128, (uint64_t)sh->phiT_stride * 2};
+    const uint32_t box[4] = {64, (uint32_t)kTcStageK, 2, (uint32_t)T};
+    sh->tci[0].tmA = make_tensor_map_bf16(sh->d_phiT, 4, dims, str, box, 128);
+  }
+  {
+    // G is ring-pair-major, [term][jp][mp][Cpad]: box of 64 columns x 1 problem x 64 ring pairs
+    // x 2 halves x every term
+    const uint64_t dims[5] = {64, (uint64_t)nmp, (uint64_t)np, (uint64_t)Cpad / 64, (uint64_t)T};
+    const uint64_t str[4] = {(uint64_t)Cpad * 2, (uint64_t)nmp * Cpad * 2, 128, (uint64_t)sh->gt_stride * 2};
+    const uint32_t box[5] = {64, 1, (uint32_t)kTcStageK, 2, (uint32_t)T};
+    sh->tci[1].tmA = make_tensor_map_bf16(sh->d_GT, 5, dims, str, box, 128);
   }
   for (TcInst& I : sh->tci) {
     I.F = (float*)sh->d_F;
@@ -235,30 +231,25 @@ void build_tc_inst_a(fnl_shells* sh) {
 }
 
 // Tensor maps of the B operands (BF16, K-major, 64B swizzle): boxes of nmax rows x two 32-deep
-// slabs (64 k per stage); rows past the table are zero-filled.  Then the two entries go to
-// the device.
+// slabs (64 k per stage) x every BF16 term; rows past the table are zero-filled.  Then the
+// two entries go to the device.
 void build_tc_inst_b(fnl_shells* sh) {
-  typedef unsigned short bf16_t;
   const int L = sh->lmax, np = sh->npairs, nmp = 2 * (L + 1), T = sh->nterms;
   const int64_t nslab = sh->row32[nmp] / 32, rows16 = sh->rows_total;
-  for (int t = 0; t < T; ++t) {
-    const bf16_t* lsyn = (const bf16_t*)sh->d_lsyn + (size_t)t * sh->lsyn_stride;
-    const bf16_t* lana = (const bf16_t*)sh->d_lana + (size_t)t * sh->lana_stride;
-    {
-      // Lambda_syn [slab][jp][32 k]
-      const uint64_t dims[3] = {32, (uint64_t)np, (uint64_t)nslab};
-      const uint64_t str[2] = {64, (uint64_t)np * 64};
-      const uint32_t box[3] = {32, (uint32_t)sh->tc_syn.nmax, 2};
-      sh->tci[0].tmB[t] = make_tensor_map_bf16(lsyn, 3, dims, str, box, 64);
-    }
-    {
-      // Lambda_ana [row16][npj]: 32 ring pairs x rows x blocks of 32 ring pairs (64 B apart;
-      // npj is a multiple of 32, so every block stays inside its row)
-      const uint64_t dims[3] = {32, (uint64_t)rows16, (uint64_t)sh->npj / 32};
-      const uint64_t str[2] = {(uint64_t)sh->npj * 2, 64};
-      const uint32_t box[3] = {32, (uint32_t)sh->tc_ana.nmax, 2};
-      sh->tci[1].tmB[t] = make_tensor_map_bf16(lana, 3, dims, str, box, 64);
-    }
+  {
+    // Lambda_syn [term][slab][jp][32 k]
+    const uint64_t dims[4] = {32, (uint64_t)np, (uint64_t)nslab, (uint64_t)T};
+    const uint64_t str[3] = {64, (uint64_t)np * 64, (uint64_t)sh->lsyn_stride * 2};
+    const uint32_t box[4] = {32, (uint32_t)sh->tc_syn.nmax, 2, (uint32_t)T};
+    sh->tci[0].tmB = make_tensor_map_bf16(sh->d_lsyn, 4, dims, str, box, 64);
+  }
+  {
+    // Lambda_ana [term][row16][npj]: 32 ring pairs x rows x blocks of 32 ring pairs (64 B
+    // apart; npj is a multiple of 32, so every block stays inside its row)
+    const uint64_t dims[4] = {32, (uint64_t)rows16, (uint64_t)sh->npj / 32, (uint64_t)T};
+    const uint64_t str[3] = {(uint64_t)sh->npj * 2, 64, (uint64_t)sh->lana_stride * 2};
+    const uint32_t box[4] = {32, (uint32_t)sh->tc_ana.nmax, 2, (uint32_t)T};
+    sh->tci[1].tmB = make_tensor_map_bf16(sh->d_lana, 4, dims, str, box, 64);
   }
   FNL_CUDA(cudaMemcpy(sh->d_tci, sh->tci, sizeof(sh->tci), cudaMemcpyHostToDevice));
   sh->tc_syn.one = sh->tci[0];
@@ -382,8 +373,7 @@ fnl_shells* clone_scratch(const fnl_shells* src) {
 }
 
 void refresh_clone(fnl_shells* c, const fnl_shells* src) {
-  for (int k = 0; k < 2; ++k)
-    for (int t = 0; t < 3; ++t) c->tci[k].tmB[t] = src->tci[k].tmB[t];
+  for (int k = 0; k < 2; ++k) c->tci[k].tmB = src->tci[k].tmB;
   FNL_CUDA(cudaMemcpy(c->d_tci, c->tci, sizeof(c->tci), cudaMemcpyHostToDevice));
   c->tc_syn = src->tc_syn;
   c->tc_ana = src->tc_ana;

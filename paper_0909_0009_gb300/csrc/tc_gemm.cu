@@ -11,18 +11,22 @@
 // and every product of terms whose indices sum to less than the term count is
 // accumulated in FP32 in tensor memory (3 products for 2 terms, 6 for 3 terms).
 //
-// Kernel structure (one persistent CTA per SM, 192 threads):
-//   warp 0      TMA producer, stages 64 deep in k: per term one box of A (128 c x 64 k: both
-//               64-column halves through a 3D/4D view, 128B swizzle) and one of B (nmax rows x
-//               two 32-deep slabs, 64B swizzle).  Few, large boxes: the copy engine's cost
-//               is per box, and 4 KB boxes cap it near a fifth of what 32 KB boxes move
+// Kernel structure (one persistent CTA per SM, 320 threads):
+//   warp 0      TMA producer, stages 64 deep in k: one box of A (per term 128 c x 64 k: both
+//               64-column halves through a view with a dimension over the halves, 128B
+//               swizzle) and one of B (per term nmax rows x two 32-deep slabs, 64B swizzle),
+//               each carrying every BF16 term through a last dimension over the terms: two
+//               boxes per stage of 28-32 KB each (4 KB boxes move about a sixth of what 32 KB
+//               boxes do per clock)
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma (M = 128, N = tile width
 //               up to 256, K = 16) from one thread, up to 4 k steps per stage and one commit
 //               per stage (each commit costs the pipe a few hundred cycles); the descriptors of
 //               every term and k step are constant offsets from one base per stage.  The leading product and the
 //               correction products accumulate in two TMEM accumulators (`cols` apart); the
 //               accumulator sets that fit (1 for 256-wide tiles, 2 for 128) rotate over tiles
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator, then per mode:
+//   warps 2-9   epilogue, two warps per TMEM lane quadrant taking alternate 32-column chunks
+//               (twice the stores in flight of one warp per quadrant): tcgen05.ld of the
+//               accumulator, then per mode:
 //               synthesis -> F (FP32); analysis -> radial quadrature of Eq. 5 reduced over
 //               the shells of the tile (T and E), or the per-shell coefficients.
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and unwinds.
@@ -40,9 +44,9 @@ namespace fnl {
 namespace {
 
 // Tensor maps of the instances of a multi-instance launch (see TcArgs::multi).
-__constant__ CUtensorMap c_tc_maps[kTcMaxInst * 6];
+__constant__ CUtensorMap c_tc_maps[kTcMaxInst * 2];
 
-constexpr int kEpiWarps = 4;
+constexpr int kEpiWarps = 8;  // two per TMEM lane quadrant, splitting a tile's 32-column chunks
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -78,23 +82,19 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
   return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, int w,
                                             uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
       ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, int w, int v,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+      ::"r"(dst), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(w), "r"(v), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
   uint64_t* drain = tempty + 2;
   uint64_t* epib = drain + 1;  // [2] rendezvous of the epilogue warps
   uint32_t* tslot = (uint32_t*)(epib + 2);
-  float* red = (float*)(smem + (size_t)S * stageBytes + 1024);  // [4 warps][256 cols][2 fields][2 parities]
+  float* red = (float*)(smem + (size_t)S * stageBytes + 1024);  // [4 quadrants][256 cols][2 fields][2 parities]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t sbase = smem_u32(smem);
@@ -251,14 +251,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       int prev_inst = -1;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
-        const CUtensorMap* mA = MULTI ? c_tc_maps + 6 * tl.inst : a.one.tmA;
-        const CUtensorMap* mB = MULTI ? c_tc_maps + 6 * tl.inst + 3 : a.one.tmB;
+        const CUtensorMap* mA = MULTI ? c_tc_maps + 2 * tl.inst : &a.one.tmA;
+        const CUtensorMap* mB = MULTI ? c_tc_maps + 2 * tl.inst + 1 : &a.one.tmB;
         if (MULTI && tl.inst != prev_inst && lane == 0) {
           // bring this instance's tensor maps into the copy engine's descriptor cache
-          for (int tm = 0; tm < a.nterms; ++tm) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mA[tm]) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mB[tm]) : "memory");
-          }
+          asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mA) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mB) : "memory");
         }
         prev_inst = tl.inst;
         const int nst = (tl.nkb + 1) / 2;
@@ -276,21 +274,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             mbar_expect_tx(&full[stage], stageBytes);
             armed |= 1u << stage;
             armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-            const uint32_t st = sbase + (uint32_t)stage * stageBytes;
-            for (int tm = 0; tm < a.nterms; ++tm) {
-              const uint32_t sa = st + (uint32_t)tm * kTcABytes;
-              const uint32_t sb = st + (uint32_t)a.nterms * kTcABytes + (uint32_t)tm * bBytes;
-              if (a.mode == TC_SYNTH) {
-                // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
-                tma_load_3d(sa, &mA[tm], 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, &full[stage]);
-                // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
-                tma_load_3d(sb, &mB[tm], 0, tl.n0, tl.r0 / 32 + 2 * sg, &full[stage]);
-              } else {
-                // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
-                tma_load_4d(sa, &mA[tm], 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, &full[stage]);
-                // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
-                tma_load_3d(sb, &mB[tm], 0, tl.r0 + tl.n0, 2 * sg, &full[stage]);
-              }
+            // every term in one box per operand: term t lands t * kTcABytes (A) or t * bBytes
+            // (B) after the operand's start
+            const uint32_t sa = sbase + (uint32_t)stage * stageBytes;
+            const uint32_t sb = sa + (uint32_t)a.nterms * kTcABytes;
+            if (a.mode == TC_SYNTH) {
+              // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
+              tma_load_4d(sa, mA, 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
+              // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
+              tma_load_4d(sb, mB, 0, tl.n0, tl.r0 / 32 + 2 * sg, 0, &full[stage]);
+            } else {
+              // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
+              tma_load_5d(sa, mA, 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
+              // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
+              tma_load_4d(sb, mB, 0, tl.r0 + tl.n0, 2 * sg, 0, &full[stage]);
             }
           }  // lane 0
           __syncwarp();
@@ -382,8 +379,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     }
   } else {
     // ------------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
-    const int ew = warp - 2;
+    const int q = warp & 3;         // TMEM lane quadrant this warp may access
+    const int h = (warp - 2) >> 2;  // which of the quadrant's two warps: chunks h, h + 2, ..
     int acc = 0;
     uint32_t aphase = 0, ephase = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -407,7 +404,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       const int c = tl.c0 + 32 * q + lane;
       const bool cvalid = c < 2 * nr;
       const int nch = (tl.nsize + 31) / 32;
-      for (int ch = 0; ch < nch; ++ch) {
+      const int last = nch - 1 - ((nch - 1 - h) & 1);  // this warp's last chunk (< 0: none)
+      if (last < 0) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+      }
+      for (int ch = h; ch < nch; ch += 2) {
         float v[32];
         const uint32_t ta = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols) + (uint32_t)(ch * 32) +
                             ((uint32_t)(32 * q) << 16);
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
-        if (ch == nch - 1) {
+        if (ch == last) {
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -464,7 +467,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           reduce_columns(tx, lane);
           reduce_columns(ex, lane);
           const int col = ch * 32 + (lane & 30);
-          float* rw = red + (size_t)ew * 1024;
+          float* rw = red + (size_t)q * 1024;  // the quadrant's two warps write disjoint chunks
           const int r = lane & 1;
           rw[(col + 0) * 4 + 0 * 2 + r] = tx[0];
           rw[(col + 1) * 4 + 0 * 2 + r] = tx[1];
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           if (k >= tl.kvalid) continue;
           float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int w = 0; w < kEpiWarps; ++w) {
+          for (int w = 0; w < 4; ++w) {
             const float* rw = red + (size_t)w * 1024 + n * 4;
             s.x += rw[0];
             s.y += rw[1];
@@ -551,7 +554,7 @@ int tc_stages(int nterms, int nmax, int mode) {
 
 void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st) {
   if (n < 1 || n > kTcMaxInst) throw Error(FNL_EINVAL, "too many instances for one tensor-core launch");
-  FNL_CUDA(cudaMemcpyToSymbolAsync(c_tc_maps, host, sizeof(CUtensorMap) * 6 * (size_t)n, 0,
+  FNL_CUDA(cudaMemcpyToSymbolAsync(c_tc_maps, host, sizeof(CUtensorMap) * 2 * (size_t)n, 0,
                                    cudaMemcpyHostToDevice, st));
 }
 

@@ -17,9 +17,10 @@ struct TcTile {
   int mp, c0, n0, nsize, nkb, r0, kvalid, inst;
 };
 
-// Operands arrive in stages 64 deep in k: per BF16 term one TMA box of A (128 columns x 64 k,
-// both 64-column halves, MN-major, 128B swizzle) and one of B (nmax rows x 64 k as two
-// 32-deep slabs, K-major, 64B swizzle), and one commit releases the stage.
+// Operands arrive in stages 64 deep in k: one TMA box of A holding every BF16 term (per term
+// 128 columns x 64 k, both 64-column halves, MN-major, 128B swizzle) and one of B (per term
+// nmax rows x 64 k as two 32-deep slabs, K-major, 64B swizzle), and one commit releases the
+// stage.
 constexpr int kTcStageK = 64;
 constexpr uint32_t kTcABytes = 128u * kTcStageK * 2u;  // A bytes per term and stage
 
@@ -31,8 +32,8 @@ constexpr int kTcMaxInst = 64;
 // parameters for one instance, a constant-memory table for several): the copy engine reads
 // a map from global memory far more slowly than from those two spaces.
 struct alignas(64) TcInst {
-  CUtensorMap tmA[3];   // per BF16 term: Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves}
-  CUtensorMap tmB[3];   // per BF16 term: Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs}
+  CUtensorMap tmA;      // Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves, terms}
+  CUtensorMap tmB;      // Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs, terms}
   float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
   float4* part;         // TC_ANA_QUAD: [Cpad / 128][nalm] (T re, T im, E re, E im)
   const float* qT;      // [L+1][nr]
@@ -43,7 +44,7 @@ struct alignas(64) TcInst {
 
 struct TcArgs {
   TcInst one;           // the single instance (multi == 0), maps and fields in parameter space
-  int multi;            // 1: maps of instance i at c_tc_maps[6 i .. 6 i + 5] (A terms, B terms),
+  int multi;            // 1: maps of instance i at c_tc_maps[2 i] (A) and c_tc_maps[2 i + 1] (B),
                         //    its other fields at insts[i]
   const TcInst* insts;  // device array indexed by TcTile::inst (multi == 1)
   const TcTile* tiles;
@@ -65,7 +66,7 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode);
 int tc_stages(int nterms, int nmax, int mode);
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st);
-// Copy n instances' maps (A0..A2, B0..B2 each) into the constant table, on `st` from pinned
+// Copy n instances' maps (A and B each) into the constant table, on `st` from pinned
 // host memory that stays unchanged until the copy has run.
 void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st);
 
