@@ -82,6 +82,11 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
   return false;
 }
 
+// One try inline, then the bounded loop.
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t* bar, uint32_t parity, int* err, int code) {
+  return mbar_try_wait(bar, parity) || mbar_wait(bar, parity, err, code);
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, int w,
                                             uint64_t* bar) {
   asm volatile(
@@ -242,8 +247,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
 
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
-    // The whole warp walks the loop (converged); lane 0 waits and issues.
-    {
+    // Lane 0 alone walks the loop, waits and issues (no warp-wide exchange per stage).
+    if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         const TcTile tl = a.tiles[t];
         const CUtensorMap* mA = MULTI ? c_tc_maps + 2 * tl.inst : &a.one.tmA;
         const CUtensorMap* mB = MULTI ? c_tc_maps + 2 * tl.inst + 1 : &a.one.tmB;
-        if (MULTI && tl.inst != prev_inst && lane == 0) {
+        if (MULTI && tl.inst != prev_inst) {
           // bring this instance's tensor maps into the copy engine's descriptor cache
           asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mA) : "memory");
           asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mB) : "memory");
@@ -261,43 +266,37 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         prev_inst = tl.inst;
         const int nst = (tl.nkb + 1) / 2;
         for (int sg = 0; sg < nst; ++sg) {
-          int good = 1;
-          if (lane == 0) good = mbar_wait(&empty[stage], phase ^ 1, a.err, 1);
-          good = __shfl_sync(0xffffffffu, good, 0);
-          if (!good) {
+          if (!mbar_wait_fast(&empty[stage], phase ^ 1, a.err, 1)) {
             ok = false;
             break;
           }
-          if (lane == 0) {
-            // boxes past the end of a tensor are zero-filled; a second slab past the tile's
-            // last k block is loaded but never read by the MMAs
-            mbar_expect_tx(&full[stage], stageBytes);
-            armed |= 1u << stage;
-            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-            // every term in one box per operand: term t lands t * kTcABytes (A) or t * bBytes
-            // (B) after the operand's start
-            const uint32_t sa = sbase + (uint32_t)stage * stageBytes;
-            const uint32_t sb = sa + (uint32_t)a.nterms * kTcABytes;
-            if (a.mode == TC_SYNTH) {
-              // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
-              tma_load_4d(sa, mA, 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
-              // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
-              tma_load_4d(sb, mB, 0, tl.n0, tl.r0 / 32 + 2 * sg, 0, &full[stage]);
-            } else {
-              // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
-              tma_load_5d(sa, mA, 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
-              // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
-              tma_load_4d(sb, mB, 0, tl.r0 + tl.n0, 2 * sg, 0, &full[stage]);
-            }
-          }  // lane 0
-          __syncwarp();
+          // boxes past the end of a tensor are zero-filled; a second slab past the tile's
+          // last k block is loaded but never read by the MMAs
+          mbar_expect_tx(&full[stage], stageBytes);
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          // every term in one box per operand: term t lands t * kTcABytes (A) or t * bBytes
+          // (B) after the operand's start
+          const uint32_t sa = sbase + (uint32_t)stage * stageBytes;
+          const uint32_t sb = sa + (uint32_t)a.nterms * kTcABytes;
+          if (a.mode == TC_SYNTH) {
+            // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
+            tma_load_4d(sa, mA, 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
+            // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
+            tma_load_4d(sb, mB, 0, tl.n0, tl.r0 / 32 + 2 * sg, 0, &full[stage]);
+          } else {
+            // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
+            tma_load_5d(sa, mA, 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
+            // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
+            tma_load_4d(sb, mB, 0, tl.r0 + tl.n0, 2 * sg, 0, &full[stage]);
+          }
           if (++stage == S) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
-      if (!ok && lane == 0) {
+      if (!ok) {
         // let the copies already issued land before the CTA unwinds (bounded)
         for (int s = 0; s < S; ++s) {
           if (!(armed >> s & 1u)) continue;
@@ -306,12 +305,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           }
         }
       }
-      __syncwarp();
     }
+    __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
-    // The whole warp walks the loop (converged); lane 0 waits, issues and commits.
-    {
+    // Lane 0 alone walks the loop, waits, issues and commits.
+    if (lane == 0) {
       // A: MN-major, 128B swizzle, halves 64 k x 128 B apart; B: K-major, 64B swizzle
       const uint64_t da0 = sdesc(sbase, (uint32_t)kTcStageK * 128u, 1024, 2);
       const uint64_t db0 = sdesc(sbase + (uint32_t)a.nterms * kTcABytes, 16, 512, 4);
@@ -323,24 +322,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       bool ok = true;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
-        int good = 1;
-        if (lane == 0) good = mbar_wait(&tempty[acc], aphase ^ 1, a.err, 2);
-        good = __shfl_sync(0xffffffffu, good, 0);
-        if (!good) break;
+        if (!mbar_wait_fast(&tempty[acc], aphase ^ 1, a.err, 2)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols);
         const uint32_t idesc = idesc_bf16(tl.nsize);
         const int nst = (tl.nkb + 1) / 2;
         for (int sg = 0; sg < nst; ++sg) {
-          good = 1;
-          if (lane == 0) good = mbar_wait(&full[stage], phase, a.err, 3);
-          good = __shfl_sync(0xffffffffu, good, 0);
-          if (!good) {
+          if (!mbar_wait_fast(&full[stage], phase, a.err, 3)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          if (lane == 0) {
+          {
             const uint32_t so = (uint32_t)stage * (stageBytes >> 4);
             const uint64_t da = da0 + so, db = db0 + so;
             const bool first = sg == 0;
@@ -355,28 +348,24 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             }
             tc_commit(&empty[stage]);
           }
-          __syncwarp();
           if (++stage == S) {
             stage = 0;
             phase ^= 1;
           }
         }
         if (!ok) break;
-        if (lane == 0) tc_commit(&tfull[acc]);
-        __syncwarp();
+        tc_commit(&tfull[acc]);
         if (++acc == a.nbuf) {
           acc = 0;
           aphase ^= 1;
         }
       }
-      // every MMA this warp issued has completed before TMEM is released (bounded)
-      if (lane == 0) {
-        tc_commit(drain);
-        for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(drain, 0); ++i) {
-        }
+      // every MMA this thread issued has completed before TMEM is released (bounded)
+      tc_commit(drain);
+      for (uint32_t i = 0; i < kWaitLimit && !mbar_try_wait(drain, 0); ++i) {
       }
-      __syncwarp();
     }
+    __syncwarp();
   } else {
     // ------------------------------------------------------------------ epilogue
     const int q = warp & 3;         // TMEM lane quadrant this warp may access
