@@ -46,7 +46,8 @@ namespace {
 // Tensor maps of the instances of a multi-instance launch (see TcArgs::multi).
 __constant__ CUtensorMap c_tc_maps[kTcMaxInst * 2];
 
-constexpr int kEpiWarps = 8;  // two per TMEM lane quadrant, splitting a tile's 32-column chunks
+constexpr int kEpiWarps = 12;                // per TMEM lane quadrant kEpiPerQuad warps take turns
+constexpr int kEpiPerQuad = kEpiWarps / 4;  // over a tile's 32-column chunks
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -127,6 +128,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading/stride byte offsets,
@@ -369,7 +383,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
   } else {
     // ------------------------------------------------------------------ epilogue
     const int q = warp & 3;         // TMEM lane quadrant this warp may access
-    const int h = (warp - 2) >> 2;  // which of the quadrant's two warps: chunks h, h + 2, ..
+    const int h = (warp - 2) >> 2;  // which of the quadrant's warps: chunks h, h + kEpiPerQuad, ..
     int acc = 0;
     uint32_t aphase = 0, ephase = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -392,17 +406,57 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       const int m = tl.mp >> 1, p = tl.mp & 1;
       const int c = tl.c0 + 32 * q + lane;
       const bool cvalid = c < 2 * nr;
+      const uint32_t tacc = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols) + ((uint32_t)(32 * q) << 16);
+      if (a.mode == TC_SYNTH) {
+        // F (FP32, ring-pair-major F[jp][mp][Cpad]) in 16-column chunks, spread over the
+        // quadrant's warps; TMEM is released after each warp's last load, before its stores
+        const int nch = (tl.nsize + 15) / 16;
+        const int last = nch - 1 < h ? -1 : h + (nch - 1 - h) / kEpiPerQuad * kEpiPerQuad;
+        if (last < 0) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+        float* out = I.F + (size_t)tl.mp * I.Cpad + c;
+        const size_t sj = (size_t)2 * (L + 1) * I.Cpad;
+        for (int ch = h; ch < nch; ch += kEpiPerQuad) {
+          float v[16];
+          tmem_ld16(tacc + (uint32_t)(ch * 16), v);
+          if (a.split) {
+            float w[16];
+            tmem_ld16(tacc + (uint32_t)(ch * 16) + (uint32_t)a.cols, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += w[j];
+          }
+          if (ch == last) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+          }
+          if (cvalid) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int jr = tl.n0 + ch * 16 + j;
+              if (ch * 16 + j < tl.nsize && jr < I.npairs) out[(size_t)jr * sj] = v[j];
+            }
+          }
+        }
+        if (++acc == a.nbuf) {
+          acc = 0;
+          aphase ^= 1;
+        }
+        continue;
+      }
       const int nch = (tl.nsize + 31) / 32;
-      const int last = nch - 1 - ((nch - 1 - h) & 1);  // this warp's last chunk (< 0: none)
+      const int last = nch - 1 < h ? -1 : h + (nch - 1 - h) / kEpiPerQuad * kEpiPerQuad;  // this warp's last chunk
       if (last < 0) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[acc]);
       }
-      for (int ch = h; ch < nch; ch += 2) {
+      for (int ch = h; ch < nch; ch += kEpiPerQuad) {
         float v[32];
-        const uint32_t ta = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols) + (uint32_t)(ch * 32) +
-                            ((uint32_t)(32 * q) << 16);
+        const uint32_t ta = tacc + (uint32_t)(ch * 32);
         tmem_ld32(ta, v);
         if (a.split) {
           float w[32];
@@ -415,18 +469,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[acc]);
         }
-        if (a.mode == TC_SYNTH) {
-          if (cvalid) {
-            // F is ring-pair-major: F[jp][mp][Cpad]
-            float* out = I.F + (size_t)tl.mp * I.Cpad + c;
-            const size_t sj = (size_t)2 * (L + 1) * I.Cpad;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int jr = tl.n0 + ch * 32 + j;
-              if (ch * 32 + j < tl.nsize && jr < I.npairs) out[(size_t)jr * sj] = v[j];
-            }
-          }
-        } else if (a.mode == TC_ANA_STORE) {
+        if (a.mode == TC_ANA_STORE) {
           if (cvalid) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -456,7 +499,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           reduce_columns(tx, lane);
           reduce_columns(ex, lane);
           const int col = ch * 32 + (lane & 30);
-          float* rw = red + (size_t)q * 1024;  // the quadrant's two warps write disjoint chunks
+          float* rw = red + (size_t)q * 1024;  // the quadrant's warps write disjoint chunks
           const int r = lane & 1;
           rw[(col + 0) * 4 + 0 * 2 + r] = tx[0];
           rw[(col + 1) * 4 + 0 * 2 + r] = tx[1];
