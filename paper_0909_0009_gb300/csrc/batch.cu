@@ -137,7 +137,7 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
   for (int i = 0; i < n; ++i) {
     const fnl_shells* s = b->run[i];
     const int64_t n2 = 2 * s->nalm;
-    fi[i] = FilterInst{s->lmax, s->nr, s->Cpad, s->nterms, s->phiT_stride, (const float*)s->d_Kf, s->d_vT, s->d_vE,
+    fi[i] = FilterInst{s->lmax, s->nr, s->Cpad, s->nterms, s->phiT_stride, s->d_Kft, s->d_vT, s->d_vE,
                        s->d_row32, (__nv_bfloat16*)s->d_phiT, s->d_aL, s->d_aL + n2, s->d_psum_part, s->d_psum};
     ci[i] = CombineInst{s->nalm, s->Cpad / 128, s->nr, (const float4*)s->d_part, s->d_psum, s->d_mu, s->d_qT,
                         s->d_qE, (const double2*)s->d_aL, (const double2*)(s->d_aL + n2), (double2*)s->d_aNL,

@@ -240,7 +240,7 @@ void build_tc_inst_b(fnl_shells* sh) {
     // Lambda_syn [term][slab][jp][32 k]
     const uint64_t dims[4] = {32, (uint64_t)np, (uint64_t)nslab, (uint64_t)T};
     const uint64_t str[3] = {64, (uint64_t)np * 64, (uint64_t)sh->lsyn_stride * 2};
-    const uint32_t box[4] = {32, (uint32_t)sh->tc_syn.nmax, 2, (uint32_t)T};
+    const uint32_t box[4] = {32, (uint32_t)sh->tc_syn.nmax, (uint32_t)kTcSlabs, (uint32_t)T};
     sh->tci[0].tmB = make_tensor_map_bf16(sh->d_lsyn, 4, dims, str, box, 64);
   }
   {
@@ -248,7 +248,7 @@ void build_tc_inst_b(fnl_shells* sh) {
     // apart; npj is a multiple of 32, so every block stays inside its row)
     const uint64_t dims[4] = {32, (uint64_t)rows16, (uint64_t)sh->npj / 32, (uint64_t)T};
     const uint64_t str[3] = {(uint64_t)sh->npj * 2, 64, (uint64_t)sh->lana_stride * 2};
-    const uint32_t box[4] = {32, (uint32_t)sh->tc_ana.nmax, 2, (uint32_t)T};
+    const uint32_t box[4] = {32, (uint32_t)sh->tc_ana.nmax, (uint32_t)kTcSlabs, (uint32_t)T};
     sh->tci[1].tmB = make_tensor_map_bf16(sh->d_lana, 4, dims, str, box, 64);
   }
   FNL_CUDA(cudaMemcpy(sh->d_tci, sh->tci, sizeof(sh->tci), cudaMemcpyHostToDevice));
@@ -668,6 +668,16 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
     } else {
       std::vector<float> kf(Kf.begin(), Kf.end()), twf(tw.begin(), tw.end()), twpf(twp.begin(), twp.end());
       sh->d_Kf = upload(sh, kf);
+      if (mixed && !synth_only) {
+        // the filter kernel's shared-memory image of K_l, transposed and padded, copied as is
+        const int nrp = (nr + 7) / 8 * 8;
+        std::vector<float> kft((size_t)(L + 1) * nr * nrp, 0.f);
+        for (int l = 0; l <= L; ++l)
+          for (int i = 0; i < nr; ++i)
+            for (int j = 0; j <= i; ++j)
+              kft[((size_t)l * nr + j) * nrp + i] = (float)Kf[((size_t)l * nr + i) * nr + j];
+        sh->d_Kft = upload(sh, kft);
+      }
       sh->d_tw = upload(sh, twf);
       sh->d_twp = upload(sh, twpf);
     }

@@ -129,6 +129,8 @@ struct fnl_shells {
   double* d_wgl = nullptr;         // [npairs]
   void* d_lam = nullptr;           // SIMT table, real type, [lam_total]
   void* d_Kf = nullptr;            // [L+1][nr][nr] real type
+  float* d_Kft = nullptr;          // tensor-core forms: [L+1][nr][nrp] FP32, Kt[j][i] = K_l[i][j]
+                                   // (nrp = nr rounded up to 8; zero above the diagonal and in the padding)
   double* d_vT = nullptr;          // [L+1][nr]  v^X_l = K_l^T q^X_l
   double* d_vE = nullptr;
   double* d_qT = nullptr;          // [L+1][nr]  q^X_l[i] = w_i r_i^2 alpha^X_l(r_i)
@@ -327,7 +329,7 @@ struct MultiOut {
 struct FilterInst {
   int L, nr, Cpad, nterms;
   int64_t term_stride;
-  const float* Kf;
+  const float* Kft;  // [L+1][nr][nrp], as fnl_shells::d_Kft
   const double* vT;
   const double* vE;
   const int64_t* row32;

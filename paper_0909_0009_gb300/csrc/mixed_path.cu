@@ -60,7 +60,7 @@ constexpr int kFCols = 64;
 __host__ __device__ inline int out_stride(int nrp) { return nrp + 4; }
 
 __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int nterms, int64_t term_stride,
-                                                             const float* __restrict__ Kf,
+                                                             const float* __restrict__ Kft,
                                                              const double* __restrict__ vT,
                                                              const double* __restrict__ vE, uint64_t seed,
                                                              uint64_t real, const double* __restrict__ noise,
@@ -77,14 +77,11 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
   // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo; then [2][kFCols][2] partial a^X_L sums (dfp)
   float* vs = nt + (size_t)max(nr * kFCols, kFCols * os);
                                                             // then [2][kFCols][2] (dfp below)
-  const float* Kl = Kf + (size_t)l * nr * nr;
-  for (int e = threadIdx.x; e < nr * nrp; e += kThreads) {
-    const int i = e / nr, j = e % nr;       // global reads along j
-    if (i < nrp) Kt[(size_t)j * nrp + i] = (i < nr && j <= i) ? Kl[(size_t)i * nr + j] : 0.f;
-  }
-  for (int e = threadIdx.x; e < nr * (nrp - nr); e += kThreads) {
-    const int j = e / (nrp - nr), i = nr + e % (nrp - nr);
-    Kt[(size_t)j * nrp + i] = 0.f;
+  // K_l arrives transposed and padded (set-up): a straight copy of nr * nrp floats
+  {
+    const float4* src = (const float4*)(Kft + (size_t)l * nr * nrp);
+    float4* dst = (float4*)Kt;
+    for (int e = threadIdx.x; e < nr * nrp / 4; e += kThreads) dst[e] = src[e];
   }
   for (int e = threadIdx.x; e < nr; e += kThreads) {
     const double t = vT[(size_t)l * nr + e], u = vE[(size_t)l * nr + e];
@@ -240,7 +237,7 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
 
 // One configuration: block b takes degree l = L - b (largest first).
 __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
-                                                             const float* __restrict__ Kf,
+                                                             const float* __restrict__ Kft,
                                                              const double* __restrict__ vT,
                                                              const double* __restrict__ vE, uint64_t seed,
                                                              uint64_t real, const double* __restrict__ noise,
@@ -248,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
                                                              __nv_bfloat16* __restrict__ phiT,
                                                              double* __restrict__ phi_api, double* __restrict__ aLT,
                                                              double* __restrict__ aLE, double* __restrict__ psum) {
-  filter_body(L - (int)blockIdx.x, L, nr, Cpad, nterms, term_stride, Kf, vT, vE, seed, real, noise, row32, phiT,
+  filter_body(L - (int)blockIdx.x, L, nr, Cpad, nterms, term_stride, Kft, vT, vE, seed, real, noise, row32, phiT,
               phi_api, aLT, aLE, psum);
 }
 
@@ -258,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_multi(const FilterInst* 
                                                               const int2* __restrict__ blocks, const MultiKeys keys) {
   const int2 b = blocks[blockIdx.x];
   const FilterInst f = inst[b.x];
-  filter_body(b.y, f.L, f.nr, f.Cpad, f.nterms, f.term_stride, f.Kf, f.vT, f.vE, keys.seed[b.x], keys.real[b.x],
+  filter_body(b.y, f.L, f.nr, f.Cpad, f.nterms, f.term_stride, f.Kft, f.vT, f.vE, keys.seed[b.x], keys.real[b.x],
               nullptr, f.row32, f.phiT, nullptr, f.aLT, f.aLE, f.psum_part);
 }
 
@@ -468,7 +465,7 @@ void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, con
                                       4 * nr + 4 * kFCols);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
-                                                     (const float*)sh->d_Kf, sh->d_vT, sh->d_vE, seed, real, noise,
+                                                     sh->d_Kft, sh->d_vT, sh->d_vE, seed, real, noise,
                                                      sh->d_row32, (__nv_bfloat16*)sh->d_phiT, phi_api, aLT, aLE,
                                                      psum ? sh->d_psum_part : nullptr);
   FNL_CUDA(cudaGetLastError());

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int S = a.stages;
-  const uint32_t bBytes = (uint32_t)a.nmax * 128u;  // B bytes per term and stage (two slabs)
+  const uint32_t bBytes = (uint32_t)a.nmax * 64u * kTcSlabs;  // B bytes per term and stage
   const uint32_t stageBytes = (uint32_t)a.nterms * (kTcABytes + bBytes);
   uint64_t* full = (uint64_t*)(smem + (size_t)S * stageBytes);
   uint64_t* empty = full + S;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mB) : "memory");
         }
         prev_inst = tl.inst;
-        const int nst = (tl.nkb + 1) / 2;
+        const int nst = (tl.nkb + kTcSlabs - 1) / kTcSlabs;
         for (int sg = 0; sg < nst; ++sg) {
           if (!mbar_wait_fast(&empty[stage], phase ^ 1, a.err, 1)) {
             ok = false;
@@ -297,12 +297,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
             tma_load_4d(sa, mA, 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
             // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
-            tma_load_4d(sb, mB, 0, tl.n0, tl.r0 / 32 + 2 * sg, 0, &full[stage]);
+            tma_load_4d(sb, mB, 0, tl.n0, tl.r0 / 32 + kTcSlabs * sg, 0, &full[stage]);
           } else {
             // A: G at problem mp, ring pairs 64 sg .., column halves c0 / 64, c0 / 64 + 1
             tma_load_5d(sa, mA, 0, tl.mp, kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
             // B: Lambda_ana rows r0 + n0 .., ring-pair blocks 2 sg, 2 sg + 1
-            tma_load_4d(sb, mB, 0, tl.r0 + tl.n0, 2 * sg, 0, &full[stage]);
+            tma_load_4d(sb, mB, 0, tl.r0 + tl.n0, kTcSlabs * sg, 0, &full[stage]);
           }
           if (++stage == S) {
             stage = 0;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols);
         const uint32_t idesc = idesc_bf16(tl.nsize);
-        const int nst = (tl.nkb + 1) / 2;
+        const int nst = (tl.nkb + kTcSlabs - 1) / kTcSlabs;
         for (int sg = 0; sg < nst; ++sg) {
           if (!mbar_wait_fast(&full[stage], phase, a.err, 3)) {
             ok = false;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             const uint32_t so = (uint32_t)stage * (stageBytes >> 4);
             const uint64_t da = da0 + so, db = db0 + so;
             const bool first = sg == 0;
-            const int nh = min(2, tl.nkb - 2 * sg);
+            const int nh = min(kTcSlabs, tl.nkb - kTcSlabs * sg);
             const uint32_t dc = d + (uint32_t)a.cols;
             if (a.nterms == 2) {
               if (a.split) issue_stage<2, true>(da, db, bterm16, bslab16, nh, d, dc, idesc, first);
@@ -573,7 +573,7 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
 }
 
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode) {
-  const size_t stage = (size_t)nterms * (kTcABytes + (size_t)nmax * 128);
+  const size_t stage = (size_t)nterms * (kTcABytes + (size_t)nmax * 64 * kTcSlabs);
   const size_t red = mode == TC_SYNTH ? 0 : 4 * 256 * 4 * sizeof(float);  // epilogue reduction (analysis)
   return 1024 /*alignment*/ + (size_t)stages * stage + 1024 /*barriers*/ + red;
 }

@@ -22,6 +22,7 @@ struct TcTile {
 // nmax rows x 64 k as two 32-deep slabs, K-major, 64B swizzle), and one commit releases the
 // stage.
 constexpr int kTcStageK = 64;
+constexpr int kTcSlabs = kTcStageK / 32;               // 32-deep B slabs per stage
 constexpr uint32_t kTcABytes = 128u * kTcStageK * 2u;  // A bytes per term and stage
 
 // Instances (configurations or realisations) in one multi-instance launch, at most.
