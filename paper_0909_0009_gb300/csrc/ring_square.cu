@@ -238,11 +238,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *(const uint32_t*)&h;
-}
-
 // BF16 terms of (x, y): term 0 = bf16(v), term t = bf16(v - sum of earlier terms)
 __device__ __forceinline__ void store_pair_terms(__nv_bfloat16* p, int64_t stride, int nterms, float x, float y) {
   const __nv_bfloat162 h0 = __floats2bfloat162_rn(x, y);

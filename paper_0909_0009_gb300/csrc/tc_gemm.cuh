@@ -32,7 +32,7 @@ constexpr int kTcMaxInst = 64;
 // device memory and every tile names its entry.  The tensor maps are kept apart (kernel
 // parameters for one instance, a constant-memory table for several): the copy engine reads
 // a map from global memory far more slowly than from those two spaces.
-struct alignas(64) TcInst {
+struct alignas(128) TcInst {  // CUtensorMap is 128-byte aligned
   CUtensorMap tmA;      // Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves, terms}
   CUtensorMap tmB;      // Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs, terms}
   float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
