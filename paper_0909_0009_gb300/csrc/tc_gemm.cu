@@ -11,7 +11,8 @@
 // and every product of terms whose indices sum to less than the term count is
 // accumulated in FP32 in tensor memory (3 products for 2 terms, 6 for 3 terms).
 //
-// Kernel structure (one persistent CTA per SM, 320 threads):
+// Kernel structure (one persistent CTA per SM, 448 threads; the producer and MMA loops run on
+// one lane each, with no warp-wide exchange per stage):
 //   warp 0      TMA producer, stages 64 deep in k: one box of A (per term 128 c x 64 k: both
 //               64-column halves through a view with a dimension over the halves, 128B
 //               swizzle) and one of B (per term nmax rows x two 32-deep slabs, 64B swizzle),
@@ -24,9 +25,9 @@
 //               every term and k step are constant offsets from one base per stage.  The leading product and the
 //               correction products accumulate in two TMEM accumulators (`cols` apart); the
 //               accumulator sets that fit (1 for 256-wide tiles, 2 for 128) rotate over tiles
-//   warps 2-9   epilogue, two warps per TMEM lane quadrant taking alternate 32-column chunks
-//               (twice the stores in flight of one warp per quadrant): tcgen05.ld of the
-//               accumulator, then per mode:
+//   warps 2-13  epilogue, three warps per TMEM lane quadrant taking turns over the tile's
+//               column chunks (16 columns for the synthesis, 32 for the analysis; more warps
+//               keep more F stores in flight): tcgen05.ld of the accumulator, then per mode:
 //               synthesis -> F (FP32); analysis -> radial quadrature of Eq. 5 reduced over
 //               the shells of the tile (T and E), or the per-shell coefficients.
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and unwinds.
