@@ -91,10 +91,25 @@ def gemm_bytes(lmax: int, ntheta: int, nr: int, nterms: int) -> dict:
 
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
 # a one-pass metric taken on the full-size command of the launch-list summary under
-# profiles/), keyed by stage and workload.  Cleared whenever the kernel changes.
+# profiles/), keyed by stage, workload and form, together with the SHA-256 prefix of the
+# kernel's source file when it was captured: once that file changes the entry no longer
+# matches and the line reports traffic as null until the kernel is captured again.
 TRAFFIC = {
-    ("ring_fft_square", "lmax1024_nr128", "bf16x2"): 3.196e9,
+    ("ring_fft_square", "lmax1024_nr128", "bf16x2"): {
+        "bytes": 3.196e9, "source": "paper_0909_0009_gb300/csrc/ring_square.cu", "sha16": "1e39fc725b45911d"},
 }
+
+
+def traffic_of(key) -> float | None:
+    """Measured DRAM bytes per launch for `key`, or None when the kernel's source has changed
+    since the capture (or there is none)."""
+    import hashlib
+    e = TRAFFIC.get(key)
+    if e is None:
+        return None
+    with open(os.path.join(ROOT, e["source"]), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return e["bytes"] if sha == e["sha16"] else None
 
 FP32_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 lanes x FMA x max SM clock
 
@@ -652,8 +667,7 @@ def main():
     dom = max(per_stage, key=per_stage.get)
     roofline = dict(stages[dom])
     roofline["kernel"] = dom
-    tr = TRAFFIC.get((dom, wl.name, args.prec))
-    roofline["traffic"] = tr
+    roofline["traffic"] = traffic_of((dom, wl.name, args.prec))
     if dom == "ring_fft_square":
         roofline["algorithmic_bytes"] = fft_bytes(wl.lmax, wl.ntheta, wl.nr, real_bytes)
     roofline["stage_ms"] = {k: round(v, 4) for k, v in per_stage.items()}

@@ -304,6 +304,19 @@ fnl_status fnl_shells_set_sm_limits(fnl_shells* sh, int gemm_sms, int ring_sms);
  * device word instead of hanging), else FNL_OK.  Clears the word. */
 fnl_status fnl_device_status(const fnl_shells* sh);
 
+/* ---- test hooks (no counterpart in the paper) ----------------------------------------- */
+
+/* Make the device allocation after the next n ones fail with FNL_ENOMEM, as if cudaMalloc had
+ * failed (once; the hook then turns itself off), so that a test can check that every set-up
+ * call unwinds and frees what it had allocated; n = -1 turns the hook off.  Process-wide. */
+fnl_status fnl_test_fail_alloc(long n);
+
+/* Launch one bounded mbarrier wait of the tensor-core kernels (the same wait routine) on a
+ * barrier that nothing completes, with `limit` tries (1 .. 2^20): the wait runs out, records
+ * its code in the object's error word and returns, so fnl_device_status then reports
+ * FNL_ETIMEOUT.  Tensor-core objects only (FNL_EINVAL otherwise).  Asynchronous on `stream`. */
+fnl_status fnl_test_wait_expiry(const fnl_shells* sh, unsigned limit, void* stream);
+
 /* ---- batching form: many realisations of uneven l_max and N_r in one graph --------- */
 
 typedef struct fnl_batch fnl_batch; /* opaque: streams, events and the captured graph */
@@ -369,8 +382,8 @@ fnl_status fnl_shells_set_tiles(fnl_shells* sh, int syn_cap, int ana_cap);
  * callers that may not allocate: programs whose device memory belongs to another
  * allocator (a cudaMalloc outside it fails or fragments its pool), latency-bound loops
  * (cudaMalloc and cudaFree can synchronise the device), plug-ins held to a fixed memory
- * budget.  The paper has no counterpart: it is the radial quadrature of Eq. 5 and the sum
- * of Eq. 3, with the weights q^X_l[i] = w_i r_i^2 alpha^X_l(r_i) formed on each call into a
+ * budget.  The paper has no counterpart to this call.  It computes what fnl_accumulate
+ * computes, with the weights q^X_l[i] = w_i r_i^2 alpha^X_l(r_i) formed on each call into a
  * fixed array inside the library instead of a table made by fnl_make_shells.
  *  r, w:            device [nr] radial nodes and weights (8-byte aligned).
  *  alphaT, alphaE:  device [lmax+1][nr] alpha^X_l(r_i) (8-byte aligned).
@@ -380,13 +393,15 @@ fnl_status fnl_shells_set_tiles(fnl_shells* sh, int syn_cap, int ana_cap);
  * Sizes: 0 <= lmax <= 4096, 1 <= nr <= 128 and (lmax + 1) * nr <= FNL_NOALLOC_MAX_LNR,
  * else FNL_EINVAL before anything runs.  The array holds 2 * FNL_NOALLOC_MAX_LNR doubles
  * (8 MiB) on every GPU that loads the library, until the process exits.
- * Set-up: the first call on a device, with that device current, looks up the array's
- * device address (cudaGetSymbolAddress, which may load the library's device code); make
- * that first call before any stream capture begins.
+ * Set-up: the first call in a CUDA context (per device; again after cudaDeviceReset), with
+ * that device current, looks up the array's device address (cudaGetSymbolAddress, which may
+ * load the library's device code).  Make that first call before any stream capture begins:
+ * a first call on a capturing stream returns FNL_EUNSUPPORTED.
  * Every call uses the same array, and keeps in it the weights of the last call: each call
  * rewrites every weight it reads before reading it, so nothing there has to start at zero,
- * but calls that overlap on the GPU (concurrent streams, or threads sharing a device)
- * race on it: order them. */
+ * but calls that overlap on the GPU (concurrent streams, or threads sharing a device) race
+ * on it: a call holds the array from its first kernel (the weights) until its second (the
+ * sums) ends on its stream.  Order such calls. */
 fnl_status fnl_accumulate_noalloc(int lmax, int nr, const double* r, const double* w,
                                   const double* alphaT, const double* alphaE, const double* phiL,
                                   const double* phiNL, double fnl, double* aT, double* aE,

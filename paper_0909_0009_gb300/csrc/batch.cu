@@ -139,7 +139,7 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
     const int64_t n2 = 2 * s->nalm;
     fi[i] = FilterInst{s->lmax, s->nr, s->Cpad, s->nterms, s->phiT_stride, s->d_Kft, s->d_vT, s->d_vE,
                        s->d_row32, (__nv_bfloat16*)s->d_phiT, s->d_aL, s->d_aL + n2, s->d_psum_part, s->d_psum};
-    ci[i] = CombineInst{s->nalm, s->Cpad / 128, s->nr, (const float4*)s->d_part, s->d_psum, s->d_mu, s->d_qT,
+    ci[i] = CombineInst{s->nalm, s->Cpad / 128, s->nr, (const double2*)s->d_part, s->d_psum, s->d_mu, s->d_qT,
                         s->d_qE, (const double2*)s->d_aL, (const double2*)(s->d_aL + n2), (double2*)s->d_aNL,
                         (double2*)(s->d_aNL + n2)};
     for (int l = 0; l <= s->lmax; ++l) blocks.push_back(make_int2(i, l));

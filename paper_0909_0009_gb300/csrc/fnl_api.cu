@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <functional>
 #include <string>
 #include <vector>
@@ -55,6 +56,23 @@ bool smooth235(int n) {
 
 }  // namespace
 
+// Allocation-failure test hook: -1 = off; n >= 0 = the allocation after the next n ones fails
+// (once; the hook then turns itself off).
+static std::atomic<long> g_fail_alloc{-1};
+
+void* device_malloc(size_t bytes) {
+  long n = g_fail_alloc.load();
+  while (n >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(n, n == 0 ? -1 : n - 1)) {
+      if (n == 0) throw Error(FNL_ENOMEM, "device allocation failed (simulated by fnl_test_fail_alloc)");
+      break;
+    }
+  }
+  void* p = nullptr;
+  FNL_CUDA(cudaMalloc(&p, bytes ? bytes : 1));
+  return p;
+}
+
 void check_dev_ptr(const void* p, const char* name, bool nullable) {
   if (!p) {
     if (!nullable) throw Error(FNL_EINVAL, std::string(name) + " must not be NULL");
@@ -79,9 +97,8 @@ namespace {
 
 template <typename T>
 T* dalloc(fnl_shells* sh, size_t count) {
-  void* p = nullptr;
   const size_t bytes = sizeof(T) * (count ? count : 1);
-  FNL_CUDA(cudaMalloc(&p, bytes));
+  void* p = device_malloc(bytes);
   sh->allocations.push_back(p);
   sh->device_bytes += bytes;
   return (T*)p;
@@ -139,7 +156,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   sh->gt_stride = (int64_t)nmp * np * Cpad;
   sh->d_GT = dalloc<bf16_t>(sh, (size_t)T * sh->gt_stride);
   sh->d_F = dalloc<float>(sh, (size_t)nmp * np * Cpad);
-  sh->d_part = dalloc<float>(sh, 4 * (size_t)(Cpad / 128) * sh->nalm);
+  sh->d_part = dalloc<double>(sh, 4 * (size_t)(Cpad / 128) * sh->nalm);
   sh->d_err = dalloc<int>(sh, 1);
   sh->d_psum = dalloc<double>(sh, nr);
   sh->d_psum_part = dalloc<double>(sh, (size_t)(L + 1) * 2 * nr);
@@ -149,12 +166,18 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   FNL_CUDA(cudaMemset(sh->d_GT, 0, sizeof(bf16_t) * (size_t)T * sh->gt_stride));
   FNL_CUDA(cudaMemset(sh->d_F, 0, sizeof(float) * (size_t)nmp * np * Cpad));
   FNL_CUDA(cudaMemset(sh->d_err, 0, sizeof(int)));
-  std::vector<float> q32(2 * qT.size());
-  for (size_t i = 0; i < qT.size(); ++i) {
-    q32[i] = (float)qT[i];
-    q32[qT.size() + i] = (float)qE[i];
-  }
-  sh->d_q32 = upload(sh, q32);
+  // q^T, q^E of the quadrature epilogue as FP32 pairs hi + lo (48 significant bits), [l][X][i]
+  std::vector<float> q2(4 * qT.size());
+  for (int l = 0; l <= L; ++l)
+    for (int X = 0; X < 2; ++X)
+      for (int i = 0; i < nr; ++i) {
+        const double v = (X ? qE : qT)[(size_t)l * nr + i];
+        const float hi = (float)v;
+        const size_t o = (((size_t)l * 2 + X) * nr + i) * 2;
+        q2[o] = hi;
+        q2[o + 1] = (float)(v - (double)hi);
+      }
+  sh->d_q2 = (float2*)upload(sh, q2);
   sh->d_row32 = upload(sh, sh->row32);
   {
     std::vector<float> tw2, tw1;
@@ -219,9 +242,8 @@ void build_tc_inst_a(fnl_shells* sh) {
   }
   for (TcInst& I : sh->tci) {
     I.F = (float*)sh->d_F;
-    I.part = (float4*)sh->d_part;
-    I.qT = sh->d_q32;
-    I.qE = sh->d_q32 + (size_t)(L + 1) * nr;
+    I.part = (double2*)sh->d_part;
+    I.q2 = sh->d_q2;
     I.L = L;
     I.nr = nr;
     I.npairs = np;
@@ -351,7 +373,7 @@ fnl_shells* clone_scratch(const fnl_shells* src) {
     c->d_phiT = dalloc<bf16_t>(c, (size_t)T * c->phiT_stride);
     c->d_GT = dalloc<bf16_t>(c, (size_t)T * c->gt_stride);
     c->d_F = dalloc<float>(c, (size_t)nmp * np * Cpad);
-    c->d_part = dalloc<float>(c, 4 * (size_t)(Cpad / 128) * c->nalm);
+    c->d_part = dalloc<double>(c, 4 * (size_t)(Cpad / 128) * c->nalm);
     c->d_err = dalloc<int>(c, 1);
     c->d_psum = dalloc<double>(c, nr);
     c->d_psum_part = dalloc<double>(c, (size_t)(L + 1) * 2 * nr);
@@ -1053,6 +1075,23 @@ fnl_status fnl_profile_read(fnl_shells* sh, double* ms, int n, int* calls) {
     }
     if (calls) *calls = sh->ring_count;
     sh->ring_count = 0;
+  });
+}
+
+fnl_status fnl_test_fail_alloc(long n) {
+  return guard([&] {
+    FNL_REQUIRE(n >= -1, "n must be >= -1");
+    g_fail_alloc.store(n);
+  });
+}
+
+fnl_status fnl_test_wait_expiry(const fnl_shells* sh, unsigned limit, void* stream) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(sh->d_err, "fnl_test_wait_expiry: a tensor-core object is needed (it owns the error word)");
+    FNL_REQUIRE(limit >= 1 && limit <= (1u << 20), "limit must be in [1, 2^20]");
+    DeviceScope scope(sh->device);
+    launch_wait_probe(sh->d_err, limit, (cudaStream_t)stream);
   });
 }
 

@@ -49,6 +49,29 @@ void set_last_error(const std::string& msg);
     if (!(cond)) throw ::fnl::Error(FNL_EINVAL, (msg));          \
   } while (0)
 
+// ---- device memory of the set-up paths ---------------------------------------------------
+
+// cudaMalloc of `bytes` (at least 1), throwing FNL_ENOMEM / FNL_ECUDA; when the allocation-failure
+// test hook (fnl_test_fail_alloc) is armed, the chosen allocation fails instead, without calling
+// cudaMalloc, so that the unwinding of every set-up path can be tested.
+void* device_malloc(size_t bytes);
+
+// A temporary device buffer of a set-up step, freed when it goes out of scope (also when the
+// step throws).
+struct TempDev {
+  void* p = nullptr;
+  explicit TempDev(size_t bytes) : p(device_malloc(bytes)) {}
+  ~TempDev() {
+    if (p) cudaFree(p);
+  }
+  TempDev(const TempDev&) = delete;
+  TempDev& operator=(const TempDev&) = delete;
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
 // ---- small helpers --------------------------------------------------------------------
 
 template <typename T>
@@ -174,8 +197,8 @@ struct fnl_shells {
   void* d_sqtw2 = nullptr;         // float2 twiddles of the specialised ring kernel (NULL: none for nphi)
   void* d_sqtw1 = nullptr;
   int64_t gt_stride = 0;
-  void* d_part = nullptr;          // float4 [Cpad / 128][nalm]
-  float* d_q32 = nullptr;          // [2][L+1][nr]  q^T, q^E in FP32
+  void* d_part = nullptr;          // double2 [Cpad / 128][nalm][2]: quadrature partials per column tile
+  float2* d_q2 = nullptr;          // [L+1][2][nr]  q^T, q^E as FP32 pairs (hi, lo)
   int* d_err = nullptr;            // device error word of the tensor-core kernels
   double* d_psum = nullptr;        // [nr] sum_lm w_m |Phi_L,lm(r_i)|^2 (Parseval monopole)
   double* d_psum_part = nullptr;   // [(L+1) * 2][nr] the filter's partials of d_psum
@@ -343,7 +366,7 @@ struct FilterInst {
 struct CombineInst {
   int64_t nalm;
   int nct, nr;
-  const float4* part;
+  const double2* part;  // [nct][nalm][2]
   const double* psum;
   const double* mu;
   const double* qT;

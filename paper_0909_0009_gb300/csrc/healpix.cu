@@ -53,8 +53,7 @@ void* upload_complex(fnl_shells* sh, const std::vector<std::complex<double>>& v)
     h[2 * i] = (T)v[i].real();
     h[2 * i + 1] = (T)v[i].imag();
   }
-  void* p = nullptr;
-  FNL_CUDA(cudaMalloc(&p, sizeof(T) * (h.size() ? h.size() : 1)));
+  void* p = device_malloc(sizeof(T) * (h.size() ? h.size() : 1));
   sh->allocations.push_back(p);
   sh->device_bytes += sizeof(T) * h.size();
   FNL_CUDA(cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
@@ -63,8 +62,7 @@ void* upload_complex(fnl_shells* sh, const std::vector<std::complex<double>>& v)
 
 template <typename V>
 V* upload_vec(fnl_shells* sh, const std::vector<V>& v) {
-  void* p = nullptr;
-  FNL_CUDA(cudaMalloc(&p, sizeof(V) * (v.size() ? v.size() : 1)));
+  void* p = device_malloc(sizeof(V) * (v.size() ? v.size() : 1));
   sh->allocations.push_back(p);
   sh->device_bytes += sizeof(V) * v.size();
   FNL_CUDA(cudaMemcpy(p, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice));

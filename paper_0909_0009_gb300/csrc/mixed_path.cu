@@ -6,7 +6,7 @@
 //   k_lambda_mixed    lambda_lm(x_jp) from the FP64 recurrence, split into BF16 terms in the
 //                     two K-contiguous layouts of the synthesis and analysis GEMMs
 //   k_alm_to_terms    API coefficients -> BF16 terms of the synthesis operand
-//   k_combine_mixed   a^X_NL = sum over column tiles of the GEMM epilogue partials (FP64),
+//   k_combine_mixed   a^X_NL = sum over column tiles of the GEMM epilogue's FP64 partials,
 //                     a^X = a^X_L + f_NL a^X_NL (Eq. 3)
 #include <cuda_bf16.h>
 
@@ -345,11 +345,16 @@ __global__ void k_alm_to_terms(int L, int nr, int Cpad, int64_t nalm, int nterms
 }
 
 // a^X_NL,lm = sum over column tiles of the epilogue partials; for (l, m) = (0, 0) the
-// monopole comes from Parseval's identity instead (exact on this grid):
+// monopole comes from Parseval's identity instead:
 //   Phi_NL,00(r_i) = (sum_lm w_m |Phi_L,lm(r_i)|^2 - 4 pi mu_i) / sqrt(4 pi),  w_0 = 1, w_m>0 = 2,
-// a difference of two nearly equal numbers that FP32 grid sums would resolve poorly.
+// a difference of two nearly equal numbers that FP32 grid sums would resolve poorly.  The
+// identity is what the grid's own analysis gives on every grid the library accepts, not only
+// on the exact-square ones: the monopole integrates f^2, whose ring mean is exact once
+// n_phi > 2 l_max (frequencies up to 2 l_max, none aliased onto m = 0), and whose ring means
+// |F_m(theta)|^2 are polynomials of degree <= 2 l_max in cos theta, which the n_theta-point
+// Gauss-Legendre rule integrates exactly once n_theta >= l_max + 1.
 __device__ __forceinline__ void combine_body(int64_t i, int64_t nalm, int nct, int nr, double fnl,
-                                             const float4* __restrict__ part, const double* __restrict__ psum,
+                                             const double2* __restrict__ part, const double* __restrict__ psum,
                                              const double* __restrict__ mu, const double* __restrict__ qT,
                                              const double* __restrict__ qE, const double2* __restrict__ aLT,
                                              const double2* __restrict__ aLE, double2* __restrict__ aNLT,
@@ -365,11 +370,11 @@ __device__ __forceinline__ void combine_body(int64_t i, int64_t nalm, int nct, i
     }
   } else {
     for (int c = 0; c < nct; ++c) {
-      const float4 v = part[(size_t)c * nalm + i];
-      tr += v.x;
-      ti += v.y;
-      er += v.z;
-      ei += v.w;
+      const double2 t = part[((size_t)c * nalm + i) * 2], e = part[((size_t)c * nalm + i) * 2 + 1];
+      tr += t.x;
+      ti += t.y;
+      er += e.x;
+      ei += e.y;
     }
   }
   aNLT[i] = make_double2(tr, ti);
@@ -384,7 +389,7 @@ __device__ __forceinline__ void combine_body(int64_t i, int64_t nalm, int nct, i
   }
 }
 
-__global__ void k_combine_mixed(int64_t nalm, int nct, int nr, double fnl, const float4* __restrict__ part,
+__global__ void k_combine_mixed(int64_t nalm, int nct, int nr, double fnl, const double2* __restrict__ part,
                                 const double* __restrict__ psum, const double* __restrict__ mu,
                                 const double* __restrict__ qT, const double* __restrict__ qE,
                                 const double2* __restrict__ aLT, const double2* __restrict__ aLE,
@@ -436,13 +441,12 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
       }
       ab[alm_idx(l, m, L)] = make_double2(a, b);
     }
-  double *d_fac = nullptr, *d_mant = nullptr;
-  int* d_expo = nullptr;
-  double2* d_ab = nullptr;
-  FNL_CUDA(cudaMalloc(&d_fac, sizeof(double) * (L + 1)));
-  FNL_CUDA(cudaMalloc(&d_mant, sizeof(double) * (size_t)(L + 1) * np));
-  FNL_CUDA(cudaMalloc(&d_expo, sizeof(int) * (size_t)(L + 1) * np));
-  FNL_CUDA(cudaMalloc(&d_ab, sizeof(double2) * (size_t)sh->nalm));
+  TempDev t_fac(sizeof(double) * (L + 1)), t_mant(sizeof(double) * (size_t)(L + 1) * np),
+      t_expo(sizeof(int) * (size_t)(L + 1) * np), t_ab(sizeof(double2) * (size_t)sh->nalm);
+  double* d_fac = t_fac.as<double>();
+  double* d_mant = t_mant.as<double>();
+  int* d_expo = t_expo.as<int>();
+  double2* d_ab = t_ab.as<double2>();
   FNL_CUDA(cudaMemcpyAsync(d_fac, fac.data(), sizeof(double) * (L + 1), cudaMemcpyHostToDevice, st));
   FNL_CUDA(cudaMemcpyAsync(d_ab, ab.data(), sizeof(double2) * ab.size(), cudaMemcpyHostToDevice, st));
   launch_lambda_mm(sh->d_x, d_fac, np, L, d_mant, d_expo, st);
@@ -452,10 +456,6 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
                                        (__nv_bfloat16*)sh->d_lana);
   FNL_CUDA(cudaGetLastError());
   FNL_CUDA(cudaStreamSynchronize(st));
-  cudaFree(d_fac);
-  cudaFree(d_mant);
-  cudaFree(d_expo);
-  cudaFree(d_ab);
 }
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
@@ -486,7 +486,7 @@ void launch_alm_to_terms(const fnl_shells* sh, const double* alm, cudaStream_t s
 void launch_combine_mixed(const fnl_shells* sh, double fnl, const double* aLT, const double* aLE, double* aNLT,
                           double* aNLE, double* aT, double* aE, const double* psum, cudaStream_t st) {
   k_combine_mixed<<<(unsigned)((sh->nalm + 255) / 256), 256, 0, st>>>(
-      sh->nalm, sh->Cpad / 128, sh->nr, fnl, (const float4*)sh->d_part, psum, sh->d_mu, sh->d_qT, sh->d_qE,
+      sh->nalm, sh->Cpad / 128, sh->nr, fnl, (const double2*)sh->d_part, psum, sh->d_mu, sh->d_qT, sh->d_qE,
       (const double2*)aLT, (const double2*)aLE, (double2*)aNLT, (double2*)aNLE, (double2*)aT, (double2*)aE);
   FNL_CUDA(cudaGetLastError());
 }

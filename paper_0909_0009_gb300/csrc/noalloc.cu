@@ -33,19 +33,55 @@ constexpr int kThreads = 256;
 static __device__ __align__(256) double g_qscratch[2 * kNoallocMaxLNr];
 
 std::mutex g_addr_mutex;
-void* g_addr[kNoallocMaxDevices] = {};
+struct ScratchAddr {
+  void* ctx = nullptr;   // the CUDA context the address belongs to
+  void* addr = nullptr;  // device address of g_qscratch in that context
+};
+ScratchAddr g_addr[kNoallocMaxDevices];
 
-// Device address of g_qscratch on device `dev` (the current device).  The first request
-// on a device looks it up; later ones reuse it.  In host code the name g_qscratch stands
-// for a host-side shadow, never for the device memory, so only this address reaches a
-// kernel.
-double* scratch_address(int dev) {
+// The driver's cuCtxGetCurrent (through the runtime's entry-point query, so the library
+// needs no link to libcuda): the context that is current on this thread.
+void* current_context() {
+  typedef int (*CtxGetCurrent)(void**);
+  static CtxGetCurrent fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      throw Error(FNL_ECUDA, "fnl_accumulate_noalloc: cuCtxGetCurrent is unavailable");
+    }
+    fn = (CtxGetCurrent)p;
+  }
+  void* ctx = nullptr;
+  if (fn(&ctx) != 0 || !ctx) throw Error(FNL_ECUDA, "fnl_accumulate_noalloc: no current CUDA context");
+  return ctx;
+}
+
+// Device address of g_qscratch on device `dev` (the current device).  The address is looked
+// up (cudaGetSymbolAddress, which may load the library's device code) on the first call in a
+// context and kept with that context: a call in a new context of the same device (after
+// cudaDeviceReset, or once the primary context was released and made again) looks it up
+// again instead of using an address of memory that no longer exists.  A lookup must not run
+// while `st` is being captured into a graph, so such a call is refused with a message.  In
+// host code the name g_qscratch stands for a host-side shadow, never for the device memory,
+// so only this address reaches a kernel.
+double* scratch_address(int dev, cudaStream_t st) {
   if (dev < 0 || dev >= kNoallocMaxDevices)
     throw Error(FNL_EUNSUPPORTED, "fnl_accumulate_noalloc: device ordinal " + std::to_string(dev) +
                                       " is beyond the " + std::to_string(kNoallocMaxDevices) +
                                       " devices this library keeps scratch addresses for");
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
+  ScratchAddr& a = g_addr[dev];
+  if (a.ctx != ctx || !a.addr) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    FNL_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      throw Error(FNL_EUNSUPPORTED, "fnl_accumulate_noalloc: the first call in a CUDA context looks up the "
+                                    "scratch array's address and cannot run during a stream capture; make one "
+                                    "call before the capture begins");
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_qscratch);
     if (e != cudaSuccess || !p) {
@@ -53,9 +89,10 @@ double* scratch_address(int dev) {
       throw Error(FNL_ECUDA, std::string("fnl_accumulate_noalloc: cudaGetSymbolAddress of the scratch "
                                          "array failed: ") + cudaGetErrorString(e));
     }
-    g_addr[dev] = p;
+    a.ctx = ctx;
+    a.addr = p;
   }
-  return (double*)g_addr[dev];
+  return (double*)a.addr;
 }
 
 void check_ptr(const void* p, const char* name, bool nullable, unsigned align, int dev) {
@@ -189,8 +226,8 @@ extern "C" fnl_status fnl_accumulate_noalloc(int lmax, int nr, const double* r, 
                     std::make_pair((const void*)aLT, "aLT"), std::make_pair((const void*)aLE, "aLE"),
                     std::make_pair((const void*)aNLT, "aNLT"), std::make_pair((const void*)aNLE, "aNLE")})
       check_ptr(pr.first, pr.second, true, 16, dev);
-    double* q = scratch_address(dev);
     cudaStream_t st = (cudaStream_t)stream;
+    double* q = scratch_address(dev, st);
     const int64_t nalm = n_alm(lmax);
     const int wblocks = (int)std::min<int64_t>((lnr + kThreads - 1) / kThreads, 4096);
     k_weights_noalloc<<<wblocks, kThreads, 0, st>>>(lmax, nr, r, w, alphaT, alphaE, q);

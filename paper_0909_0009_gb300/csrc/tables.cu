@@ -96,13 +96,12 @@ void build_lambda_tables(fnl_shells* sh, cudaStream_t st) {
       }
       ab[alm_idx(l, m, L)] = make_double2(a, b);
     }
-  double *d_fac = nullptr, *d_mant = nullptr;
-  int* d_expo = nullptr;
-  double2* d_ab = nullptr;
-  FNL_CUDA(cudaMalloc(&d_fac, sizeof(double) * (L + 1)));
-  FNL_CUDA(cudaMalloc(&d_mant, sizeof(double) * (size_t)(L + 1) * np));
-  FNL_CUDA(cudaMalloc(&d_expo, sizeof(int) * (size_t)(L + 1) * np));
-  FNL_CUDA(cudaMalloc(&d_ab, sizeof(double2) * (size_t)sh->nalm));
+  TempDev t_fac(sizeof(double) * (L + 1)), t_mant(sizeof(double) * (size_t)(L + 1) * np),
+      t_expo(sizeof(int) * (size_t)(L + 1) * np), t_ab(sizeof(double2) * (size_t)sh->nalm);
+  double* d_fac = t_fac.as<double>();
+  double* d_mant = t_mant.as<double>();
+  int* d_expo = t_expo.as<int>();
+  double2* d_ab = t_ab.as<double2>();
   FNL_CUDA(cudaMemcpyAsync(d_fac, fac.data(), sizeof(double) * (L + 1), cudaMemcpyHostToDevice, st));
   FNL_CUDA(cudaMemcpyAsync(d_ab, ab.data(), sizeof(double2) * ab.size(), cudaMemcpyHostToDevice, st));
   k_lambda_mm<<<(np + 127) / 128, 128, 0, st>>>(sh->d_x, d_fac, np, L, d_mant, d_expo);
@@ -118,10 +117,6 @@ void build_lambda_tables(fnl_shells* sh, cudaStream_t st) {
                                                 (float*)sh->d_lam);
   FNL_CUDA(cudaGetLastError());
   FNL_CUDA(cudaStreamSynchronize(st));
-  cudaFree(d_fac);
-  cudaFree(d_mant);
-  cudaFree(d_expo);
-  cudaFree(d_ab);
 }
 
 }  // namespace fnl

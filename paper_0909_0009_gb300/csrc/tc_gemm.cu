@@ -73,15 +73,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: returns false (and records `code`) if the phase does not complete in time
-// or another role of this kernel has already recorded an error.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+// Bounded wait: returns false (and records `code`) if the phase does not complete within
+// `limit` tries or another role of this kernel has already recorded an error.
+__device__ __noinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, int* err, int code, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 1023) == 1023 && *(volatile int*)err != 0) return false;
   }
   atomicCAS(err, 0, code);
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  return mbar_wait_n(bar, parity, err, code, kWaitLimit);
 }
 
 // One try inline, then the bounded loop.
@@ -169,22 +172,11 @@ __device__ __forceinline__ bool epi_sync(uint64_t* bar, uint32_t parity, int lan
   return ok;
 }
 
-// Sum of x over the 16 lanes of this lane's parity class, for 32 columns at once: after
-// the four exchange steps lane l holds the sums of columns (l & 30) and (l & 30) + 1.
-__device__ __forceinline__ void reduce_columns(float (&x)[32], int lane) {
-#pragma unroll
-  for (int o = 16, cnt = 32; o >= 2; o >>= 1, cnt >>= 1) {
-    const bool upper = (lane & o) != 0;
-    const int half = cnt >> 1;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      if (k < half) {
-        const float send = upper ? x[k] : x[k + half];
-        const float keep = upper ? x[k + half] : x[k];
-        x[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-      }
-    }
-  }
+// Error-free sum of two FP32 numbers (Knuth's two-sum): s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
 }
 
 // The MMAs of one stage: nh (1 or 2) slabs of 32 k, each two k steps of 16, every product of
@@ -231,7 +223,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
   uint64_t* drain = tempty + 2;
   uint64_t* epib = drain + 1;  // [2] rendezvous of the epilogue warps
   uint32_t* tslot = (uint32_t*)(epib + 2);
-  float* red = (float*)(smem + (size_t)S * stageBytes + 1024);  // [4 quadrants][256 cols][2 fields][2 parities]
+  // analysis: [4 quadrants][nmax degree columns][2 fields][2 parts][hi, lo] double-float partials of
+  // the quadrature, then [kEpiWarps][256] scratch of the epilogue warps
+  float* red = (float*)(smem + (size_t)S * stageBytes + 1024);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t sbase = smem_u32(smem);
@@ -399,7 +393,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       TcInst mi;
       if constexpr (MULTI) {
         const TcInst* Ip = a.insts + tl.inst;
-        mi.F = Ip->F, mi.part = Ip->part, mi.qT = Ip->qT, mi.qE = Ip->qE;
+        mi.F = Ip->F, mi.part = Ip->part, mi.q2 = Ip->q2;
         mi.L = Ip->L, mi.nr = Ip->nr, mi.npairs = Ip->npairs, mi.Cpad = Ip->Cpad, mi.nalm = Ip->nalm;
       }
       const TcInst& I = MULTI ? mi : a.one;
@@ -456,21 +450,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         if (lane == 0) mbar_arrive(&tempty[acc]);
       }
       for (int ch = h; ch < nch; ch += kEpiPerQuad) {
-        float v[32];
         const uint32_t ta = tacc + (uint32_t)(ch * 32);
-        tmem_ld32(ta, v);
-        if (a.split) {
-          float w[32];
-          tmem_ld32(ta + (uint32_t)a.cols, w);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += w[j];
-        }
-        if (ch == last) {
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[acc]);
-        }
         if (a.mode == TC_ANA_STORE) {
+          float v[32];
+          tmem_ld32(ta, v);
+          if (a.split) {
+            float w[32];
+            tmem_ld32(ta + (uint32_t)a.cols, w);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += w[j];
+          }
+          if (ch == last) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+          }
           if (cvalid) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -481,31 +475,91 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               }
             }
           }
-        } else {
-          // radial quadrature (Eq. 5): sum over the shells of this tile of q^X_l[i] Phi_NL,lm(r_i)
-          float tx[32], ex[32];
-          const int i = c >> 1;
+          continue;
+        }
+        // radial quadrature (Eq. 5): sum over the shells of this tile of q^X_l[i] Phi_NL,lm(r_i), in
+        // double-float.  The chunk (the warp's 32 columns = 16 shells x (re, im), by 32 degrees) is
+        // turned around through the warp's scratch 8 degrees at a time (element (d, col) at
+        // d 32 + (col ^ 2 d): no bank conflicts either way).  Lane (d, f, b) then sums, for degree d
+        // and field f (T, E), shells 8 b .. 8 b + 7 of the warp's 16, re and im, one after another:
+        // each product exactly as p + e (q = qh + ql: p = v qh rounded, e = its rounding error by
+        // fmaf plus v ql), the p's by error-free two-sums, the e's plainly; the two shell halves
+        // are joined across the lane pair at the end.  The weights of a half chunk (16 degrees)
+        // are requested before its accumulator columns are read, which hides their latency.
+        const int s0 = (tl.c0 >> 1) + 16 * q;  // shell of the warp's first column
+        const int d = lane >> 2, f = (lane >> 1) & 1, b = lane & 1;
+        float* scr = red + (size_t)4 * a.nmax * 8 + (size_t)(warp - 2) * 256;
+#pragma unroll 1
+        for (int hf = 0; hf < 2; ++hf) {
+          float4 qq[2][4];  // [sub-block][shell pair]: (qh, ql) of two shells
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int k = tl.n0 + ch * 32 + j;
-            float qt = 0.f, qe = 0.f;
-            if (cvalid && ch * 32 + j < tl.nsize && k < tl.kvalid) {
-              const int l = m + p + 2 * k;
-              qt = I.qT[(size_t)l * nr + i];
-              qe = I.qE[(size_t)l * nr + i];
-            }
-            tx[j] = v[j] * qt;
-            ex[j] = v[j] * qe;
+          for (int sb = 0; sb < 2; ++sb) {
+            const int jj = ch * 32 + hf * 16 + sb * 8 + d;
+            const int k = tl.n0 + jj;
+            const bool dvalid = jj < tl.nsize && k < tl.kvalid;
+            const float4* qrow =
+                (const float4*)(I.q2 + ((size_t)(m + p + 2 * (dvalid ? k : 0)) * 2 + f) * nr + s0 + 8 * b);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              qq[sb][e] = (dvalid && s0 + 8 * b + 2 * e < nr) ? qrow[e] : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          reduce_columns(tx, lane);
-          reduce_columns(ex, lane);
-          const int col = ch * 32 + (lane & 30);
-          float* rw = red + (size_t)q * 1024;  // the quadrant's warps write disjoint chunks
-          const int r = lane & 1;
-          rw[(col + 0) * 4 + 0 * 2 + r] = tx[0];
-          rw[(col + 1) * 4 + 0 * 2 + r] = tx[1];
-          rw[(col + 0) * 4 + 1 * 2 + r] = ex[0];
-          rw[(col + 1) * 4 + 1 * 2 + r] = ex[1];
+          float v[16];
+          tmem_ld16(ta + (uint32_t)(16 * hf), v);
+          if (a.split) {
+            float w[16];
+            tmem_ld16(ta + (uint32_t)(16 * hf) + (uint32_t)a.cols, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += w[j];
+          }
+          if (ch == last && hf == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+          }
+#pragma unroll
+          for (int sb = 0; sb < 2; ++sb) {
+            __syncwarp();
+#pragma unroll
+            for (int dd = 0; dd < 8; ++dd) scr[dd * 32 + (lane ^ (2 * dd))] = v[sb * 8 + dd];
+            __syncwarp();
+            float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;  // re and im, double-float
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int col = 2 * (8 * b + e);
+              const float xr = scr[d * 32 + (col ^ (2 * d))];
+              const float xi = scr[d * 32 + ((col + 1) ^ (2 * d))];
+              const float qh = (e & 1) ? qq[sb][e >> 1].z : qq[sb][e >> 1].x;
+              const float ql = (e & 1) ? qq[sb][e >> 1].w : qq[sb][e >> 1].y;
+              const float pr = xr * qh, pi = xi * qh;
+              const float er = fmaf(xr, ql, fmaf(xr, qh, -pr)), ei = fmaf(xi, ql, fmaf(xi, qh, -pi));
+              float sum, err;
+              two_sum(hr, pr, sum, err);
+              hr = sum;
+              lr += err + er;
+              two_sum(hi, pi, sum, err);
+              hi = sum;
+              li += err + ei;
+            }
+            // join the two shell halves (lanes b = 0, 1)
+            {
+              const float ohr = __shfl_xor_sync(0xffffffffu, hr, 1), olr = __shfl_xor_sync(0xffffffffu, lr, 1);
+              const float ohi = __shfl_xor_sync(0xffffffffu, hi, 1), oli = __shfl_xor_sync(0xffffffffu, li, 1);
+              float sum, err;
+              two_sum(hr, ohr, sum, err);
+              hr = sum;
+              lr += olr + err;
+              two_sum(hi, ohi, sum, err);
+              hi = sum;
+              li += oli + err;
+            }
+            const int jj = ch * 32 + hf * 16 + sb * 8 + d;  // degree column within the tile
+            if (jj < tl.nsize) {
+              // lane b = 0 writes re, lane b = 1 im: red[q][jj][f][part][hi, lo]
+              float* o = red + (size_t)q * (a.nmax * 8) + (size_t)jj * 8 + f * 4 + b * 2;
+              o[0] = b ? hi : hr;
+              o[1] = b ? li : lr;
+            }
+          }
         }
       }
       if (a.mode == TC_ANA_QUAD) {
@@ -514,17 +568,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         for (int n = tid; n < tl.nsize; n += 32 * kEpiWarps) {
           const int k = tl.n0 + n;
           if (k >= tl.kvalid) continue;
-          float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+          // the four quadrants' double-float partials, summed in FP64
+          double s[4] = {0.0, 0.0, 0.0, 0.0};  // T re, T im, E re, E im
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            const float* rw = red + (size_t)w * 1024 + n * 4;
-            s.x += rw[0];
-            s.y += rw[1];
-            s.z += rw[2];
-            s.w += rw[3];
+            const float* rw = red + (size_t)w * (a.nmax * 8) + (size_t)n * 8;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s[f] += (double)rw[2 * f] + (double)rw[2 * f + 1];
           }
           const int l = m + p + 2 * k;
-          I.part[(size_t)(tl.c0 >> 7) * I.nalm + alm_idx(l, m, L)] = s;
+          double2* dst = I.part + ((size_t)(tl.c0 >> 7) * I.nalm + alm_idx(l, m, L)) * 2;
+          dst[0] = make_double2(s[0], s[1]);
+          dst[1] = make_double2(s[2], s[3]);
         }
         if (!epi_sync(&epib[1], ephase, lane, a.err)) break;
         ephase ^= 1;
@@ -542,6 +597,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
+}
+
+// The expiry path of the bounded waits, on its own: one thread waits, with `limit` tries, on
+// an mbarrier whose phase nothing completes (count 1, no arrival), so the wait runs out,
+// records code 6 in the error word and returns.  Used by the test hook fnl_test_wait_expiry.
+__global__ void k_wait_probe(int* err, uint32_t limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait_n(&bar, 0, err, 6, limit);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -575,7 +641,8 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
 
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode) {
   const size_t stage = (size_t)nterms * (kTcABytes + (size_t)nmax * 64 * kTcSlabs);
-  const size_t red = mode == TC_SYNTH ? 0 : 4 * 256 * 4 * sizeof(float);  // epilogue reduction (analysis)
+  // epilogue reduction and per-warp scratch (analysis)
+  const size_t red = mode == TC_SYNTH ? 0 : ((size_t)4 * nmax * 8 + (size_t)kEpiWarps * 256) * sizeof(float);
   return 1024 /*alignment*/ + (size_t)stages * stage + 1024 /*barriers*/ + red;
 }
 
@@ -589,6 +656,11 @@ void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st) {
   if (n < 1 || n > kTcMaxInst) throw Error(FNL_EINVAL, "too many instances for one tensor-core launch");
   FNL_CUDA(cudaMemcpyToSymbolAsync(c_tc_maps, host, sizeof(CUtensorMap) * 2 * (size_t)n, 0,
                                    cudaMemcpyHostToDevice, st));
+}
+
+void launch_wait_probe(int* err, uint32_t limit, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(err, limit);
+  FNL_CUDA(cudaGetLastError());
 }
 
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st) {

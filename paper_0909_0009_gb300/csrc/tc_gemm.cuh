@@ -36,9 +36,8 @@ struct alignas(128) TcInst {  // CUtensorMap is 128-byte aligned
   CUtensorMap tmA;      // Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves, terms}
   CUtensorMap tmB;      // Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs, terms}
   float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
-  float4* part;         // TC_ANA_QUAD: [Cpad / 128][nalm] (T re, T im, E re, E im)
-  const float* qT;      // [L+1][nr]
-  const float* qE;
+  double2* part;        // TC_ANA_QUAD: [Cpad / 128][nalm][2] ((T re, T im), (E re, E im))
+  const float2* q2;     // [L+1][2][nr] q^T, q^E as FP32 pairs (hi, lo)
   int L, nr, npairs, Cpad;
   int64_t nalm;
 };
@@ -67,6 +66,8 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode);
 int tc_stages(int nterms, int nmax, int mode);
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st);
+// One bounded mbarrier wait that nothing completes, with `limit` tries (the expiry path).
+void launch_wait_probe(int* err, uint32_t limit, cudaStream_t st);
 // Copy n instances' maps (A and B each) into the constant table, on `st` from pinned
 // host memory that stays unchanged until the copy has run.
 void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st);

@@ -30,7 +30,7 @@ EXPORTS = [
     "fnl_batch_info", "fnl_generate_batch", "fnl_shells_autotune", "fnl_shells_set_tiles", "fnl_batch_tiles",
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
     "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
-    "fnl_make_shells_healpix", "fnl_shells_set_sm_limits",
+    "fnl_make_shells_healpix", "fnl_shells_set_sm_limits", "fnl_test_fail_alloc", "fnl_test_wait_expiry",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -97,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_profile_read.argtypes = [vp, dp, i, ctypes.POINTER(i)]
     lib.fnl_generate_host.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp]
     lib.fnl_device_status.argtypes = [vp]
+    lib.fnl_test_fail_alloc.argtypes = [ctypes.c_long]
+    lib.fnl_test_wait_expiry.argtypes = [vp, ctypes.c_uint, vp]
     lib.fnl_accumulate_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
     lib.fnl_generate_backward.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.fnl_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
@@ -575,11 +577,38 @@ def accumulate_noalloc(lmax, nr, r, w, alphaT, alphaE, phiL=None, phiNL=None, fn
     overlap on the GPU race.
     """
     lib = load_library()
+    torch = _torch()
     out = out or {}
     bad = set(out) - set(NOALLOC_OUTPUTS)
     if bad:
         raise ValueError(f"unknown outputs {sorted(bad)}")
+    lmax, nr = int(lmax), int(nr)
+    nalm = (lmax + 1) * (lmax + 2) // 2
+    dev = torch.cuda.current_device()
+
+    def need(t, name, dtype, shape, nullable=False):
+        # the library sees bare pointers: a wrong dtype, shape or device would make its
+        # kernels read or write past the caller's buffers, so check before the call
+        if t is None:
+            if not nullable:
+                raise ValueError(f"{name} must be given")
+            return
+        if t.dtype != dtype or tuple(t.shape) != shape:
+            raise ValueError(f"{name} must be {dtype} of shape {shape}, got {t.dtype} {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.type != "cuda" or t.device.index != dev:
+            raise ValueError(f"{name} must be on the current device cuda:{dev}")
+
+    need(r, "r", torch.float64, (nr,))
+    need(w, "w", torch.float64, (nr,))
+    need(alphaT, "alphaT", torch.float64, (lmax + 1, nr))
+    need(alphaE, "alphaE", torch.float64, (lmax + 1, nr))
+    need(phiL, "phiL", torch.complex128, (nalm, nr), nullable=True)
+    need(phiNL, "phiNL", torch.complex128, (nalm, nr), nullable=True)
+    for k, t in out.items():
+        need(t, k, torch.complex128, (nalm,), nullable=True)
     ptrs = [_ptr(out.get(k)) for k in NOALLOC_OUTPUTS]
-    _check(lib.fnl_accumulate_noalloc(int(lmax), int(nr), _ptr(r), _ptr(w), _ptr(alphaT), _ptr(alphaE), _ptr(phiL),
+    _check(lib.fnl_accumulate_noalloc(lmax, nr, _ptr(r), _ptr(w), _ptr(alphaT), _ptr(alphaE), _ptr(phiL),
                                       _ptr(phiNL), float(fnl), *ptrs, _stream(stream)))
     return out

@@ -15,10 +15,17 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 STAGE_BOUND = {"bf16x2": 2e-5, "bf16x3": 3e-6}
+# the stated precision of the mixed forms: a^X and a^X_NL within rel 1e-5 of the FP64 path
 TARGET = 1e-5
-# a^X_NL bound for the small cases: few terms per sum, so the 2-term split's 2^-17 operand
-# error does not average down there
-NL_BOUND = {"bf16x2": 3e-5, "bf16x3": TARGET}
+
+
+def nl_bound(prec: str, nr: int) -> float:
+    """The a^X_NL bar of a configuration.  1e-5 for bf16x3 and FP32 everywhere, and for bf16x2
+    from N_r = 16 shells on (measured 5.6e-6 .. 7.2e-6 for l_max 7 .. 1024).  With fewer shells
+    the quadrature averages the two-term split's per-shell error (about 1.5e-5 rms after the
+    synthesis, the square and the analysis) over too few independent shells, and a single draw
+    reaches 1.0e-5 (l_max 7, N_r 8): there the bar is 2e-5."""
+    return 2e-5 if (prec == "bf16x2" and nr < 16) else TARGET
 
 
 def rel_l2(got, ref):
@@ -112,11 +119,32 @@ def test_generate_matches_fp64_path(F, prec, lmax, nr, ntheta, nphi):
             assert rel_l2(host(a[k]), host(b[k])) < 1e-6, k
         # a^X carries f_NL times the error of a^X_NL
         for k in ("aT", "aE", "aNLT", "aNLE"):
-            assert rel_l2(host(a[k]), host(b[k])) < NL_BOUND[prec], (k, rel_l2(host(a[k]), host(b[k])))
+            assert rel_l2(host(a[k]), host(b[k])) < nl_bound(prec, nr), (k, rel_l2(host(a[k]), host(b[k])))
     c.mx.device_status()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x2", "bf16x3"])
+@pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(32, 8, 33, 72), (32, 16, 40, 72), (48, 16, 52, 100)])
+def test_generate_on_under_resolved_grids(F, prec, lmax, nr, ntheta, nphi):
+    """Grids below the exact-square size (n_theta < (3 l_max + 2) / 2, n_phi < 3 l_max + 1,
+    down to the smallest accepted n_theta = l_max + 1): the square's coefficients are aliased
+    by the grid, and the mixed forms must give the oracle's aliased values.  Their monopole
+    comes from Parseval's identity, which equals the grid's own analysis on every accepted
+    grid (pinned on the CPU by test_parseval_monopole_on_minimal_grids).  The FP32 form sums the
+    monopole on the grid like the oracle, in FP32."""
+    c = Pair(F, lmax, nr, ntheta, nphi, prec)
+    n = O.philox_noise(lmax, nr, 3, 0)
+    ref = O.generate(c.K, n, c.grid, c.r, c.w, c.aT, c.aE, 40.0, mu=c.mu)
+    out = c.mx.generate(3, 0, 40.0)
+    for k in ("aT", "aE", "aNLT", "aNLE"):
+        assert rel_l2(host(out[k]), ref[k]) < nl_bound(prec, nr), (k, rel_l2(host(out[k]), ref[k]))
+    if prec != "fp32":  # the FP32 form sums the cancelling f^2 - mu on the grid (~1e-5 relative)
+        mono = abs(host(out["aNLT"])[0] - ref["aNLT"][0]) / abs(ref["aNLT"][0])
+        assert mono < TARGET, mono
+    c.mx.device_status()
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
 def test_generate_against_oracle_small(F, prec):
     c = Pair(F, 32, 16, 49, 100, prec)
     n = O.philox_noise(32, 16, 1, 0)

@@ -233,8 +233,9 @@ def test_fp32_form_medium(F, medium):
         a32 = c32.generate(seed, 0, fnl)
         for k in ("aT", "aE", "aNLT", "aNLE"):
             e = rel_l2(host(a32[k]), host(a64[k]))
-            # FP32 Legendre sums over <= 257 terms, FP32 FFT of 800 points, squared: ~1e-6
-            assert e < 2e-5, (k, e)
+            # the stated bar of the reduced-precision forms (rel 1e-5); FP32 Legendre sums over
+            # <= 257 terms and an FP32 FFT of 800 points give ~5e-7 here
+            assert e < 1e-5, (k, e)
 
 
 # ---------------------------------------------------------------------------------------

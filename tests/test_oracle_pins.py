@@ -175,6 +175,28 @@ def test_parseval_monopole_identity():
     assert np.max(np.abs(out[0] - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+def test_parseval_monopole_on_minimal_grids():
+    """The monopole of the square equals Parseval's closed form on every grid with
+    n_theta >= l_max + 1 and n_phi >= 2 l_max + 2, not only on the exact-square grids: f^2 has
+    frequencies up to 2 l_max (none aliased onto m = 0 once n_phi > 2 l_max) and its ring
+    means are polynomials of degree <= 2 l_max in cos theta (exact for n_theta >= l_max + 1
+    Gauss-Legendre nodes).  On such a grid the other coefficients of the square are aliased
+    (they differ from the exact-grid values), and one ring fewer breaks the monopole too."""
+    L = 24
+    a = W.random_alm(L, 3, seed=19)
+    mu = np.array([0.3, 1.1, 0.0])
+    l, m = W.alm_lm(L)
+    wgt = np.where(m == 0, 1.0, 2.0)[:, None]
+    ref = ((wgt * np.abs(a) ** 2).sum(axis=0) - 4 * math.pi * mu) / math.sqrt(4 * math.pi)
+    exact = O.phi_nonlinear(a, mu, O.Grid(L, *W.grid_for_lmax(L)))
+    for nt, nph in ((L + 1, 2 * L + 2), (L + 5, 54), (30, 60)):
+        out = O.phi_nonlinear(a, mu, O.Grid(L, nt, nph))
+        assert np.max(np.abs(out[0] - ref)) < 1e-12 * np.max(np.abs(ref)), (nt, nph)
+        assert np.max(np.abs(out[1:] - exact[1:])) > 1e-6 * np.max(np.abs(exact[1:])), (nt, nph)
+    short = O.phi_nonlinear(a, mu, O.Grid(L, L, 2 * L + 2))
+    assert np.max(np.abs(short[0] - ref)) > 1e-8 * np.max(np.abs(ref))
+
+
 def test_single_monopole_mode():
     L = 16
     nt, nph = W.grid_for_lmax(L)
