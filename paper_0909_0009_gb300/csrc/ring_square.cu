@@ -96,8 +96,11 @@ __device__ __forceinline__ Tw tw_const<25>(int e) { return kTw25.w[e]; }
 
 // ---- complex helpers -------------------------------------------------------------------
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// A complex value is a float2 (re, im): complex sums and differences, and products with a
+// real constant, are one packed f32x2 instruction (sm_100 and later) instead of two.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 pk(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
   return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
 }
@@ -119,7 +122,8 @@ __device__ __forceinline__ float2 twiddle(float2 v, int e) {
   if (4 * e == 3 * M) return mul_i<-SG>(v);
   const Tw w = tw_const<M>(e);
   const float s = SG > 0 ? w.s : -w.s;
-  return make_float2(v.x * w.c - v.y * s, v.x * s + v.y * w.c);
+  const float2 t = __fmul2_rn(v, pk(w.c));  // (re c, im c)
+  return make_float2(fmaf(-v.y, s, t.x), fmaf(v.x, s, t.y));
 }
 
 // ---- in-register DFTs, natural order in and out: v'[k] = sum_n v[n] w_R^(SG n k) -------
@@ -140,11 +144,13 @@ template <int SG>
 struct Dft<4, SG> {
   __device__ __forceinline__ static void run(float2* v) {
     const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    const float2 s13 = cadd(v[1], v[3]), d13 = mul_i<SG>(csub(v[1], v[3]));
+    const float2 s13 = cadd(v[1], v[3]), t = csub(v[1], v[3]);
     v[0] = cadd(s02, s13);
-    v[1] = cadd(d02, d13);
     v[2] = csub(s02, s13);
-    v[3] = csub(d02, d13);
+    // d02 +- SG i t, with i t = (-t.y, t.x)
+    const float2 plus = make_float2(d02.x - t.y, d02.y + t.x), minus = make_float2(d02.x + t.y, d02.y - t.x);
+    v[1] = SG > 0 ? plus : minus;
+    v[3] = SG > 0 ? minus : plus;
   }
 };
 
@@ -156,16 +162,16 @@ struct Dft<5, SG> {
     constexpr float s1 = (float)(SG * tsin(1, 5)), s2 = (float)(SG * tsin(2, 5));
     const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
     const float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
-    const float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
-    const float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
-    // i * (s1 d1 + s2 d2) and i * (s2 d1 - s1 d2)
-    const float2 b1 = make_float2(-(s1 * d1.y + s2 * d2.y), s1 * d1.x + s2 * d2.x);
-    const float2 b2 = make_float2(-(s2 * d1.y - s1 * d2.y), s2 * d1.x - s1 * d2.x);
+    const float2 a1 = __ffma2_rn(t2, pk(c2), __ffma2_rn(t1, pk(c1), v[0]));
+    const float2 a2 = __ffma2_rn(t2, pk(c1), __ffma2_rn(t1, pk(c2), v[0]));
+    // u1 = s1 d1 + s2 d2, u2 = s2 d1 - s1 d2; the outputs add and subtract i u
+    const float2 u1 = __ffma2_rn(d2, pk(s2), __fmul2_rn(d1, pk(s1)));
+    const float2 u2 = __ffma2_rn(d2, pk(-s1), __fmul2_rn(d1, pk(s2)));
     v[0] = cadd(v[0], cadd(t1, t2));
-    v[1] = cadd(a1, b1);
-    v[4] = csub(a1, b1);
-    v[2] = cadd(a2, b2);
-    v[3] = csub(a2, b2);
+    v[1] = make_float2(a1.x - u1.y, a1.y + u1.x);
+    v[4] = make_float2(a1.x + u1.y, a1.y - u1.x);
+    v[2] = make_float2(a2.x - u2.y, a2.y + u2.x);
+    v[3] = make_float2(a2.x + u2.y, a2.y - u2.x);
   }
 };
 
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1)
       }
       Dft<N1, 1>::run(v);
 #pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) v[n1] = make_float2(v[n1].x * v[n1].x - mu, v[n1].y * v[n1].y - mu);
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = __ffma2_rn(v[n1], v[n1], pk(-mu));
       Dft<N1, -1>::run(v);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) B[base + k1] = k1 ? cmulc(v[k1], w[k1 * T]) : v[k1];
