@@ -209,7 +209,9 @@ __device__ __forceinline__ void issue_stage(uint64_t da, uint64_t db, uint32_t b
   }
 }
 
-template <bool MULTI>
+// MODE (TcMode) is a template parameter, so that each mode's kernel is compiled with only its own
+// epilogue (the quadrature's registers do not weigh on the synthesis, and the other way round).
+template <bool MULTI, int MODE>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           // (B) after the operand's start
           const uint32_t sa = sbase + (uint32_t)stage * stageBytes;
           const uint32_t sb = sa + (uint32_t)a.nterms * kTcABytes;
-          if (a.mode == TC_SYNTH) {
+          if constexpr (MODE == TC_SYNTH) {
             // A: Phi rows r0 + 64 sg .., column halves c0 / 64, c0 / 64 + 1
             tma_load_4d(sa, mA, 0, tl.r0 + kTcStageK * sg, tl.c0 >> 6, 0, &full[stage]);
             // B: slabs r0 / 32 + 2 sg, + 1, ring pairs n0 ..
@@ -392,9 +394,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       // once per tile (stores through F or part could alias the array)
       TcInst mi;
       if constexpr (MULTI) {
+        // only the fields this launch's mode reads (fewer live registers)
         const TcInst* Ip = a.insts + tl.inst;
-        mi.F = Ip->F, mi.part = Ip->part, mi.q2 = Ip->q2;
-        mi.L = Ip->L, mi.nr = Ip->nr, mi.npairs = Ip->npairs, mi.Cpad = Ip->Cpad, mi.nalm = Ip->nalm;
+        mi.L = Ip->L, mi.nr = Ip->nr;
+        if constexpr (MODE == TC_SYNTH) {
+          mi.F = Ip->F, mi.npairs = Ip->npairs, mi.Cpad = Ip->Cpad;
+        } else {
+          mi.part = Ip->part, mi.q2 = Ip->q2, mi.nalm = Ip->nalm;
+        }
       }
       const TcInst& I = MULTI ? mi : a.one;
       const int L = I.L, nr = I.nr;
@@ -402,7 +409,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       const int c = tl.c0 + 32 * q + lane;
       const bool cvalid = c < 2 * nr;
       const uint32_t tacc = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols) + ((uint32_t)(32 * q) << 16);
-      if (a.mode == TC_SYNTH) {
+      if constexpr (MODE == TC_SYNTH) {
         // F (FP32, ring-pair-major F[jp][mp][Cpad]) in 16-column chunks, spread over the
         // quadrant's warps; TMEM is released after each warp's last load, before its stores
         const int nch = (tl.nsize + 15) / 16;
@@ -451,7 +458,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       }
       for (int ch = h; ch < nch; ch += kEpiPerQuad) {
         const uint32_t ta = tacc + (uint32_t)(ch * 32);
-        if (a.mode == TC_ANA_STORE) {
+        if constexpr (MODE == TC_ANA_STORE) {
           float v[32];
           tmem_ld32(ta, v);
           if (a.split) {
@@ -485,24 +492,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         // each product exactly as p + e (q = qh + ql: p = v qh rounded, e = its rounding error by
         // fmaf plus v ql), the p's by error-free two-sums, the e's plainly; the two shell halves
         // are joined across the lane pair at the end.  The weights of a half chunk (16 degrees)
-        // are requested before its accumulator columns are read, which hides their latency.
+        // are requested together, right after its accumulator columns are read.
         const int s0 = (tl.c0 >> 1) + 16 * q;  // shell of the warp's first column
         const int d = lane >> 2, f = (lane >> 1) & 1, b = lane & 1;
         float* scr = red + (size_t)4 * a.nmax * 8 + (size_t)(warp - 2) * 256;
 #pragma unroll 1
         for (int hf = 0; hf < 2; ++hf) {
-          float4 qq[2][4];  // [sub-block][shell pair]: (qh, ql) of two shells
-#pragma unroll
-          for (int sb = 0; sb < 2; ++sb) {
-            const int jj = ch * 32 + hf * 16 + sb * 8 + d;
-            const int k = tl.n0 + jj;
-            const bool dvalid = jj < tl.nsize && k < tl.kvalid;
-            const float4* qrow =
-                (const float4*)(I.q2 + ((size_t)(m + p + 2 * (dvalid ? k : 0)) * 2 + f) * nr + s0 + 8 * b);
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              qq[sb][e] = (dvalid && s0 + 8 * b + 2 * e < nr) ? qrow[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
           float v[16];
           tmem_ld16(ta + (uint32_t)(16 * hf), v);
           if (a.split) {
@@ -515,6 +510,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
+          }
+          float4 qq[2][4];  // [sub-block][shell pair]: (qh, ql) of two shells
+#pragma unroll
+          for (int sb = 0; sb < 2; ++sb) {
+            const int jj = ch * 32 + hf * 16 + sb * 8 + d;
+            const int k = tl.n0 + jj;
+            const bool dvalid = jj < tl.nsize && k < tl.kvalid;
+            const float4* qrow =
+                (const float4*)(I.q2 + ((size_t)(m + p + 2 * (dvalid ? k : 0)) * 2 + f) * nr + s0 + 8 * b);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              qq[sb][e] = (dvalid && s0 + 8 * b + 2 * e < nr) ? qrow[e] : make_float4(0.f, 0.f, 0.f, 0.f);
           }
 #pragma unroll
           for (int sb = 0; sb < 2; ++sb) {
@@ -562,7 +569,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           }
         }
       }
-      if (a.mode == TC_ANA_QUAD) {
+      if constexpr (MODE == TC_ANA_QUAD) {
         if (!epi_sync(&epib[0], ephase, lane, a.err)) break;
         const int tid = threadIdx.x - 64;
         for (int n = tid; n < tl.nsize; n += 32 * kEpiWarps) {
@@ -667,12 +674,18 @@ void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st) {
   const size_t smem = tc_smem_bytes(args.nterms, args.nmax, args.stages, args.mode);
   if (smem > 227 * 1024 || args.stages < 1) throw Error(FNL_EUNSUPPORTED, "tensor-core tile does not fit shared memory");
   const int grid = std::max(1, std::min(args.ntiles, sms));
+  auto run = [&](auto kern) {
+    FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, kThreadsTc, smem, st>>>(args);
+  };
   if (args.multi) {
-    FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_gemm<true><<<grid, kThreadsTc, smem, st>>>(args);
+    if (args.mode == TC_SYNTH) run(k_tc_gemm<true, TC_SYNTH>);
+    else if (args.mode == TC_ANA_QUAD) run(k_tc_gemm<true, TC_ANA_QUAD>);
+    else throw Error(FNL_EUNSUPPORTED, "per-shell analysis output runs for one configuration per launch");
   } else {
-    FNL_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_gemm<false><<<grid, kThreadsTc, smem, st>>>(args);
+    if (args.mode == TC_SYNTH) run(k_tc_gemm<false, TC_SYNTH>);
+    else if (args.mode == TC_ANA_QUAD) run(k_tc_gemm<false, TC_ANA_QUAD>);
+    else run(k_tc_gemm<false, TC_ANA_STORE>);
   }
   FNL_CUDA(cudaGetLastError());
 }
