@@ -111,8 +111,6 @@ def traffic_of(key) -> float | None:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
     return e["bytes"] if sha == e["sha16"] else None
 
-FP32_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 lanes x FMA x max SM clock
-
 
 # ---------------------------------------------------------------------------------------
 # clocks during the timed region
@@ -574,6 +572,10 @@ def main():
     torch.cuda.synchronize()
     e2e_value = job_throughput(world, e2e_steps, max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{local}"))
 
+    # ---- measured FMA rates of this GPU (project kernels, CUDA events), the denominators of the
+    # ALU-bound stages: FP32 for the filter and the ring DFTs, FP64 for the FP64 path
+    fma64, fma32 = F.measure_fma_peaks(local)
+
     # ---- the FP64 GPU path on the same filters and noise: throughput and the error of the
     # timed form against it (the metric's "mixed vs FP64")
     fp64 = None
@@ -639,21 +641,22 @@ def main():
                      "unit": "TFLOP/s", "peak_source": f"bf16 sustained ({pk_kind}); executed = {mult} x useful flops",
                      "hbm_frac": gb[st_name] / sec / 1e9 / pk["hbm_gbs"]}
             elif args.prec == "fp32":
-                e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": FP32_TFLOPS, "unit": "TFLOP/s",
-                     "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz"}
+                e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": fma32, "unit": "TFLOP/s",
+                     "peak_source": "FP32 FFMA rate (measured, fnl_measure_fma_peaks)"}
             else:
-                e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": 1.25, "unit": "TFLOP/s",
-                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}
+                e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": fma64, "unit": "TFLOP/s",
+                     "peak_source": "FP64 DFMA rate (measured, fnl_measure_fma_peaks)"}
         elif st_name == "ring_fft_square":
             e = {"bound": "alu", "achieved": fft_flops(wl.ntheta, wl.nphi, wl.nr) / sec / 1e12,
-                 "peak": FP32_TFLOPS if args.prec != "fp64" else 1.25, "unit": "TFLOP/s",
-                 "peak_source": ("FP32 pipes: 152 SMs x 128 lanes x 2 flops x 2070 MHz" if args.prec != "fp64"
-                                 else "nominal GB300 FP64 rate") + "; flops by 5 N log2 N",
+                 "peak": fma32 if args.prec != "fp64" else fma64, "unit": "TFLOP/s",
+                 "peak_source": ("FP32 FFMA" if args.prec != "fp64" else "FP64 DFMA")
+                                + " rate (measured, fnl_measure_fma_peaks); flops by 5 N log2 N",
                  "hbm_frac": fft_bytes(wl.lmax, wl.ntheta, wl.nr, real_bytes) / sec / 1e9 / pk["hbm_gbs"]}
         elif st_name == "filter":
             e = {"bound": "alu", "achieved": filter_flops(wl.lmax, wl.nr) / sec / 1e12,
-                 "peak": FP32_TFLOPS if args.prec != "fp64" else 1.25, "unit": "TFLOP/s",
-                 "peak_source": "FP32 FFMA: 152 SMs x 128 lanes x 2 flops x 2070 MHz"}
+                 "peak": fma32 if args.prec != "fp64" else fma64, "unit": "TFLOP/s",
+                 "peak_source": ("FP32 FFMA" if args.prec != "fp64" else "FP64 DFMA")
+                                + " rate (measured, fnl_measure_fma_peaks)"}
         else:
             if mixed:  # epilogue partials (float4 per column tile) and a^X_L in, a^X and a^X_NL out
                 qb = W.n_alm(wl.lmax) * ((wl.nr * 2 + 127) // 128 * 16 + 2 * 16 + 4 * 16)
@@ -685,6 +688,9 @@ def main():
         "gpu_launches": (6 if args.prec in ("bf16x2", "bf16x3") else 5) * args.steps,
         "tiles": {"synthesis": tiles[0], "analysis": tiles[1]},
         "clocks": clk,
+        "fma_peaks": {"fp64_tflops": fma64, "fp32_tflops": fma32,
+                      "how": "fnl_measure_fma_peaks: 8 independent FMA chains per thread, 8 blocks of 256 per SM, "
+                             "median of 5 launches of ~10 ms, CUDA events"},
     }
     if batch is not None:
         line["batch"] = batch

@@ -425,6 +425,14 @@ fnl_status fnl_profile_enable(fnl_shells* sh, int slots);
  * receives their number.  Waits for those calls to finish and restarts the count. */
 fnl_status fnl_profile_read(fnl_shells* sh, double* ms, int n, int* calls);
 
+/* ---- measured arithmetic peaks (for the rooflines; no counterpart in the paper) ------- */
+
+/* FP64 and FP32 fused multiply-add rates of device `device` in TFLOP/s (2 flops per FMA), each
+ * measured with a kernel of independent FMA chains filling every SM (median of five timed
+ * launches of ~10 ms, CUDA events).  Either output may be NULL.  Synchronous; allocates a small
+ * temporary buffer. */
+fnl_status fnl_measure_fma_peaks(int device, double* fp64_tflops, double* fp32_tflops);
+
 /* ---- host-side set-up helpers (no GPU needed) -------------------------------------- */
 
 /* n-point Gauss-Legendre rule: x (host [n], north to south, x_j = cos theta_j), w (host [n]). */

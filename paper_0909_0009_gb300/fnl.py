@@ -31,6 +31,7 @@ EXPORTS = [
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
     "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
     "fnl_make_shells_healpix", "fnl_shells_set_sm_limits", "fnl_test_fail_alloc", "fnl_test_wait_expiry",
+    "fnl_measure_fma_peaks",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_device_status.argtypes = [vp]
     lib.fnl_test_fail_alloc.argtypes = [ctypes.c_long]
     lib.fnl_test_wait_expiry.argtypes = [vp, ctypes.c_uint, vp]
+    lib.fnl_measure_fma_peaks.argtypes = [i, dp, dp]
     lib.fnl_accumulate_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
     lib.fnl_generate_backward.argtypes = [vp, u64, u64, d, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.fnl_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
@@ -559,6 +561,14 @@ class Batch:
         pE = (ctypes.c_void_p * n)(*[o[1].data_ptr() for o in out])
         _check(_lib.fnl_generate_batch(self.handle, sd, rl, _dptr(fv), pT, pE, _stream(stream)))
         return out
+
+
+def measure_fma_peaks(device: int = 0) -> tuple[float, float]:
+    """(FP64, FP32) fused multiply-add rates of the device in TFLOP/s, measured by the library."""
+    lib = load_library()
+    d64, d32 = ctypes.c_double(), ctypes.c_double()
+    _check(lib.fnl_measure_fma_peaks(int(device), ctypes.byref(d64), ctypes.byref(d32)))
+    return d64.value, d32.value
 
 
 NOALLOC_OUTPUTS = ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]
