@@ -303,7 +303,8 @@ def measure_batch(F, prec: str, device: int, reps: int = 3) -> dict:
 
 def measure_adjoint(F, device: int, reps: int = 3) -> dict:
     """Differentiation form at l_max = 512, N_r = 96 (769 x 1600): fnl_generate and
-    fnl_generate_backward (dL/dn and dL/df_NL, maps recomputed) in FP64 and FP32."""
+    fnl_generate_backward (dL/dn and dL/df_NL, maps recomputed) in FP64, FP32 and bf16x2 (the
+    tensor-core form: both syntheses and the analysis on tcgen05)."""
     import torch
     wl = W.GRAD
     r, w = W.radial_grid(wl.nr)
@@ -311,7 +312,7 @@ def measure_adjoint(F, device: int, reps: int = 3) -> dict:
     K = W.random_lower_filters(wl.lmax, wl.nr, seed=2, scale=8e-5)
     stream = torch.cuda.current_stream()
     res = {"workload": wl.name, "lmax": wl.lmax, "nr": wl.nr, "ntheta": wl.ntheta, "nphi": wl.nphi}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "bf16x2"):
         sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=prec, device=device)
         g = torch.randn(sh.nalm, dtype=torch.complex128, device=f"cuda:{device}")
         fw = sh.generate(2, 0, wl.fnl[0])

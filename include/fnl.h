@@ -152,8 +152,10 @@ fnl_status fnl_generate(const fnl_shells* sh, uint64_t seed, uint64_t realisatio
  * The chain rule through steps (i)-(v) (Eq. 9, the synthesis, Eq. 2, the analysis, Eq. 5,
  * Eq. 3), with mu a constant: dL/dPhi_NL = f_NL q^X gX; dL/dPhi_L = c_m analysis(2 f s) +
  * q^X gX, s the synthesis of dL/dPhi_NL with m > 0 halved, c_0 = 1 and c_m = 2; dL/dn =
- * K_l^T dL/dPhi_L.  The maps f and s are recomputed on the ring grid, not stored.
- * FNL_FP64 and FNL_FP32 objects only (FNL_EUNSUPPORTED otherwise). */
+ * K_l^T dL/dPhi_L.  The maps f and s are recomputed on the ring grid, not stored.  Every
+ * precision form on the Gauss-Legendre grid: the tensor-core forms run both syntheses and the
+ * analysis as their tcgen05 GEMMs (operands split into BF16 terms, FP32 accumulation), the ring
+ * product and K_l^T in FP32 (FNL_EUNSUPPORTED on the HEALPix grid and on batch clones). */
 fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl,
                                  const double* noise, const double* gT, const double* gE,
                                  const double* aNLT, const double* aNLE, double* grad_noise,

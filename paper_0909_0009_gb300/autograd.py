@@ -9,7 +9,8 @@ them; it keeps only a^T_NL and a^E_NL of the forward call (2 nalm complex number
 PyTorch's gradient of a real loss with respect to a complex tensor is dL/dRe + i dL/dIm,
 which is exactly the pair layout the C ABI takes and returns, so no conversion is done.
 The imaginary part of every m = 0 noise entry is ignored by the forward and gets a zero
-gradient.  The FNL_FP64 and FNL_FP32 forms have an adjoint; the tensor-core forms raise.
+gradient.  Every precision form has an adjoint; the tensor-core forms run it on their
+tcgen05 GEMMs (HEALPix objects raise).
 """
 from __future__ import annotations
 

@@ -1,4 +1,6 @@
-// Adjoint of the generator (differentiation form) for the SIMT forms (FP64 and FP32).
+// Adjoint of the generator (differentiation form): the SIMT forms (FP64, FP32) and the
+// tensor-core forms (BF16X2, BF16X3), which run the same chain with their own kernels for the
+// two syntheses (tcgen05 GEMMs), the ring product and the analysis (tcgen05, per-shell output).
 //
 // For a real loss L of a^T and a^E with gX = dL/da^X (pairs dL/dRe, dL/dIm) the chain rule
 // through steps (i)-(v) gives
@@ -14,6 +16,7 @@
 #include <algorithm>
 
 #include "fnl_internal.cuh"
+#include "mixed.cuh"
 
 namespace fnl {
 
@@ -55,12 +58,38 @@ __global__ void k_adjoint_source(int L, int nr, int64_t nalm, const int64_t* __r
   phi[(row0[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * C + c] = (T)v;
 }
 
+// The same for the tensor-core forms: H~ written as BF16 terms of the synthesis operand (the
+// Phi rows in their 32-row packing, Cpad columns), so that the tensor-core synthesis GEMM gives s.
+__global__ void k_adjoint_source_terms(int L, int nr, int Cpad, int64_t nalm, int nterms, int64_t term_stride,
+                                       const int64_t* __restrict__ row32, const double* __restrict__ qT,
+                                       const double* __restrict__ qE, double fnl, const double* __restrict__ gT,
+                                       const double* __restrict__ gE, __nv_bfloat16* __restrict__ phiT) {
+  const int C = 2 * nr;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nalm * C) return;
+  const int64_t idx = t / C;
+  const int c = (int)(t % C);
+  const int i = c >> 1, part = c & 1;
+  int l, m;
+  lm_of_entry(idx, L, l, m);
+  double v = 0.0;
+  if (gT) v += qT[(size_t)l * nr + i] * gT[2 * idx + part];
+  if (gE) v += qE[(size_t)l * nr + i] * gE[2 * idx + part];
+  v *= fnl;
+  if (m > 0) v *= 0.5;
+  if (m == 0 && part) v = 0.0;
+  store_terms_d(phiT + (row32[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * Cpad + c, term_stride, nterms, v);
+}
+
 // dL/dn for degree l = L - blockIdx.x: Phibar = c_m phi_rows + q^T_l gT + q^E_l gE, then
-// nbar_j = sum_{i >= j} K_l[i, j] Phibar_i for every m <= l.
-template <typename T>
+// nbar_j = sum_{i >= j} K_l[i, j] Phibar_i for every m <= l.  With API_ROWS the analysis of
+// 2 f s comes in the API layout [nalm][nr][2] in FP64 (the tensor-core forms' per-shell
+// analysis output), else in the SIMT rows [rows][2 nr] of the real type.
+template <typename T, bool API_ROWS = false>
 __global__ void __launch_bounds__(kThreads) k_adjoint_filter(int L, int nr, int64_t nalm, const T* __restrict__ Kf,
                                                              const int64_t* __restrict__ row0,
                                                              const T* __restrict__ phi,
+                                                             const double* __restrict__ api_rows,
                                                              const double* __restrict__ qT,
                                                              const double* __restrict__ qE,
                                                              const double* __restrict__ gT,
@@ -80,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_filter(int L, int nr, int6
     __syncthreads();  // K staged; the previous m's Phibar consumed
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
       const int i = c >> 1, part = c & 1;
-      double v = cm * (double)phi[row * C + c];
+      double v = cm * (API_ROWS ? api_rows[(size_t)idx * C + c] : (double)phi[row * C + c]);
       if (gT) v += qT[(size_t)l * nr + i] * gT[2 * idx + part];
       if (gE) v += qE[(size_t)l * nr + i] * gE[2 * idx + part];
       pb[c] = (T)v;
@@ -145,16 +174,33 @@ void adjoint_filter_impl(const fnl_shells* sh, const double* gT, const double* g
   const int nr = sh->nr;
   const size_t smem = sizeof(T) * ((size_t)2 * nr + (size_t)nr * (nr + 1));
   FNL_CUDA(cudaFuncSetAttribute(k_adjoint_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_adjoint_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf, sh->d_row0,
-                                                            (const T*)sh->d_phi, sh->d_qT, sh->d_qE, gT, gE, grad);
+  if (sh->nterms) {
+    FNL_CUDA(cudaFuncSetAttribute(k_adjoint_filter<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_adjoint_filter<T, true><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf,
+                                                                    sh->d_row0, nullptr, sh->d_adjA, sh->d_qT,
+                                                                    sh->d_qE, gT, gE, grad);
+  } else {
+    k_adjoint_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf, sh->d_row0,
+                                                              (const T*)sh->d_phi, nullptr, sh->d_qT, sh->d_qE, gT,
+                                                              gE, grad);
+  }
   FNL_CUDA(cudaGetLastError());
 }
 
 }  // namespace
 
 void launch_adjoint_source(const fnl_shells* sh, double fnl, const double* gT, const double* gE, cudaStream_t st) {
-  if (sh->real_is_double) adjoint_source_impl<double>(sh, fnl, gT, gE, st);
-  else adjoint_source_impl<float>(sh, fnl, gT, gE, st);
+  if (sh->nterms) {
+    const int64_t n = sh->nalm * sh->C;
+    k_adjoint_source_terms<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        sh->lmax, sh->nr, sh->Cpad, sh->nalm, sh->nterms, sh->phiT_stride, sh->d_row32, sh->d_qT, sh->d_qE, fnl, gT,
+        gE, (__nv_bfloat16*)sh->d_phiT);
+    FNL_CUDA(cudaGetLastError());
+  } else if (sh->real_is_double) {
+    adjoint_source_impl<double>(sh, fnl, gT, gE, st);
+  } else {
+    adjoint_source_impl<float>(sh, fnl, gT, gE, st);
+  }
 }
 
 void launch_adjoint_filter(const fnl_shells* sh, const double* gT, const double* gE, double* grad_noise,

@@ -719,6 +719,12 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       if (nside) setup_healpix(sh);
     } else {
       setup_mixed(sh, qT, qE);
+      if (!synth_only) {
+        // the adjoint's second spectrum buffer and its per-shell analysis output
+        sh->d_F2 = dalloc<float>(sh, (size_t)nmp * np * sh->Cpad);
+        sh->d_adjA = dalloc<double>(sh, 2 * (size_t)sh->nalm * nr);
+        FNL_CUDA(cudaMemset(sh->d_F2, 0, sizeof(float) * (size_t)nmp * np * sh->Cpad));
+      }
     }
     FNL_CUDA(cudaDeviceSynchronize());
     auto hs = std::make_shared<HostSetup>();
@@ -981,9 +987,9 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
   return guard([&] {
     check_shells(sh);
     DeviceScope scope(sh->device);
-    if (sh->nterms)
-      throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward runs in the FNL_FP64 and FNL_FP32 forms");
     if (sh->nside) throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward runs on the Gauss-Legendre grid");
+    if (sh->nterms && (!sh->d_F2 || sh->owner))
+      throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward needs a shells object made by fnl_make_shells");
     check_dev_ptr(noise, "noise", true);
     check_dev_ptr(gT, "gT", true);
     check_dev_ptr(gE, "gE", true);
@@ -1012,6 +1018,19 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
       launch_dot_fnl(sh, gT, gE, aNLT, aNLE, grad_fnl, st);
     }
     if (!grad_noise) return;
+    if (sh->nterms) {
+      // the same chain on the tensor cores: both syntheses and the analysis are tcgen05 GEMMs
+      launch_filter_mixed(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + n2, nullptr, nullptr, st);  // Phi_L
+      launch_tc(sh, sh->tc_syn, TC_SYNTH, nullptr, st);                                   // F of f
+      launch_adjoint_source(sh, fnl, gT, gE, st);                                        // H~ as BF16 terms
+      TcArgs syn2 = sh->tc_syn;
+      syn2.one.F = (float*)sh->d_F2;
+      launch_tc(sh, syn2, TC_SYNTH, nullptr, st);                                         // F of s
+      launch_ring_product(sh, st);                                                        // G = DFT(2 f s)
+      launch_tc(sh, sh->tc_ana, TC_ANA_STORE, sh->d_adjA, st);                            // analysis(2 f s)
+      launch_adjoint_filter(sh, gT, gE, grad_noise, st);                                  // K^T (c_m rows + q g)
+      return;
+    }
     launch_filter(sh, seed, realisation, noise, sh->d_aL, sh->d_aL + n2, nullptr, st);  // Phi_L rows
     launch_synth_gemm(sh, st);                                                          // F of f
     launch_adjoint_source(sh, fnl, gT, gE, st);                                         // rows of H~

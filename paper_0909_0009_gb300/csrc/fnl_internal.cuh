@@ -199,6 +199,8 @@ struct fnl_shells {
   int64_t gt_stride = 0;
   void* d_part = nullptr;          // double2 [Cpad / 128][nalm][2]: quadrature partials per column tile
   float2* d_q2 = nullptr;          // [L+1][2][nr]  q^T, q^E as FP32 pairs (hi, lo)
+  void* d_F2 = nullptr;            // adjoint: the spectra of s, float as d_F (owner objects only)
+  double* d_adjA = nullptr;        // adjoint: analysis of 2 f s per shell, [nalm][nr][2]
   int* d_err = nullptr;            // device error word of the tensor-core kernels
   double* d_psum = nullptr;        // [nr] sum_lm w_m |Phi_L,lm(r_i)|^2 (Parseval monopole)
   double* d_psum_part = nullptr;   // [(L+1) * 2][nr] the filter's partials of d_psum

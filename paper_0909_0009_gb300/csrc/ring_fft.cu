@@ -267,6 +267,7 @@ struct FftArgs {
   const cplx<T>* twp;    // per-pass twiddles
   const T* F;            // [2(L+1)][npairs][C]
   T* G;                  // [2(L+1)][npairs][C]
+  const T* F2;           // product mode: the second spectrum (NULL: G, SIMT forms)
   const double* mu;      // [nr]
   const double* wgl;     // [npairs]
   const double* maps_in; // [nr][ntheta][nphi]
@@ -360,10 +361,11 @@ __global__ void __launch_bounds__(256) k_ring_fft(const FftArgs<T> a) {
   }
 }
 
-// Product mode of the adjoint: per (shell, ring pair) the spectra F1 = a.F and F2 = a.G (both
-// in the SIMT layout) are taken to the ring values z1, z2 (north + i south) as in the square,
-// w = 2 Re z1 Re z2 + i 2 Im z1 Im z2, and W = DFT(w) is written over F2 as S and D (same
-// scale and equator rule as the square).  Each block reads its entries of F2 before it writes.
+// Product mode of the adjoint: per (shell, ring pair) the spectra F1 = a.F and F2 (a.F2, or
+// a.G in the SIMT forms) are taken to the ring values z1, z2 (north + i south) as in the square,
+// w = 2 Re z1 Re z2 + i 2 Im z1 Im z2, and W = DFT(w) is written as S and D (same scale and
+// equator rule as the square): over F2 in G in the SIMT forms (each block reads its entries of
+// F2 before it writes), as BF16 terms in GT in the tensor-core forms.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
   for (int m = threadIdx.x; m <= L; m += blockDim.x) {
     const size_t oe = (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
     const size_t oo = (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
-    const T* src[2] = {a.F, a.G};
+    const T* src[2] = {a.F, a.F2 ? a.F2 : a.G};
     cplx<T>* dst[2] = {b0, b2};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -422,13 +424,24 @@ __global__ void __launch_bounds__(256) k_ring_product(const FftArgs<T> a) {
       S = {(gn.x + gs.x) * scale, (gn.y + gs.y) * scale};
       D = {(gn.x - gs.x) * scale, (gn.y - gs.y) * scale};
     }
-    T* ge = a.G + (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
-    T* go = a.G + (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
-    ge[0] = S.x;
-    ge[1] = S.y;
-    if (m < L) {
-      go[0] = D.x;
-      go[1] = D.y;
+    const size_t oe = (size_t)(2 * m) * a.sp + (size_t)jp * a.sj + 2 * s;
+    const size_t oo = (size_t)(2 * m + 1) * a.sp + (size_t)jp * a.sj + 2 * s;
+    if (a.nterms) {
+      store_terms(a.GT + oe, a.gt_stride, a.nterms, (float)S.x);
+      store_terms(a.GT + oe + 1, a.gt_stride, a.nterms, (float)S.y);
+      if (m < L) {
+        store_terms(a.GT + oo, a.gt_stride, a.nterms, (float)D.x);
+        store_terms(a.GT + oo + 1, a.gt_stride, a.nterms, (float)D.y);
+      }
+    } else {
+      T* ge = a.G + oe;
+      T* go = a.G + oo;
+      ge[0] = S.x;
+      ge[1] = S.y;
+      if (m < L) {
+        go[0] = D.x;
+        go[1] = D.y;
+      }
     }
   }
 }
@@ -938,9 +951,19 @@ void ring_product_impl(const fnl_shells* sh, cudaStream_t st) {
   a.nr = sh->nr;
   a.ntheta = sh->ntheta;
   a.npairs = sh->npairs;
-  a.C = sh->C;
-  a.sp = (int64_t)sh->npairs * sh->C;
-  a.sj = sh->C;
+  if (sh->nterms) {  // tensor-core forms: both spectra ring-pair-major FP32, output as BF16 terms
+    a.C = sh->Cpad;
+    a.sp = sh->Cpad;
+    a.sj = (int64_t)2 * (sh->lmax + 1) * sh->Cpad;
+    a.F2 = (const T*)sh->d_F2;
+    a.nterms = sh->nterms;
+    a.gt_stride = sh->gt_stride;
+    a.GT = (__nv_bfloat16*)sh->d_GT;
+  } else {
+    a.C = sh->C;
+    a.sp = (int64_t)sh->npairs * sh->C;
+    a.sj = sh->C;
+  }
   a.plan = sh->fft;
   a.tw = (const cplx<T>*)sh->d_tw;
   a.twp = (const cplx<T>*)sh->d_twp;
@@ -956,7 +979,7 @@ void ring_product_impl(const fnl_shells* sh, cudaStream_t st) {
 }
 
 void launch_ring_product(const fnl_shells* sh, cudaStream_t st) {
-  if (sh->nterms) throw Error(FNL_EUNSUPPORTED, "the adjoint ring product runs in the SIMT forms");
+  if (sh->nterms && !sh->d_F2) throw Error(FNL_EUNSUPPORTED, "this object has no second spectrum buffer");
   if (sh->real_is_double) ring_product_impl<double>(sh, st);
   else ring_product_impl<float>(sh, st);
 }
