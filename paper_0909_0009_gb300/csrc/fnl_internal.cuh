@@ -323,6 +323,9 @@ void launch_ring_cubic(const fnl_shells* sh, int nsh, double* part, cudaStream_t
 // The same with the specialised ring kernel of the tensor-core forms (ring_square.cu); false if
 // the object's ring length has none.
 bool launch_ring_cubic_sq(const fnl_shells* sh, int nsh, double* part, cudaStream_t st);
+// Specialised adjoint rings of the tensor-core forms (ring_square.cu): 2 f s from the spectra of f
+// (d_F) and s (d_F2) into d_GT; false if the object's ring length has none.
+bool launch_ring_product_sq(const fnl_shells* sh, cudaStream_t st);
 // Stokes maps (maps.cu): tables once, then I, Q, U of one set of a_lm.
 void maps_prepare(fnl_shells* sh);
 void launch_maps(const fnl_shells* sh, const double* aT, const double* aE, const double* aB, double* maps,

@@ -980,6 +980,7 @@ void ring_product_impl(const fnl_shells* sh, cudaStream_t st) {
 
 void launch_ring_product(const fnl_shells* sh, cudaStream_t st) {
   if (sh->nterms && !sh->d_F2) throw Error(FNL_EUNSUPPORTED, "this object has no second spectrum buffer");
+  if (sh->nterms && launch_ring_product_sq(sh, st)) return;
   if (sh->real_is_double) ring_product_impl<double>(sh, st);
   else ring_product_impl<float>(sh, st);
 }

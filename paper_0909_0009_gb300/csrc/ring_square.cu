@@ -612,6 +612,209 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_cubic_
   cp_async_wait_all();
 }
 
+// Rings of the adjoint (differentiation form) in the tensor-core forms: per (ring pair, shell)
+// the spectra of f (F1) and of s (F2) go to their ring values z1, z2 (north + i south), the
+// product w = 2 Re z1 Re z2 + i 2 Im z1 Im z2 (the square's adjoint, 2 f s) goes back by the
+// forward DFT, and S and D are written as BF16 terms with the square's scale and equator rule.
+// Work item = (ring pair, G / 2 shells): groups 0 .. G/2 - 1 transform the f spectra of the
+// item's shells, groups G/2 .. G - 1 their s spectra; after the inverse half of phase 2 the s
+// groups leave their ring values in shared memory, and each f group multiplies them into its
+// own (still in registers) and runs the forward half and phases 3a, 3b alone.
+struct ProdArgs {
+  int L, nr, ntheta, npairs, N, nterms;
+  int64_t sp, sj;      // F1, F2 and G strides between problems mp and ring pairs jp (elements)
+  int64_t gt_stride;   // elements between BF16 terms of G
+  const float* F1;     // [jp][mp][Cpad]: spectra of f
+  const float* F2;     // [jp][mp][Cpad]: spectra of s
+  __nv_bfloat16* GT;   // [term][jp][mp][Cpad]
+  const float2* tw2;
+  const float2* tw1;
+  const double* wgl;   // [npairs]
+};
+
+template <int N1, int P, int Q, int PAD, int G>
+__global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_product_sq(const __grid_constant__ ProdArgs a) {
+  constexpr int T = P * Q;
+  constexpr int TG = (T + 31) / 32 * 32;
+  constexpr int N = N1 * P * Q;
+  constexpr int S = N1 * P + PAD;
+  constexpr int NB = N1 * P + S * (Q - 1);
+  constexpr int H = G / 2;  // shells of an item
+  static_assert(NB >= N && H % 2 == 0, "layout");
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* buf = (float2*)smem;                    // [G][NB]
+  float2* stg = buf + (size_t)G * NB;             // [2 L + 1][G]: f fields, then s fields
+  float2* tw2 = stg + (size_t)(2 * a.L + 1) * G;  // [N1][Q][P]
+  float2* tw1 = tw2 + (size_t)N1 * T;             // [P][Q]
+  for (int i = threadIdx.x; i < N1 * T; i += blockDim.x) tw2[i] = a.tw2[i];
+  for (int i = threadIdx.x; i < T; i += blockDim.x) tw1[i] = a.tw1[i];
+  const int groups = a.nr / H;
+  const int items = groups * a.npairs;
+  const int g = threadIdx.x / TG, u = threadIdx.x % TG;
+  const bool is_f = g < H;
+  float2* B = buf + (size_t)g * NB;
+  const int L = a.L;
+
+  auto prefetch = [&](int item) {
+    const int jp = item / groups, s0 = (item % groups) * H;
+    const float* src1 = a.F1 + (size_t)jp * a.sj + 2 * s0;
+    const float* src2 = a.F2 + (size_t)jp * a.sj + 2 * s0;
+    constexpr int Q4 = H / 2;  // 16-byte copies per row and field
+    for (int q = threadIdx.x; q < (2 * L + 1) * 2 * Q4; q += blockDim.x) {
+      const int mp = q / (2 * Q4), h = q % (2 * Q4);
+      const bool second = h >= Q4;
+      const int hh = second ? h - Q4 : h;
+      cp_async16(stg + (size_t)mp * G + (second ? H : 0) + 2 * hh, (second ? src2 : src1) + (size_t)mp * a.sp + 4 * hh);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  if (item < items) prefetch(item);
+  for (; item < items; item += gridDim.x) {
+    const int jp = item / groups, s0 = (item % groups) * H;
+    const double wgl = a.wgl[jp];
+    cp_async_wait_all();
+    __syncthreads();  // staged rows visible; the previous item's buffers are free
+    for (int t = threadIdx.x; t < (L + 1) * G; t += blockDim.x) {
+      const int gg = t % G, m = t / G;
+      const float2 E = stg[(size_t)(2 * m) * G + gg];
+      const float2 O = m < L ? stg[(size_t)(2 * m + 1) * G + gg] : make_float2(0.f, 0.f);
+      const float2 FN = cadd(E, O), FS = csub(E, O);
+      float2* Bg = buf + (size_t)gg * NB;
+      if (m == 0) {
+        Bg[0] = make_float2(FN.x, FS.x);
+      } else {
+        Bg[m + PAD * (m / (N1 * P))] = make_float2(FN.x - FS.y, FN.y + FS.x);
+        const int k = N - m;
+        Bg[k + PAD * (k / (N1 * P))] = make_float2(FN.x + FS.y, FS.x - FN.y);
+      }
+    }
+    __syncthreads();
+    if (item + (int)gridDim.x < items) prefetch(item + gridDim.x);
+    // phase 1a: DFT_Q over b (inverse), entries in l_max < k < N - l_max are zero
+#pragma unroll 1
+    for (int t = u; t < N1 * P; t += TG) {
+      float2 v[Q];
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        const int k = t + N1 * P * b;
+        v[b] = (k > L && k < N - L) ? make_float2(0.f, 0.f) : B[t + S * b];
+      }
+      Dft<Q, 1>::run(v);
+#pragma unroll
+      for (int c = 0; c < Q; ++c) B[t + S * c] = v[c];
+    }
+    group_sync<TG>(g);
+    // phase 1b: twiddle w_PQ^(a c), DFT_P over a (inverse)
+#pragma unroll 1
+    for (int t = u; t < N1 * Q; t += TG) {
+      const int c = t % Q, k1 = t / Q;
+      const int base = k1 + S * c;
+      float2 v[P];
+#pragma unroll
+      for (int aa = 0; aa < P; ++aa) {
+        const float2 x = B[base + N1 * aa];
+        v[aa] = aa ? cmul(x, tw1[aa * Q + c]) : x;
+      }
+      Dft<P, 1>::run(v);
+#pragma unroll
+      for (int d = 0; d < P; ++d) B[base + N1 * d] = v[d];
+    }
+    group_sync<TG>(g);
+    // phase 2: twiddle w_N^(k1 n2), DFT_N1 (inverse) -> ring values; the s groups leave theirs in
+    // shared memory, the f groups keep theirs in registers, multiply, and go back (forward)
+    {
+      const int d = u % P, c = u / P;
+      const int base = N1 * d + S * c;
+      const float2* w = tw2 + c * P + d;
+      float2 v[N1];
+      if (u < T) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const float2 x = B[base + k1];
+          v[k1] = k1 ? cmul(x, w[k1 * T]) : x;
+        }
+        Dft<N1, 1>::run(v);
+        if (!is_f) {
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1) B[base + n1] = v[n1];
+        }
+      }
+      __syncthreads();  // the s ring values are in place
+      if (is_f && u < T) {
+        const float2* Bs = buf + (size_t)(g + H) * NB;
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+          const float2 y = Bs[base + n1];
+          v[n1] = make_float2(2.f * v[n1].x * y.x, 2.f * v[n1].y * y.y);
+        }
+        Dft<N1, -1>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) B[base + k1] = k1 ? cmulc(v[k1], w[k1 * T]) : v[k1];
+      }
+    }
+    if (is_f) {
+      group_sync<TG>(g);
+      // phase 3a: DFT_P over d (forward), twiddle w_PQ^(-a c)
+#pragma unroll 1
+      for (int t = u; t < N1 * Q; t += TG) {
+        const int c = t % Q, k1 = t / Q;
+        const int base = k1 + S * c;
+        float2 v[P];
+#pragma unroll
+        for (int d = 0; d < P; ++d) v[d] = B[base + N1 * d];
+        Dft<P, -1>::run(v);
+#pragma unroll
+        for (int aa = 0; aa < P; ++aa) B[base + N1 * aa] = aa ? cmulc(v[aa], tw1[aa * Q + c]) : v[aa];
+      }
+      group_sync<TG>(g);
+      // phase 3b: DFT_Q over c (forward); W_k kept for k <= l_max and k >= N - l_max
+#pragma unroll 1
+      for (int t = u; t < N1 * P; t += TG) {
+        float2 v[Q];
+#pragma unroll
+        for (int c = 0; c < Q; ++c) v[c] = B[t + S * c];
+        Dft<Q, -1>::run(v);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          const int k = t + N1 * P * b;
+          if (k <= L || k >= N - L) B[t + S * b] = v[b];
+        }
+      }
+    }
+    __syncthreads();
+    // S and D of every shell of the item, as BF16 terms
+    const int south = a.ntheta - 1 - jp;
+    const bool equator = (south == jp);
+    const float scale = (float)(6.28318530717958647692 / N * wgl);
+    __nv_bfloat16* out = a.GT + (size_t)jp * a.sj + 2 * s0;
+    for (int t = threadIdx.x; t < (L + 1) * H; t += blockDim.x) {
+      const int gg = t % H, m = t / H;
+      const float2* Bg = buf + (size_t)gg * NB;
+      const float2 wm = Bg[m + PAD * (m / (N1 * P))];
+      const int kc = m ? N - m : 0;
+      const float2 wc = Bg[kc + PAD * (kc / (N1 * P))];
+      const float gnx = (wm.x + wc.x) * 0.5f, gny = (wm.y - wc.y) * 0.5f;
+      const float gsx = (wm.y + wc.y) * 0.5f, gsy = -(wm.x - wc.x) * 0.5f;
+      float Sx, Sy, Dx, Dy;
+      if (equator) {
+        Sx = Dx = gnx * scale;
+        Sy = Dy = gny * scale;
+      } else {
+        Sx = (gnx + gsx) * scale;
+        Sy = (gny + gsy) * scale;
+        Dx = (gnx - gsx) * scale;
+        Dy = (gny - gsy) * scale;
+      }
+      __nv_bfloat16* o = out + (size_t)(2 * m) * a.sp + 2 * gg;
+      store_pair_terms(o, a.gt_stride, a.nterms, Sx, Sy);
+      if (m < L) store_pair_terms(o + a.sp, a.gt_stride, a.nterms, Dx, Dy);
+    }
+  }
+  cp_async_wait_all();
+}
+
 struct SqConfig {
   int N, N1, P, Q, G;
 };
@@ -650,6 +853,21 @@ void launch_cube(const CubeArgs& a, int sms, cudaStream_t st) {
   int per_sm = 0;
   FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * TG, smem));
   const int items = (a.nsh / (G / 2)) * a.npairs;
+  const int grid = std::max(1, std::min(items, sms * std::max(per_sm, 1)));
+  kern<<<grid, G * TG, smem, st>>>(a);
+  FNL_CUDA(cudaGetLastError());
+}
+
+template <int N1, int P, int Q, int PAD, int G>
+void launch_prod(const ProdArgs& a, int sms, cudaStream_t st) {
+  constexpr int T = P * Q, TG = (T + 31) / 32 * 32, S = N1 * P + PAD, NB = N1 * P + S * (Q - 1);
+  const size_t smem = sizeof(float2) * ((size_t)G * NB + (size_t)(2 * a.L + 1) * G + (size_t)N1 * T + T);
+  if (smem > 227 * 1024) throw Error(FNL_EUNSUPPORTED, "adjoint ring staging exceeds shared memory");
+  auto kern = k_ring_product_sq<N1, P, Q, PAD, G>;
+  FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  FNL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * TG, smem));
+  const int items = (a.nr / (G / 2)) * a.npairs;
   const int grid = std::max(1, std::min(items, sms * std::max(per_sm, 1)));
   kern<<<grid, G * TG, smem, st>>>(a);
   FNL_CUDA(cudaGetLastError());
@@ -775,6 +993,39 @@ bool launch_ring_cubic_sq(const fnl_shells* sh, int nsh, double* part, cudaStrea
     case 1600: launch_cube<25, 8, 8, 2, 8>(a, sh->sms, st); return true;
     case 800: launch_cube<25, 8, 4, 4, 8>(a, sh->sms, st); return true;
     case 400: launch_cube<25, 4, 4, 2, 8>(a, sh->sms, st); return true;
+    default: return false;
+  }
+}
+
+// Specialised adjoint rings of the tensor-core forms (f spectra in d_F, s spectra in d_F2, 2 f s
+// as BF16 terms in d_GT); false if this configuration has none (the caller then runs the general
+// kernel).  The shells of an item are half the square kernel's group, since every shell holds
+// two fields.
+bool launch_ring_product_sq(const fnl_shells* sh, cudaStream_t st) {
+  const int G = ring_square_group(sh);
+  if (!G || !sh->d_F2 || sh->nr % (G / 2) || (G / 2) % 2) return false;
+  ProdArgs a;
+  a.L = sh->lmax;
+  a.nr = sh->nr;
+  a.ntheta = sh->ntheta;
+  a.npairs = sh->npairs;
+  a.N = sh->nphi;
+  a.nterms = sh->nterms;
+  a.sp = sh->Cpad;
+  a.sj = (int64_t)2 * (sh->lmax + 1) * sh->Cpad;
+  a.gt_stride = sh->gt_stride;
+  a.F1 = (const float*)sh->d_F;
+  a.F2 = (const float*)sh->d_F2;
+  a.GT = (__nv_bfloat16*)sh->d_GT;
+  a.tw2 = (const float2*)sh->d_sqtw2;
+  a.tw1 = (const float2*)sh->d_sqtw1;
+  a.wgl = sh->d_wgl;
+  switch (sh->nphi) {
+    case 3200: launch_prod<25, 16, 8, 2, 4>(a, sh->sms, st); return true;
+    case 3125: launch_prod<25, 25, 5, 2, 4>(a, sh->sms, st); return true;
+    case 1600: launch_prod<25, 8, 8, 2, 8>(a, sh->sms, st); return true;
+    case 800: launch_prod<25, 8, 4, 4, 8>(a, sh->sms, st); return true;
+    case 400: launch_prod<25, 4, 4, 2, 8>(a, sh->sms, st); return true;
     default: return false;
   }
 }
