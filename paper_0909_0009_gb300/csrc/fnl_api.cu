@@ -218,6 +218,16 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
 
 }  // namespace
 
+// Tensor map of an F buffer (FP32 [npairs][nmp][Cpad]) for the synthesis epilogue's tensor
+// stores: boxes of 32 columns x 1 problem x 16 ring pairs.
+CUtensorMap f_tensor_map(const fnl_shells* sh, const void* F) {
+  const int nmp = 2 * (sh->lmax + 1);
+  const uint64_t dims[3] = {(uint64_t)sh->Cpad, (uint64_t)nmp, (uint64_t)sh->npairs};
+  const uint64_t str[2] = {(uint64_t)sh->Cpad * 4, (uint64_t)nmp * sh->Cpad * 4};
+  const uint32_t box[3] = {32, 1, 16};
+  return make_tensor_map_f32(F, 3, dims, str, box);
+}
+
 // The per-configuration part of the tensor-core GEMMs' arguments that does not depend on
 // the tile shape: the A tensor maps (BF16, MN-major, 128B swizzle; boxes of 64 columns x 64 k
 // x both 64-column halves of a 128-column tile, through a view whose next dimension steps over
@@ -240,6 +250,7 @@ void build_tc_inst_a(fnl_shells* sh) {
     const uint32_t box[5] = {64, 1, (uint32_t)kTcStageK, 2, (uint32_t)T};
     sh->tci[1].tmA = make_tensor_map_bf16(sh->d_GT, 5, dims, str, box, 128);
   }
+  sh->tci[0].tmF = f_tensor_map(sh, sh->d_F);
   for (TcInst& I : sh->tci) {
     I.F = (float*)sh->d_F;
     I.part = (double2*)sh->d_part;
@@ -723,6 +734,7 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
         // the adjoint's second spectrum buffer and its per-shell analysis output
         sh->d_F2 = dalloc<float>(sh, (size_t)nmp * np * sh->Cpad);
         sh->d_adjA = dalloc<double>(sh, 2 * (size_t)sh->nalm * nr);
+        sh->tmF2 = f_tensor_map(sh, sh->d_F2);
         FNL_CUDA(cudaMemset(sh->d_F2, 0, sizeof(float) * (size_t)nmp * np * sh->Cpad));
       }
     }
@@ -1025,6 +1037,7 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
       launch_adjoint_source(sh, fnl, gT, gE, st);                                        // H~ as BF16 terms
       TcArgs syn2 = sh->tc_syn;
       syn2.one.F = (float*)sh->d_F2;
+      syn2.one.tmF = sh->tmF2;
       launch_tc(sh, syn2, TC_SYNTH, nullptr, st);                                         // F of s
       launch_ring_product(sh, st);                                                        // G = DFT(2 f s)
       launch_tc(sh, sh->tc_ana, TC_ANA_STORE, sh->d_adjA, st);                            // analysis(2 f s)

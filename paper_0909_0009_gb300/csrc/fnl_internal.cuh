@@ -201,6 +201,7 @@ struct fnl_shells {
   float2* d_q2 = nullptr;          // [L+1][2][nr]  q^T, q^E as FP32 pairs (hi, lo)
   void* d_F2 = nullptr;            // adjoint: the spectra of s, float as d_F (owner objects only)
   double* d_adjA = nullptr;        // adjoint: analysis of 2 f s per shell, [nalm][nr][2]
+  CUtensorMap tmF2{};              // adjoint: tensor map of d_F2 for the synthesis's tensor stores
   int* d_err = nullptr;            // device error word of the tensor-core kernels
   double* d_psum = nullptr;        // [nr] sum_lm w_m |Phi_L,lm(r_i)|^2 (Parseval monopole)
   double* d_psum_part = nullptr;   // [(L+1) * 2][nr] the filter's partials of d_psum

@@ -108,6 +108,18 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// Tensor store of a shared-memory box to global memory (bulk async group), its commit, and the
+// wait until the copy engine has read every committed box out of shared memory.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int x, int y, int z, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+               ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
@@ -421,6 +433,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         }
         float* out = I.F + (size_t)tl.mp * I.Cpad + c;
         const size_t sj = (size_t)2 * (L + 1) * I.Cpad;
+        // one instance: the chunk (32 columns x 16 ring pairs) goes through the warp's 2 KB of
+        // shared memory and out by one tensor store, which keeps the F writes off the load/store
+        // path; several instances: plain stores
+        float* fst = red + (size_t)(warp - 2) * 512;
         for (int ch = h; ch < nch; ch += kEpiPerQuad) {
           float v[16];
           tmem_ld16(tacc + (uint32_t)(ch * 16), v);
@@ -435,7 +451,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
           }
-          if (cvalid) {
+          if constexpr (!MULTI) {
+            if (lane == 0) bulk_wait_read();  // the previous chunk's box has left the buffer
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) fst[j * 32 + lane] = v[j];  // box order: [16 ring pairs][32 c]
+            fence_proxy_async();
+            __syncwarp();
+            // a box that starts past the last ring pair holds no row: not issued (a box that
+            // runs past it is clipped by the copy engine)
+            if (lane == 0 && tl.n0 + ch * 16 < I.npairs) {
+              tma_store_3d(&a.one.tmF, tl.c0 + 32 * q, tl.mp, tl.n0 + ch * 16, smem_u32(fst));
+              bulk_commit();
+            }
+          } else if (cvalid) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int jr = tl.n0 + ch * 16 + j;
@@ -598,6 +627,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     }
   }
 
+  if constexpr (MODE == TC_SYNTH && !MULTI) {
+    if (warp >= 2 && lane == 0) bulk_wait_all();  // this warp's tensor stores are complete
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -631,6 +663,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
+CUtensorMap make_tensor_map_f32(const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                                const uint32_t* box) {
+  CUtensorMap m;
+  uint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base),
+                           (const cuuint64_t*)dims, (const cuuint64_t*)strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(FNL_ECUDA, "cuTensorMapEncodeTiled (FP32) failed with code " + std::to_string((int)r));
+  return m;
+}
+
 CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                                  const uint32_t* box, int swizzle_bytes) {
   CUtensorMap m;
@@ -648,8 +692,10 @@ CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dim
 
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode) {
   const size_t stage = (size_t)nterms * (kTcABytes + (size_t)nmax * 64 * kTcSlabs);
-  // epilogue reduction and per-warp scratch (analysis)
-  const size_t red = mode == TC_SYNTH ? 0 : ((size_t)4 * nmax * 8 + (size_t)kEpiWarps * 256) * sizeof(float);
+  // epilogue: per-warp 2 KB staging of F boxes (synthesis), or the quadrature's reduction and
+  // per-warp scratch (analysis)
+  const size_t red = mode == TC_SYNTH ? (size_t)kEpiWarps * 512 * sizeof(float)
+                                      : ((size_t)4 * nmax * 8 + (size_t)kEpiWarps * 256) * sizeof(float);
   return 1024 /*alignment*/ + (size_t)stages * stage + 1024 /*barriers*/ + red;
 }
 

@@ -35,6 +35,8 @@ constexpr int kTcMaxInst = 64;
 struct alignas(128) TcInst {  // CUtensorMap is 128-byte aligned
   CUtensorMap tmA;      // Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves, terms}
   CUtensorMap tmB;      // Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs, terms}
+  CUtensorMap tmF;      // TC_SYNTH, one instance per launch: F as FP32 [npairs][nmp][Cpad], box
+                        // {32 c, 1 problem, 16 ring pairs} for the epilogue's tensor stores
   float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
   double2* part;        // TC_ANA_QUAD: [Cpad / 128][nalm][2] ((T re, T im), (E re, E im))
   const float2* q2;     // [L+1][2][nr] q^T, q^E as FP32 pairs (hi, lo)
@@ -63,6 +65,9 @@ struct TcArgs {
 
 CUtensorMap make_tensor_map_bf16(const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                                  const uint32_t* box, int swizzle_bytes);
+// The same for an FP32 tensor, without swizzle.
+CUtensorMap make_tensor_map_f32(const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                                const uint32_t* box);
 size_t tc_smem_bytes(int nterms, int nmax, int stages, int mode);
 int tc_stages(int nterms, int nmax, int mode);
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st);
