@@ -127,9 +127,9 @@ fnl_status fnl_shells_mu(const fnl_shells* sh, double* mu_out);
 
 /* One realisation, Sect. 2 steps (i)-(v), entirely on the device.
  *  seed, realisation: key of the counter-based noise (Philox4x64-10): the noise of shell j
- *      and entry idx comes from counter (idx, j >> 1, realisation, 0), key (seed, 0);
- *      Box-Muller of output words (0,1) for even j, (2,3) for odd j; m > 0 entries get
- *      unit complex variance, m = 0 entries are real N(0, 1).
+ *      and entry idx comes from counter (idx, j >> 2, realisation, 0), key (seed, 0), output
+ *      word j & 3, whose two 32-bit halves are the Box-Muller uniforms ((hi + 1) 2^-32 and
+ *      lo 2^-32); m > 0 entries get unit complex variance, m = 0 entries are real N(0, 1).
  *  fnl:   f_NL of Eq. 1.
  *  noise: device [nr][nalm][2] explicit n_lm(r_j) (imaginary part of m = 0 ignored), or
  *      NULL to draw it from (seed, realisation).

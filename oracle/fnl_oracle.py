@@ -395,26 +395,26 @@ def philox4x64(c0, c1, c2, c3, k0, k1, rounds: int = 10):
 def philox_noise(lmax: int, nr: int, seed: int, realisation: int) -> np.ndarray:
     """White noise n_lm(r_j) drawn from (seed, realisation), shape [nr, nalm] complex.
 
-    Counter (idx(l, m), j >> 1, realisation, 0), key (seed, 0).  Shell j uses output
-    words (0, 1) if j is even and (2, 3) if j is odd:
-      u1 = ((w_a >> 11) + 1) 2^-53 in (0, 1],  u2 = (w_b >> 11) 2^-53 in [0, 1),
+    Counter (idx(l, m), j >> 2, realisation, 0), key (seed, 0).  Shell j uses output word
+    w = w_{j mod 4}, split into two 32-bit halves:
+      u1 = ((w >> 32) + 1) 2^-32 in (0, 1],  u2 = (w mod 2^32) 2^-32 in [0, 1),
       rho = sqrt(-2 ln u1), g1 = rho cos(2 pi u2), g2 = rho sin(2 pi u2)  (Box-Muller).
     n = (g1 + i g2) / sqrt(2) for m > 0 (unit complex variance); n = g1 for m = 0.
     """
     na = n_alm(lmax)
     idx = np.arange(na, dtype=np.uint64)
     out = np.empty((nr, na), dtype=np.complex128)
-    s11 = np.uint64(11)
-    for jp in range((nr + 1) // 2):
-        w = philox4x64(idx, np.uint64(jp), np.uint64(realisation), np.uint64(0),
+    s32 = np.uint64(32)
+    low = np.uint64(0xFFFFFFFF)
+    for jq in range((nr + 3) // 4):
+        w = philox4x64(idx, np.uint64(jq), np.uint64(realisation), np.uint64(0),
                        np.uint64(seed), np.uint64(0))
-        for half in range(2):
-            j = 2 * jp + half
+        for q in range(4):
+            j = 4 * jq + q
             if j >= nr:
                 break
-            wa, wb = w[2 * half], w[2 * half + 1]
-            u1 = ((wa >> s11) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
-            u2 = (wb >> s11).astype(np.float64) * 2.0 ** -53
+            u1 = ((w[q] >> s32) + np.uint64(1)).astype(np.float64) * 2.0 ** -32
+            u2 = (w[q] & low).astype(np.float64) * 2.0 ** -32
             rho = np.sqrt(-2.0 * np.log(u1))
             g1 = rho * np.cos(2.0 * math.pi * u2)
             g2 = rho * np.sin(2.0 * math.pi * u2)

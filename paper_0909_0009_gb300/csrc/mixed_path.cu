@@ -51,7 +51,7 @@ __device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, flo
 // lower triangular, so row tile t (rows 4t .. 4t + 3) needs 4t + 4 terms: each thread owns
 // the 4-row tiles r and nt4 - 1 - r (r = thread row, warp-uniform up to one) times 4 columns,
 // which gives every thread and every warp the same number of multiply-adds.  The noise tile
-// is drawn by all threads (Philox4x64 + FP32 Box-Muller); a^X_L = v^X_l . n per column
+// is drawn by all threads (Philox4x64, one call per four shells, + FP32 Box-Muller); a^X_L = v^X_l . n per column
 // (Eq. 5 applied to Eq. 9), each dot product split over two threads.
 constexpr int kFCols = 64;
 
@@ -91,7 +91,7 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
     vs[3 * nr + e] = (float)(u - (double)(float)u);
   }
   const int64_t nalm = (int64_t)(L + 1) * (L + 2) / 2;
-  const int npair = (nr + 1) / 2;
+  const int nquad = (nr + 3) / 4;
   // GEMM: thread row r = tid / 16 owns row tiles ta = r and tb = nt4 - 1 - r, columns 4 cb ..
   const int r4 = threadIdx.x >> 4, cb = threadIdx.x & 15;
   const int nt4 = nrp / 4, ta = r4, tb = nt4 - 1 - r4;
@@ -117,17 +117,18 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
         *(float2*)(nt + (size_t)j * kFCols + 2 * mb) = v;
       }
     } else {
-      for (int t = threadIdx.x; t < npair * (kFCols / 2); t += kThreads) {
-        const int jp = t / (kFCols / 2), mb = t % (kFCols / 2), m = m0 + mb;
-        float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-        if (mb < nm) {
-          uint64_t w[4];
-          noise_words(seed, real, alm_idx(l, m, L), jp, w);
-          v0 = noise_value_f32(box_muller_f32(w[0], w[1]), m);
-          v1 = noise_value_f32(box_muller_f32(w[2], w[3]), m);
+      // one Philox call gives the draws of four shells (one 64-bit word each)
+      for (int t = threadIdx.x; t < nquad * (kFCols / 2); t += kThreads) {
+        const int jq = t / (kFCols / 2), mb = t % (kFCols / 2), m = m0 + mb;
+        uint64_t w[4] = {0, 0, 0, 0};
+        if (mb < nm) noise_words(seed, real, alm_idx(l, m, L), jq, w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * jq + q;
+          if (j >= nr) break;
+          const float2 v = mb < nm ? noise_value_f32(box_muller_f32(w[q]), m) : make_float2(0.f, 0.f);
+          *(float2*)(nt + (size_t)j * kFCols + 2 * mb) = v;
         }
-        *(float2*)(nt + (size_t)(2 * jp) * kFCols + 2 * mb) = v0;
-        if (2 * jp + 1 < nr) *(float2*)(nt + (size_t)(2 * jp + 1) * kFCols + 2 * mb) = v1;
       }
     }
     __syncthreads();

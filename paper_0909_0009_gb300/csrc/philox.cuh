@@ -30,21 +30,22 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64
   }
 }
 
-// The four output words for noise entry idx of shells 2 jp and 2 jp + 1.
-__device__ __forceinline__ void noise_words(uint64_t seed, uint64_t real, int64_t idx, int jp,
+// The four output words for noise entry idx of shells 4 jq .. 4 jq + 3: counter
+// (idx, jq, realisation, 0), key (seed, 0); shell j takes word j & 3.
+__device__ __forceinline__ void noise_words(uint64_t seed, uint64_t real, int64_t idx, int jq,
                                             uint64_t w[4]) {
   w[0] = (uint64_t)idx;
-  w[1] = (uint64_t)jp;
+  w[1] = (uint64_t)jq;
   w[2] = real;
   w[3] = 0;
   philox4x64_10(w, seed, 0);
 }
 
-// Box-Muller in FP64: u1 = ((wa >> 11) + 1) 2^-53 in (0, 1], u2 = (wb >> 11) 2^-53 in [0, 1),
-// (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
-__device__ __forceinline__ double2 box_muller(uint64_t wa, uint64_t wb) {
-  const double u1 = (double)((wa >> 11) + 1) * 0x1p-53;
-  const double u2 = (double)(wb >> 11) * 0x1p-53;
+// Box-Muller in FP64 from one 64-bit word: u1 = ((w >> 32) + 1) 2^-32 in (0, 1],
+// u2 = (w mod 2^32) 2^-32 in [0, 1), (g1, g2) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+__device__ __forceinline__ double2 box_muller(uint64_t w) {
+  const double u1 = (double)((w >> 32) + 1) * 0x1p-32;
+  const double u2 = (double)(w & 0xffffffffull) * 0x1p-32;
   const double rho = sqrt(-2.0 * log(u1));
   double s, c;
   sincospi(2.0 * u2, &s, &c);
@@ -58,12 +59,12 @@ __device__ __forceinline__ double2 noise_value(double2 g, int m) {
   return make_double2(g.x * h, g.y * h);
 }
 
-// Noise in FP32 from the same Philox words as the FP64 path (the FP32 and mixed forms): the
-// 53-bit uniforms are rounded to FP32 (relative 2^-24), so draws agree with the FP64 path to
-// ~1e-7.
-__device__ __forceinline__ float2 box_muller_f32(uint64_t wa, uint64_t wb) {
-  const float u1 = __ull2float_rn((wa >> 11) + 1) * 0x1p-53f;
-  const float u2 = __ull2float_rn(wb >> 11) * 0x1p-53f;
+// Noise in FP32 from the same words as the FP64 path (the FP32 and mixed forms): the uniforms
+// are the FP64 path's rounded once to FP32 (relative 2^-24), so draws agree with it to ~1e-7.
+__device__ __forceinline__ float2 box_muller_f32(uint64_t w) {
+  const uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w;
+  const float u1 = hi == 0xffffffffu ? 1.0f : __uint2float_rn(hi + 1u) * 0x1p-32f;
+  const float u2 = __uint2float_rn(lo) * 0x1p-32f;
   const float rho = sqrtf(-2.0f * logf(u1));
   float s, c;
   sincospif(2.0f * u2, &s, &c);

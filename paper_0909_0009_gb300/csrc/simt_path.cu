@@ -56,18 +56,18 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
     } else {
       // the FP64 form draws in FP64; the FP32 form through the FP32 Box-Muller of the mixed
       // forms (the FP64 pipe of this part is far too slow for a transcendental per draw)
-      for (int jp = threadIdx.x; jp < (nr + 1) / 2; jp += kThreads) {
+      for (int jq = threadIdx.x; jq < (nr + 3) / 4; jq += kThreads) {
         uint64_t w[4];
-        noise_words(seed, real, idx, jp, w);
-        if (sizeof(T) == sizeof(double)) {
-          ns[2 * jp] = noise_value(box_muller(w[0], w[1]), m);
-          if (2 * jp + 1 < nr) ns[2 * jp + 1] = noise_value(box_muller(w[2], w[3]), m);
-        } else {
-          const float2 g0 = noise_value_f32(box_muller_f32(w[0], w[1]), m);
-          ns[2 * jp] = make_double2(g0.x, g0.y);
-          if (2 * jp + 1 < nr) {
-            const float2 g1 = noise_value_f32(box_muller_f32(w[2], w[3]), m);
-            ns[2 * jp + 1] = make_double2(g1.x, g1.y);
+        noise_words(seed, real, idx, jq, w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * jq + q;
+          if (j >= nr) break;
+          if (sizeof(T) == sizeof(double)) {
+            ns[j] = noise_value(box_muller(w[q]), m);
+          } else {
+            const float2 g = noise_value_f32(box_muller_f32(w[q]), m);
+            ns[j] = make_double2(g.x, g.y);
           }
         }
       }

@@ -138,9 +138,17 @@ def test_generate_on_under_resolved_grids(F, prec, lmax, nr, ntheta, nphi):
     out = c.mx.generate(3, 0, 40.0)
     for k in ("aT", "aE", "aNLT", "aNLE"):
         assert rel_l2(host(out[k]), ref[k]) < nl_bound(prec, nr), (k, rel_l2(host(out[k]), ref[k]))
-    if prec != "fp32":  # the FP32 form sums the cancelling f^2 - mu on the grid (~1e-5 relative)
-        mono = abs(host(out["aNLT"])[0] - ref["aNLT"][0]) / abs(ref["aNLT"][0])
-        assert mono < TARGET, mono
+    if prec != "fp32":  # the FP32 form sums the cancelling f^2 - mu on the grid
+        # the monopole is a difference of two nearly equal sums (the sky mean of Phi_L^2 and
+        # 4 pi mu) and may be far smaller than either: its error is bounded relative to the terms
+        phiL = O.phi_linear(c.K, n)
+        _, m = W.alm_lm(lmax)
+        wgt = np.where(m == 0, 1.0, 2.0)[:, None]
+        qT = O.quadrature_weights(c.r, c.w, c.aT)
+        terms = float(np.dot(np.abs(qT[0]), ((wgt * np.abs(phiL) ** 2).sum(axis=0) + 4 * np.pi * c.mu)
+                             / np.sqrt(4 * np.pi)))
+        mono = abs(host(out["aNLT"])[0] - ref["aNLT"][0])
+        assert mono < 1e-6 * terms, (mono, terms)
     c.mx.device_status()
 
 
