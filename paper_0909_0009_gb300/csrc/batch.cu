@@ -154,18 +154,19 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
 
   // Legendre GEMMs: one tile list over all instances, the tiles of one (instance, problem)
   // adjacent, groups largest first; instance maps for the constant table
-  FNL_CUDA(cudaMallocHost(&b->pinned, sizeof(CUtensorMap) * 4 * (size_t)n));
+  FNL_CUDA(cudaMallocHost(&b->pinned, sizeof(CUtensorMap) * 6 * (size_t)n));
   b->h_maps_syn = (CUtensorMap*)b->pinned;
-  b->h_maps_ana = b->h_maps_syn + 2 * (size_t)n;
+  b->h_maps_ana = b->h_maps_syn + 3 * (size_t)n;
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<TcInst> insts(n);
     std::vector<std::pair<int64_t, std::vector<TcTile>>> groups;
     for (int i = 0; i < n; ++i) {
       const fnl_shells* s = b->run[i];
       insts[i] = s->tci[dir];
-      CUtensorMap* maps = (dir ? b->h_maps_ana : b->h_maps_syn) + 2 * (size_t)i;
+      CUtensorMap* maps = (dir ? b->h_maps_ana : b->h_maps_syn) + 3 * (size_t)i;
       maps[0] = s->tci[dir].tmA;
       maps[1] = s->tci[dir].tmB;
+      maps[2] = s->tci[0].tmF;  // read by the synthesis epilogue only
       const std::vector<TcTile>& tl = dir ? s->tiles_ana_h : s->tiles_syn_h;
       for (size_t k = 0; k < tl.size(); ++k) {
         if (k == 0 || tl[k].mp != tl[k - 1].mp) groups.push_back({0, {}});

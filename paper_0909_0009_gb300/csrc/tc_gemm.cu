@@ -45,7 +45,7 @@ namespace fnl {
 namespace {
 
 // Tensor maps of the instances of a multi-instance launch (see TcArgs::multi).
-__constant__ CUtensorMap c_tc_maps[kTcMaxInst * 2];
+__constant__ CUtensorMap c_tc_maps[kTcMaxInst * 3];
 
 constexpr int kEpiWarps = 12;                // per TMEM lane quadrant kEpiPerQuad warps take turns
 constexpr int kEpiPerQuad = kEpiWarps / 4;  // over a tile's 32-column chunks
@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
       int prev_inst = -1;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const TcTile tl = a.tiles[t];
-        const CUtensorMap* mA = MULTI ? c_tc_maps + 2 * tl.inst : &a.one.tmA;
-        const CUtensorMap* mB = MULTI ? c_tc_maps + 2 * tl.inst + 1 : &a.one.tmB;
+        const CUtensorMap* mA = MULTI ? c_tc_maps + 3 * tl.inst : &a.one.tmA;
+        const CUtensorMap* mB = MULTI ? c_tc_maps + 3 * tl.inst + 1 : &a.one.tmB;
         if (MULTI && tl.inst != prev_inst) {
           // bring this instance's tensor maps into the copy engine's descriptor cache
           asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)mA) : "memory");
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         const TcInst* Ip = a.insts + tl.inst;
         mi.L = Ip->L, mi.nr = Ip->nr;
         if constexpr (MODE == TC_SYNTH) {
-          mi.F = Ip->F, mi.npairs = Ip->npairs, mi.Cpad = Ip->Cpad;
+          mi.npairs = Ip->npairs;
         } else {
           mi.part = Ip->part, mi.q2 = Ip->q2, mi.nalm = Ip->nalm;
         }
@@ -431,12 +431,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[acc]);
         }
-        float* out = I.F + (size_t)tl.mp * I.Cpad + c;
-        const size_t sj = (size_t)2 * (L + 1) * I.Cpad;
-        // one instance: the chunk (32 columns x 16 ring pairs) goes through the warp's 2 KB of
-        // shared memory and out by one tensor store, which keeps the F writes off the load/store
-        // path; several instances: plain stores
+        // the chunk (32 columns x 16 ring pairs) goes through the warp's 2 KB of shared memory
+        // and out by one tensor store, which keeps the F writes off the load/store path
         float* fst = red + (size_t)(warp - 2) * 512;
+        const CUtensorMap* mF = MULTI ? c_tc_maps + 3 * tl.inst + 2 : &a.one.tmF;
         for (int ch = h; ch < nch; ch += kEpiPerQuad) {
           float v[16];
           tmem_ld16(tacc + (uint32_t)(ch * 16), v);
@@ -451,25 +449,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
           }
-          if constexpr (!MULTI) {
-            if (lane == 0) bulk_wait_read();  // the previous chunk's box has left the buffer
-            __syncwarp();
+          if (lane == 0) bulk_wait_read();  // the previous chunk's box has left the buffer
+          __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) fst[j * 32 + lane] = v[j];  // box order: [16 ring pairs][32 c]
-            fence_proxy_async();
-            __syncwarp();
-            // a box that starts past the last ring pair holds no row: not issued (a box that
-            // runs past it is clipped by the copy engine)
-            if (lane == 0 && tl.n0 + ch * 16 < I.npairs) {
-              tma_store_3d(&a.one.tmF, tl.c0 + 32 * q, tl.mp, tl.n0 + ch * 16, smem_u32(fst));
-              bulk_commit();
-            }
-          } else if (cvalid) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int jr = tl.n0 + ch * 16 + j;
-              if (ch * 16 + j < tl.nsize && jr < I.npairs) out[(size_t)jr * sj] = v[j];
-            }
+          for (int j = 0; j < 16; ++j) fst[j * 32 + lane] = v[j];  // box order: [16 ring pairs][32 c]
+          fence_proxy_async();
+          __syncwarp();
+          // a box that starts past the last ring pair holds no row: not issued (a box that
+          // runs past it is clipped by the copy engine)
+          if (lane == 0 && tl.n0 + ch * 16 < I.npairs) {
+            tma_store_3d(mF, tl.c0 + 32 * q, tl.mp, tl.n0 + ch * 16, smem_u32(fst));
+            bulk_commit();
           }
         }
         if (++acc == a.nbuf) {
@@ -627,7 +617,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
     }
   }
 
-  if constexpr (MODE == TC_SYNTH && !MULTI) {
+  if constexpr (MODE == TC_SYNTH) {
     if (warp >= 2 && lane == 0) bulk_wait_all();  // this warp's tensor stores are complete
   }
   tc_fence_before();
@@ -707,7 +697,7 @@ int tc_stages(int nterms, int nmax, int mode) {
 
 void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st) {
   if (n < 1 || n > kTcMaxInst) throw Error(FNL_EINVAL, "too many instances for one tensor-core launch");
-  FNL_CUDA(cudaMemcpyToSymbolAsync(c_tc_maps, host, sizeof(CUtensorMap) * 2 * (size_t)n, 0,
+  FNL_CUDA(cudaMemcpyToSymbolAsync(c_tc_maps, host, sizeof(CUtensorMap) * 3 * (size_t)n, 0,
                                    cudaMemcpyHostToDevice, st));
 }
 

@@ -35,8 +35,8 @@ constexpr int kTcMaxInst = 64;
 struct alignas(128) TcInst {  // CUtensorMap is 128-byte aligned
   CUtensorMap tmA;      // Phi (synthesis) or G (analysis), box {64 c, 64 k, 2 halves, terms}
   CUtensorMap tmB;      // Lambda_syn or Lambda_ana, box {32 k, nmax rows, 2 slabs, terms}
-  CUtensorMap tmF;      // TC_SYNTH, one instance per launch: F as FP32 [npairs][nmp][Cpad], box
-                        // {32 c, 1 problem, 16 ring pairs} for the epilogue's tensor stores
+  CUtensorMap tmF;      // TC_SYNTH: F as FP32 [npairs][nmp][Cpad], box {32 c, 1 problem, 16 ring
+                        // pairs} for the epilogue's tensor stores
   float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
   double2* part;        // TC_ANA_QUAD: [Cpad / 128][nalm][2] ((T re, T im), (E re, E im))
   const float2* q2;     // [L+1][2][nr] q^T, q^E as FP32 pairs (hi, lo)
@@ -46,8 +46,8 @@ struct alignas(128) TcInst {  // CUtensorMap is 128-byte aligned
 
 struct TcArgs {
   TcInst one;           // the single instance (multi == 0), maps and fields in parameter space
-  int multi;            // 1: maps of instance i at c_tc_maps[2 i] (A) and c_tc_maps[2 i + 1] (B),
-                        //    its other fields at insts[i]
+  int multi;            // 1: maps of instance i at c_tc_maps[3 i] (A), c_tc_maps[3 i + 1] (B) and
+                        //    c_tc_maps[3 i + 2] (F), its other fields at insts[i]
   const TcInst* insts;  // device array indexed by TcTile::inst (multi == 1)
   const TcTile* tiles;
   int ntiles;
@@ -73,7 +73,7 @@ int tc_stages(int nterms, int nmax, int mode);
 void launch_tc_gemm(const TcArgs& args, int sms, cudaStream_t st);
 // One bounded mbarrier wait that nothing completes, with `limit` tries (the expiry path).
 void launch_wait_probe(int* err, uint32_t limit, cudaStream_t st);
-// Copy n instances' maps (A and B each) into the constant table, on `st` from pinned
+// Copy n instances' maps (A, B and F each) into the constant table, on `st` from pinned
 // host memory that stays unchanged until the copy has run.
 void upload_tc_maps(const CUtensorMap* host, int n, cudaStream_t st);
 

@@ -8,6 +8,13 @@ For profilers and quick timing of a configuration that is not one of the named w
   python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --ntheta 1537 --nphi 3200 --ksw --reps 3
   python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --nside 512 --prec fp32 --reps 2
   python -m paper_0909_0009_gb300.run_case --lmax 1024 --nr 128 --ntheta 1537 --nphi 3200 --quad 64 --reps 0
+  python -m paper_0909_0009_gb300.run_case --batch --prec bf16x2 --reps 3
+
+`--batch` runs the uneven 64-realisation batch of the batching form (l_max in {128, 256, 512,
+1024}, N_r in {32, 64, 96, 128}): the whole batch as one graph, the batch split by band limit,
+and every distinct configuration as single calls with its stage times. With `--profile-range`
+one graph launch of the whole batch runs between cudaProfilerStart and cudaProfilerStop (for
+`ncu --profile-from-start off`), and nothing else is timed.
 
 Filters are seeded lower-triangular matrices of the covariance's amplitude (the cost of the
 path does not depend on their values); noise is the Philox draw of (seed 1, realisation i).
@@ -23,10 +30,94 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def batch_main(args) -> int:
+    import collections
+
+    import torch
+
+    import workloads as W
+    from paper_0909_0009_gb300 import fnl as F
+
+    F.load_library()
+    insts = W.batch_instances()
+    objs = {}
+    for x in insts:
+        if (x.lmax, x.nr) not in objs:
+            r, w = W.radial_grid(x.nr)
+            aT, aE = W.transfer_kernels(x.lmax, r)
+            K = W.random_lower_filters(x.lmax, x.nr, seed=x.lmax + x.nr, scale=8e-5)
+            sh = F.Shells(x.lmax, x.nr, x.ntheta, x.nphi, r, w, aT, aE, K=K, prec=args.prec)
+            sh.autotune()
+            objs[(x.lmax, x.nr)] = sh
+    st = torch.cuda.current_stream()
+    reps = max(args.reps, 1)
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(n):
+            fn(i)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def run_batch(sub, profile=False):
+        b = F.Batch([objs[(x.lmax, x.nr)] for x in sub])
+        sd, rl, fn = [x.seed for x in sub], [x.realisation for x in sub], [x.fnl for x in sub]
+        out = b.generate(sd, rl, fn)
+        b.generate(sd, rl, fn, out=out)
+        torch.cuda.synchronize()
+        if profile:
+            torch.cuda.profiler.start()
+            b.generate(sd, rl, fn, out=out)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+            t = 0.0
+        else:
+            t = timed(lambda i: b.generate(sd, rl, fn, out=out), reps)
+        tiles = b.tiles()
+        b.close()
+        return t, tiles
+
+    if args.profile_range:
+        run_batch(insts, profile=True)
+        return 0
+    t, tiles = run_batch(insts)
+    print(f"whole batch: {len(insts)} realisations, {t:.3f} ms per graph launch, tiles {tiles}")
+    for lm in sorted({x.lmax for x in insts}):
+        sub = [x for x in insts if x.lmax == lm]
+        t, tiles = run_batch(sub)
+        print(f"  l_max {lm}: {len(sub)} realisations, {t:.3f} ms, tiles {tiles}")
+    count = collections.Counter((x.lmax, x.nr) for x in insts)
+    total = 0.0
+    for (lm, nr), c in sorted(count.items()):
+        sh = objs[(lm, nr)]
+        for i in range(3):
+            sh.generate(1, i, args.fnl, parts=False)
+        n = max(5, min(200, int(2000 / ((lm / 128) ** 3 * nr / 32))))
+        ms = timed(lambda i: sh.generate(1, i, args.fnl, parts=False), n)
+        sh.profile(5)
+        for i in range(5):
+            sh.generate(1, i, args.fnl, parts=False)
+        torch.cuda.synchronize()
+        stg, calls = sh.stage_ms()
+        sh.profile(0)
+        total += c * ms
+        per = {k: round(v / max(calls, 1), 4) for k, v in stg.items()}
+        print(f"  single calls l_max {lm} N_r {nr} (x{c}): {ms:.4f} ms; {per}")
+    print(f"sum of single calls: {total:.3f} ms")
+    for sh in objs.values():
+        sh.close()
+    return 0
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--lmax", type=int, required=True)
-    ap.add_argument("--nr", type=int, required=True)
+    ap.add_argument("--batch", action="store_true", help="the uneven 64-realisation batch (see above)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="with --batch: one graph launch inside a cudaProfilerStart/Stop range, nothing timed")
+    ap.add_argument("--lmax", type=int, default=0)
+    ap.add_argument("--nr", type=int, default=0)
     ap.add_argument("--ntheta", type=int, default=0)
     ap.add_argument("--nphi", type=int, default=0)
     ap.add_argument("--nside", type=int, default=0, help="HEALPix grid of this nside (FP64 / FP32 forms)")
@@ -41,6 +132,10 @@ def main(argv=None) -> int:
     ap.add_argument("--maps", action="store_true",
                     help="also make the Stokes I, Q, U maps of each realisation (fnl_maps) and time them")
     args = ap.parse_args(argv)
+    if args.batch:
+        return batch_main(args)
+    if args.lmax <= 0 or args.nr <= 0:
+        ap.error("--lmax and --nr are required (or --batch)")
 
     import torch
 
