@@ -98,6 +98,26 @@ typedef struct {
  * Gauss-Legendre grid only (FNL_EUNSUPPORTED here). */
 fnl_status fnl_make_shells_healpix(const fnl_shell_desc* desc, int nside, int device, fnl_shells** out);
 
+/* A shell shard of a configuration: the object runs steps (i)-(v) for shells j0 .. j1 - 1 of
+ * `desc` (desc->nr shells in all, 0 <= j0 < j1 <= desc->nr) and for no other, so that the work
+ * of one realisation can be spread over several devices.  The paper keeps the seeds so that
+ * Phi_L can be regenerated at any radius (Sect. 3); here each shard draws, from the same
+ * counter-based generator, the noise of the shells its rows of K_l reach (0 .. j1 - 1), and
+ * K_l, mu, q^X and v^X are those of the whole configuration restricted to the shard's rows.
+ * fnl_generate's outputs are then partial sums: Eq. 5 and Eq. 3 are sums over shells, so
+ * a^X_L, a^X_NL and a^X summed over shards that partition 0 .. nr - 1 equal the whole
+ * configuration's up to the rounding order of those sums.  Per-shell inputs and outputs
+ * (fnl_filter, fnl_synth, fnl_analyse, fnl_square, fnl_accumulate) are the shard's shells, and
+ * an explicit `noise` is [j1][nalm][2] (shells 0 .. j1 - 1 of the configuration).  The
+ * Gauss-Legendre grid and every precision form; fnl_shells_info reports the shard's nr.
+ * fnl_generate_backward and fnl_ksw_create return FNL_EUNSUPPORTED for a shard, and a batch
+ * runs shards in stream mode.  FNL_EINVAL for a range outside 0 <= j0 < j1 <= desc->nr. */
+fnl_status fnl_make_shells_shard(const fnl_shell_desc* desc, int j0, int j1, int device, fnl_shells** out);
+
+/* The shard of an object (any pointer may be NULL): its first shell j0, its shell count nr
+ * and the configuration's nr_total (j0 = 0 and nr = nr_total for fnl_make_shells). */
+fnl_status fnl_shells_shard(const fnl_shells* sh, int* j0, int* nr, int* nr_total);
+
 /* Library version string. */
 const char* fnl_version(void);
 
@@ -131,8 +151,8 @@ fnl_status fnl_shells_mu(const fnl_shells* sh, double* mu_out);
  *      word j & 3, whose two 32-bit halves are the Box-Muller uniforms ((hi + 1) 2^-32 and
  *      lo 2^-32); m > 0 entries get unit complex variance, m = 0 entries are real N(0, 1).
  *  fnl:   f_NL of Eq. 1.
- *  noise: device [nr][nalm][2] explicit n_lm(r_j) (imaginary part of m = 0 ignored), or
- *      NULL to draw it from (seed, realisation).
+ *  noise: device [nr][nalm][2] explicit n_lm(r_j) (imaginary part of m = 0 ignored; a shell
+ *      shard [j0, j1) reads [j1][nalm][2]), or NULL to draw it from (seed, realisation).
  *  aT, aE:     device [nalm][2]: a^X = a^X_L + f_NL a^X_NL (Eq. 3), or NULL.
  *  aLT, aLE:   device [nalm][2]: a^X_L (Eq. 5 applied to Phi_L), or NULL.
  *  aNLT, aNLE: device [nalm][2]: a^X_NL (Eq. 5 applied to Phi_NL), or NULL.
@@ -327,9 +347,9 @@ typedef struct fnl_batch fnl_batch; /* opaque: streams, events and the captured 
  * grid and precision, all on one device; one object may appear several times).  Every
  * instance gets scratch of its own: a repeated object of the tensor-core forms is given
  * scratch clones that share its tables (device memory the batch allocates and frees).
- *  - Multi-instance mode, when every instance is in one tensor-core form, has a ring length
- *    with a specialised ring kernel (800, 1600, 3125, 3200; N_r a multiple of its shell
- *    group) and n <= 64: each stage of the path is one launch over all instances (the ring
+ *  - Multi-instance mode, when every instance is a whole configuration (no shell shard) in
+ *    one tensor-core form, has a ring length with a specialised ring kernel (800, 1600, 3125,
+ *    3200; N_r a multiple of its shell group) and n <= 64: each stage of the path is one launch over all instances (the ring
  *    stage one per ring length present).  The tile shape, common to all instances, is picked
  *    here by timing whole batches, and set on the shells objects (synchronous).
  *  - Stream mode otherwise: instances are dealt, largest first (work ~ (l_max + 1)^3 N_r), to

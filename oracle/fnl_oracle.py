@@ -27,6 +27,10 @@ written from the spin raising and lowering operators (``spin2_functions``); thei
 operators evaluated by finite differences of scipy's Y_lm, the closed form of 2Y_20,
 orthonormality on the grid, the spin-2 analysis round trip, Parseval and the E/B rotation.
 
+A shell shard (``generate_shard``: the recipe's per-shell terms for shells j0 .. j1 - 1) is
+pinned by the sum over a partition of the shells equalling ``generate``, and by its a^X_L
+against the whole configuration's v^X . n restricted to the shard's rows, written out.
+
 The adjoint (``generate_backward`` and the transposes it chains) is the chain rule
 through these steps; its pins are the dot-product test of every transpose against its
 pinned forward map and central finite differences of a loss through ``generate``.
@@ -495,6 +499,29 @@ def generate(K, noise, grid: Grid, r, w, alphaT, alphaE, fnl: float, mu=None, sh
     return out
 
 
+def generate_shard(K, noise, grid: Grid, r, w, alphaT, alphaE, fnl: float, j0: int, j1: int, mu=None):
+    """Shells j0 .. j1 - 1 of the recipe: their Phi_L (rows j0 .. j1 - 1 of Eq. 9, which read
+    the noise of shells 0 .. j1 - 1 only), their Phi_NL (steps (ii)-(iv), shell by shell) and
+    their terms of the radial quadrature (Eq. 5) and of Eq. 3.  noise [nr, nalm] holds every
+    shell of the configuration; mu (default: ``mu_ensemble(K)``) is the configuration's.
+
+    Eq. 5 and Eq. 3 are sums over shells of per-shell terms, so the outputs of shards that
+    partition 0 .. nr - 1 sum to ``generate``'s aLT, aLE, aNLT, aNLE, aT, aE."""
+    sel = np.arange(j0, j1)
+    phiL = phi_linear(K, noise)[:, sel]
+    if mu is None:
+        mu = mu_ensemble(K)
+    qT = quadrature_weights(r, w, alphaT)[:, sel]
+    qE = quadrature_weights(r, w, alphaE)[:, sel]
+    phiNL = phi_nonlinear(phiL, np.asarray(mu)[sel], grid)
+    out = {"phiL": phiL, "phiNL": phiNL,
+           "aLT": radial_quadrature(phiL, qT), "aLE": radial_quadrature(phiL, qE),
+           "aNLT": radial_quadrature(phiNL, qT), "aNLE": radial_quadrature(phiNL, qE)}
+    out["aT"] = out["aLT"] + fnl * out["aNLT"]
+    out["aE"] = out["aLE"] + fnl * out["aNLE"]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Adjoint of the generator (differentiation form): gradients of a real loss L of
 # a^T and a^E with respect to the white noise n and to f_NL.  Complex numbers are
@@ -681,7 +708,7 @@ __all__ = [
     "FOUR_PI", "FLUSH", "gauss_legendre", "lambda_mm", "lambda_column", "lambda_table", "Grid",
     "synthesis", "analysis", "spherical_jn_table", "k_rule", "covariance", "filters",
     "mu_ensemble", "philox4x64", "philox_noise", "phi_linear", "phi_nonlinear",
-    "quadrature_weights", "radial_quadrature", "generate", "synthesis_adjoint", "analysis_adjoint",
+    "quadrature_weights", "radial_quadrature", "generate", "generate_shard", "synthesis_adjoint", "analysis_adjoint",
     "phi_linear_adjoint", "radial_quadrature_adjoint", "generate_backward", "spin2_functions", "maps_iqu",
     "analysis_spin2",
 ]

@@ -5,8 +5,9 @@
 // (i)-(v) (Sect. 2).  Every instance gets scratch of its own: the first instance of a
 // shells object uses the object's, later ones use scratch clones that share its tables.
 //
-// Multi-instance mode (every instance in a tensor-core form with a specialised ring kernel,
-// at most kTcMaxInst of them): each stage is ONE launch over all instances --
+// Multi-instance mode (every instance a whole configuration in a tensor-core form with a
+// specialised ring kernel, at most kTcMaxInst of them): each stage is ONE launch over all
+// instances --
 //   k_filter_multi + k_psum_multi   step (i): blocks are (instance, degree), largest first
 //   k_tc_gemm<true>, synthesis      step (ii) Legendre: one persistent tile list over all
 //                                   instances (instance tensor maps in constant memory)
@@ -368,7 +369,7 @@ fnl_status fnl_batch_create(fnl_shells* const* shells, int n, int nstreams, fnl_
     b->multi = n <= kTcMaxInst;
     for (int i = 0; i < n && b->multi; ++i)
       b->multi = b->run[i]->nterms == b->run[0]->nterms && b->run[i]->tc_split == b->run[0]->tc_split &&
-                 ring_square_group(b->run[i]) > 0;
+                 ring_square_group(b->run[i]) > 0 && b->run[i]->nr == b->run[i]->nr_total;  // shards: streams
     FNL_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
     if (b->multi) {
       b->streams.assign(1, nullptr);

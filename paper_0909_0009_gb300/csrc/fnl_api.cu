@@ -492,6 +492,25 @@ fnl_status fnl_make_shells(const fnl_shell_desc* d, int device, fnl_shells** out
   return st;
 }
 
+fnl_status fnl_make_shells_shard(const fnl_shell_desc* d, int j0, int j1, int device, fnl_shells** out) {
+  return guard([&] {
+    FNL_REQUIRE(out, "out must not be NULL");
+    *out = nullptr;
+    FNL_REQUIRE(d, "desc is NULL");
+    FNL_REQUIRE(j0 >= 0 && j0 < j1 && j1 <= d->nr, "the shard must be a range 0 <= j0 < j1 <= nr");
+    *out = make_shells_core(d, device, false, 0, j0, j1);
+  });
+}
+
+fnl_status fnl_shells_shard(const fnl_shells* sh, int* j0, int* nr, int* nr_total) {
+  return guard([&] {
+    check_shells(sh);
+    if (j0) *j0 = sh->j0;
+    if (nr) *nr = sh->nr;
+    if (nr_total) *nr_total = sh->nr_total;
+  });
+}
+
 fnl_status fnl_make_shells_healpix(const fnl_shell_desc* d, int nside, int device, fnl_shells** out) {
   return guard([&] {
     FNL_REQUIRE(out, "out must not be NULL");
@@ -505,7 +524,7 @@ fnl_status fnl_make_shells_healpix(const fnl_shell_desc* d, int nside, int devic
 
 namespace fnl {
 
-fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_only, int nside) {
+fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_only, int nside, int sj0, int sj1) {
   fnl_shells* sh = nullptr;
   try {
     FNL_REQUIRE(d_in, "desc is NULL");
@@ -517,7 +536,21 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       dd.nphi = 4 * nside;
     }
     const fnl_shell_desc* d = &dd;
-    validate_desc(d, synth_only, nside > 0);
+    const int nr_full = d->nr;
+    const bool shard = sj1 >= 0;
+    if (shard) {
+      // validate the configuration as a whole (its nr is the full shell count), then the range
+      FNL_REQUIRE(!synth_only && !nside, "shell shards are made on the Gauss-Legendre grid");
+      FNL_REQUIRE(d->nr >= 1, "nr must be >= 1");
+      FNL_REQUIRE(sj0 >= 0 && sj0 < sj1 && sj1 <= d->nr, "the shard must be a range 0 <= j0 < j1 <= nr");
+      dd.nr = sj1 - sj0;  // the checks of validate_desc on the shard's own shell count
+      validate_desc(d, false, false);
+      dd.nr = nr_full;
+    } else {
+      validate_desc(d, synth_only, nside > 0);
+      sj0 = 0;
+      sj1 = nr_full;
+    }
     const bool mixed = (d->prec == FNL_BF16X2 || d->prec == FNL_BF16X3);
     int ndev = 0;
     FNL_CUDA(cudaGetDeviceCount(&ndev));
@@ -532,9 +565,13 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
     }
     sh = new fnl_shells;
     sh->device = device;
-    const int L = d->lmax, nr = d->nr;
+    // nr: the object's shells (j0 .. j0 + nr - 1 of the configuration); ncol: the noise shells
+    // their rows of K_l reach
+    const int L = d->lmax, j0 = sj0, nr = sj1 - sj0, ncol = sj1;
     sh->lmax = L;
     sh->nr = nr;
+    sh->j0 = j0;
+    sh->nr_total = nr_full;
     sh->ntheta = d->ntheta;
     sh->nphi = d->nphi;
     sh->prec = d->prec;
@@ -598,49 +635,59 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       sh->wgl.assign(wg.begin(), wg.begin() + np);
     }
 
-    // ---- filters K_l (Eq. 9)
-    const size_t kk = synth_only ? 0 : (size_t)(L + 1) * nr * nr;
-    std::vector<double> Kf(kk);
+    // ---- filters K_l (Eq. 9) of the whole configuration, then the object's rows of them
+    const size_t kk = synth_only ? 0 : (size_t)(L + 1) * nr_full * nr_full;
+    std::vector<double> Kfull(kk);
     if (synth_only) {
       // a synthesis-only object (internal): no filters, mu, q or v
     } else if (d->K) {
       for (int l = 0; l <= L; ++l)
-        for (int i = 0; i < nr; ++i)
-          for (int j = 0; j < nr; ++j)
-            Kf[((size_t)l * nr + i) * nr + j] = (j <= i) ? d->K[((size_t)l * nr + i) * nr + j] : 0.0;
+        for (int i = 0; i < nr_full; ++i)
+          for (int j = 0; j < nr_full; ++j)
+            Kfull[((size_t)l * nr_full + i) * nr_full + j] = (j <= i) ? d->K[((size_t)l * nr_full + i) * nr_full + j] : 0.0;
     } else {
       std::vector<double> Cv(kk);
-      covariance(L, nr, d->r, d->A, d->ns, d->kmin, d->kmax, d->nk, Cv.data());
-      cholesky_filters(L, nr, Cv.data(), d->jitter_rel, Kf.data());
+      covariance(L, nr_full, d->r, d->A, d->ns, d->kmin, d->kmax, d->nk, Cv.data());
+      cholesky_filters(L, nr_full, Cv.data(), d->jitter_rel, Kfull.data());
     }
-    for (size_t i = 0; i < kk; ++i) FNL_REQUIRE(std::isfinite(Kf[i]), "filters contain non-finite values");
+    for (size_t i = 0; i < kk; ++i) FNL_REQUIRE(std::isfinite(Kfull[i]), "filters contain non-finite values");
+    // Kf[l][i][j] = K_l[j0 + i][j], j < ncol: the rows the object computes (all of K_l when whole)
+    std::vector<double> Kf(synth_only ? 0 : (size_t)(L + 1) * nr * ncol);
+    for (int l = 0; l <= (synth_only ? -1 : L); ++l)
+      for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < ncol; ++j)
+          Kf[((size_t)l * nr + i) * ncol + j] = Kfull[((size_t)l * nr_full + j0 + i) * nr_full + j];
 
-    // ---- mu (Eq. 2), q^X and v^X (Eq. 5)
+    // ---- mu (Eq. 2), q^X and v^X (Eq. 5) of the object's shells
     sh->mu.assign(nr, 0.0);
     if (synth_only) {
     } else if (d->mu) {
-      for (int i = 0; i < nr; ++i) sh->mu[i] = d->mu[i];
+      for (int i = 0; i < nr; ++i) sh->mu[i] = d->mu[j0 + i];
     } else {
       for (int l = 0; l <= L; ++l)
         for (int i = 0; i < nr; ++i) {
           double s = 0.0;
-          for (int j = 0; j <= i; ++j) s += Kf[((size_t)l * nr + i) * nr + j] * Kf[((size_t)l * nr + i) * nr + j];
+          for (int j = 0; j <= j0 + i; ++j) s += Kf[((size_t)l * nr + i) * ncol + j] * Kf[((size_t)l * nr + i) * ncol + j];
           sh->mu[i] += (2.0 * l + 1.0) / (4.0 * M_PI) * s;
         }
     }
-    std::vector<double> qT((size_t)(L + 1) * nr), qE((size_t)(L + 1) * nr), vT(qT.size(), 0.0), vE(qE.size(), 0.0);
+    std::vector<double> qT((size_t)(L + 1) * nr), qE((size_t)(L + 1) * nr);
+    std::vector<double> vT((size_t)(L + 1) * ncol, 0.0), vE((size_t)(L + 1) * ncol, 0.0);
     for (int l = 0; l <= L; ++l)
       for (int i = 0; i < nr; ++i) {
-        const double f = d->w[i] * d->r[i] * d->r[i];
-        qT[(size_t)l * nr + i] = f * d->alphaT[(size_t)l * nr + i];
-        qE[(size_t)l * nr + i] = f * d->alphaE[(size_t)l * nr + i];
+        const int g = j0 + i;
+        const double f = d->w[g] * d->r[g] * d->r[g];
+        qT[(size_t)l * nr + i] = f * d->alphaT[(size_t)l * nr_full + g];
+        qE[(size_t)l * nr + i] = f * d->alphaE[(size_t)l * nr_full + g];
       }
+    // v^X_l[j] = sum over the object's rows i of K_l[j0 + i][j] q^X_l[i]: a^X_L = v^X . n is then
+    // the quadrature of the object's shells of Phi_L (Eq. 5), whatever shards it is split into
     for (int l = 0; l <= (synth_only ? -1 : L); ++l)
       for (int i = 0; i < nr; ++i)
-        for (int j = 0; j <= i; ++j) {
-          const double k = Kf[((size_t)l * nr + i) * nr + j];
-          vT[(size_t)l * nr + j] += k * qT[(size_t)l * nr + i];
-          vE[(size_t)l * nr + j] += k * qE[(size_t)l * nr + i];
+        for (int j = 0; j <= j0 + i; ++j) {
+          const double k = Kf[((size_t)l * nr + i) * ncol + j];
+          vT[(size_t)l * ncol + j] += k * qT[(size_t)l * nr + i];
+          vE[(size_t)l * ncol + j] += k * qE[(size_t)l * nr + i];
         }
 
     // ---- FFT plan and twiddles e^{-2 pi i k / nphi}
@@ -704,11 +751,11 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       if (mixed && !synth_only) {
         // the filter kernel's shared-memory image of K_l, transposed and padded, copied as is
         const int nrp = (nr + 7) / 8 * 8;
-        std::vector<float> kft((size_t)(L + 1) * nr * nrp, 0.f);
+        std::vector<float> kft((size_t)(L + 1) * ncol * nrp, 0.f);
         for (int l = 0; l <= L; ++l)
           for (int i = 0; i < nr; ++i)
-            for (int j = 0; j <= i; ++j)
-              kft[((size_t)l * nr + j) * nrp + i] = (float)Kf[((size_t)l * nr + i) * nr + j];
+            for (int j = 0; j <= j0 + i; ++j)
+              kft[((size_t)l * ncol + j) * nrp + i] = (float)Kf[((size_t)l * nr + i) * ncol + j];
         sh->d_Kft = upload(sh, kft);
       }
       sh->d_tw = upload(sh, twf);
@@ -741,10 +788,15 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
     FNL_CUDA(cudaDeviceSynchronize());
     auto hs = std::make_shared<HostSetup>();
     hs->K = std::move(Kf);
-    hs->r.assign(d->r, d->r + nr);
-    hs->w.assign(d->w, d->w + nr);
-    hs->alphaT.assign(d->alphaT, d->alphaT + (size_t)(L + 1) * nr);
-    hs->alphaE.assign(d->alphaE, d->alphaE + (size_t)(L + 1) * nr);
+    hs->r.assign(d->r + j0, d->r + j0 + nr);
+    hs->w.assign(d->w + j0, d->w + j0 + nr);
+    hs->alphaT.resize((size_t)(L + 1) * nr);
+    hs->alphaE.resize((size_t)(L + 1) * nr);
+    for (int l = 0; l <= L; ++l)
+      for (int i = 0; i < nr; ++i) {
+        hs->alphaT[(size_t)l * nr + i] = d->alphaT[(size_t)l * nr_full + j0 + i];
+        hs->alphaE[(size_t)l * nr + i] = d->alphaE[(size_t)l * nr_full + j0 + i];
+      }
     hs->vT = std::move(vT);
     hs->vE = std::move(vE);
     sh->host = hs;
@@ -1000,6 +1052,8 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
     check_shells(sh);
     DeviceScope scope(sh->device);
     if (sh->nside) throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward runs on the Gauss-Legendre grid");
+    if (sh->nr != sh->nr_total)
+      throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward needs a whole configuration, not a shell shard");
     if (sh->nterms && (!sh->d_F2 || sh->owner))
       throw Error(FNL_EUNSUPPORTED, "fnl_generate_backward needs a shells object made by fnl_make_shells");
     check_dev_ptr(noise, "noise", true);

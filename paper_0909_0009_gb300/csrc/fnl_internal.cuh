@@ -125,6 +125,9 @@ struct fnl_shells {
   int device = 0;
   int lmax = 0, nr = 0, ntheta = 0, nphi = 0, prec = 0;
   int npairs = 0, C = 0;
+  // shell shard: the object's nr shells are shells j0 .. j0 + nr - 1 of a configuration of
+  // nr_total shells (j0 = 0 and nr_total = nr for a whole configuration)
+  int j0 = 0, nr_total = 0;
   int64_t nalm = 0;
   bool real_is_double = true;  // SIMT real type: double (FP64) or float (FP32 and mixed)
   size_t device_bytes = 0;
@@ -151,10 +154,11 @@ struct fnl_shells {
   double* d_x = nullptr;           // [npairs]
   double* d_wgl = nullptr;         // [npairs]
   void* d_lam = nullptr;           // SIMT table, real type, [lam_total]
-  void* d_Kf = nullptr;            // [L+1][nr][nr] real type
-  float* d_Kft = nullptr;          // tensor-core forms: [L+1][nr][nrp] FP32, Kt[j][i] = K_l[i][j]
+  void* d_Kf = nullptr;            // [L+1][nr][ncol] real type: row i holds K_l[j0 + i][0 .. ncol),
+                                   // ncol = j0 + nr (the noise shells the object's rows need)
+  float* d_Kft = nullptr;          // tensor-core forms: [L+1][ncol][nrp] FP32, Kt[j][i] = K_l[j0 + i][j]
                                    // (nrp = nr rounded up to 8; zero above the diagonal and in the padding)
-  double* d_vT = nullptr;          // [L+1][nr]  v^X_l = K_l^T q^X_l
+  double* d_vT = nullptr;          // [L+1][ncol]  v^X_l[j] = sum_i K_l[j0 + i][j] q^X_l[i]
   double* d_vE = nullptr;
   double* d_qT = nullptr;          // [L+1][nr]  q^X_l[i] = w_i r_i^2 alpha^X_l(r_i)
   double* d_qE = nullptr;
@@ -277,7 +281,9 @@ void destroy_clone(fnl_shells* c);
 void build_tc_inst_a(fnl_shells* sh);
 // fnl_make_shells; with synth_only, an object without filters (K, mu, q and v zero) of up to
 // 256 fields, used for the synthesis of other fields (the estimator's A and B maps).
-fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only, int nside = 0);
+// j0, j1: the shell shard [j0, j1) of the configuration (j1 < 0: every shell).
+fnl_shells* make_shells_core(const fnl_shell_desc* d, int device, bool synth_only, int nside = 0, int j0 = 0,
+                             int j1 = -1);
 // HEALPix rings (healpix.cu): z, ring length and phi offset of rings 1 .. 4 nside - 1 (north to
 // south); the per-ring-pair tables of the HEALPix ring kernel.
 void healpix_rings(int nside, std::vector<double>& z, std::vector<int>& n, std::vector<double>& phi0);

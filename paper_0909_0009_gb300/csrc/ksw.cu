@@ -370,6 +370,8 @@ fnl_status fnl_ksw_create(const fnl_shells* sh, fnl_ksw** out) {
     check_shells(sh);
     FNL_REQUIRE(!sh->synth_only && !sh->owner && sh->host, "fnl_ksw_create: not on an internal object");
     if (sh->nside) throw Error(FNL_EUNSUPPORTED, "the estimator runs on the Gauss-Legendre grid");
+    if (sh->nr != sh->nr_total)
+      throw Error(FNL_EUNSUPPORTED, "the estimator needs a whole configuration, not a shell shard");
     DeviceScope scope(sh->device);
     const int L = sh->lmax, nr = sh->nr, np = sh->npairs;
     const size_t ts = sh->real_is_double ? 16 : 8;

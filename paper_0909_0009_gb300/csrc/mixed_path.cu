@@ -46,9 +46,11 @@ __device__ __forceinline__ void df_add_square(float& hi, float& lo, float x, flo
 }
 
 // Step (i) as a register-tiled FP32 GEMM per degree l (block per l, largest first):
-//   Phi_l[i][col] = sum_{j <= i} K_l[i][j] n_l[j][col],  col = 2 (m - m0) + {re, im}
-// over chunks of 32 orders m (64 columns).  K_l is staged transposed in shared memory.  K_l is
-// lower triangular, so row tile t (rows 4t .. 4t + 3) needs 4t + 4 terms: each thread owns
+//   Phi_l[i][col] = sum_{j <= j0 + i} K_l[j0 + i][j] n_l[j][col],  col = 2 (m - m0) + {re, im}
+// over chunks of 32 orders m (64 columns), for the object's nr rows, shells j0 .. j0 + nr - 1
+// of its configuration (j0 = 0 unless it is a shell shard), which need the noise of shells
+// 0 .. ncol - 1 (ncol = j0 + nr).  K_l is staged transposed in shared memory.  K_l is lower
+// triangular, so row tile t (rows 4t .. 4t + 3) needs j0 + 4t + 4 terms: each thread owns
 // the 4-row tiles r and nt4 - 1 - r (r = thread row, warp-uniform up to one) times 4 columns,
 // which gives every thread and every warp the same number of multiply-adds.  The noise tile
 // is drawn by all threads (Philox4x64, one call per four shells, + FP32 Box-Muller); a^X_L = v^X_l . n per column
@@ -59,7 +61,8 @@ constexpr int kFCols = 64;
 // that the float4 stores of 8 lanes (consecutive column blocks) hit distinct bank quads.
 __host__ __device__ inline int out_stride(int nrp) { return nrp + 4; }
 
-__device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int nterms, int64_t term_stride,
+__device__ __forceinline__ void filter_body(int l, int L, int nr, int j0, int ncol, int Cpad, int nterms,
+                                            int64_t term_stride,
                                                              const float* __restrict__ Kft,
                                                              const double* __restrict__ vT,
                                                              const double* __restrict__ vE, uint64_t seed,
@@ -70,34 +73,33 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
                                                              double* __restrict__ aLE, double* __restrict__ psum) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nrp = (nr + 7) / 8 * 8;        // rows padded to the 8-row thread tiles
-  float* Kt = (float*)smem;                // [nr][nrp]  Kt[j][i] = K_l[i][j]
+  float* Kt = (float*)smem;                // [ncol][nrp]  Kt[j][i] = K_l[j0 + i][j]
   // output tile [col][i], row stride os (see out_stride)
   const int os = out_stride(nrp);
-  float* nt = Kt + (size_t)nr * nrp;       // [nr][kFCols] noise tile, then [kFCols][os] output tile
-  // [4][nr]: v^T hi, v^E hi, v^T lo, v^E lo; then [2][kFCols][2] partial a^X_L sums (dfp)
-  float* vs = nt + (size_t)max(nr * kFCols, kFCols * os);
-                                                            // then [2][kFCols][2] (dfp below)
-  // K_l arrives transposed and padded (set-up): a straight copy of nr * nrp floats
+  float* nt = Kt + (size_t)ncol * nrp;     // [ncol][kFCols] noise tile, then [kFCols][os] output tile
+  // [4][ncol]: v^T hi, v^E hi, v^T lo, v^E lo; then [2][kFCols][2] partial a^X_L sums (dfp)
+  float* vs = nt + (size_t)max(ncol * kFCols, kFCols * os);
+  // K_l arrives transposed and padded (set-up): a straight copy of ncol * nrp floats
   {
-    const float4* src = (const float4*)(Kft + (size_t)l * nr * nrp);
+    const float4* src = (const float4*)(Kft + (size_t)l * ncol * nrp);
     float4* dst = (float4*)Kt;
-    for (int e = threadIdx.x; e < nr * nrp / 4; e += kThreads) dst[e] = src[e];
+    for (int e = threadIdx.x; e < ncol * nrp / 4; e += kThreads) dst[e] = src[e];
   }
-  for (int e = threadIdx.x; e < nr; e += kThreads) {
-    const double t = vT[(size_t)l * nr + e], u = vE[(size_t)l * nr + e];
+  for (int e = threadIdx.x; e < ncol; e += kThreads) {
+    const double t = vT[(size_t)l * ncol + e], u = vE[(size_t)l * ncol + e];
     vs[e] = (float)t;
-    vs[nr + e] = (float)u;
-    vs[2 * nr + e] = (float)(t - (double)(float)t);
-    vs[3 * nr + e] = (float)(u - (double)(float)u);
+    vs[ncol + e] = (float)u;
+    vs[2 * ncol + e] = (float)(t - (double)(float)t);
+    vs[3 * ncol + e] = (float)(u - (double)(float)u);
   }
   const int64_t nalm = (int64_t)(L + 1) * (L + 2) / 2;
-  const int nquad = (nr + 3) / 4;
+  const int nquad = (ncol + 3) / 4;
   // GEMM: thread row r = tid / 16 owns row tiles ta = r and tb = nt4 - 1 - r, columns 4 cb ..
   const int r4 = threadIdx.x >> 4, cb = threadIdx.x & 15;
   const int nt4 = nrp / 4, ta = r4, tb = nt4 - 1 - r4;
   const bool rows_active = r4 < nt4 / 2;
-  const int ja = min(nr, 4 * ta + 4), jb = min(nr, 4 * tb + 4);
-  float* dfp = vs + 4 * nr;                // [2][kFCols][2]: second halves of the a^X_L sums
+  const int ja = min(ncol, j0 + 4 * ta + 4), jb = min(ncol, j0 + 4 * tb + 4);
+  float* dfp = vs + 4 * ncol;              // [2][kFCols][2]: second halves of the a^X_L sums
   // write-out phase: thread -> shell ws = threadIdx.x % 128, orders mb = threadIdx.x / 128 (+2 ...)
   const int ws = threadIdx.x & 127, wh = threadIdx.x >> 7;
   float ph = 0.f, pl = 0.f;  // sum_m w_m |Phi_L,lm(r_ws)|^2 over this thread's orders (double-float)
@@ -107,7 +109,7 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
     __syncthreads();
     // ---- noise tile n[j][col]
     if (noise) {
-      for (int t = threadIdx.x; t < nr * (kFCols / 2); t += kThreads) {
+      for (int t = threadIdx.x; t < ncol * (kFCols / 2); t += kThreads) {
         const int j = t / (kFCols / 2), mb = t % (kFCols / 2), m = m0 + mb;
         float2 v = make_float2(0.f, 0.f);
         if (mb < nm) {
@@ -125,7 +127,7 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = 4 * jq + q;
-          if (j >= nr) break;
+          if (j >= ncol) break;
           const float2 v = mb < nm ? noise_value_f32(box_muller_f32(w[q]), m) : make_float2(0.f, 0.f);
           *(float2*)(nt + (size_t)j * kFCols + 2 * mb) = v;
         }
@@ -138,10 +140,10 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
     const bool a_active = (acol >> 1) < nm;
     float sh = 0.f, sl = 0.f;
     if (a_active) {
-      const float* vh = vs + af * nr;
-      const float* vl = vs + (2 + af) * nr;
-      const int j0 = ah ? nr / 2 : 0, j1 = ah ? nr : nr / 2;
-      for (int j = j0; j < j1; ++j) {
+      const float* vh = vs + af * ncol;
+      const float* vl = vs + (2 + af) * ncol;
+      const int jlo = ah ? ncol / 2 : 0, jhi = ah ? ncol : ncol / 2;
+      for (int j = jlo; j < jhi; ++j) {
         const float n = nt[(size_t)j * kFCols + acol];
         const float p = vh[j] * n;
         df_add(sh, sl, p, fmaf(vh[j], n, -p) + vl[j] * n);
@@ -237,7 +239,8 @@ __device__ __forceinline__ void filter_body(int l, int L, int nr, int Cpad, int 
 }
 
 // One configuration: block b takes degree l = L - b (largest first).
-__global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int Cpad, int nterms, int64_t term_stride,
+__global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int j0, int Cpad, int nterms,
+                                                             int64_t term_stride,
                                                              const float* __restrict__ Kft,
                                                              const double* __restrict__ vT,
                                                              const double* __restrict__ vE, uint64_t seed,
@@ -246,8 +249,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_gemm(int L, int nr, int 
                                                              __nv_bfloat16* __restrict__ phiT,
                                                              double* __restrict__ phi_api, double* __restrict__ aLT,
                                                              double* __restrict__ aLE, double* __restrict__ psum) {
-  filter_body(L - (int)blockIdx.x, L, nr, Cpad, nterms, term_stride, Kft, vT, vE, seed, real, noise, row32, phiT,
-              phi_api, aLT, aLE, psum);
+  filter_body(L - (int)blockIdx.x, L, nr, j0, j0 + nr, Cpad, nterms, term_stride, Kft, vT, vE, seed, real, noise,
+              row32, phiT, phi_api, aLT, aLE, psum);
 }
 
 // Several instances in one launch: block b takes (instance, degree) = blocks[b] (ordered by
@@ -256,8 +259,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_filter_multi(const FilterInst* 
                                                               const int2* __restrict__ blocks, const MultiKeys keys) {
   const int2 b = blocks[blockIdx.x];
   const FilterInst f = inst[b.x];
-  filter_body(b.y, f.L, f.nr, f.Cpad, f.nterms, f.term_stride, f.Kft, f.vT, f.vE, keys.seed[b.x], keys.real[b.x],
-              nullptr, f.row32, f.phiT, nullptr, f.aLT, f.aLE, f.psum_part);
+  filter_body(b.y, f.L, f.nr, 0, f.nr, f.Cpad, f.nterms, f.term_stride, f.Kft, f.vT, f.vE, keys.seed[b.x],
+              keys.real[b.x], nullptr, f.row32, f.phiT, nullptr, f.aLT, f.aLE, f.psum_part);
 }
 
 // psum[s] = sum over the filter's partials of shell s: strided per-thread sums, then a tree
@@ -461,11 +464,11 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
-  const int nr = sh->nr, nrp = (nr + 7) / 8 * 8;
-  const size_t smem = sizeof(float) * ((size_t)nr * nrp + (size_t)std::max(nr * kFCols, kFCols * out_stride(nrp)) +
-                                      4 * nr + 4 * kFCols);
+  const int nr = sh->nr, nrp = (nr + 7) / 8 * 8, ncol = sh->j0 + nr;
+  const size_t smem = sizeof(float) * ((size_t)ncol * nrp + (size_t)std::max(ncol * kFCols, kFCols * out_stride(nrp)) +
+                                      4 * ncol + 4 * kFCols);
   FNL_CUDA(cudaFuncSetAttribute(k_filter_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->Cpad, sh->nterms, sh->phiT_stride,
+  k_filter_gemm<<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->j0, sh->Cpad, sh->nterms, sh->phiT_stride,
                                                      sh->d_Kft, sh->d_vT, sh->d_vE, seed, real, noise,
                                                      sh->d_row32, (__nv_bfloat16*)sh->d_phiT, phi_api, aLT, aLE,
                                                      psum ? sh->d_psum_part : nullptr);

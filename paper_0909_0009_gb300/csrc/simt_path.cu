@@ -19,9 +19,12 @@ constexpr int kThreads = 256;
 // Step (i): one block per degree l (largest first); K_l and v^X_l staged in shared memory;
 // for every m <= l draw (or read) n_lm(r_j), write Phi_L,lm(r_i) = sum_{j<=i} K_l[i,j] n_j
 // into the internal [rows][C] buffer (and optionally the API layout), and a^X_L,lm = v . n.
+// The object's nr rows are the shells j0 .. j0 + nr - 1 of its configuration (j0 = 0 unless
+// it is a shell shard); they need the noise of shells 0 .. ncol - 1, ncol = j0 + nr, and the
+// staged K_l is [nr][ncol] (row i holds K_l[j0 + i][0 .. ncol)).
 // ---------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __restrict__ Kf,
+__global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, int j0, int ncol, const T* __restrict__ Kf,
                                                      const double* __restrict__ vT,
                                                      const double* __restrict__ vE, uint64_t seed,
                                                      uint64_t real, const double* __restrict__ noise,
@@ -31,24 +34,24 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
   extern __shared__ __align__(16) unsigned char smem[];
   const int l = L - blockIdx.x;
   const int C = 2 * nr;
-  double2* ns = (double2*)smem;                   // [nr] noise of the current (l, m)
-  double* vs = (double*)(ns + nr);                // [2][nr]
-  double* red = vs + 2 * nr;                      // [4][kThreads / 32]
-  T* Ks = (T*)(red + 4 * (kThreads / 32));        // [nr][nr + 1] (padded rows: no bank conflicts)
-  T* nt = Ks + (size_t)nr * (nr + 1);             // [2][nr] the noise in T (re, then im)
-  const int ldk = nr + 1;
-  const T* Kl = Kf + (size_t)l * nr * nr;
-  for (int e = threadIdx.x; e < nr * nr; e += kThreads) Ks[(e / nr) * ldk + (e % nr)] = Kl[e];
-  for (int e = threadIdx.x; e < nr; e += kThreads) {
-    vs[e] = vT[(size_t)l * nr + e];
-    vs[nr + e] = vE[(size_t)l * nr + e];
+  double2* ns = (double2*)smem;                   // [ncol] noise of the current (l, m)
+  double* vs = (double*)(ns + ncol);              // [2][ncol]
+  double* red = vs + 2 * ncol;                    // [4][kThreads / 32]
+  T* Ks = (T*)(red + 4 * (kThreads / 32));        // [nr][ncol + 1] (padded rows: no bank conflicts)
+  T* nt = Ks + (size_t)nr * (ncol + 1);           // [2][ncol] the noise in T (re, then im)
+  const int ldk = ncol + 1;
+  const T* Kl = Kf + (size_t)l * nr * ncol;
+  for (int e = threadIdx.x; e < nr * ncol; e += kThreads) Ks[(e / ncol) * ldk + (e % ncol)] = Kl[e];
+  for (int e = threadIdx.x; e < ncol; e += kThreads) {
+    vs[e] = vT[(size_t)l * ncol + e];
+    vs[ncol + e] = vE[(size_t)l * ncol + e];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int m = 0; m <= l; ++m) {
     const int64_t idx = alm_idx(l, m, L);
     __syncthreads();
     if (noise) {
-      for (int j = threadIdx.x; j < nr; j += kThreads) {
+      for (int j = threadIdx.x; j < ncol; j += kThreads) {
         double2 v = ((const double2*)noise)[(size_t)j * (size_t)(((int64_t)(L + 1) * (L + 2)) / 2) + idx];
         if (m == 0) v.y = 0.0;
         ns[j] = v;
@@ -56,13 +59,13 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
     } else {
       // the FP64 form draws in FP64; the FP32 form through the FP32 Box-Muller of the mixed
       // forms (the FP64 pipe of this part is far too slow for a transcendental per draw)
-      for (int jq = threadIdx.x; jq < (nr + 3) / 4; jq += kThreads) {
+      for (int jq = threadIdx.x; jq < (ncol + 3) / 4; jq += kThreads) {
         uint64_t w[4];
         noise_words(seed, real, idx, jq, w);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = 4 * jq + q;
-          if (j >= nr) break;
+          if (j >= ncol) break;
           if (sizeof(T) == sizeof(double)) {
             ns[j] = noise_value(box_muller(w[q]), m);
           } else {
@@ -73,18 +76,18 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
       }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < nr; j += kThreads) {
+    for (int j = threadIdx.x; j < ncol; j += kThreads) {
       nt[j] = (T)ns[j].x;
-      nt[nr + j] = (T)ns[j].y;
+      nt[ncol + j] = (T)ns[j].y;
     }
     // a^X_L = sum_j v^X_l[j] n_j  (FP64)
     double tr = 0.0, ti = 0.0, er = 0.0, ei = 0.0;
-    for (int j = threadIdx.x; j < nr; j += kThreads) {
+    for (int j = threadIdx.x; j < ncol; j += kThreads) {
       const double2 n = ns[j];
       tr += vs[j] * n.x;
       ti += vs[j] * n.y;
-      er += vs[nr + j] * n.x;
-      ei += vs[nr + j] * n.y;
+      er += vs[ncol + j] * n.x;
+      ei += vs[ncol + j] * n.y;
     }
     for (int o = 16; o; o >>= 1) {
       tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -99,15 +102,15 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, const T* __r
       red[24 + warp] = ei;
     }
     __syncthreads();  // nt complete
-    // Phi_L,lm(r_i) = sum_{j <= i} K_l[i, j] n_j
+    // Phi_L,lm(r_i) = sum_{j <= j0 + i} K_l[j0 + i, j] n_j
     const int p = (l - m) & 1;
     const int64_t row = row0[2 * m + p] + ((l - m) >> 1);
     for (int c = threadIdx.x; c < C; c += kThreads) {
       const int i = c >> 1, r = c & 1;
       T acc = 0;
       const T* Ki = Ks + (size_t)i * ldk;
-      const T* nj = nt + (r ? nr : 0);
-      for (int j = 0; j <= i; ++j) acc += Ki[j] * nj[j];
+      const T* nj = nt + (r ? ncol : 0);
+      for (int j = 0; j <= j0 + i; ++j) acc += Ki[j] * nj[j];
       phi[row * C + c] = acc;
       if (phi_api) phi_api[((size_t)idx * nr + i) * 2 + r] = (double)acc;
     }
@@ -367,12 +370,13 @@ __global__ void k_phi_to_alm(int L, int nr, int64_t nalm, const int64_t* __restr
 template <typename T>
 void filter_impl(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                  double* aLE, double* phi_api, cudaStream_t st) {
-  const int nr = sh->nr;
-  const size_t smem = sizeof(double2) * nr + sizeof(double) * 2 * nr + sizeof(double) * 4 * (kThreads / 32) +
-                      sizeof(T) * (size_t)nr * (nr + 1) + sizeof(T) * 2 * (size_t)nr;
+  const int nr = sh->nr, ncol = sh->j0 + sh->nr;
+  const size_t smem = sizeof(double2) * ncol + sizeof(double) * 2 * ncol + sizeof(double) * 4 * (kThreads / 32) +
+                      sizeof(T) * (size_t)nr * (ncol + 1) + sizeof(T) * 2 * (size_t)ncol;
   FNL_CUDA(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, (const T*)sh->d_Kf, sh->d_vT, sh->d_vE, seed,
-                                                    real, noise, sh->d_row0, (T*)sh->d_phi, phi_api, aLT, aLE);
+  k_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->j0, ncol, (const T*)sh->d_Kf, sh->d_vT,
+                                                    sh->d_vE, seed, real, noise, sh->d_row0, (T*)sh->d_phi,
+                                                    phi_api, aLT, aLE);
   FNL_CUDA(cudaGetLastError());
 }
 

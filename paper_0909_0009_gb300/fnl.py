@@ -31,7 +31,7 @@ EXPORTS = [
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
     "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
     "fnl_make_shells_healpix", "fnl_shells_set_sm_limits", "fnl_test_fail_alloc", "fnl_test_wait_expiry",
-    "fnl_measure_fma_peaks",
+    "fnl_measure_fma_peaks", "fnl_make_shells_shard", "fnl_shells_shard",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_quad_fit.argtypes = [vp, i, ctypes.POINTER(i), dp, dp]
     lib.fnl_make_shells_healpix.argtypes = [ctypes.POINTER(ShellDesc), i, i, ctypes.POINTER(vp)]
     lib.fnl_shells_set_sm_limits.argtypes = [vp, i, i]
+    lib.fnl_make_shells_shard.argtypes = [ctypes.POINTER(ShellDesc), i, i, i, ctypes.POINTER(vp)]
+    lib.fnl_shells_shard.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy",
                         "fnl_quad_destroy"):
@@ -202,10 +204,12 @@ class Shells:
     """Device tables and scratch for one configuration (wraps fnl_make_shells)."""
 
     def __init__(self, lmax, nr, ntheta, nphi, r, w, alphaT, alphaE, K=None, cov: Cov | None = None,
-                 mu=None, prec="fp64", device=0, nside: int | None = None):
+                 mu=None, prec="fp64", device=0, nside: int | None = None, shard: tuple | None = None):
         """Gauss-Legendre ring grid of ntheta x nphi; or, with nside, the HEALPix grid of
         12 nside^2 pixels (fnl_make_shells_healpix; ntheta and nphi are then ignored and maps are
-        [nr][npix] in RING order)."""
+        [nr][npix] in RING order).  With shard = (j0, j1) the object is the shell shard
+        [j0, j1) of the nr-shell configuration described (fnl_make_shells_shard): its per-shell
+        arrays have j1 - j0 shells and fnl_generate returns its partial sums."""
         lib = load_library()
         if nside:
             ntheta, nphi = 4 * nside - 1, 4 * nside
@@ -229,13 +233,19 @@ class Shells:
         d.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         h = ctypes.c_void_p()
         if nside:
+            assert shard is None, "shell shards are made on the Gauss-Legendre grid"
             _check(lib.fnl_make_shells_healpix(ctypes.byref(d), int(nside), device, ctypes.byref(h)))
+        elif shard is not None:
+            _check(lib.fnl_make_shells_shard(ctypes.byref(d), int(shard[0]), int(shard[1]), device,
+                                             ctypes.byref(h)))
         else:
             _check(lib.fnl_make_shells(ctypes.byref(d), device, ctypes.byref(h)))
         self.nside = nside or 0
         self.npix = 12 * nside * nside if nside else ntheta * nphi
         self._keep = []
         self.handle = h
+        self.j0, self.nr_total = (int(shard[0]), nr) if shard is not None else (0, nr)
+        nr = int(shard[1]) - int(shard[0]) if shard is not None else nr
         self.lmax, self.nr, self.ntheta, self.nphi = lmax, nr, ntheta, nphi
         self.nalm = (lmax + 1) * (lmax + 2) // 2
         self.device = device
@@ -319,8 +329,9 @@ class Shells:
         if out is None:
             out = {k: self._alm() for k in names}
         ptrs = [_ptr(out.get(k)) for k in ["aT", "aE", "aLT", "aLE", "aNLT", "aNLE"]]
-        if noise is not None:
-            assert noise.dtype == _torch().complex128 and noise.is_contiguous() and noise.shape == (self.nr, self.nalm)
+        if noise is not None:  # shells 0 .. j0 + nr - 1 of the configuration
+            assert (noise.dtype == _torch().complex128 and noise.is_contiguous()
+                    and noise.shape == (self.j0 + self.nr, self.nalm))
         _check(_lib.fnl_generate(self.handle, seed, realisation, float(fnl), _ptr(noise), *ptrs, _stream(stream)))
         return out
 

@@ -408,6 +408,47 @@ def test_fnl0_linear_part_is_the_filtered_noise_projection():
     assert np.max(np.abs(out["aLT"] - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("parts", [[(0, 6)], [(0, 3), (3, 6)], [(0, 1), (1, 4), (4, 5), (5, 6)]])
+def test_shell_shards_sum_to_the_whole_recipe(parts):
+    # Eq. 5 and Eq. 3 sum per-shell terms: shards partitioning the shells add up to the recipe
+    r, w, aT, aE, K, g = _small_setup()
+    n = O.philox_noise(12, 6, seed=7, realisation=1)
+    whole = O.generate(K, n, g, r, w, aT, aE, 25.0)
+    acc = {k: 0.0 for k in ("aT", "aE", "aLT", "aLE", "aNLT", "aNLE")}
+    for j0, j1 in parts:
+        sh = O.generate_shard(K, n, g, r, w, aT, aE, 25.0, j0, j1)
+        assert sh["phiL"].shape[1] == j1 - j0
+        for k in acc:
+            acc[k] = acc[k] + sh[k]
+    for k in acc:
+        assert np.max(np.abs(acc[k] - whole[k])) < 1e-12 * np.max(np.abs(whole[k])), k
+    # the per-shell fields of a shard are the whole recipe's columns
+    sh = O.generate_shard(K, n, g, r, w, aT, aE, 25.0, 2, 5)
+    assert np.max(np.abs(sh["phiNL"] - whole["phiNL"][:, 2:5])) < 1e-12 * np.max(np.abs(whole["phiNL"]))
+
+
+def test_shard_reads_the_noise_of_its_rows_only():
+    # rows j0 .. j1 - 1 of the lower-triangular K_l reach the noise of shells < j1: a shard's
+    # output does not change when the noise of later shells does, and its a^X_L is v' . n with
+    # v'_l = K_l[j0:j1]^T q_l[j0:j1], written out here
+    r, w, aT, aE, K, g = _small_setup()
+    n = O.philox_noise(12, 6, seed=9, realisation=0)
+    j0, j1 = 2, 4
+    a = O.generate_shard(K, n, g, r, w, aT, aE, 10.0, j0, j1)
+    n2 = n.copy()
+    n2[j1:] = 1e3 * (1 + 1j)
+    b = O.generate_shard(K, n2, g, r, w, aT, aE, 10.0, j0, j1)
+    for k in ("aT", "aE", "aLT", "aNLE"):
+        assert np.array_equal(a[k], b[k]), k
+    q = O.quadrature_weights(r, w, aE)
+    l, m = W.alm_lm(12)
+    nn = n.copy()
+    nn[:, m == 0] = nn[:, m == 0].real
+    v = np.einsum("lij,li->lj", K[:, j0:j1, :], q[:, j0:j1])
+    ref = np.einsum("ij,ji->i", v[l], nn)
+    assert np.max(np.abs(a["aLE"] - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
 # ---------------------------------------------------------------------------
 # Planted mistakes: each must be caught by a pin above
 # ---------------------------------------------------------------------------
