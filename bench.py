@@ -301,6 +301,38 @@ def measure_batch(F, prec: str, device: int, reps: int = 3) -> dict:
     return d
 
 
+def measure_sharded(F, wl, r, w, aT, aE, K, prec: str, device: int, steps: int, fnl: float, dist) -> dict:
+    """Shell-sharded mode over all ranks (N > 1): each rank holds the shard of its shell range
+    (fnl_make_shells_shard) and every step is ONE realisation of the workload, its partial
+    outputs summed by one all-reduce (paper_0909_0009_gb300.sharded).  Strong scaling: the
+    work per step is fixed as N grows.  Timed with CUDA events between barriers, max over ranks."""
+    import torch
+
+    from paper_0909_0009_gb300 import sharded
+    drv = sharded.ShardedShells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=prec, device=device)
+    if drv.shells is not None and prec in ("bf16x2", "bf16x3"):
+        drv.shells.autotune()
+    buf = torch.empty((2, drv.nalm), dtype=torch.complex128, device=f"cuda:{device}")
+    for i in range(3):
+        drv.generate(1, 20_000 + i, fnl, parts=False, buf=buf)
+    dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        drv.generate(1, i, fnl, parts=False, buf=buf)
+    e1.record(stream)
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, f"cuda:{device}")
+    out = {"value": steps / (ms / 1e3), "unit": UNIT, "scaling": "strong", "steps": steps,
+           "ms_per_realisation": ms / steps, "shell_range_rank0": list(drv.range),
+           "collective": "one all-reduce (sum) of a^T, a^E per realisation (2 x n_alm complex128)"}
+    drv.close()
+    return out
+
+
 def measure_adjoint(F, device: int, reps: int = 3) -> dict:
     """Differentiation form at l_max = 512, N_r = 96 (769 x 1600): fnl_generate and
     fnl_generate_backward (dL/dn and dL/df_NL, maps recomputed) in FP64, FP32 and bf16x2 (the
@@ -493,6 +525,8 @@ def main():
     ap.add_argument("--no-ksw", action="store_true", help="skip the cubic-estimator measurement")
     ap.add_argument("--no-quad", action="store_true", help="skip the optimal-quadrature measurement")
     ap.add_argument("--no-healpix", action="store_true", help="skip the HEALPix-grid measurement")
+    ap.add_argument("--no-sharded", action="store_true",
+                    help="with N > 1: skip the shell-sharded measurement (one realisation over all ranks)")
     ap.add_argument("--tiles", default="auto",
                     help="tensor-core tile widths 'synthesis,analysis' (default: picked by fnl_shells_autotune)")
     args = ap.parse_args()
@@ -605,6 +639,10 @@ def main():
         d64.close()
         del d64, out64, ref, b
 
+    # shell-sharded mode (N > 1, every rank takes part): one realisation spread over the ranks
+    sharded = (None if world == 1 or args.no_sharded
+               else measure_sharded(F, wl, r, w, aT, aE, K, args.prec, local, min(args.steps, 50), fnl, dist))
+
     # the secondary measurements run once, on rank 0 (the other ranks wait at the final barrier)
     lead = rank == 0
     maps = None if args.no_maps or not lead else measure_maps(F, sh, out, local)
@@ -693,6 +731,8 @@ def main():
                       "how": "fnl_measure_fma_peaks: 8 independent FMA chains per thread, 8 blocks of 256 per SM, "
                              "median of 5 launches of ~10 ms, CUDA events"},
     }
+    if sharded is not None:
+        line["sharded"] = sharded
     if batch is not None:
         line["batch"] = batch
     if adjoint is not None:
