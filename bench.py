@@ -333,6 +333,55 @@ def measure_sharded(F, wl, r, w, aT, aE, K, prec: str, device: int, steps: int, 
     return out
 
 
+def measure_pipelined(F, sh, wl, r, w, aT, aE, K, prec: str, tiles, device: int, fnl: float, steps: int = 100) -> dict:
+    """Two realisations in flight: the timed object and a second one of the same configuration
+    (its own scratch) on two streams, realisations alternating between them, with and without
+    the persistent GEMMs capped at half the SMs (fnl_shells_set_sm_limits).  Per-stream stage
+    times from each object's stage events.  Against the serial loop of the headline."""
+    import torch
+    sh2 = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec=prec, device=device)
+    if prec in ("bf16x2", "bf16x3"):
+        sh2.set_tiles(*tiles)
+    objs = [sh, sh2]
+    outs = [{k: o._alm() for k in ("aT", "aE")} for o in objs]
+    streams = [torch.cuda.Stream(device), torch.cuda.Stream(device)]
+    res = {}
+    for name, lim in (("two_streams", (0, 0)), ("two_streams_gemm_half_sms", (76, 0))):
+        for o in objs:
+            o.set_sm_limits(*lim)
+        for k in range(2):
+            objs[k].generate(1, 30_000 + k, fnl, parts=False, out=outs[k], stream=streams[k])
+        torch.cuda.synchronize()
+        for o in objs:
+            o.profile(slots=steps)
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(torch.cuda.current_stream())
+        for st in streams:
+            st.wait_event(start)
+        for i in range(steps // 2):
+            for k in range(2):
+                objs[k].generate(1, 2 * i + k, fnl, parts=False, out=outs[k], stream=streams[k])
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for k in range(2):
+            ends[k].record(streams[k])
+        torch.cuda.synchronize()
+        ms = max(start.elapsed_time(e) for e in ends)
+        per_stream = []
+        for o in objs:
+            stg, calls = o.stage_ms()
+            o.profile(0)
+            per_stream.append({k: round(v / max(calls, 1), 4) for k, v in stg.items()})
+        for o in objs:
+            o.set_sm_limits(0, 0)
+        res[name] = {"value": (steps // 2) * 2 / (ms / 1e3), "unit": UNIT, "sm_limits": list(lim),
+                     "stage_ms_per_stream": per_stream}
+    sh2.close()
+    res["note"] = ("two shells objects on two streams, realisations alternating; the kernels of the two "
+                   "streams overlap only where one leaves SMs idle (every stage fills all SMs and scales "
+                   "with 1 / SMs), so the serial loop is as fast")
+    return res
+
+
 def measure_adjoint(F, device: int, reps: int = 3) -> dict:
     """Differentiation form at l_max = 512, N_r = 96 (769 x 1600): fnl_generate and
     fnl_generate_backward (dL/dn and dL/df_NL, maps recomputed) in FP64, FP32 and bf16x2 (the
@@ -525,6 +574,8 @@ def main():
     ap.add_argument("--no-ksw", action="store_true", help="skip the cubic-estimator measurement")
     ap.add_argument("--no-quad", action="store_true", help="skip the optimal-quadrature measurement")
     ap.add_argument("--no-healpix", action="store_true", help="skip the HEALPix-grid measurement")
+    ap.add_argument("--no-pipelined", action="store_true",
+                    help="skip the two-stream measurement (two realisations in flight)")
     ap.add_argument("--no-sharded", action="store_true",
                     help="with N > 1: skip the shell-sharded measurement (one realisation over all ranks)")
     ap.add_argument("--tiles", default="auto",
@@ -652,6 +703,8 @@ def main():
     batch = (None if args.no_batch or not lead or args.prec not in ("bf16x2", "bf16x3")
              else measure_batch(F, args.prec, local))
     adjoint = None if args.no_adjoint or not lead else measure_adjoint(F, local)
+    pipelined = (None if args.no_pipelined or not lead or args.prec not in ("bf16x2", "bf16x3")
+                 else measure_pipelined(F, sh, wl, r, w, aT, aE, K, args.prec, tiles, local, fnl))
 
     if rank != 0:
         if world > 1:
@@ -733,6 +786,8 @@ def main():
     }
     if sharded is not None:
         line["sharded"] = sharded
+    if pipelined is not None:
+        line["pipelined"] = pipelined
     if batch is not None:
         line["batch"] = batch
     if adjoint is not None:
