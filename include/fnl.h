@@ -68,7 +68,7 @@ typedef enum {
 /* Description of one configuration (host memory; read during fnl_make_shells only). */
 typedef struct {
   int lmax;    /* band limit, 1 <= lmax <= 4096 */
-  int nr;      /* number of radial shells, 1 <= nr <= 128 (mixed precisions: nr % 8 == 0) */
+  int nr;      /* number of radial shells, 1 <= nr <= 128 */
   int ntheta;  /* Gauss-Legendre rings, ntheta >= lmax + 1 (exact square needs (3 lmax + 2) / 2) */
   int nphi;    /* points per ring, 2/3/5-smooth, nphi >= 2 lmax + 2 (exact square needs 3 lmax + 1) */
   const double* r;      /* host [nr]: radial nodes r_i (Mpc) */

@@ -166,14 +166,17 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
   FNL_CUDA(cudaMemset(sh->d_GT, 0, sizeof(bf16_t) * (size_t)T * sh->gt_stride));
   FNL_CUDA(cudaMemset(sh->d_F, 0, sizeof(float) * (size_t)nmp * np * Cpad));
   FNL_CUDA(cudaMemset(sh->d_err, 0, sizeof(int)));
-  // q^T, q^E of the quadrature epilogue as FP32 pairs hi + lo (48 significant bits), [l][X][i]
-  std::vector<float> q2(4 * qT.size());
+  // q^T, q^E of the quadrature epilogue as FP32 pairs hi + lo (48 significant bits), [l][X][i],
+  // rows of an even number of shells (zero-padded) so that the epilogue's 16-byte loads of two
+  // shells stay aligned
+  const int nre = (nr + 1) & ~1;
+  std::vector<float> q2((size_t)(L + 1) * 2 * nre * 2, 0.f);
   for (int l = 0; l <= L; ++l)
     for (int X = 0; X < 2; ++X)
       for (int i = 0; i < nr; ++i) {
         const double v = (X ? qE : qT)[(size_t)l * nr + i];
         const float hi = (float)v;
-        const size_t o = (((size_t)l * 2 + X) * nr + i) * 2;
+        const size_t o = (((size_t)l * 2 + X) * nre + i) * 2;
         q2[o] = hi;
         q2[o + 1] = (float)(v - (double)hi);
       }

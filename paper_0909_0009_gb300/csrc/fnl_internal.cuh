@@ -202,7 +202,7 @@ struct fnl_shells {
   void* d_sqtw1 = nullptr;
   int64_t gt_stride = 0;
   void* d_part = nullptr;          // double2 [Cpad / 128][nalm][2]: quadrature partials per column tile
-  float2* d_q2 = nullptr;          // [L+1][2][nr]  q^T, q^E as FP32 pairs (hi, lo)
+  float2* d_q2 = nullptr;          // [L+1][2][nre]  q^T, q^E as FP32 pairs (hi, lo), nre = nr rounded up to even
   void* d_F2 = nullptr;            // adjoint: the spectra of s, float as d_F (owner objects only)
   double* d_adjA = nullptr;        // adjoint: analysis of 2 f s per shell, [nalm][nr][2]
   CUtensorMap tmF2{};              // adjoint: tensor map of d_F2 for the synthesis's tensor stores

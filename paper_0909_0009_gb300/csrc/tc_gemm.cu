@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
             const int k = tl.n0 + jj;
             const bool dvalid = jj < tl.nsize && k < tl.kvalid;
             const float4* qrow =
-                (const float4*)(I.q2 + ((size_t)(m + p + 2 * (dvalid ? k : 0)) * 2 + f) * nr + s0 + 8 * b);
+                (const float4*)(I.q2 + ((size_t)(m + p + 2 * (dvalid ? k : 0)) * 2 + f) * ((nr + 1) & ~1) + s0 + 8 * b);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
               qq[sb][e] = (dvalid && s0 + 8 * b + 2 * e < nr) ? qrow[e] : make_float4(0.f, 0.f, 0.f, 0.f);

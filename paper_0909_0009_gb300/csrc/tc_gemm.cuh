@@ -39,7 +39,7 @@ struct alignas(128) TcInst {  // CUtensorMap is 128-byte aligned
                         // pairs} for the epilogue's tensor stores
   float* F;             // TC_SYNTH: [npairs][nmp][Cpad] (ring-pair-major)
   double2* part;        // TC_ANA_QUAD: [Cpad / 128][nalm][2] ((T re, T im), (E re, E im))
-  const float2* q2;     // [L+1][2][nr] q^T, q^E as FP32 pairs (hi, lo)
+  const float2* q2;     // [L+1][2][nre] q^T, q^E as FP32 pairs (hi, lo), nre = nr rounded up to even
   int L, nr, npairs, Cpad;
   int64_t nalm;
 };

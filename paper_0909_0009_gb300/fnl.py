@@ -317,9 +317,10 @@ class Shells:
         _check(_lib.fnl_shells_set_tiles(self.handle, int(syn_cap), int(ana_cap)))
 
     # -- tensors
-    def _alm(self, n=1):
+    def _alm(self, n=None):
+        """complex128 [nalm] (n None) or [nalm, n] on the object's device."""
         torch = _torch()
-        return torch.empty((self.nalm,) if n == 1 else (self.nalm, n), dtype=torch.complex128,
+        return torch.empty((self.nalm,) if n is None else (self.nalm, n), dtype=torch.complex128,
                            device=f"cuda:{self.device}")
 
     def generate(self, seed: int, realisation: int, fnl: float, noise=None, parts: bool = True,

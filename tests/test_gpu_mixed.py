@@ -101,6 +101,30 @@ def test_ring_square_specialised_sizes(F, prec, lmax, nr, ntheta, nphi):
 
 
 @pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
+@pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(1, 1, 2, 4), (1, 3, 3, 6), (2, 5, 4, 8), (5, 7, 9, 16),
+                                                  (9, 13, 15, 30), (17, 6, 27, 54)])
+def test_edge_configurations(F, prec, lmax, nr, ntheta, nphi):
+    """The smallest band limits and grids, one shell and shell counts that fill no shell group
+    or 128-column tile (odd, below 8): the square per shell within the stage bound, and whole
+    realisations against the FP64 path (a^X_L within 1e-6; a^X_NL for the three-term split
+    within the 1e-5 bar, and for the two-term split within the per-shell stage bound, since a
+    handful of shells averages nothing)."""
+    c = Pair(F, lmax, nr, ntheta, nphi, prec)
+    phiL = O.phi_linear(c.K, O.philox_noise(lmax, nr, 3, 1))
+    got = host(c.mx.square(cuda(phiL)))
+    assert rel_l2(got, O.phi_nonlinear(phiL, c.mu, c.grid)) < 3 * STAGE_BOUND[prec]
+    nl = TARGET if prec == "bf16x3" else 3 * STAGE_BOUND[prec]
+    for seed, fnl in ((1, 30.0), (4, 0.0)):
+        a = c.mx.generate(seed, 0, fnl)
+        b = c.d64.generate(seed, 0, fnl)
+        for k in ("aLT", "aLE"):
+            assert rel_l2(host(a[k]), host(b[k])) < 1e-6, k
+        for k in ("aNLT", "aNLE"):
+            assert rel_l2(host(a[k]), host(b[k])) < nl, (k, rel_l2(host(a[k]), host(b[k])))
+    c.mx.device_status()
+
+
+@pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
 def test_filter_matches_oracle(F, prec):
     c = Pair(F, 64, 32, 97, 200, prec)
     phi = host(c.mx.filter(seed=7, realisation=2))
