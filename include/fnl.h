@@ -252,7 +252,8 @@ typedef struct fnl_ksw fnl_ksw; /* opaque: weights, normalisation, a synthesis o
  * N is summed here in FP64 over all l1 <= l2 <= l3 (synchronous; a fraction of a second at
  * l_max 1024).  Needs 3 n_phi complex values of the object's real type in shared memory
  * (FNL_EINVAL above 227 KB).  Allocates device memory (a second set of synthesis scratch for
- * 2 nr fields); `sh` must outlive the estimator. */
+ * 2 nr fields); `sh` must outlive the estimator.  FNL_EUNSUPPORTED for a shell shard and, in the
+ * tensor-core forms, for an odd shell count. */
 fnl_status fnl_ksw_create(const fnl_shells* sh, fnl_ksw** out);
 void fnl_ksw_destroy(fnl_ksw* k);
 

@@ -372,6 +372,9 @@ fnl_status fnl_ksw_create(const fnl_shells* sh, fnl_ksw** out) {
     if (sh->nside) throw Error(FNL_EUNSUPPORTED, "the estimator runs on the Gauss-Legendre grid");
     if (sh->nr != sh->nr_total)
       throw Error(FNL_EUNSUPPORTED, "the estimator needs a whole configuration, not a shell shard");
+    // the tensor-core coefficient kernel takes the shells of a field two at a time
+    if (sh->nterms && sh->nr % 2)
+      throw Error(FNL_EUNSUPPORTED, "the estimator of the tensor-core forms needs an even shell count");
     DeviceScope scope(sh->device);
     const int L = sh->lmax, nr = sh->nr, np = sh->npairs;
     const size_t ts = sh->real_is_double ? 16 : 8;

@@ -103,7 +103,8 @@ def test_grad_fnl_with_and_without_forward_parts(small):
 
 
 @pytest.mark.parametrize("prec,bar", [("bf16x2", 1e-5), ("bf16x3", 1e-6)])
-@pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(32, 16, 49, 100), (256, 64, 385, 800)])
+@pytest.mark.parametrize("lmax,nr,ntheta,nphi", [(32, 16, 49, 100), (256, 64, 385, 800), (9, 5, 15, 30),
+                                                  (17, 7, 27, 54)])
 def test_backward_tensor_core_forms(F, prec, bar, lmax, nr, ntheta, nphi):
     """The adjoint of the tensor-core forms (both syntheses and the analysis as tcgen05 GEMMs on
     BF16-split operands, FP32 ring product and K_l^T) against the oracle's FP64 chain rule.

@@ -75,6 +75,17 @@ def test_fp64_statistic_and_norm_match_oracle(F, L, nr, nt, nph, independent):
         assert abs(k.norm - nref) < 1e-12 * nref, (k.norm, nref)
 
 
+def test_odd_shell_count_of_the_tensor_core_forms_is_refused(F):
+    # the tensor-core coefficient kernel takes a field's shells two at a time; the SIMT forms
+    # take any count (the FP64 cases above include 3 and 5 shells)
+    r, w, aT, aE, K = kernels(24, 5, False)
+    sh = F.Shells(24, 5, 37, 75, r, w, aT, aE, K=K, prec="bf16x2")
+    with pytest.raises(F.FnlError) as e:
+        F.Ksw(sh)
+    assert e.value.code == 4 and "even" in str(e.value)
+    sh.close()
+
+
 def test_band_limit_one_has_no_estimator(F):
     sh, k, wts = setup(F, 1, 2, 3, 6, "fp64", False)
     aT, aE = sky(1, seed=1)

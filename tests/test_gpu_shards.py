@@ -43,7 +43,7 @@ def _host(out):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x2", "bf16x3"])
-@pytest.mark.parametrize("parts", [[(0, 16), (16, 32)], [(0, 8), (8, 24), (24, 32)]])
+@pytest.mark.parametrize("parts", [[(0, 16), (16, 32)], [(0, 8), (8, 24), (24, 32)], [(0, 5), (5, 18), (18, 32)]])
 def test_shards_sum_to_the_whole_configuration(F, prec, parts):
     r, w, aT, aE, K = _inputs()
     whole = F.Shells(LMAX, NR, NT, NP, r, w, aT, aE, K=K, prec=prec)
