@@ -97,6 +97,32 @@ def test_multi_instance_batch_matches_single_calls(F, prec):
     assert rel_l2(host(out[4][0]), host(ref["aT"])) < 1e-5
 
 
+def test_batch_runs_shell_shards_in_stream_mode(F):
+    """Shell shards (fnl_make_shells_shard) in a batch: stream mode, every instance bit for bit
+    equal to its single call, and the shards of one realisation adding up to the whole object."""
+    lmax, nr, grid = 100, 16, (151, 800)
+    r, w = W.radial_grid(nr)
+    aT, aE = W.transfer_kernels(lmax, r)
+    K = W.random_lower_filters(lmax, nr, seed=9, scale=8e-5)
+    whole = F.Shells(lmax, nr, *grid, r, w, aT, aE, K=K, prec="bf16x2")
+    s0 = F.Shells(lmax, nr, *grid, r, w, aT, aE, K=K, prec="bf16x2", shard=(0, 8))
+    s1 = F.Shells(lmax, nr, *grid, r, w, aT, aE, K=K, prec="bf16x2", shard=(8, 16))
+    inst = [s0, s1, s0]
+    b = F.Batch(inst)
+    assert not b.multi
+    seeds, reals, fnls = [3, 3, 4], [1, 1, 0], [20.0, 20.0, -5.0]
+    out = b.generate(seeds, reals, fnls)
+    assert_same(out, singles(inst, seeds, reals, fnls))
+    ref = whole.generate(3, 1, 20.0, parts=False)
+    for j, k in enumerate(("aT", "aE")):
+        got = host(out[0][j]) + host(out[1][j])
+        want = host(ref[k])
+        assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want)), k
+    b.close()
+    for sh in (whole, s0, s1):
+        sh.close()
+
+
 def test_batch_rejects_bad_arguments(F):
     A = make(F, 16, 8)
     with pytest.raises(F.FnlError):
