@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfnl.so")
 
-SOURCES = ["fnl_api.cu", "tables.cu", "simt_path.cu", "ring_fft.cu", "ring_square.cu", "tc_gemm.cu", "mixed_path.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "maps.cu", "ksw.cu", "quadrature.cu", "healpix.cu", "peaks.cu", "setup_host.cpp"]
+SOURCES = ["fnl_api.cu", "tables.cu", "simt_path.cu", "ring_fft.cu", "ring_square.cu", "tc_gemm.cu", "mixed_path.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "maps.cu", "ksw.cu", "quadrature.cu", "healpix.cu", "peaks.cu", "filter_tc.cu", "setup_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -227,7 +227,11 @@ void enqueue_multi(fnl_batch* b, const uint64_t* seeds, const uint64_t* reals, c
     out.aT[i] = (double2*)aT[i];
     out.aE[i] = (double2*)aE[i];
   }
-  launch_filter_multi(b->d_finst, b->d_blocks, b->nblocks, keys, b->max_nr, b->n, st);
+  // step (i): the tensor-core filter of each instance (the same launch as its single call)
+  for (int i = 0; i < b->n; ++i) {
+    const fnl_shells* s = b->run[i];
+    launch_filter_mixed(s, seeds[i], reals[i], nullptr, s->d_aL, s->d_aL + 2 * s->nalm, nullptr, s->d_psum, st);
+  }
   upload_tc_maps(b->h_maps_syn, b->n, st);
   launch_tc_gemm(b->tsyn, b->run[0]->sms, st);
   for (const fnl_batch::Ring& r : b->rings)

@@ -760,6 +760,7 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
             for (int j = 0; j <= j0 + i; ++j)
               kft[((size_t)l * ncol + j) * nrp + i] = (float)Kf[((size_t)l * nr + i) * ncol + j];
         sh->d_Kft = upload(sh, kft);
+        build_filter_terms(sh, Kf);
       }
       sh->d_tw = upload(sh, twf);
       sh->d_twp = upload(sh, twpf);

@@ -156,6 +156,8 @@ struct fnl_shells {
   void* d_lam = nullptr;           // SIMT table, real type, [lam_total]
   void* d_Kf = nullptr;            // [L+1][nr][ncol] real type: row i holds K_l[j0 + i][0 .. ncol),
                                    // ncol = j0 + nr (the noise shells the object's rows need)
+  void* d_Kterm = nullptr;         // tensor-core forms: BF16 [3 terms][L+1][128 j][128 i] of K_l[j0 + i][j]
+  CUtensorMap tmK{};               // its tensor map (one box per degree: every term, both halves of i)
   float* d_Kft = nullptr;          // tensor-core forms: [L+1][ncol][nrp] FP32, Kt[j][i] = K_l[j0 + i][j]
                                    // (nrp = nr rounded up to 8; zero above the diagonal and in the padding)
   double* d_vT = nullptr;          // [L+1][ncol]  v^X_l[j] = sum_i K_l[j0 + i][j] q^X_l[i]
@@ -401,6 +403,11 @@ void launch_combine_multi(const CombineInst* inst, int64_t max_nalm, int ninst, 
 
 // ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
 void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st);
+// Tensor-core filter (filter_tc.cu): the BF16 terms of K_l and their tensor map (set-up; Kf is
+// [L+1][nr][ncol] as d_Kf), and step (i) with per-degree monopole partials psum_part [L+1][nr].
+void build_filter_terms(fnl_shells* sh, const std::vector<double>& Kf);
+void launch_filter_tc(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
+                      double* aLE, double* phi_api, double* psum_part, cudaStream_t st);
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, double* psum, cudaStream_t st);
 void launch_alm_to_terms(const fnl_shells* sh, const double* alm, cudaStream_t st);

@@ -464,6 +464,14 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
+  if (sh->d_Kterm) {  // on the tensor cores: one monopole partial per degree and shell
+    launch_filter_tc(sh, seed, real, noise, aLT, aLE, phi_api, psum ? sh->d_psum_part : nullptr, st);
+    if (psum) {
+      k_psum_reduce<<<sh->nr, 256, 0, st>>>(sh->lmax + 1, sh->nr, sh->d_psum_part, psum);
+      FNL_CUDA(cudaGetLastError());
+    }
+    return;
+  }
   const int nr = sh->nr, nrp = (nr + 7) / 8 * 8, ncol = sh->j0 + nr;
   const size_t smem = sizeof(float) * ((size_t)ncol * nrp + (size_t)std::max(ncol * kFCols, kFCols * out_stride(nrp)) +
                                       4 * ncol + 4 * kFCols);
