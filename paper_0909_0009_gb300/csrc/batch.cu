@@ -6,18 +6,20 @@
 // shells object uses the object's, later ones use scratch clones that share its tables.
 //
 // Multi-instance mode (every instance a whole configuration in a tensor-core form with a
-// specialised ring kernel, at most kTcMaxInst of them): each stage is ONE launch over all
-// instances --
-//   k_filter_multi + k_psum_multi   step (i): blocks are (instance, degree), largest first
+// specialised ring kernel, at most kTcMaxInst of them): each stage after the filter is ONE
+// launch over all instances --
+//   k_filter_tc + k_psum_reduce     step (i): the tensor-core filter of each instance, the same
+//                                   launches as its single call (a persistent kernel per instance)
 //   k_tc_gemm<true>, synthesis      step (ii) Legendre: one persistent tile list over all
 //                                   instances (instance tensor maps in constant memory)
 //   k_ring_square<.., true>         steps (ii)-(iv) ring DFTs and square, one launch per ring
 //                                   length present (the kernel is specialised per length)
 //   k_tc_gemm<true>, analysis       steps (iv), (v)
 //   k_combine_multi                 Eq. 3
-// so a batch of 64 uneven realisations is 6 + (ring lengths) launches, captured once into a
-// graph and replayed with new keys and outputs.  The tile shape, the same for every instance
-// of a launch, is picked by timing whole batches (fnl_batch_create).
+// so a batch of n realisations is 2 n + 3 + (ring lengths) launches, captured into one graph
+// per call (an update of the instantiated graph) with the call's keys and outputs.  The tile
+// shape, the same for every instance of a launch, is picked by timing whole batches
+// (fnl_batch_create).
 //
 // Stream mode (any other batch: SIMT forms, ring lengths without a specialised kernel):
 // instances are dealt, largest first (work ~ (l_max + 1)^3 N_r), to up to `nstreams`
@@ -32,7 +34,6 @@
 #include "fnl_internal.cuh"
 
 using fnl::CombineInst;
-using fnl::FilterInst;
 using fnl::TcArgs;
 using fnl::TcInst;
 using fnl::TcTile;
@@ -55,9 +56,6 @@ struct fnl_batch {
   std::vector<int> versions;          // tile versions of the owners when the arrays were built
   std::vector<void*> dev;             // device arrays (owned)
   void* pinned = nullptr;             // host tensor maps (owned, pinned)
-  FilterInst* d_finst = nullptr;
-  int2* d_blocks = nullptr;
-  int nblocks = 0, max_nr = 0;
   TcArgs tsyn{}, tana{};
   CUtensorMap* h_maps_syn = nullptr;
   CUtensorMap* h_maps_ana = nullptr;
@@ -129,28 +127,17 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
   for (fnl_shells* r : b->run) b->versions.push_back(owner_of(r)->tiles_version);
   const int n = b->n;
 
-  // step (i): instances and (instance, degree) blocks, largest degree first
-  std::vector<FilterInst> fi(n);
-  std::vector<int2> blocks;
+  // step (v): the instances' combine arguments
   std::vector<CombineInst> ci(n);
-  b->max_nr = 0;
   b->max_nalm = 0;
   for (int i = 0; i < n; ++i) {
     const fnl_shells* s = b->run[i];
     const int64_t n2 = 2 * s->nalm;
-    fi[i] = FilterInst{s->lmax, s->nr, s->Cpad, s->nterms, s->phiT_stride, s->d_Kft, s->d_vT, s->d_vE,
-                       s->d_row32, (__nv_bfloat16*)s->d_phiT, s->d_aL, s->d_aL + n2, s->d_psum_part, s->d_psum};
     ci[i] = CombineInst{s->nalm, s->Cpad / 128, s->nr, (const double2*)s->d_part, s->d_psum, s->d_mu, s->d_qT,
                         s->d_qE, (const double2*)s->d_aL, (const double2*)(s->d_aL + n2), (double2*)s->d_aNL,
                         (double2*)(s->d_aNL + n2)};
-    for (int l = 0; l <= s->lmax; ++l) blocks.push_back(make_int2(i, l));
-    b->max_nr = std::max(b->max_nr, s->nr);
     b->max_nalm = std::max(b->max_nalm, s->nalm);
   }
-  std::stable_sort(blocks.begin(), blocks.end(), [](const int2& a, const int2& c) { return a.y > c.y; });
-  b->d_finst = upload_vec(b, fi);
-  b->d_blocks = upload_vec(b, blocks);
-  b->nblocks = (int)blocks.size();
   b->d_cinst = upload_vec(b, ci);
 
   // Legendre GEMMs: one tile list over all instances, the tiles of one (instance, problem)
@@ -218,11 +205,8 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
 // The launches of one batch call on `st` (no synchronisation; captured by the caller).
 void enqueue_multi(fnl_batch* b, const uint64_t* seeds, const uint64_t* reals, const double* fnl, double* const* aT,
                    double* const* aE, cudaStream_t st) {
-  MultiKeys keys{};
   MultiOut out{};
   for (int i = 0; i < b->n; ++i) {
-    keys.seed[i] = seeds[i];
-    keys.real[i] = reals[i];
     out.fnl[i] = fnl[i];
     out.aT[i] = (double2*)aT[i];
     out.aE[i] = (double2*)aE[i];

@@ -1,5 +1,5 @@
 // Step (i) of the tensor-core forms on the 5th-generation tensor cores: the noise n_lm(r_j) is
-// drawn (Philox4x64-10 + Box-Muller, as in the SIMT filter) and Phi_L = K_l n (Eq. 9) is a GEMM
+// drawn (Philox4x64-10 + FP32 Box-Muller, as in the FP32 form) and Phi_L = K_l n (Eq. 9) is a GEMM
 // per degree l:
 //   D[i][col] = sum_j K_l[j0 + i][j] n[j][col],  M = 128 shells i, N = 64 columns (32 orders m,
 //   re and im), K = 128 noise shells j

@@ -752,14 +752,7 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       std::vector<float> kf(Kf.begin(), Kf.end()), twf(tw.begin(), tw.end()), twpf(twp.begin(), twp.end());
       sh->d_Kf = upload(sh, kf);
       if (mixed && !synth_only) {
-        // the filter kernel's shared-memory image of K_l, transposed and padded, copied as is
-        const int nrp = (nr + 7) / 8 * 8;
-        std::vector<float> kft((size_t)(L + 1) * ncol * nrp, 0.f);
-        for (int l = 0; l <= L; ++l)
-          for (int i = 0; i < nr; ++i)
-            for (int j = 0; j <= j0 + i; ++j)
-              kft[((size_t)l * ncol + j) * nrp + i] = (float)Kf[((size_t)l * nr + i) * ncol + j];
-        sh->d_Kft = upload(sh, kft);
+        // the BF16 terms of K_l and their tensor map for the tensor-core filter
         build_filter_terms(sh, Kf);
       }
       sh->d_tw = upload(sh, twf);

@@ -158,8 +158,6 @@ struct fnl_shells {
                                    // ncol = j0 + nr (the noise shells the object's rows need)
   void* d_Kterm = nullptr;         // tensor-core forms: BF16 [3 terms][L+1][128 j][128 i] of K_l[j0 + i][j]
   CUtensorMap tmK{};               // its tensor map (one box per degree: every term, both halves of i)
-  float* d_Kft = nullptr;          // tensor-core forms: [L+1][ncol][nrp] FP32, Kt[j][i] = K_l[j0 + i][j]
-                                   // (nrp = nr rounded up to 8; zero above the diagonal and in the padding)
   double* d_vT = nullptr;          // [L+1][ncol]  v^X_l[j] = sum_i K_l[j0 + i][j] q^X_l[i]
   double* d_vE = nullptr;
   double* d_qT = nullptr;          // [L+1][nr]  q^X_l[i] = w_i r_i^2 alpha^X_l(r_i)
@@ -352,29 +350,11 @@ void launch_dot_fnl(const fnl_shells* sh, const double* gT, const double* gE, co
 
 // ---- several instances (configurations or realisations) in one launch (batch.cu) ----------
 
-// Per-launch keys and outputs of up to kTcMaxInst instances (kernel parameters).
-struct MultiKeys {
-  uint64_t seed[kTcMaxInst];
-  uint64_t real[kTcMaxInst];
-};
+// Per-launch outputs of up to kTcMaxInst instances (kernel parameters).
 struct MultiOut {
   double fnl[kTcMaxInst];
   double2* aT[kTcMaxInst];
   double2* aE[kTcMaxInst];
-};
-// Step (i) of one instance: its tables and scratch (device array entry).
-struct FilterInst {
-  int L, nr, Cpad, nterms;
-  int64_t term_stride;
-  const float* Kft;  // [L+1][nr][nrp], as fnl_shells::d_Kft
-  const double* vT;
-  const double* vE;
-  const int64_t* row32;
-  __nv_bfloat16* phiT;
-  double* aLT;
-  double* aLE;
-  double* psum_part;
-  double* psum;
 };
 // Step (v) of one instance.
 struct CombineInst {
@@ -397,8 +377,6 @@ size_t ring_square_args_size();
 void ring_square_args(const fnl_shells* sh, void* out);
 void launch_ring_square_multi(const fnl_shells* proto, const void* d_inst, const int* d_item0, int ninst, int maxL,
                               int items, cudaStream_t st);
-void launch_filter_multi(const FilterInst* inst, const int2* blocks, int nblocks, const MultiKeys& keys, int max_nr,
-                         int ninst, cudaStream_t st);
 void launch_combine_multi(const CombineInst* inst, int64_t max_nalm, int ninst, const MultiOut& out, cudaStream_t st);
 
 // ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
