@@ -748,10 +748,12 @@ def main():
             e = {"bound": "alu", "achieved": filter_flops(wl.lmax, wl.nr) / sec / 1e12,
                  "peak": fma32 if args.prec != "fp64" else fma64, "unit": "TFLOP/s",
                  "peak_source": ("FP32 FFMA" if args.prec != "fp64" else "FP64 DFMA")
-                                + " rate (measured, fnl_measure_fma_peaks)"}
+                                + " rate (measured, fnl_measure_fma_peaks); flops of K_l n (Eq. 9)"
+                                + ("; the product runs on the tensor cores and the stage is bound by the "
+                                   "noise draws (Philox, Box-Muller) on the ALUs" if mixed else "")}
         else:
-            if mixed:  # epilogue partials (float4 per column tile) and a^X_L in, a^X and a^X_NL out
-                qb = W.n_alm(wl.lmax) * ((wl.nr * 2 + 127) // 128 * 16 + 2 * 16 + 4 * 16)
+            if mixed:  # epilogue partials (two FP64 pairs per column tile) and a^X_L in, a^X and a^X_NL out
+                qb = W.n_alm(wl.lmax) * ((wl.nr * 2 + 127) // 128 * 32 + 2 * 16 + 4 * 16)
             else:      # Phi_NL rows and a^X_L in, a^X and a^X_NL out
                 qb = W.n_alm(wl.lmax) * (2 * wl.nr * real_bytes + 2 * 16 + 4 * 16)
             e = {"bound": "hbm", "achieved": qb / sec / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
