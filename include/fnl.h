@@ -150,6 +150,8 @@ fnl_status fnl_shells_mu(const fnl_shells* sh, double* mu_out);
  *      and entry idx comes from counter (idx, j >> 2, realisation, 0), key (seed, 0), output
  *      word j & 3, whose two 32-bit halves are the Box-Muller uniforms ((hi + 1) 2^-32 and
  *      lo 2^-32); m > 0 entries get unit complex variance, m = 0 entries are real N(0, 1).
+ *      FNL_FP64 evaluates the Box-Muller transform in FP64, FNL_FP32 in FP32, and the
+ *      tensor-core forms in FP32 with approximate transcendentals (absolute error < 2^-21).
  *  fnl:   f_NL of Eq. 1.
  *  noise: device [nr][nalm][2] explicit n_lm(r_j) (imaginary part of m = 0 ignored; a shell
  *      shard [j0, j1) reads [j1][nalm][2]), or NULL to draw it from (seed, realisation).
