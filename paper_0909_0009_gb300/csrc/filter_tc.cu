@@ -16,10 +16,11 @@
 //               shared memory in the MMA's layout (N-major rows of 64 columns, 128B swizzle);
 //               a lane takes one order of the chunk, a warp up to three quads of shells, and
 //               each lane's partial sums of a^X_L over its shells go to shared memory
-//   warps 11-14 epilogue, one per TMEM lane quadrant (a lane = a shell): the a^X_L sums over
-//               the noise warps' partials, tcgen05.ld of the two accumulators, Phi_L as BF16
-//               terms of the synthesis operand, the monopole sums
-//   warp 15     allocates TMEM, loads K_l (all three terms in one TMA box of 96 KB per degree)
+//   warps 11-18 epilogue, two per TMEM lane quadrant (a lane = a shell), each taking half of a
+//               chunk's orders: the a^X_L sums over the noise warps' partials, tcgen05.ld of
+//               the two accumulators, Phi_L as BF16 terms of the synthesis operand, the
+//               monopole sums
+//   warp 19     allocates TMEM, loads K_l (all three terms in one TMA box of 96 KB per degree)
 //               and issues the MMAs from one lane
 // Every mbarrier wait is bounded; on expiry the kernel records an error and unwinds.
 #include <cuda_bf16.h>
@@ -36,8 +37,9 @@ namespace fnl {
 
 namespace {
 
-constexpr int kFtcNoiseWarps = 11;                // warps 0 .. 10: noise; 11 .. 14: epilogue
-constexpr int kFtcMmaWarp = kFtcNoiseWarps + 4;    // warp 15
+constexpr int kFtcNoiseWarps = 11;                // warps 0 .. 10: noise
+constexpr int kFtcEpiWarps = 8;                   // warps 11 .. 18: epilogue, two per TMEM lane quadrant
+constexpr int kFtcMmaWarp = kFtcNoiseWarps + kFtcEpiWarps;  // warp 19
 constexpr int kFtcThreads = 32 * (kFtcMmaWarp + 1);
 constexpr int kFtcCols = 64;                       // N: 32 orders x (re, im)
 constexpr uint32_t kFtcKTerm = 128u * 128u * 2u;   // one BF16 term of K_l: 2 halves x 128 j x 128 B
@@ -63,7 +65,7 @@ struct FtcArgs {
   double* phi_api;        // [nalm][nr][2] or NULL
   double* aLT;            // [nalm][2]
   double* aLE;
-  double* psum_part;      // [L+1][nr] or NULL
+  double* psum_part;      // [L+1][2][nr] or NULL (the two halves of the orders)
   int* err;
 };
 
@@ -156,9 +158,9 @@ __global__ void __launch_bounds__(kFtcThreads, 1)
       mbar_init(&nfull[s], kFtcNoiseWarps);
       mbar_init(&nempty[s], 1);
       mbar_init(&tfull[s], 1);
-      mbar_init(&tempty[s], 4);
+      mbar_init(&tempty[s], kFtcEpiWarps);
       mbar_init(&afull[s], kFtcNoiseWarps);
-      mbar_init(&aempty[s], 4);
+      mbar_init(&aempty[s], kFtcEpiWarps);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(kFtcThreads, 1)
   } else if (warp < kFtcMmaWarp) {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;           // TMEM lane quadrant: shells 32 q .. 32 q + 31
+    const int h = (warp - kFtcNoiseWarps) >> 2;  // which half of a chunk's orders: 16 h .. 16 h + 15
     const int i = 32 * q + lane;      // this lane's shell (local index)
     const bool ivalid = i < a.nr;
     // sum_m w_m |Phi_L,lm(r_i)|^2 of the current degree, double-float: (re^2, im^2) pairs in two
@@ -292,16 +295,19 @@ __global__ void __launch_bounds__(kFtcThreads, 1)
           break;
         }
         {
-          const int t = 32 * q + lane, mi = t >> 2, v = t & 3, m = 32 * c + mi;
-          float hs = 0.f, ls = 0.f, hs2 = 0.f, ls2 = 0.f;  // two chains, joined
+          // the half's 16 orders x 4 values over 128 threads: two threads per sum (noise warps
+          // of either parity), joined across the lane pair
+          const int t = 32 * q + lane, mi = 16 * h + (t >> 3), v = (t >> 1) & 3, par2 = t & 1;
+          const int m = 32 * c + mi;
+          float hs = 0.f, ls = 0.f;
 #pragma unroll
-          for (int w = 0; w < kFtcNoiseWarps; ++w) {
+          for (int w = par2; w < kFtcNoiseWarps; w += 2) {
             const float* pw = part + (((size_t)s * kFtcNoiseWarps + w) * 32 + mi) * 8 + 2 * v;
-            if (w & 1) df_add(hs2, ls2, pw[0], pw[1]);
-            else df_add(hs, ls, pw[0], pw[1]);
+            df_add(hs, ls, pw[0], pw[1]);
           }
-          df_add(hs, ls, hs2, ls2);
-          if (m <= l) {
+          const float oh = __shfl_xor_sync(0xffffffffu, hs, 1), ol = __shfl_xor_sync(0xffffffffu, ls, 1);
+          df_add(hs, ls, oh, ol);
+          if (par2 == 0 && m <= l) {
             const int64_t idx = alm_idx(l, m, L);
             (v < 2 ? a.aLT : a.aLE)[2 * idx + (v & 1)] = (double)hs + (double)ls;
           }
@@ -320,9 +326,9 @@ __global__ void __launch_bounds__(kFtcThreads, 1)
           const int m = 32 * c + lane;
           if (m <= l) rowv = a.row32[2 * m + ((l - m) & 1)] + ((l - m) >> 1);
         }
-        // four groups of 8 orders: 16 columns of both accumulators each
+        // the half's two groups of 8 orders: 16 columns of both accumulators each
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 2 * h; g < 2 * h + 2; ++g) {
           float v[16];
           {
             float y[16];
@@ -330,7 +336,7 @@ __global__ void __launch_bounds__(kFtcThreads, 1)
 #pragma unroll
             for (int k = 0; k < 16; ++k) v[k] += y[k];
           }
-          if (g == 3) {
+          if (g == 2 * h + 1) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[s]);
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(kFtcThreads, 1)
       df_add2(ph[0], pl[0], ph[1], pl[1]);
       float sh = ph[0].x, sl = pl[0].x;
       df_add(sh, sl, ph[0].y, pl[0].y);
-      if (a.psum_part && ivalid) a.psum_part[(size_t)l * a.nr + i] = (double)sh + (double)sl;
+      if (a.psum_part && ivalid) a.psum_part[((size_t)l * 2 + h) * a.nr + i] = (double)sh + (double)sl;
 #pragma unroll
       for (int k = 0; k < 2; ++k) ph[k] = pl[k] = make_float2(0.f, 0.f);
     }

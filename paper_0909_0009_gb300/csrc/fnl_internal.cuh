@@ -382,7 +382,7 @@ void launch_combine_multi(const CombineInst* inst, int64_t max_nalm, int ninst, 
 // ---- mixed-precision forms (mixed_path.cu, tc_gemm.cu) -------------------------------------
 void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st);
 // Tensor-core filter (filter_tc.cu): the BF16 terms of K_l and their tensor map (set-up; Kf is
-// [L+1][nr][ncol] as d_Kf), and step (i) with per-degree monopole partials psum_part [L+1][nr].
+// [L+1][nr][ncol] as d_Kf), and step (i) with monopole partials psum_part [L+1][2][nr].
 void build_filter_terms(fnl_shells* sh, const std::vector<double>& Kf);
 void launch_filter_tc(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                       double* aLE, double* phi_api, double* psum_part, cudaStream_t st);

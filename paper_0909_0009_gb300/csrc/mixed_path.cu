@@ -201,10 +201,10 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                          double* aLE, double* phi_api, double* psum, cudaStream_t st) {
-  // on the tensor cores, one monopole partial per degree and shell
+  // on the tensor cores, two monopole partials per degree and shell
   launch_filter_tc(sh, seed, real, noise, aLT, aLE, phi_api, psum ? sh->d_psum_part : nullptr, st);
   if (psum) {
-    k_psum_reduce<<<sh->nr, 256, 0, st>>>(sh->lmax + 1, sh->nr, sh->d_psum_part, psum);
+    k_psum_reduce<<<sh->nr, 256, 0, st>>>(2 * (sh->lmax + 1), sh->nr, sh->d_psum_part, psum);
     FNL_CUDA(cudaGetLastError());
   }
 }
