@@ -778,7 +778,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 2 * sh.nalm * 16, "steps": e2e_steps,
                 "note": "fnl_generate_host: inputs are the (seed, realisation, f_NL) scalars; a^T and a^E "
-                        "copied to pinned host memory every step"},
+                        "land in pinned host memory every step (written by the path's last kernel "
+                        "through the buffers' device mapping); the step's time includes them"},
         "gpu_launches": (6 if args.prec in ("bf16x2", "bf16x3") else 5) * args.steps,
         "tiles": {"synthesis": tiles[0], "analysis": tiles[1]},
         "clocks": clk,

@@ -183,9 +183,10 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
                                  const double* aNLT, const double* aNLE, double* grad_noise,
                                  double* grad_fnl, void* stream);
 
-/* fnl_generate with host outputs: the same path, then the requested results (host
- * [nalm][2] each, any may be NULL; pinned memory gives asynchronous copies) are copied
- * device-to-host on `stream`.  The caller synchronises the stream before reading them. */
+/* fnl_generate with host outputs (host [nalm][2] each, any may be NULL): the same path on
+ * `stream`.  A page-locked buffer (cudaHostAlloc, cudaHostRegister) is written by the path's
+ * last kernel through its device mapping; any other buffer receives a device-to-host copy on
+ * `stream` after the path.  The caller synchronises the stream before reading them. */
 fnl_status fnl_generate_host(const fnl_shells* sh, uint64_t seed, uint64_t realisation, double fnl,
                              double* aT, double* aE, double* aNLT, double* aNLE, void* stream);
 

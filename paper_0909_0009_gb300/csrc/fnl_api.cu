@@ -1112,14 +1112,29 @@ fnl_status fnl_generate_host(const fnl_shells* sh, uint64_t seed, uint64_t reali
     DeviceScope scope(sh->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n2 = 2 * sh->nalm;
-    double* dT = sh->d_aOut;
-    double* dE = sh->d_aOut + n2;
-    run_generate(sh, seed, realisation, fnl, nullptr, dT, dE, nullptr, nullptr, nullptr, nullptr, st);
     const size_t bytes = sizeof(double) * (size_t)n2;
-    if (aT) FNL_CUDA(cudaMemcpyAsync(aT, dT, bytes, cudaMemcpyDeviceToHost, st));
-    if (aE) FNL_CUDA(cudaMemcpyAsync(aE, dE, bytes, cudaMemcpyDeviceToHost, st));
-    if (aNLT) FNL_CUDA(cudaMemcpyAsync(aNLT, sh->d_aNL, bytes, cudaMemcpyDeviceToHost, st));
-    if (aNLE) FNL_CUDA(cudaMemcpyAsync(aNLE, sh->d_aNL + n2, bytes, cudaMemcpyDeviceToHost, st));
+    // page-locked host buffers are written by the last kernel itself, through their device
+    // mapping (over the chip-to-chip link where the host memory sits); other buffers get a copy
+    auto mapped = [](double* h) -> double* {
+      if (!h) return nullptr;
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      return at.type == cudaMemoryTypeHost && at.devicePointer ? (double*)at.devicePointer : nullptr;
+    };
+    double* mT = mapped(aT);
+    double* mE = mapped(aE);
+    double* mNT = mapped(aNLT);
+    double* mNE = mapped(aNLE);
+    double* dT = mT ? mT : sh->d_aOut;
+    double* dE = mE ? mE : sh->d_aOut + n2;
+    run_generate(sh, seed, realisation, fnl, nullptr, dT, dE, nullptr, nullptr, mNT, mNE, st);
+    if (aT && !mT) FNL_CUDA(cudaMemcpyAsync(aT, dT, bytes, cudaMemcpyDeviceToHost, st));
+    if (aE && !mE) FNL_CUDA(cudaMemcpyAsync(aE, dE, bytes, cudaMemcpyDeviceToHost, st));
+    if (aNLT && !mNT) FNL_CUDA(cudaMemcpyAsync(aNLT, sh->d_aNL, bytes, cudaMemcpyDeviceToHost, st));
+    if (aNLE && !mNE) FNL_CUDA(cudaMemcpyAsync(aNLE, sh->d_aNL + n2, bytes, cudaMemcpyDeviceToHost, st));
   });
 }
 

@@ -292,8 +292,9 @@ class Shells:
 
     def generate_host(self, seed: int, realisation: int, fnl: float, aT: np.ndarray, aE: np.ndarray,
                       aNLT=None, aNLE=None, stream=None):
-        """fnl_generate with host outputs (complex128 arrays of nalm; pinned memory for async copies).
-        The caller synchronises the stream before reading them."""
+        """fnl_generate with host outputs (complex128 arrays of nalm, any but aT/aE may be None):
+        page-locked arrays are written by the path's last kernel, others receive a copy.  The
+        caller synchronises the stream before reading them."""
         def hp(a):
             if a is None:
                 return None

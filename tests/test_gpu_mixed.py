@@ -124,6 +124,28 @@ def test_edge_configurations(F, prec, lmax, nr, ntheta, nphi):
     c.mx.device_status()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x2"])
+def test_host_outputs_equal_device_outputs(F, prec):
+    """fnl_generate_host writes page-locked buffers from the path's last kernel and copies into
+    pageable ones; both must equal fnl_generate's device outputs bit for bit."""
+    import torch
+    c = Pair(F, 40, 16, 61, 125, prec)
+    ref = {k: host(v) for k, v in c.mx.generate(7, 2, 25.0).items()}
+    na = c.mx.nalm
+    pinned = [torch.empty(na, dtype=torch.complex128, pin_memory=True).numpy() for _ in range(4)]
+    pageable = [np.empty(na, dtype=np.complex128) for _ in range(4)]
+    for bufs in (pinned, pageable, [pinned[0], pageable[1], None, pinned[3]]):
+        for b in bufs:
+            if b is not None:
+                b[:] = np.nan
+        c.mx.generate_host(7, 2, 25.0, bufs[0], bufs[1], bufs[2], bufs[3])
+        torch.cuda.synchronize()
+        for b, k in zip(bufs, ("aT", "aE", "aNLT", "aNLE")):
+            if b is not None:
+                assert np.array_equal(b, ref[k]), k
+    c.mx.device_status()
+
+
 @pytest.mark.parametrize("prec", ["bf16x2", "bf16x3"])
 def test_filter_matches_oracle(F, prec):
     c = Pair(F, 64, 32, 97, 200, prec)
