@@ -147,9 +147,21 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
   b->h_maps_ana = b->h_maps_syn + 3 * (size_t)n;
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<TcInst> insts(n);
-    std::vector<std::pair<int64_t, std::vector<TcTile>>> groups;
+    // (work, configuration, tiles) of every (instance, problem); equal work is kept together by
+    // configuration, so that instances sharing one Legendre table (repeats of an object) read
+    // its slabs back to back and find them in L2
+    struct Group {
+      int64_t work;
+      int cfg;
+      std::vector<TcTile> tiles;
+    };
+    std::vector<Group> groups;
+    std::vector<const fnl_shells*> cfgs;
     for (int i = 0; i < n; ++i) {
       const fnl_shells* s = b->run[i];
+      const fnl_shells* o = owner_of(s);
+      const int cfg = (int)(std::find(cfgs.begin(), cfgs.end(), o) - cfgs.begin());
+      if (cfg == (int)cfgs.size()) cfgs.push_back(o);
       insts[i] = s->tci[dir];
       CUtensorMap* maps = (dir ? b->h_maps_ana : b->h_maps_syn) + 3 * (size_t)i;
       maps[0] = s->tci[dir].tmA;
@@ -157,16 +169,18 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
       maps[2] = s->tci[0].tmF;  // read by the synthesis epilogue only
       const std::vector<TcTile>& tl = dir ? s->tiles_ana_h : s->tiles_syn_h;
       for (size_t k = 0; k < tl.size(); ++k) {
-        if (k == 0 || tl[k].mp != tl[k - 1].mp) groups.push_back({0, {}});
+        if (k == 0 || tl[k].mp != tl[k - 1].mp) groups.push_back({0, cfg, {}});
         TcTile t = tl[k];
         t.inst = i;
-        groups.back().first += (int64_t)t.nkb * t.nsize;
-        groups.back().second.push_back(t);
+        groups.back().work += (int64_t)t.nkb * t.nsize;
+        groups.back().tiles.push_back(t);
       }
     }
-    std::stable_sort(groups.begin(), groups.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+    std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& c) {
+      return a.work != c.work ? a.work > c.work : a.cfg < c.cfg;
+    });
     std::vector<TcTile> tiles;
-    for (const auto& g : groups) tiles.insert(tiles.end(), g.second.begin(), g.second.end());
+    for (const auto& g : groups) tiles.insert(tiles.end(), g.tiles.begin(), g.tiles.end());
     TcArgs a = dir ? b->run[0]->tc_ana : b->run[0]->tc_syn;
     a.one = TcInst{};
     a.multi = 1;
