@@ -132,3 +132,28 @@ def test_shard_info_and_refusals(F):
         with pytest.raises(F.FnlError) as e:
             F.Shells(LMAX, NR, NT, NP, r, w, aT, aE, K=K, prec="fp64", shard=bad)
         assert e.value.code == 1, bad
+
+
+@pytest.mark.parametrize("world", [2, 8])
+def test_full_size_shards_sum_to_the_whole_configuration(F, world):
+    """The bench's sharded configuration (l_max 1024, N_r 128, 1537 x 3200, bf16x2): the shards
+    of `world` ranks (shell_ranges, units of 8 shells) sum to the whole object's outputs."""
+    from paper_0909_0009_gb300 import sharded
+    wl = W.FULL
+    r, w = W.radial_grid(wl.nr)
+    aT, aE = W.transfer_kernels(wl.lmax, r)
+    K = W.random_lower_filters(wl.lmax, wl.nr, seed=21, scale=8e-5)
+    whole = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec="bf16x2")
+    ref = _host(whole.generate(2, 3, 30.0))
+    whole.close()
+    acc = {k: 0.0 for k in OUTS}
+    for j0, j1 in sharded.shell_ranges(wl.nr, world):
+        sh = F.Shells(wl.lmax, wl.nr, wl.ntheta, wl.nphi, r, w, aT, aE, K=K, prec="bf16x2", shard=(j0, j1))
+        got = _host(sh.generate(2, 3, 30.0))
+        for k in OUTS:
+            acc[k] = acc[k] + got[k]
+        sh.device_status()
+        sh.close()
+    for k in OUTS:
+        scale = np.max(np.abs(ref[k]))
+        assert np.max(np.abs(acc[k] - ref[k])) <= 1e-12 * scale, (k, np.max(np.abs(acc[k] - ref[k])) / scale)
