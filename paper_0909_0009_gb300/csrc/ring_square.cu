@@ -569,33 +569,36 @@ __global__ void __launch_bounds__(G * ((P * Q + 31) / 32 * 32), 1) k_ring_cubic_
       for (int d = 0; d < P; ++d) B[base + N1 * d] = v[d];
     }
     group_sync<TG>(g);
-    // phase 2 (inverse half): twiddle w_N^(k1 n2), DFT_N1 -> ring values, back in place
+    // phase 2 (inverse half): twiddle w_N^(k1 n2), DFT_N1 -> ring values.  The B groups leave
+    // theirs in shared memory; each A group keeps its own in registers and, once the B values
+    // have landed, sums A B^2 over the ring points it holds.
+    const int base2 = N1 * (u % P) + S * (u / P);
+    float2 v[N1];
     if (u < T) {
-      const int d = u % P, c = u / P;
-      const int base = N1 * d + S * c;
-      const float2* w = tw2 + c * P + d;
-      float2 v[N1];
+      const float2* w = tw2 + (u / P) * P + u % P;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
-        const float2 x = B[base + k1];
+        const float2 x = B[base2 + k1];
         v[k1] = k1 ? cmul(x, w[k1 * T]) : x;
       }
       Dft<N1, 1>::run(v);
+      if (g >= H) {
 #pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) B[base + n1] = v[n1];
+        for (int n1 = 0; n1 < N1; ++n1) B[base2 + n1] = v[n1];
+      }
     }
-    __syncthreads();  // A and B ring values of every shell in place
+    __syncthreads();  // the B ring values of every shell in place
     if (g < H) {
-      const float2* BA = buf + (size_t)g * NB;
       const float2* BB = buf + (size_t)(g + H) * NB;
       const bool equator = (a.ntheta - 1 - jp == jp);
-      float accf = 0.f;  // N / TG terms per thread in FP32, the block sums in FP64
-      for (int t = u; t < N; t += TG) {
-        const int n1 = t % N1, r = t / N1, d = r % P, c = r / P;
-        const int pos = N1 * d + S * c + n1;
-        const float2 x = BA[pos], y = BB[pos];
-        accf += x.x * y.x * y.x;
-        if (!equator) accf += x.y * y.y * y.y;
+      float accf = 0.f;  // N1 terms per thread in FP32, the block sums in FP64
+      if (u < T) {
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+          const float2 y = BB[base2 + n1];
+          accf += v[n1].x * y.x * y.x;
+          if (!equator) accf += v[n1].y * y.y * y.y;
+        }
       }
       double acc = (double)accf;
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
