@@ -36,55 +36,90 @@ __device__ __forceinline__ void lm_of_entry(int64_t idx, int L, int& l, int& m) 
 }
 
 // H~ in the internal rows: f_NL (q^T_l[i] gT + q^E_l[i] gE), halved for m > 0; the imaginary
-// part of m = 0 is zero.  One thread per (idx, column c = 2 i + part).
+// part of m = 0 is zero.  One warp per entry idx = (l, m): the warp finds (l, m) once, reads the
+// entry's gT, gE once, and its lanes take the shells i (both parts) of the row.
+__device__ __forceinline__ void source_value(const double* qT, const double* qE, const double* gT,
+                                             const double* gE, int64_t idx, int l, int nr, int i, int m,
+                                             double fnl, double& re, double& im) {
+  double v[2];
+#pragma unroll
+  for (int part = 0; part < 2; ++part) {
+    double x = 0.0;
+    if (gT) x += qT[(size_t)l * nr + i] * gT[2 * idx + part];
+    if (gE) x += qE[(size_t)l * nr + i] * gE[2 * idx + part];
+    x *= fnl;
+    if (m > 0) x *= 0.5;
+    v[part] = x;
+  }
+  re = v[0];
+  im = m == 0 ? 0.0 : v[1];
+}
+
 template <typename T>
-__global__ void k_adjoint_source(int L, int nr, int64_t nalm, const int64_t* __restrict__ row0,
-                                 const double* __restrict__ qT, const double* __restrict__ qE, double fnl,
-                                 const double* __restrict__ gT, const double* __restrict__ gE, T* __restrict__ phi) {
-  const int C = 2 * nr;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nalm * C) return;
-  const int64_t idx = t / C;
-  const int c = (int)(t % C);
-  const int i = c >> 1, part = c & 1;
+__global__ void __launch_bounds__(kThreads) k_adjoint_source(int L, int nr, int64_t nalm,
+                                                             const int64_t* __restrict__ row0,
+                                                             const double* __restrict__ qT,
+                                                             const double* __restrict__ qE, double fnl,
+                                                             const double* __restrict__ gT,
+                                                             const double* __restrict__ gE, T* __restrict__ phi) {
+  const int64_t idx = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (idx >= nalm) return;
   int l, m;
   lm_of_entry(idx, L, l, m);
-  double v = 0.0;
-  if (gT) v += qT[(size_t)l * nr + i] * gT[2 * idx + part];
-  if (gE) v += qE[(size_t)l * nr + i] * gE[2 * idx + part];
-  v *= fnl;
-  if (m > 0) v *= 0.5;
-  if (m == 0 && part) v = 0.0;
-  phi[(row0[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * C + c] = (T)v;
+  T* row = phi + (row0[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * (int64_t)(2 * nr);
+  for (int i = threadIdx.x & 31; i < nr; i += 32) {
+    double re, im;
+    source_value(qT, qE, gT, gE, idx, l, nr, i, m, fnl, re, im);
+    row[2 * i] = (T)re;
+    row[2 * i + 1] = (T)im;
+  }
 }
 
 // The same for the tensor-core forms: H~ written as BF16 terms of the synthesis operand (the
-// Phi rows in their 32-row packing, Cpad columns), so that the tensor-core synthesis GEMM gives s.
-__global__ void k_adjoint_source_terms(int L, int nr, int Cpad, int64_t nalm, int nterms, int64_t term_stride,
-                                       const int64_t* __restrict__ row32, const double* __restrict__ qT,
-                                       const double* __restrict__ qE, double fnl, const double* __restrict__ gT,
-                                       const double* __restrict__ gE, __nv_bfloat16* __restrict__ phiT) {
-  const int C = 2 * nr;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nalm * C) return;
-  const int64_t idx = t / C;
-  const int c = (int)(t % C);
-  const int i = c >> 1, part = c & 1;
+// Phi rows in their 32-row packing, Cpad columns), so that the tensor-core synthesis GEMM gives
+// s; each lane writes the (re, im) pair of its shells as paired BF16 terms.
+__global__ void __launch_bounds__(kThreads) k_adjoint_source_terms(int L, int nr, int Cpad, int64_t nalm, int nterms,
+                                                                   int64_t term_stride,
+                                                                   const int64_t* __restrict__ row32,
+                                                                   const double* __restrict__ qT,
+                                                                   const double* __restrict__ qE, double fnl,
+                                                                   const double* __restrict__ gT,
+                                                                   const double* __restrict__ gE,
+                                                                   __nv_bfloat16* __restrict__ phiT) {
+  const int64_t idx = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  if (idx >= nalm) return;
   int l, m;
   lm_of_entry(idx, L, l, m);
-  double v = 0.0;
-  if (gT) v += qT[(size_t)l * nr + i] * gT[2 * idx + part];
-  if (gE) v += qE[(size_t)l * nr + i] * gE[2 * idx + part];
-  v *= fnl;
-  if (m > 0) v *= 0.5;
-  if (m == 0 && part) v = 0.0;
-  store_terms_d(phiT + (row32[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * Cpad + c, term_stride, nterms, v);
+  __nv_bfloat16* row = phiT + (row32[2 * m + ((l - m) & 1)] + ((l - m) >> 1)) * Cpad;
+  for (int i = threadIdx.x & 31; i < nr; i += 32) {
+    double re, im;
+    source_value(qT, qE, gT, gE, idx, l, nr, i, m, fnl, re, im);
+    // term t of each value: bf16 of the value less the earlier terms, rounded from FP64
+    const __nv_bfloat162 h0 = __halves2bfloat162(__double2bfloat16(re), __double2bfloat16(im));
+    const double r1 = re - (double)__low2float(h0), i1 = im - (double)__high2float(h0);
+    const __nv_bfloat162 h1 = __halves2bfloat162(__double2bfloat16(r1), __double2bfloat16(i1));
+    __nv_bfloat162* o = (__nv_bfloat162*)(row + 2 * i);
+    o[0] = h0;
+    o[term_stride / 2] = h1;
+    if (nterms > 2)
+      o[term_stride] = __halves2bfloat162(__double2bfloat16(r1 - (double)__low2float(h1)),
+                                          __double2bfloat16(i1 - (double)__high2float(h1)));
+  }
 }
 
-// dL/dn for degree l = L - blockIdx.x: Phibar = c_m phi_rows + q^T_l gT + q^E_l gE, then
-// nbar_j = sum_{i >= j} K_l[i, j] Phibar_i for every m <= l.  With API_ROWS the analysis of
-// 2 f s comes in the API layout [nalm][nr][2] in FP64 (the tensor-core forms' per-shell
-// analysis output), else in the SIMT rows [rows][2 nr] of the real type.
+// dL/dn for degree l = L - blockIdx.x and the orders m = kAfM blockIdx.y .. (<= l):
+// Phibar = c_m phi_rows + q^T_l gT + q^E_l gE is staged as a [nr][2 kAfM] tile (columns
+// (m, part)), then nbar_j = sum_{i >= j} K_l[i, j] Phibar_i for the whole tile.  K_l is staged
+// with zeros above the diagonal, so each output is a plain sum over i; a thread holds a register
+// tile of rows j = rg + 32 r (r < 4) and 8 columns, and runs i from its first row rg.  With
+// API_ROWS the analysis of 2 f s comes in the API layout [nalm][nr][2] in FP64 (the tensor-core
+// forms' per-shell analysis output), else in the SIMT rows [rows][2 nr] of the real type.
+constexpr int kAfM = 32;                // orders per tile
+constexpr int kAfCols = 2 * kAfM;       // columns (m, part) per tile
+constexpr int kAfRows = 4;              // rows j per thread: nr <= 128
+template <typename T>
+constexpr int af_ldp() { return kAfCols + 16 / (int)sizeof(T); }  // row stride of the tile (16-byte aligned)
+
 template <typename T, bool API_ROWS = false>
 __global__ void __launch_bounds__(kThreads) k_adjoint_filter(int L, int nr, int64_t nalm, const T* __restrict__ Kf,
                                                              const int64_t* __restrict__ row0,
@@ -95,31 +130,65 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_filter(int L, int nr, int6
                                                              const double* __restrict__ gT,
                                                              const double* __restrict__ gE,
                                                              double* __restrict__ grad) {
+  const int l = L - blockIdx.x, m0 = kAfM * blockIdx.y;
+  if (m0 > l) return;
+  const int nm = min(kAfM, l + 1 - m0);  // orders of this tile
   extern __shared__ __align__(16) unsigned char smem[];
-  const int l = L - blockIdx.x;
+  constexpr int ldp = af_ldp<T>();
   const int C = 2 * nr, ldk = nr + 1;
-  T* pb = (T*)smem;                   // [C] Phibar of the current (l, m)
-  T* Ks = pb + C;                     // [nr][nr + 1]
+  T* P = (T*)smem;                        // [nr][ldp] Phibar of the tile
+  T* Ks = P + (size_t)nr * ldp;           // [nr][nr + 1] K_l, zero above the diagonal
   const T* Kl = Kf + (size_t)l * nr * nr;
-  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) Ks[(e / nr) * ldk + (e % nr)] = Kl[e];
-  for (int m = 0; m <= l; ++m) {
-    const int64_t idx = alm_idx(l, m, L);
-    const int64_t row = row0[2 * m + ((l - m) & 1)] + ((l - m) >> 1);
-    const double cm = m ? 2.0 : 1.0;
-    __syncthreads();  // K staged; the previous m's Phibar consumed
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-      const int i = c >> 1, part = c & 1;
-      double v = cm * (API_ROWS ? api_rows[(size_t)idx * C + c] : (double)phi[row * C + c]);
-      if (gT) v += qT[(size_t)l * nr + i] * gT[2 * idx + part];
-      if (gE) v += qE[(size_t)l * nr + i] * gE[2 * idx + part];
-      pb[c] = (T)v;
+  for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
+    const int i = e / nr, j = e % nr;
+    Ks[i * ldk + j] = j <= i ? Kl[e] : (T)0;
+  }
+  for (int e = threadIdx.x; e < kAfM * C; e += blockDim.x) {
+    const int ml = e / C, c = e % C, i = c >> 1, part = c & 1;
+    T v = (T)0;
+    if (ml < nm) {
+      const int m = m0 + ml;
+      const int64_t idx = alm_idx(l, m, L);
+      const int64_t row = row0[2 * m + ((l - m) & 1)] + ((l - m) >> 1);
+      double x = (m ? 2.0 : 1.0) * (API_ROWS ? api_rows[(size_t)idx * C + c] : (double)phi[row * C + c]);
+      if (gT) x += qT[(size_t)l * nr + i] * gT[2 * idx + part];
+      if (gE) x += qE[(size_t)l * nr + i] * gE[2 * idx + part];
+      v = (T)x;
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-      const int j = c >> 1, part = c & 1;
-      T acc = 0;
-      for (int i = j; i < nr; ++i) acc += Ks[(size_t)i * ldk + j] * pb[2 * i + part];
-      grad[((size_t)j * nalm + idx) * 2 + part] = (m == 0 && part) ? 0.0 : (double)acc;
+    P[(size_t)i * ldp + 2 * ml + part] = v;
+  }
+  __syncthreads();
+  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;  // 8 column groups x 32 row groups
+  T acc[kAfRows][8];
+#pragma unroll
+  for (int r = 0; r < kAfRows; ++r)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[r][q] = (T)0;
+  for (int i = rg; i < nr; ++i) {
+    T kv[kAfRows];
+#pragma unroll
+    for (int r = 0; r < kAfRows; ++r) kv[r] = rg + 32 * r < nr ? Ks[i * ldk + rg + 32 * r] : (T)0;
+    T pv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pv[q] = P[(size_t)i * ldp + 8 * cg + q];
+#pragma unroll
+    for (int r = 0; r < kAfRows; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[r][q] += kv[r] * pv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < kAfRows; ++r) {
+    const int j = rg + 32 * r;
+    if (j >= nr) continue;
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      const int ml = (8 * cg + q) >> 1;
+      if (ml >= nm) continue;
+      const int m = m0 + ml;
+      const int64_t idx = alm_idx(l, m, L);
+      double* o = grad + ((size_t)j * nalm + idx) * 2;
+      o[0] = (double)acc[r][q];
+      o[1] = m == 0 ? 0.0 : (double)acc[r][q + 1];
     }
   }
 }
@@ -161,28 +230,29 @@ __global__ void __launch_bounds__(kThreads) k_dot_final(int nparts, const double
   }
 }
 
+unsigned warp_blocks(int64_t nalm) { return (unsigned)((nalm + kThreads / 32 - 1) / (kThreads / 32)); }
+
 template <typename T>
 void adjoint_source_impl(const fnl_shells* sh, double fnl, const double* gT, const double* gE, cudaStream_t st) {
-  const int64_t n = sh->nalm * sh->C;
-  k_adjoint_source<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sh->lmax, sh->nr, sh->nalm, sh->d_row0,
-                                                                    sh->d_qT, sh->d_qE, fnl, gT, gE, (T*)sh->d_phi);
+  k_adjoint_source<T><<<warp_blocks(sh->nalm), kThreads, 0, st>>>(sh->lmax, sh->nr, sh->nalm, sh->d_row0, sh->d_qT,
+                                                                   sh->d_qE, fnl, gT, gE, (T*)sh->d_phi);
   FNL_CUDA(cudaGetLastError());
 }
 
 template <typename T>
 void adjoint_filter_impl(const fnl_shells* sh, const double* gT, const double* gE, double* grad, cudaStream_t st) {
   const int nr = sh->nr;
-  const size_t smem = sizeof(T) * ((size_t)2 * nr + (size_t)nr * (nr + 1));
-  FNL_CUDA(cudaFuncSetAttribute(k_adjoint_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (nr > 32 * kAfRows) throw Error(FNL_EUNSUPPORTED, "the adjoint filter takes at most 128 shells");
+  const size_t smem = sizeof(T) * ((size_t)nr * af_ldp<T>() + (size_t)nr * (nr + 1));
+  const dim3 grid(sh->lmax + 1, (sh->lmax + kAfM) / kAfM);  // (degree, order tile); tiles past l exit
   if (sh->nterms) {
     FNL_CUDA(cudaFuncSetAttribute(k_adjoint_filter<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_adjoint_filter<T, true><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf,
-                                                                    sh->d_row0, nullptr, sh->d_adjA, sh->d_qT,
-                                                                    sh->d_qE, gT, gE, grad);
+    k_adjoint_filter<T, true><<<grid, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf, sh->d_row0,
+                                                            nullptr, sh->d_adjA, sh->d_qT, sh->d_qE, gT, gE, grad);
   } else {
-    k_adjoint_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf, sh->d_row0,
-                                                              (const T*)sh->d_phi, nullptr, sh->d_qT, sh->d_qE, gT,
-                                                              gE, grad);
+    FNL_CUDA(cudaFuncSetAttribute(k_adjoint_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_adjoint_filter<T><<<grid, kThreads, smem, st>>>(sh->lmax, nr, sh->nalm, (const T*)sh->d_Kf, sh->d_row0,
+                                                      (const T*)sh->d_phi, nullptr, sh->d_qT, sh->d_qE, gT, gE, grad);
   }
   FNL_CUDA(cudaGetLastError());
 }
@@ -191,8 +261,7 @@ void adjoint_filter_impl(const fnl_shells* sh, const double* gT, const double* g
 
 void launch_adjoint_source(const fnl_shells* sh, double fnl, const double* gT, const double* gE, cudaStream_t st) {
   if (sh->nterms) {
-    const int64_t n = sh->nalm * sh->C;
-    k_adjoint_source_terms<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+    k_adjoint_source_terms<<<warp_blocks(sh->nalm), kThreads, 0, st>>>(
         sh->lmax, sh->nr, sh->Cpad, sh->nalm, sh->nterms, sh->phiT_stride, sh->d_row32, sh->d_qT, sh->d_qE, fnl, gT,
         gE, (__nv_bfloat16*)sh->d_phiT);
     FNL_CUDA(cudaGetLastError());
