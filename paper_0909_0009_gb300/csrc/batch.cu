@@ -188,6 +188,7 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
     a.tiles = upload_vec(b, tiles);
     a.ntiles = (int)tiles.size();
     a.alm_out = nullptr;
+    a.store_f32 = 0;
     a.err = b->run[0]->d_err;
     (dir ? b->tana : b->tsyn) = a;
   }

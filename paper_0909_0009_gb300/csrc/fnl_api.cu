@@ -210,6 +210,7 @@ void setup_mixed(fnl_shells* sh, const std::vector<double>& qT, const std::vecto
     a->nterms = T;
     a->split = sh->tc_split;
     a->alm_out = nullptr;
+    a->store_f32 = 0;
     a->err = sh->d_err;
   }
   sh->tc_syn.insts = sh->d_tci;
@@ -435,10 +436,12 @@ void release_shells(fnl_shells* sh) {
 
 namespace {
 
-void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st) {
+void launch_tc(const fnl_shells* sh, const TcArgs& base, int mode, double* alm_out, cudaStream_t st,
+               bool store_f32 = false) {
   TcArgs a = base;
   a.mode = mode;
   a.alm_out = alm_out;
+  a.store_f32 = store_f32 ? 1 : 0;
   launch_tc_gemm(a, sh->sms_gemm ? sh->sms_gemm : sh->sms, st);
 }
 
@@ -725,6 +728,8 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
     sh->d_vE = upload(sh, vE);
     sh->d_qT = upload(sh, qT);
     sh->d_qE = upload(sh, qE);
+    sh->d_qT32 = upload(sh, std::vector<float>(qT.begin(), qT.end()));
+    sh->d_qE32 = upload(sh, std::vector<float>(qE.begin(), qE.end()));
     sh->d_mu = upload(sh, sh->mu);
     sh->d_tiles_syn = upload(sh, ts_syn);
     sh->d_tiles_ana = upload(sh, ts_ana);
@@ -777,7 +782,7 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       if (!synth_only) {
         // the adjoint's second spectrum buffer and its per-shell analysis output
         sh->d_F2 = dalloc<float>(sh, (size_t)nmp * np * sh->Cpad);
-        sh->d_adjA = dalloc<double>(sh, 2 * (size_t)sh->nalm * nr);
+        sh->d_adjA = dalloc<float>(sh, 2 * (size_t)sh->nalm * nr);
         sh->tmF2 = f_tensor_map(sh, sh->d_F2);
         FNL_CUDA(cudaMemset(sh->d_F2, 0, sizeof(float) * (size_t)nmp * np * sh->Cpad));
       }
@@ -1091,7 +1096,7 @@ fnl_status fnl_generate_backward(const fnl_shells* sh, uint64_t seed, uint64_t r
       syn2.one.tmF = sh->tmF2;
       launch_tc(sh, syn2, TC_SYNTH, nullptr, st);                                         // F of s
       launch_ring_product(sh, st);                                                        // G = DFT(2 f s)
-      launch_tc(sh, sh->tc_ana, TC_ANA_STORE, sh->d_adjA, st);                            // analysis(2 f s)
+      launch_tc(sh, sh->tc_ana, TC_ANA_STORE, (double*)sh->d_adjA, st, true);            // analysis(2 f s), FP32
       launch_adjoint_filter(sh, gT, gE, grad_noise, st);                                  // K^T (c_m rows + q g)
       return;
     }

@@ -162,6 +162,8 @@ struct fnl_shells {
   double* d_vE = nullptr;
   double* d_qT = nullptr;          // [L+1][nr]  q^X_l[i] = w_i r_i^2 alpha^X_l(r_i)
   double* d_qE = nullptr;
+  float* d_qT32 = nullptr;         // FP32 copies of q^T, q^E (the adjoint's FP32 and tensor-core forms)
+  float* d_qE32 = nullptr;
   double* d_mu = nullptr;          // [nr]
   void* d_tw = nullptr;            // [nphi] complex real type, e^{-2 pi i k / nphi}
   void* d_twp = nullptr;           // per-pass twiddles: pass p, [(r - 1) Ns_p + k] = e^{-2 pi i r k / (Ns_p R_p)}
@@ -204,7 +206,7 @@ struct fnl_shells {
   void* d_part = nullptr;          // double2 [Cpad / 128][nalm][2]: quadrature partials per column tile
   float2* d_q2 = nullptr;          // [L+1][2][nre]  q^T, q^E as FP32 pairs (hi, lo), nre = nr rounded up to even
   void* d_F2 = nullptr;            // adjoint: the spectra of s, float as d_F (owner objects only)
-  double* d_adjA = nullptr;        // adjoint: analysis of 2 f s per shell, [nalm][nr][2]
+  float* d_adjA = nullptr;         // adjoint: analysis of 2 f s per shell, [nalm][nr][2] (FP32 accumulators)
   CUtensorMap tmF2{};              // adjoint: tensor map of d_F2 for the synthesis's tensor stores
   int* d_err = nullptr;            // device error word of the tensor-core kernels
   double* d_psum = nullptr;        // [nr] sum_lm w_m |Phi_L,lm(r_i)|^2 (Parseval monopole)

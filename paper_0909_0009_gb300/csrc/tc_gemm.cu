@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               const int k = tl.n0 + ch * 32 + j;
               if (ch * 32 + j < tl.nsize && k < tl.kvalid) {
                 const int l = m + p + 2 * k;
-                a.alm_out[alm_idx(l, m, L) * (2 * nr) + c] = (double)v[j];
+                const int64_t o = alm_idx(l, m, L) * (2 * nr) + c;
+                if (a.store_f32) ((float*)a.alm_out)[o] = v[j];
+                else a.alm_out[o] = (double)v[j];
               }
             }
           }

@@ -60,6 +60,7 @@ struct TcArgs {
   int nbuf;             // accumulator sets in TMEM (double buffering when 2)
   int stages;
   double* alm_out;      // TC_ANA_STORE (one configuration per launch): [nalm][nr][2]
+  int store_f32;        // TC_ANA_STORE: 1 writes those values as FP32 (the accumulators' own type)
   int* err;             // device error word (0 = ok)
 };
 
