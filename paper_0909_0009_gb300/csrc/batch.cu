@@ -172,7 +172,7 @@ void build_multi(fnl_batch* b, int syn_w, int ana_w) {
         if (k == 0 || tl[k].mp != tl[k - 1].mp) groups.push_back({0, cfg, {}});
         TcTile t = tl[k];
         t.inst = i;
-        groups.back().work += (int64_t)t.nkb * t.nsize;
+        groups.back().work += (int64_t)(t.nkb - t.kb0) * t.nsize;
         groups.back().tiles.push_back(t);
       }
     }

@@ -322,13 +322,20 @@ void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap, bool exact) {
   for (int mp = 0; mp < nmp; ++mp) {
     const int K = sh->K[mp];
     if (!K) continue;
-    for (int n0 = 0; n0 < np; n0 += sh->nsyn)
+    // ring pairs below jmin carry only |lambda| < kLambdaSkip for this order: synthesis tiles
+    // wholly below it are left out (F keeps its zeros there) and the others write zeros there;
+    // the analysis k loop starts at the 64-ring-pair stage holding jmin
+    const int jz = sh->jmin.empty() ? 0 : sh->jmin[mp / 2];
+    const int kb0 = std::min(jz / kTcStageK, ((np + 31) / 32 - 1) / kTcSlabs) * kTcSlabs;  // >= 1 stage left
+    for (int n0 = 0; n0 < np; n0 += sh->nsyn) {
+      if (n0 + sh->nsyn <= jz) continue;
       for (int ct = 0; ct < ctiles; ++ct)
-        ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0});
+        ts.push_back({mp, 128 * ct, n0, sh->nsyn, (K + 31) / 32, (int)sh->row32[mp], K, 0, jz, 0});
+    }
     for (int n0 = 0; n0 < K;) {
       const int n = std::min(ana_cap, round_up(K - n0, 16));
       for (int ct = 0; ct < ctiles; ++ct)
-        ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0});
+        ta.push_back({mp, 128 * ct, n0, n, (np + 31) / 32, (int)sh->row0[mp], K, 0, 0, kb0});
       n0 += n;
     }
   }
@@ -339,7 +346,7 @@ void configure_tc(fnl_shells* sh, int syn_cap, int ana_cap, bool exact) {
     std::vector<std::pair<int64_t, int>> groups;  // (cost, first index) per problem
     for (size_t i = 0; i < v.size(); ++i) {
       if (i == 0 || v[i].mp != v[i - 1].mp) groups.push_back({0, (int)i});
-      groups.back().first += (int64_t)v[i].nkb * v[i].nsize;
+      groups.back().first += (int64_t)(v[i].nkb - v[i].kb0) * v[i].nsize;
     }
     std::stable_sort(groups.begin(), groups.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
     std::vector<TcTile> out;

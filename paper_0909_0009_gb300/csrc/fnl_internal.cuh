@@ -26,6 +26,13 @@
 
 namespace fnl {
 
+// Ring pairs of an order m where every |lambda_lm| (l = m .. l_max) stays below this bound lie in
+// the polar cap where the associated Legendre functions of that order decay; the tensor-core
+// GEMMs leave them out.  The dropped terms change F_m by at most 2^-30 sum_l |a_lm| and the
+// analysis by at most 2^-30 sum_j w_j |G_m(theta_j)|: below 1e-7 of either result, far under the
+// BF16 split's 4e-6.
+constexpr double kLambdaSkip = 0x1p-30;
+
 // ---- error handling -----------------------------------------------------------------
 
 struct Error : std::runtime_error {
@@ -138,6 +145,8 @@ struct fnl_shells {
 
   // problem geometry
   std::vector<int> K;          // [2(L+1)]
+  std::vector<int> jmin;       // [L+1] tensor-core forms: first ring pair (from the pole) where some
+                               // |lambda_lm| >= kLambdaSkip; the GEMMs leave out the ring pairs below
   std::vector<int> KP;         // K rounded up to 16
   std::vector<int64_t> row0;   // first row of problem mp in the [rows][C] phi buffer (SIMT)
   std::vector<int64_t> lam0;   // first element of problem mp in the SIMT lambda table

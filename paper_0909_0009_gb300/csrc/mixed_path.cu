@@ -44,12 +44,14 @@ __global__ void __launch_bounds__(256) k_psum_reduce(int nparts, int nr, const d
 __device__ __forceinline__ double flushed(double v) { return fabs(v) < 1e-290 ? 0.0 : v; }
 
 // One thread per (jp, m): lambda_lm(x_jp) for l = m..L by the FP64 recurrence, written as BF16
-// terms into Lambda_syn[slab(mp, k / 32)][jp][k % 32] and Lambda_ana[row16(mp) + k][jp].
+// terms into Lambda_syn[slab(mp, k / 32)][jp][k % 32] and Lambda_ana[row16(mp) + k][jp]; jmin[m]
+// becomes the first ring pair (from the pole) where some |lambda_lm| reaches kLambdaSkip.
 __global__ void k_lambda_mixed(const double* __restrict__ x, const double* __restrict__ mant,
                                const int* __restrict__ expo, const double2* __restrict__ ab,
                                const int64_t* __restrict__ row32, const int64_t* __restrict__ row16, int npairs,
                                int npj, int L, int nterms, int64_t syn_stride, int64_t ana_stride,
-                               __nv_bfloat16* __restrict__ lsyn, __nv_bfloat16* __restrict__ lana) {
+                               __nv_bfloat16* __restrict__ lsyn, __nv_bfloat16* __restrict__ lana,
+                               int* __restrict__ jmin) {
   const int jp = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (jp >= npairs) return;
@@ -57,6 +59,7 @@ __global__ void k_lambda_mixed(const double* __restrict__ x, const double* __res
   double y1 = mant[(size_t)m * npairs + jp], y2 = 0.0;
   int e = expo[(size_t)m * npairs + jp];
   const int64_t base = alm_idx(0, m, L);
+  double vmax = 0.0;
   for (int l = m; l <= L; ++l) {
     if (l > m) {
       const double2 c = ab[base + l];
@@ -70,12 +73,14 @@ __global__ void k_lambda_mixed(const double* __restrict__ x, const double* __res
       }
     }
     const double v = flushed(ldexp(y1, e));
+    vmax = fmax(vmax, fabs(v));
     const int d = l - m, p = d & 1, k = d >> 1;
     const int mp = 2 * m + p;
     const int64_t slab = row32[mp] / 32 + k / 32;
     store_terms_d(lsyn + (slab * npairs + jp) * 32 + (k & 31), syn_stride, nterms, v);
     store_terms_d(lana + (row16[mp] + k) * (int64_t)npj + jp, ana_stride, nterms, v);
   }
+  if (vmax >= kLambdaSkip) atomicMin(&jmin[m], jp);
 }
 
 // API coefficients [nalm][nr][2] -> BF16 terms of Phi rows (row32 packing, Cpad columns).
@@ -191,12 +196,18 @@ void build_lambda_tables_mixed(fnl_shells* sh, cudaStream_t st) {
   FNL_CUDA(cudaMemcpyAsync(d_fac, fac.data(), sizeof(double) * (L + 1), cudaMemcpyHostToDevice, st));
   FNL_CUDA(cudaMemcpyAsync(d_ab, ab.data(), sizeof(double2) * ab.size(), cudaMemcpyHostToDevice, st));
   launch_lambda_mm(sh->d_x, d_fac, np, L, d_mant, d_expo, st);
+  TempDev t_jmin(sizeof(int) * (L + 1));
+  int* d_jmin = t_jmin.as<int>();
+  FNL_CUDA(cudaMemsetAsync(d_jmin, 0x7f, sizeof(int) * (L + 1), st));  // above any ring pair
   dim3 grid((np + 127) / 128, L + 1);
   k_lambda_mixed<<<grid, 128, 0, st>>>(sh->d_x, d_mant, d_expo, d_ab, sh->d_row32, sh->d_row0, np, sh->npj, L,
                                        sh->nterms, sh->lsyn_stride, sh->lana_stride, (__nv_bfloat16*)sh->d_lsyn,
-                                       (__nv_bfloat16*)sh->d_lana);
+                                       (__nv_bfloat16*)sh->d_lana, d_jmin);
   FNL_CUDA(cudaGetLastError());
+  sh->jmin.assign(L + 1, 0);
+  FNL_CUDA(cudaMemcpyAsync(sh->jmin.data(), d_jmin, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st));
   FNL_CUDA(cudaStreamSynchronize(st));
+  for (int& j : sh->jmin) j = std::min(j, np);
 }
 
 void launch_filter_mixed(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,

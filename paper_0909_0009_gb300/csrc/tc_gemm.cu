@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         }
         prev_inst = tl.inst;
         const int nst = (tl.nkb + kTcSlabs - 1) / kTcSlabs;
-        for (int sg = 0; sg < nst; ++sg) {
+        for (int sg = tl.kb0 / kTcSlabs; sg < nst; ++sg) {
           if (!mbar_wait_fast(&empty[stage], phase ^ 1, a.err, 1)) {
             ok = false;
             break;
@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)acc * (uint32_t)(a.split ? 2 * a.cols : a.cols);
         const uint32_t idesc = idesc_bf16(tl.nsize);
-        const int nst = (tl.nkb + kTcSlabs - 1) / kTcSlabs;
-        for (int sg = 0; sg < nst; ++sg) {
+        const int nst = (tl.nkb + kTcSlabs - 1) / kTcSlabs, sg0 = tl.kb0 / kTcSlabs;
+        for (int sg = sg0; sg < nst; ++sg) {
           if (!mbar_wait_fast(&full[stage], phase, a.err, 3)) {
             ok = false;
             break;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           {
             const uint32_t so = (uint32_t)stage * (stageBytes >> 4);
             const uint64_t da = da0 + so, db = db0 + so;
-            const bool first = sg == 0;
+            const bool first = sg == sg0;
             const int nh = min(kTcSlabs, tl.nkb - kTcSlabs * sg);
             const uint32_t dc = d + (uint32_t)a.cols;
             if (a.nterms == 2) {
@@ -327,8 +327,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           }
           if (lane == 0) bulk_wait_read();  // the previous chunk's box has left the buffer
           __syncwarp();
+          // ring pairs below the tile's jz are written as zeros (their lambda are negligible)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) fst[j * 32 + lane] = v[j];  // box order: [16 ring pairs][32 c]
+          for (int j = 0; j < 16; ++j) fst[j * 32 + lane] = tl.n0 + ch * 16 + j < tl.jz ? 0.f : v[j];  // box order: [16 ring pairs][32 c]
           fence_proxy_async();
           __syncwarp();
           // a box that starts past the last ring pair holds no row: not issued (a box that

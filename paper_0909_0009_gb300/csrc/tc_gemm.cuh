@@ -12,9 +12,13 @@ enum TcMode { TC_SYNTH = 0, TC_ANA_QUAD = 1, TC_ANA_STORE = 2 };
 // One output tile: problem mp = 2 m + p, column tile c0 (multiple of 128), N range
 // [n0, n0 + nsize) (ring pairs for the synthesis, degrees k for the analysis), nkb
 // 32-deep k blocks, r0 = first row of the problem in the packed operand, kvalid = K_mp,
-// inst = the configuration (TcInst) the tile belongs to.
+// inst = the configuration (TcInst) the tile belongs to.  Ring pairs below the order's jmin
+// (where every |lambda_lm| < 2^-30) are left out: the synthesis writes their rows of F as
+// zeros (jz = jmin), and the analysis starts its k loop at the 32-deep block kb0 (the
+// 64-ring-pair stage holding jmin).
 struct TcTile {
   int mp, c0, n0, nsize, nkb, r0, kvalid, inst;
+  int jz, kb0;
 };
 
 // Operands arrive in stages 64 deep in k: one TMA box of A holding every BF16 term (per term
