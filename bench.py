@@ -723,15 +723,23 @@ def main():
     mult = {"bf16x2": 3, "bf16x3": 6}.get(args.prec, 1)
     flops_dir = legendre_flops(wl.lmax, wl.ntheta, wl.nr)
     gb = gemm_bytes(wl.lmax, wl.ntheta, wl.nr, nterm) if mixed else {}
+    # the tensor-core GEMMs leave out the polar ring pairs of negligible lambda: their executed
+    # share of the dense work (fnl_shells_gemm_work) scales the flops and the operand bytes
+    share = dict(zip(("synthesis_gemm", "analysis_gemm"), sh.gemm_work())) if mixed else {}
     real_bytes = 8 if args.prec == "fp64" else 4
     stages = {}
     for st_name, ms_ in per_stage.items():
         sec = ms_ / 1e3
         if st_name in ("synthesis_gemm", "analysis_gemm"):
             if mixed:
-                e = {"bound": "tensor", "achieved": flops_dir * mult / sec / 1e12, "peak": pk["bf16_tflops_sustained"],
-                     "unit": "TFLOP/s", "peak_source": f"bf16 sustained ({pk_kind}); executed = {mult} x useful flops",
-                     "hbm_frac": gb[st_name] / sec / 1e9 / pk["hbm_gbs"]}
+                sh_ = share[st_name]
+                e = {"bound": "tensor", "achieved": flops_dir * sh_ * mult / sec / 1e12,
+                     "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                     "peak_source": f"bf16 sustained ({pk_kind}); executed = {mult} x useful flops of the "
+                                    f"{sh_:.3f} share of the dense Legendre work the GEMM runs (the polar ring "
+                                    f"pairs where every |lambda_lm| < 2^-30 are left out)",
+                     "work_share": sh_, "dense_equivalent_tflops": flops_dir * mult / sec / 1e12,
+                     "hbm_frac": gb[st_name] * sh_ / sec / 1e9 / pk["hbm_gbs"]}
             elif args.prec == "fp32":
                 e = {"bound": "alu", "achieved": flops_dir / sec / 1e12, "peak": fma32, "unit": "TFLOP/s",
                      "peak_source": "FP32 FFMA rate (measured, fnl_measure_fma_peaks)"}

@@ -399,6 +399,15 @@ fnl_status fnl_shells_autotune(fnl_shells* sh, void* stream, int* nsyn, int* nan
  * Synchronises the device.  FNL_EINVAL for the SIMT forms. */
 fnl_status fnl_shells_set_tiles(fnl_shells* sh, int syn_cap, int ana_cap);
 
+/* Share of the dense Legendre work (sum over the problems (m, parity) of K_mp x npairs
+ * multiply-adds per column) that the tensor-core GEMMs execute with the current tiles: the
+ * GEMMs leave out, per order m, the polar ring pairs where every |lambda_lm| < 2^-30 (whole
+ * synthesis tiles, and the analysis's 64-ring-pair k stages below the first live ring pair), a
+ * standard SHT economy whose dropped terms stay below 1e-7 of the results.  *syn, *ana
+ * (nullable) receive the two shares in (0, 1].  FNL_EINVAL for the SIMT forms (they compute
+ * everything). */
+fnl_status fnl_shells_gemm_work(const fnl_shells* sh, double* syn, double* ana);
+
 /* ---- step (v) without any allocation ---------------------------------------------- */
 
 /* Largest (lmax + 1) * nr that fnl_accumulate_noalloc accepts. */

@@ -519,6 +519,21 @@ fnl_status fnl_shells_autotune(fnl_shells* sh, void* stream, int* nsyn, int* nan
   });
 }
 
+fnl_status fnl_shells_gemm_work(const fnl_shells* sh, double* syn, double* ana) {
+  return guard([&] {
+    check_shells(sh);
+    FNL_REQUIRE(sh->nterms, "the SIMT forms compute every ring pair");
+    const int np = sh->npairs, ctiles = sh->Cpad / 128;
+    double dense = 0.0, s = 0.0, a = 0.0;
+    for (int K : sh->K) dense += (double)K * np;
+    for (const TcTile& t : sh->tiles_syn_h) s += (double)t.kvalid * std::min(t.nsize, np - t.n0);
+    for (const TcTile& t : sh->tiles_ana_h)
+      a += (double)std::min(t.nsize, t.kvalid - t.n0) * std::max(0, np - 32 * t.kb0);
+    if (syn) *syn = dense > 0 ? s / ctiles / dense : 1.0;
+    if (ana) *ana = dense > 0 ? a / ctiles / dense : 1.0;
+  });
+}
+
 fnl_status fnl_shells_set_tiles(fnl_shells* sh, int syn_cap, int ana_cap) {
   return guard([&] {
     check_shells(sh);

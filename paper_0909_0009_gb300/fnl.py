@@ -31,7 +31,7 @@ EXPORTS = [
     "fnl_maps_prepare", "fnl_maps", "fnl_ksw_create", "fnl_ksw_destroy", "fnl_ksw_info", "fnl_ksw_statistic",
     "fnl_quad_create", "fnl_quad_destroy", "fnl_quad_moments", "fnl_quad_greedy", "fnl_quad_fit", "fnl_quad_error",
     "fnl_make_shells_healpix", "fnl_shells_set_sm_limits", "fnl_test_fail_alloc", "fnl_test_wait_expiry",
-    "fnl_measure_fma_peaks", "fnl_make_shells_shard", "fnl_shells_shard",
+    "fnl_measure_fma_peaks", "fnl_make_shells_shard", "fnl_shells_shard", "fnl_shells_gemm_work",
 ]
 STAGES = ["filter", "synthesis_gemm", "ring_fft_square", "analysis_gemm", "quadrature"]
 
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fnl_shells_set_sm_limits.argtypes = [vp, i, i]
     lib.fnl_make_shells_shard.argtypes = [ctypes.POINTER(ShellDesc), i, i, i, ctypes.POINTER(vp)]
     lib.fnl_shells_shard.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.fnl_shells_gemm_work.argtypes = [vp, dp, dp]
     for name in EXPORTS:
         if name not in ("fnl_version", "fnl_last_error", "fnl_shells_destroy", "fnl_batch_destroy", "fnl_ksw_destroy",
                         "fnl_quad_destroy"):
@@ -316,6 +317,13 @@ class Shells:
 
     def set_tiles(self, syn_cap: int, ana_cap: int):
         _check(_lib.fnl_shells_set_tiles(self.handle, int(syn_cap), int(ana_cap)))
+
+    def gemm_work(self) -> tuple[float, float]:
+        """fnl_shells_gemm_work: the shares of the dense Legendre work the synthesis and the
+        analysis GEMMs execute (the polar ring pairs of negligible lambda are left out)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.fnl_shells_gemm_work(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     # -- tensors
     def _alm(self, n=None):

@@ -244,3 +244,25 @@ def test_sm_limits_change_no_result(F):
     sh.set_sm_limits(0, 0)
     with pytest.raises(F.FnlError):
         sh.set_sm_limits(-1, 0)
+
+
+def test_gemm_work_shares(F):
+    """fnl_shells_gemm_work: on an exact l_max 512 grid the tensor-core GEMMs leave out part of
+    the polar ring pairs (both shares below 1); other synthesis tiles skip other whole tiles and
+    leave the analysis's share alone; the SIMT forms compute everything and refuse the call."""
+    lmax, nr, nt, nph = 512, 16, 769, 1600
+    r, w = W.radial_grid(nr)
+    aT, aE = W.transfer_kernels(lmax, r)
+    K = W.random_lower_filters(lmax, nr, seed=3, scale=8e-5)
+    sh = F.Shells(lmax, nr, nt, nph, r, w, aT, aE, K=K, prec="bf16x2")
+    sh.set_tiles(112, 128)
+    syn, ana = sh.gemm_work()
+    assert 0.6 < syn < 0.99 and 0.6 < ana < 0.99, (syn, ana)
+    sh.set_tiles(256, 128)
+    syn2, ana2 = sh.gemm_work()
+    assert 0.6 < syn2 <= 1.0 and ana2 == ana, (syn2, ana2)
+    sh.close()
+    d = F.Shells(lmax, nr, nt, nph, r, w, aT, aE, K=K, prec="fp32")
+    with pytest.raises(F.FnlError):
+        d.gemm_work()
+    d.close()
