@@ -389,6 +389,7 @@ fnl_shells* clone_scratch(const fnl_shells* src) {
   c->owner = src->owner ? src->owner : src;
   c->maps_ready = false;
   c->d_mapL = c->d_mapW = c->d_mapX = c->d_Fiqu = nullptr;
+  c->d_maps_jmin = nullptr;
   try {
     typedef unsigned short bf16_t;
     const int L = c->lmax, nr = c->nr, np = c->npairs, nmp = 2 * (L + 1), T = c->nterms, Cpad = c->Cpad;

@@ -236,6 +236,8 @@ struct fnl_shells {
   void* d_mapW = nullptr;
   void* d_mapX = nullptr;
   void* d_Fiqu = nullptr;
+  int* d_maps_jmin = nullptr;      // [L+1] first ring pair where some |lambda|, |W|, |X| of order m
+                                   // reaches the maps' bound (2^-30 FP32 tables, 2^-60 FP64)
 
   // HEALPix ring grid (nside > 0; FP64 and FP32 forms): ring pair j = ring j + 1 and its mirror
   int nside = 0;

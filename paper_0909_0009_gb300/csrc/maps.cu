@@ -39,11 +39,19 @@ __device__ __forceinline__ int64_t map_row(int m, int p, int k, int L) {
   return alm_idx(m, m, L) + (p ? (L - m + 2) / 2 : 0) + k;
 }
 
-// One thread per (jp, m): lambda, W, X for l = m..L into the three tables.
+// Ring pairs of an order m where every |lambda|, |W|, |X| stays below this bound (in the polar
+// cap where the functions of that order decay) are left out of the ring sums: 2^-30 for the
+// FP32 tables (the dropped terms stay below 1e-8 of the maps), 2^-60 for the FP64 ones.
+template <typename T>
+constexpr double maps_skip() { return sizeof(T) == 4 ? 0x1p-30 : 0x1p-60; }
+
+// One thread per (jp, m): lambda, W, X for l = m..L into the three tables; jmin[m] becomes the
+// first ring pair (from the pole) where one of them reaches maps_skip<T>().
 template <typename T>
 __global__ void k_maps_tables(const double* __restrict__ x, const double* __restrict__ mant,
                               const int* __restrict__ expo, const double2* __restrict__ ab, int npairs, int npj,
-                              int L, T* __restrict__ tl, T* __restrict__ tw, T* __restrict__ tx) {
+                              int L, T* __restrict__ tl, T* __restrict__ tw, T* __restrict__ tx,
+                              int* __restrict__ jmin) {
   const int jp = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (jp >= npairs) return;
@@ -51,6 +59,7 @@ __global__ void k_maps_tables(const double* __restrict__ x, const double* __rest
   double y1 = mant[(size_t)m * npairs + jp], y2 = 0.0;  // lam_l, lam_{l-1} (mantissas, shared exponent)
   int e = expo[(size_t)m * npairs + jp];
   const int64_t base = alm_idx(0, m, L);
+  double vmax = 0.0;
   for (int l = m; l <= L; ++l) {
     if (l > m) {
       const double2 c = ab[base + l];
@@ -73,10 +82,13 @@ __global__ void k_maps_tables(const double* __restrict__ x, const double* __rest
     }
     const int d = l - m;
     const int64_t o = map_row(m, d & 1, d >> 1, L) * npj + jp;
-    tl[o] = (T)flushed_d(ldexp(y1, e));
-    tw[o] = (T)flushed_d(ldexp(w, e));
-    tx[o] = (T)flushed_d(ldexp(xv, e));
+    const double vl = flushed_d(ldexp(y1, e)), vw = flushed_d(ldexp(w, e)), vx = flushed_d(ldexp(xv, e));
+    vmax = fmax(vmax, fmax(fabs(vl), fmax(fabs(vw), fabs(vx))));
+    tl[o] = (T)vl;
+    tw[o] = (T)vw;
+    tx[o] = (T)vx;
   }
+  if (vmax >= maps_skip<T>()) atomicMin(&jmin[m], jp);
 }
 
 // Stages the coefficients of m (three fields, l = m..L) into sa[3 (l - m) + field] as T.
@@ -122,14 +134,15 @@ constexpr int kMapsSlices = 4;   // k slices of a block: slice s sums k = s, s +
 constexpr int kMapsBatch = 4;    // k steps of a slice whose loads are issued together
 
 // Block (x, m): ring pairs x * 32 N .. of order m (N = 16 / sizeof(T) per thread), 128 threads =
-// 32 vectors x 4 k slices.  The coefficients of m are staged in shared memory as T; each thread
+// 32 vectors x 4 k slices.  A vector wholly below jmin[m] reads no table and writes zeros.  The coefficients of m are staged in shared memory as T; each thread
 // sums its slice of l for the even and odd parts of I_m, Q_m, U_m on its N ring pairs (in T),
 // loading the lambda, W, X rows of kMapsBatch steps before using them; slice 0 then adds the
 // other slices' sums in a fixed order and writes F.
 template <typename T>
 __global__ void __launch_bounds__(kMapsQ * kMapsSlices) k_maps_rings(
     const T* __restrict__ tl, const T* __restrict__ tw, const T* __restrict__ tx, int npairs, int npj, int L,
-    const double* __restrict__ aT, const double* __restrict__ aE, const double* __restrict__ aB, T* __restrict__ F) {
+    const double* __restrict__ aT, const double* __restrict__ aE, const double* __restrict__ aB,
+    const int* __restrict__ jmin, T* __restrict__ F) {
   constexpr int N = Vec16<T>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = blockIdx.y;
@@ -149,7 +162,7 @@ __global__ void __launch_bounds__(kMapsQ * kMapsSlices) k_maps_rings(
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int c = 0; c < 6; ++c) acc[j][p][c] = (T)0;
-  if (live) {
+  if (live && jp0 + N > jmin[m]) {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int Kp = (L - m - p + 2) / 2;
@@ -249,8 +262,10 @@ void build_tables(fnl_shells* sh) {
     launch_lambda_mm(sh->d_x, d_fac, np, L, d_mant, d_expo, 0);
     const size_t bytes = sizeof(T) * (size_t)sh->nalm * sh->npj;
     for (void* t : {sh->d_mapL, sh->d_mapW, sh->d_mapX}) FNL_CUDA(cudaMemset(t, 0, bytes));
+    FNL_CUDA(cudaMemset(sh->d_maps_jmin, 0x7f, sizeof(int) * (L + 1)));  // above any ring pair
     k_maps_tables<T><<<dim3((np + 127) / 128, L + 1), 128>>>(sh->d_x, d_mant, d_expo, d_ab, np, sh->npj, L,
-                                                             (T*)sh->d_mapL, (T*)sh->d_mapW, (T*)sh->d_mapX);
+                                                             (T*)sh->d_mapL, (T*)sh->d_mapW, (T*)sh->d_mapX,
+                                                             sh->d_maps_jmin);
     FNL_CUDA(cudaGetLastError());
     FNL_CUDA(cudaDeviceSynchronize());
   } catch (...) {
@@ -267,9 +282,9 @@ void maps_prepare(fnl_shells* sh) {
   const size_t ts = sh->real_is_double ? sizeof(double) : sizeof(float);
   const size_t tb = ts * (size_t)sh->nalm * sh->npj;
   const size_t fb = ts * (size_t)2 * (sh->lmax + 1) * sh->npairs * 6;
-  void* p[4] = {nullptr, nullptr, nullptr, nullptr};
-  const size_t sz[4] = {tb, tb, tb, fb};
-  for (int i = 0; i < 4; ++i) {
+  void* p[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const size_t sz[5] = {tb, tb, tb, fb, sizeof(int) * (size_t)(sh->lmax + 1)};
+  for (int i = 0; i < 5; ++i) {
     const cudaError_t e = cudaMalloc(&p[i], sz[i]);
     if (e != cudaSuccess) {
       for (int j = 0; j < i; ++j) cudaFree(p[j]);
@@ -281,7 +296,8 @@ void maps_prepare(fnl_shells* sh) {
   sh->d_mapW = p[1];
   sh->d_mapX = p[2];
   sh->d_Fiqu = p[3];
-  for (int i = 0; i < 4; ++i) {
+  sh->d_maps_jmin = (int*)p[4];
+  for (int i = 0; i < 5; ++i) {
     sh->allocations.push_back(p[i]);
     sh->device_bytes += sz[i];
   }
@@ -299,7 +315,8 @@ void maps_rings_impl(const fnl_shells* sh, const double* aT, const double* aE, c
   const size_t smem = sizeof(T) * (kMapsSlices - 1) * 12 * N * kMapsQ + sizeof(cplx<T>) * 3 * (size_t)(L + 1);
   FNL_CUDA(cudaFuncSetAttribute(k_maps_rings<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_maps_rings<T><<<dim3((nvec + kMapsQ - 1) / kMapsQ, L + 1), kMapsQ * kMapsSlices, smem, st>>>(
-      (const T*)sh->d_mapL, (const T*)sh->d_mapW, (const T*)sh->d_mapX, np, sh->npj, L, aT, aE, aB, (T*)sh->d_Fiqu);
+      (const T*)sh->d_mapL, (const T*)sh->d_mapW, (const T*)sh->d_mapX, np, sh->npj, L, aT, aE, aB,
+      sh->d_maps_jmin, (T*)sh->d_Fiqu);
   FNL_CUDA(cudaGetLastError());
 }
 
