@@ -784,6 +784,28 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       FNL_CUDA(cudaMemset(sh->d_F, 0, fg));
       FNL_CUDA(cudaMemset(sh->d_G, 0, fg));
       build_lambda_tables(sh, 0);
+      // with jmin known, the SIMT tile lists leave out the polar ring pairs of each order where
+      // every |lambda_lm| is negligible: synthesis row tiles wholly below jmin write zeros without
+      // a k step, and the analysis skips its 16-ring-pair k steps below jmin
+      {
+        std::vector<Tile> ts, ta;
+        const int ctiles = (C + 63) / 64;
+        for (int mp = 0; mp < nmp; ++mp) {
+          if (sh->K[mp] == 0) continue;
+          const int jz = sh->jmin[mp / 2];
+          const int kp = (sh->K[mp] + 15) / 16 * 16;
+          for (int rt = 0; rt < (np + 63) / 64; ++rt)  // zero tiles still write their zeros: the
+            for (int ct = 0; ct < ctiles; ++ct)       // adjoint's synthesis writes into G
+              ts.push_back({mp, rt, ct, (rt + 1) * 64 <= jz ? kp : 0});
+          for (int rt = 0; rt < (sh->K[mp] + 63) / 64; ++rt)
+            for (int ct = 0; ct < ctiles; ++ct) ta.push_back({mp, rt, ct, jz / 16 * 16});
+        }
+        FNL_REQUIRE(ts.size() <= (size_t)sh->n_tiles_syn && ta.size() <= (size_t)sh->n_tiles_ana, "tile lists");
+        FNL_CUDA(cudaMemcpy(sh->d_tiles_syn, ts.data(), sizeof(Tile) * ts.size(), cudaMemcpyHostToDevice));
+        FNL_CUDA(cudaMemcpy(sh->d_tiles_ana, ta.data(), sizeof(Tile) * ta.size(), cudaMemcpyHostToDevice));
+        sh->n_tiles_syn = (int)ts.size();
+        sh->n_tiles_ana = (int)ta.size();
+      }
       if (nside) setup_healpix(sh);
     } else {
       setup_mixed(sh, qT, qE);

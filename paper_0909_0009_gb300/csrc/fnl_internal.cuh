@@ -109,7 +109,10 @@ struct FftPlan {
 
 // Tile of a SIMT grouped GEMM: problem mp, row tile, column tile.
 struct Tile {
-  int mp, rt, ct, pad;
+  int mp, rt, ct;
+  int q0;  // first k of the tile's k loop: the analysis's first ring pair (a multiple of 16), past
+           // which the polar ring pairs of negligible lambda lie; a synthesis tile whose ring pairs
+           // all lie there gets the padded depth, runs no k step and writes zeros
 };
 
 // ---- the shells object ---------------------------------------------------------------

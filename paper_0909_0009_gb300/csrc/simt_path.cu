@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_synth_gemm(const Tile* __restrict_
   const T* B = phi + row0[mp] * C;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T acc[4][4] = {};
-  for (int k0 = 0; k0 < KP; k0 += BK) {
+  for (int k0 = t.q0; k0 < KP; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
       const int r = e >> 4, kk = e & 15;
       As[kk][r] = (j0 + r < npairs) ? A[(int64_t)(j0 + r) * KP + k0 + kk] : (T)0;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) k_analysis_gemm(const Tile* __restri
   const T* B = G + (int64_t)mp * npairs * C;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T acc[4][4] = {};
-  for (int q0 = 0; q0 < npairs; q0 += BK) {
+  for (int q0 = t.q0; q0 < npairs; q0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
       const int kk = e >> 6, r = e & 63;
       As[kk][r] = (q0 + kk < npairs && k0 + r < KP) ? A[(int64_t)(q0 + kk) * KP + k0 + r] : (T)0;

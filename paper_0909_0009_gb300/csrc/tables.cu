@@ -9,6 +9,7 @@
 // lambda_mm is carried as mantissa * 2^exponent so that sin(theta)^m never underflows,
 // and the l recurrence runs on mantissas with a shared exponent moved by 2^500 steps.
 // Values with |lambda| < 1e-290 are stored as exact zeros.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -39,13 +40,20 @@ __global__ void k_lambda_mm(const double* __restrict__ x, const double* __restri
 
 __device__ __forceinline__ double flushed(double v) { return fabs(v) < 1e-290 ? 0.0 : v; }
 
+// Ring pairs of an order where every |lambda_lm| stays below this bound are left out of the SIMT
+// GEMMs: 2^-30 for the FP32 form (as the tensor-core forms), 2^-60 for the FP64 one (the dropped
+// terms stay far below its 1e-12 bar).
+template <typename T>
+constexpr double simt_skip() { return sizeof(T) == 4 ? 0x1p-30 : 0x1p-60; }
+
 // One thread per (jp, m); writes lambda_lm(x_jp) for l = m..L into the SIMT table
-// lam[lam0[mp] + jp * KP[mp] + k], l = m + p + 2k.
+// lam[lam0[mp] + jp * KP[mp] + k], l = m + p + 2k; jmin[m] becomes the first ring pair (from
+// the pole) where some |lambda_lm| reaches simt_skip<T>().
 template <typename T>
 __global__ void k_lambda_table(const double* __restrict__ x, const double* __restrict__ mant,
                                const int* __restrict__ expo, const double2* __restrict__ ab,
                                const int64_t* __restrict__ lam0, const int* __restrict__ K, int npairs,
-                               int L, T* __restrict__ lam) {
+                               int L, T* __restrict__ lam, int* __restrict__ jmin) {
   const int jp = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (jp >= npairs) return;
@@ -55,6 +63,7 @@ __global__ void k_lambda_table(const double* __restrict__ x, const double* __res
   const int KP0 = (K[2 * m] + 15) / 16 * 16, KP1 = (K[2 * m + 1] + 15) / 16 * 16;
   T* row0 = lam + lam0[2 * m] + (int64_t)jp * KP0;
   T* row1 = lam + lam0[2 * m + 1] + (int64_t)jp * KP1;
+  double vmax = fabs(flushed(ldexp(y1, e)));
   row0[0] = (T)flushed(ldexp(y1, e));
   const int64_t base = alm_idx(0, m, L);
   for (int l = m + 1; l <= L; ++l) {
@@ -67,11 +76,14 @@ __global__ void k_lambda_table(const double* __restrict__ x, const double* __res
       y2 *= 0x1p-500;
       e += 500;
     }
-    const T v = (T)flushed(ldexp(y1, e));
+    const double vd = flushed(ldexp(y1, e));
+    vmax = fmax(vmax, fabs(vd));
+    const T v = (T)vd;
     const int d = l - m;
     if (d & 1) row1[d >> 1] = v;
     else row0[d >> 1] = v;
   }
+  if (vmax >= simt_skip<T>()) atomicMin(&jmin[m], jp);
 }
 
 }  // namespace
@@ -108,15 +120,21 @@ void build_lambda_tables(fnl_shells* sh, cudaStream_t st) {
   FNL_CUDA(cudaGetLastError());
   const size_t tbytes = sh->real_is_double ? sizeof(double) : sizeof(float);
   FNL_CUDA(cudaMemsetAsync(sh->d_lam, 0, tbytes * (size_t)sh->lam_total, st));
+  TempDev t_jmin(sizeof(int) * (L + 1));
+  int* d_jmin = t_jmin.as<int>();
+  FNL_CUDA(cudaMemsetAsync(d_jmin, 0x7f, sizeof(int) * (L + 1), st));  // above any ring pair
   dim3 grid((np + 127) / 128, L + 1);
   if (sh->real_is_double)
     k_lambda_table<double><<<grid, 128, 0, st>>>(sh->d_x, d_mant, d_expo, d_ab, sh->d_lam0, sh->d_K, np, L,
-                                                 (double*)sh->d_lam);
+                                                 (double*)sh->d_lam, d_jmin);
   else
     k_lambda_table<float><<<grid, 128, 0, st>>>(sh->d_x, d_mant, d_expo, d_ab, sh->d_lam0, sh->d_K, np, L,
-                                                (float*)sh->d_lam);
+                                                (float*)sh->d_lam, d_jmin);
   FNL_CUDA(cudaGetLastError());
+  sh->jmin.assign(L + 1, 0);
+  FNL_CUDA(cudaMemcpyAsync(sh->jmin.data(), d_jmin, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st));
   FNL_CUDA(cudaStreamSynchronize(st));
+  for (int& j : sh->jmin) j = std::min(j, np);
 }
 
 }  // namespace fnl
