@@ -16,14 +16,28 @@ namespace {
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------------------
-// Step (i): one block per degree l (largest first); K_l and v^X_l staged in shared memory;
-// for every m <= l draw (or read) n_lm(r_j), write Phi_L,lm(r_i) = sum_{j<=i} K_l[i,j] n_j
-// into the internal [rows][C] buffer (and optionally the API layout), and a^X_L,lm = v . n.
-// The object's nr rows are the shells j0 .. j0 + nr - 1 of its configuration (j0 = 0 unless
-// it is a shell shard); they need the noise of shells 0 .. ncol - 1, ncol = j0 + nr, and the
-// staged K_l is [nr][ncol] (row i holds K_l[j0 + i][0 .. ncol)).
+// Step (i) in tiles: a block per (degree l = L - blockIdx.x, largest first, and 32 orders
+// m0 = 32 blockIdx.y ..).  K_l is staged with zeros right of the diagonal and v^X_l beside it;
+// the tile's noise n_lm(r_j) is drawn (or read) into a [ncol][64 columns (m, part)] tile; a warp
+// per order forms a^X_L,lm = v^X_l . n (FP64); and Phi_L,lm(r_i) = sum_{j <= j0 + i} K_l[j0 + i, j] n_j
+// is a register tile per thread: rows i = rg + 32 r (r < ROWS), 8 columns.  The object's nr rows
+// are the shells j0 .. j0 + nr - 1 of its configuration (j0 = 0 unless it is a shell shard); they
+// need the noise of shells 0 .. ncol - 1, ncol = j0 + nr, and the staged K_l is [nr][ncol] (row i
+// holds K_l[j0 + i][0 .. ncol)).  One block per degree with the orders in turn made the largest
+// degree's block the whole kernel's time (4 ms at l_max 512 in FP32).
 // ---------------------------------------------------------------------------------------
+constexpr int kFlM = 32;            // orders per tile
+constexpr int kFlCols = 2 * kFlM;   // columns (m, part)
+constexpr int kFlMaxRows = 4;       // rows per thread: nr <= 128
 template <typename T>
+constexpr int fl_ldp() { return kFlCols + 16 / (int)sizeof(T); }  // noise tile row stride (16-byte aligned)
+
+template <typename T>
+size_t filter_smem(int nr, int ncol) {
+  return sizeof(double) * 2 * (size_t)ncol + sizeof(T) * ((size_t)ncol * fl_ldp<T>() + (size_t)nr * (ncol + 1));
+}
+
+template <typename T, int ROWS>
 __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, int j0, int ncol, const T* __restrict__ Kf,
                                                      const double* __restrict__ vT,
                                                      const double* __restrict__ vE, uint64_t seed,
@@ -31,63 +45,79 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, int j0, int 
                                                      const int64_t* __restrict__ row0, T* __restrict__ phi,
                                                      double* __restrict__ phi_api, double* __restrict__ aLT,
                                                      double* __restrict__ aLE) {
+  const int l = L - blockIdx.x, m0 = kFlM * blockIdx.y;
+  if (m0 > l) return;
+  const int nm = min(kFlM, l + 1 - m0);  // orders of this tile
   extern __shared__ __align__(16) unsigned char smem[];
-  const int l = L - blockIdx.x;
-  const int C = 2 * nr;
-  double2* ns = (double2*)smem;                   // [ncol] noise of the current (l, m)
-  double* vs = (double*)(ns + ncol);              // [2][ncol]
-  double* red = vs + 2 * ncol;                    // [4][kThreads / 32]
-  T* Ks = (T*)(red + 4 * (kThreads / 32));        // [nr][ncol + 1] (padded rows: no bank conflicts)
-  T* nt = Ks + (size_t)nr * (ncol + 1);           // [2][ncol] the noise in T (re, then im)
-  const int ldk = ncol + 1;
+  constexpr int ldp = fl_ldp<T>();
+  const int C = 2 * nr, ldk = ncol + 1;
+  double* vs = (double*)smem;                    // [2][ncol] v^T_l, v^E_l
+  T* P = (T*)(vs + 2 * ncol);                    // [ncol][ldp] the tile's noise, columns (m, part)
+  T* Ks = P + (size_t)ncol * ldp;                // [nr][ncol + 1] K_l rows, zero right of the diagonal
   const T* Kl = Kf + (size_t)l * nr * ncol;
-  for (int e = threadIdx.x; e < nr * ncol; e += kThreads) Ks[(e / ncol) * ldk + (e % ncol)] = Kl[e];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nr; i += kThreads / 32)
+    for (int j = lane; j < ncol; j += 32) Ks[i * ldk + j] = j <= j0 + i ? Kl[(size_t)i * ncol + j] : (T)0;
   for (int e = threadIdx.x; e < ncol; e += kThreads) {
     vs[e] = vT[(size_t)l * ncol + e];
     vs[ncol + e] = vE[(size_t)l * ncol + e];
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int m = 0; m <= l; ++m) {
-    const int64_t idx = alm_idx(l, m, L);
-    __syncthreads();
-    if (noise) {
-      for (int j = threadIdx.x; j < ncol; j += kThreads) {
-        double2 v = ((const double2*)noise)[(size_t)j * (size_t)(((int64_t)(L + 1) * (L + 2)) / 2) + idx];
-        if (m == 0) v.y = 0.0;
-        ns[j] = v;
-      }
-    } else {
-      // the FP64 form draws in FP64; the FP32 form through the FP32 Box-Muller of the mixed
-      // forms (the FP64 pipe of this part is far too slow for a transcendental per draw)
-      for (int jq = threadIdx.x; jq < (ncol + 3) / 4; jq += kThreads) {
+  // the tile's noise: work item (order, quad of shells)
+  const int nq = (ncol + 3) / 4;
+  for (int e = threadIdx.x; e < kFlM * nq; e += kThreads) {
+    const int ml = e / nq, jq = e % nq, m = m0 + ml;
+    T re[4] = {(T)0, (T)0, (T)0, (T)0}, im[4] = {(T)0, (T)0, (T)0, (T)0};
+    if (ml < nm) {
+      const int64_t idx = alm_idx(l, m, L);
+      if (noise) {
+        const int64_t nalm = ((int64_t)(L + 1) * (L + 2)) / 2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * jq + q;
+          if (j < ncol) {
+            const double2 v = ((const double2*)noise)[(size_t)j * nalm + idx];
+            re[q] = (T)v.x;
+            im[q] = m == 0 ? (T)0 : (T)v.y;
+          }
+        }
+      } else {
+        // the FP64 form draws in FP64; the FP32 form through the FP32 Box-Muller of the mixed
+        // forms (the FP64 pipe of this part is far too slow for a transcendental per draw)
         uint64_t w[4];
         noise_words(seed, real, idx, jq, w);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int j = 4 * jq + q;
-          if (j >= ncol) break;
           if (sizeof(T) == sizeof(double)) {
-            ns[j] = noise_value(box_muller(w[q]), m);
+            const double2 g = noise_value(box_muller(w[q]), m);
+            re[q] = (T)g.x;
+            im[q] = (T)g.y;
           } else {
             const float2 g = noise_value_f32(box_muller_f32(w[q]), m);
-            ns[j] = make_double2(g.x, g.y);
+            re[q] = (T)g.x;
+            im[q] = (T)g.y;
           }
         }
       }
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < ncol; j += kThreads) {
-      nt[j] = (T)ns[j].x;
-      nt[ncol + j] = (T)ns[j].y;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * jq + q;
+      if (j < ncol) {
+        P[(size_t)j * ldp + 2 * ml] = re[q];
+        P[(size_t)j * ldp + 2 * ml + 1] = im[q];
+      }
     }
-    // a^X_L = sum_j v^X_l[j] n_j  (FP64)
+  }
+  __syncthreads();
+  // a^X_L = sum_j v^X_l[j] n_j (FP64), a warp per order
+  for (int ml = warp; ml < nm; ml += kThreads / 32) {
     double tr = 0.0, ti = 0.0, er = 0.0, ei = 0.0;
-    for (int j = threadIdx.x; j < ncol; j += kThreads) {
-      const double2 n = ns[j];
-      tr += vs[j] * n.x;
-      ti += vs[j] * n.y;
-      er += vs[ncol + j] * n.x;
-      ei += vs[ncol + j] * n.y;
+    for (int j = lane; j < ncol; j += 32) {
+      const double nx = (double)P[(size_t)j * ldp + 2 * ml], ny = (double)P[(size_t)j * ldp + 2 * ml + 1];
+      tr += vs[j] * nx;
+      ti += vs[j] * ny;
+      er += vs[ncol + j] * nx;
+      ei += vs[ncol + j] * ny;
     }
     for (int o = 16; o; o >>= 1) {
       tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -96,35 +126,59 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, int j0, int 
       ei += __shfl_xor_sync(0xffffffffu, ei, o);
     }
     if (lane == 0) {
-      red[warp] = tr;
-      red[8 + warp] = ti;
-      red[16 + warp] = er;
-      red[24 + warp] = ei;
+      const int64_t idx = alm_idx(l, m0 + ml, L);
+      ((double2*)aLT)[idx] = make_double2(tr, ti);
+      ((double2*)aLE)[idx] = make_double2(er, ei);
     }
-    __syncthreads();  // nt complete
-    // Phi_L,lm(r_i) = sum_{j <= j0 + i} K_l[j0 + i, j] n_j
-    const int p = (l - m) & 1;
-    const int64_t row = row0[2 * m + p] + ((l - m) >> 1);
-    for (int c = threadIdx.x; c < C; c += kThreads) {
-      const int i = c >> 1, r = c & 1;
-      T acc = 0;
-      const T* Ki = Ks + (size_t)i * ldk;
-      const T* nj = nt + (r ? ncol : 0);
-      for (int j = 0; j <= j0 + i; ++j) acc += Ki[j] * nj[j];
-      phi[row * C + c] = acc;
-      if (phi_api) phi_api[((size_t)idx * nr + i) * 2 + r] = (double)acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        s0 += red[w];
-        s1 += red[8 + w];
-        s2 += red[16 + w];
-        s3 += red[24 + w];
+  }
+  // Phi_L: rows i = rg + 32 r, columns 8 cg .. 8 cg + 7; the row of largest i bounds j
+  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+  T acc[ROWS][8];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[r][q] = (T)0;
+  const int jend = min(ncol, j0 + rg + 32 * (ROWS - 1) + 1);
+  for (int j = 0; j < jend; ++j) {
+    T kv[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) kv[r] = rg + 32 * r < nr ? Ks[(rg + 32 * r) * ldk + j] : (T)0;
+    T pv[8];
+    {
+      const T* src = P + (size_t)j * ldp + 8 * cg;  // 8 consecutive values of a 16-byte aligned row
+      if constexpr (sizeof(T) == 4) {
+        const float4 u0 = ((const float4*)src)[0], u1 = ((const float4*)src)[1];
+        pv[0] = u0.x, pv[1] = u0.y, pv[2] = u0.z, pv[3] = u0.w, pv[4] = u1.x, pv[5] = u1.y, pv[6] = u1.z, pv[7] = u1.w;
+      } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const double2 u = ((const double2*)src)[h];
+          pv[2 * h] = u.x, pv[2 * h + 1] = u.y;
+        }
       }
-      ((double2*)aLT)[idx] = make_double2(s0, s1);
-      ((double2*)aLE)[idx] = make_double2(s2, s3);
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[r][q] += kv[r] * pv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int i = rg + 32 * r;
+    if (i >= nr) continue;
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      const int ml = (8 * cg + q) >> 1;
+      if (ml >= nm) continue;
+      const int m = m0 + ml;
+      const int64_t row = row0[2 * m + ((l - m) & 1)] + ((l - m) >> 1);
+      phi[row * C + 2 * i] = acc[r][q];
+      phi[row * C + 2 * i + 1] = acc[r][q + 1];
+      if (phi_api) {
+        double* o = phi_api + ((size_t)alm_idx(l, m, L) * nr + i) * 2;
+        o[0] = (double)acc[r][q];
+        o[1] = (double)acc[r][q + 1];
+      }
     }
   }
 }
@@ -371,12 +425,20 @@ template <typename T>
 void filter_impl(const fnl_shells* sh, uint64_t seed, uint64_t real, const double* noise, double* aLT,
                  double* aLE, double* phi_api, cudaStream_t st) {
   const int nr = sh->nr, ncol = sh->j0 + sh->nr;
-  const size_t smem = sizeof(double2) * ncol + sizeof(double) * 2 * ncol + sizeof(double) * 4 * (kThreads / 32) +
-                      sizeof(T) * (size_t)nr * (ncol + 1) + sizeof(T) * 2 * (size_t)ncol;
-  FNL_CUDA(cudaFuncSetAttribute(k_filter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_filter<T><<<sh->lmax + 1, kThreads, smem, st>>>(sh->lmax, nr, sh->j0, ncol, (const T*)sh->d_Kf, sh->d_vT,
-                                                    sh->d_vE, seed, real, noise, sh->d_row0, (T*)sh->d_phi,
-                                                    phi_api, aLT, aLE);
+  const size_t smem = filter_smem<T>(nr, ncol);
+  const dim3 grid(sh->lmax + 1, (sh->lmax + kFlM) / kFlM);  // (degree, order tile); tiles past l exit
+  auto run = [&](auto kern) {
+    FNL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, kThreads, smem, st>>>(sh->lmax, nr, sh->j0, ncol, (const T*)sh->d_Kf, sh->d_vT, sh->d_vE, seed,
+                                       real, noise, sh->d_row0, (T*)sh->d_phi, phi_api, aLT, aLE);
+  };
+  switch ((nr + 31) / 32) {
+    case 1: run(k_filter<T, 1>); break;
+    case 2: run(k_filter<T, 2>); break;
+    case 3: run(k_filter<T, 3>); break;
+    case kFlMaxRows: run(k_filter<T, kFlMaxRows>); break;
+    default: throw Error(FNL_EUNSUPPORTED, "the filter takes at most 128 shells");
+  }
   FNL_CUDA(cudaGetLastError());
 }
 
