@@ -108,6 +108,9 @@ struct FftPlan {
 };
 
 // Tile of a SIMT grouped GEMM: problem mp, row tile, column tile.
+// Output tiles of the SIMT Legendre GEMMs: kSimtBM rows (ring pairs or degrees) x kSimtBN
+// columns, kSimtBK-deep k steps.
+constexpr int kSimtBM = 128, kSimtBN = 64, kSimtBK = 8;
 struct Tile {
   int mp, rt, ct;
   int q0;  // first k of the tile's k loop: the analysis's first ring pair (a multiple of 16), past

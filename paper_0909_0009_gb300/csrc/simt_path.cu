@@ -184,9 +184,44 @@ __global__ void __launch_bounds__(kThreads) k_filter(int L, int nr, int j0, int 
 }
 
 // ---------------------------------------------------------------------------------------
-// Grouped SIMT GEMMs.  64 x 64 output tile, 16-deep k slices, 4 x 4 outputs per thread.
+// Grouped SIMT GEMMs.  128 x 64 output tile (kSimtBM x kSimtBN), 8-deep k steps, 8 x 4 outputs
+// per thread; the next step's operands are loaded into registers while the current one is
+// multiplied out of shared memory.  A tile's k loop starts at its q0 (see Tile).
 // ---------------------------------------------------------------------------------------
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BM = kSimtBM, BN = kSimtBN, BK = kSimtBK;
+static_assert(BM == 128 && BN == 64 && BK == 8 && kThreads == 256, "the thread layout below");
+
+// out[r][c] += sum_kk As[kk][r] Bs[kk][c] over one step, thread (tx, ty): rows 8 ty .. 8 ty + 7,
+// columns 4 tx .. 4 tx + 3 (16-byte aligned rows of the staged tiles)
+template <typename T>
+__device__ __forceinline__ void simt_step(const T (*As)[BM + 4], const T (*Bs)[BN + 4], int tx, int ty,
+                                          T (&acc)[8][4]) {
+#pragma unroll
+  for (int kk = 0; kk < BK; ++kk) {
+    T a[8], b[4];
+    if constexpr (sizeof(T) == 4) {
+      const float4 a0 = *(const float4*)&As[kk][8 * ty], a1 = *(const float4*)&As[kk][8 * ty + 4];
+      const float4 b0 = *(const float4*)&Bs[kk][4 * tx];
+      a[0] = a0.x, a[1] = a0.y, a[2] = a0.z, a[3] = a0.w, a[4] = a1.x, a[5] = a1.y, a[6] = a1.z, a[7] = a1.w;
+      b[0] = b0.x, b[1] = b0.y, b[2] = b0.z, b[3] = b0.w;
+    } else {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const double2 u = *(const double2*)&As[kk][8 * ty + 2 * h];
+        a[2 * h] = u.x, a[2 * h + 1] = u.y;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const double2 u = *(const double2*)&Bs[kk][4 * tx + 2 * h];
+        b[2 * h] = u.x, b[2 * h + 1] = u.y;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+}
 
 // F[mp][jp][c] = sum_k Lambda[mp][jp][k] Phi[mp][k][c]   (rows jp, columns c, depth k)
 template <typename T>
@@ -196,47 +231,50 @@ __global__ void __launch_bounds__(kThreads) k_synth_gemm(const Tile* __restrict_
                                                          const int64_t* __restrict__ row0,
                                                          const T* __restrict__ lam, const T* __restrict__ phi,
                                                          T* __restrict__ F, int npairs, int C) {
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  __shared__ __align__(16) T As[BK][BM + 4];
+  __shared__ __align__(16) T Bs[BK][BN + 4];
   const Tile t = tiles[blockIdx.x];
   const int mp = t.mp, j0 = t.rt * BM, c0 = t.ct * BN;
   const int KP = (K[mp] + 15) / 16 * 16;
   const T* A = lam + lam0[mp];
   const T* B = phi + row0[mp] * C;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][4] = {};
+  // loaders: A rows (2 threads a row, 4 consecutive k each), B 2 entries a thread
+  const int ar = threadIdx.x >> 1, ak = (threadIdx.x & 1) * 4;
+  const bool arow = j0 + ar < npairs;
+  T ra[4], rb[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ra[i] = arow ? A[(int64_t)(j0 + ar) * KP + k0 + ak + i] : (T)0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = threadIdx.x + kThreads * i, kk = e >> 6, cc = e & 63;
+      rb[i] = c0 + cc < C ? B[(int64_t)(k0 + kk) * C + c0 + cc] : (T)0;
+    }
+  };
+  T acc[8][4] = {};
+  if (t.q0 < KP) load(t.q0);
   for (int k0 = t.q0; k0 < KP; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
-      const int r = e >> 4, kk = e & 15;
-      As[kk][r] = (j0 + r < npairs) ? A[(int64_t)(j0 + r) * KP + k0 + kk] : (T)0;
-    }
-    for (int e = threadIdx.x; e < BN * BK; e += kThreads) {
-      const int kk = e >> 6, cc = e & 63;
-      Bs[kk][cc] = (c0 + cc < C) ? B[(int64_t)(k0 + kk) * C + c0 + cc] : (T)0;
-    }
-    __syncthreads();
+    __syncthreads();  // the previous step's tiles are consumed
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+    for (int i = 0; i < 4; ++i) As[ak + i][ar] = ra[i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    for (int i = 0; i < 2; ++i) {
+      const int e = threadIdx.x + kThreads * i;
+      Bs[e >> 6][e & 63] = rb[i];
     }
     __syncthreads();
+    if (k0 + BK < KP) load(k0 + BK);
+    simt_step<T>(As, Bs, tx, ty, acc);
   }
   T* out = F + (int64_t)mp * npairs * C;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = j0 + ty + 16 * i;
+  for (int i = 0; i < 8; ++i) {
+    const int r = j0 + 8 * ty + i;
     if (r >= npairs) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
+      const int c = c0 + 4 * tx + j;
       if (c < C) out[(int64_t)r * C + c] = acc[i][j];
     }
   }
@@ -250,8 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_analysis_gemm(const Tile* __restri
                                                             const int64_t* __restrict__ row0,
                                                             const T* __restrict__ lam, const T* __restrict__ G,
                                                             T* __restrict__ phi, int npairs, int C) {
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
+  __shared__ __align__(16) T As[BK][BM + 4];
+  __shared__ __align__(16) T Bs[BK][BN + 4];
   const Tile t = tiles[blockIdx.x];
   const int mp = t.mp, k0 = t.rt * BM, c0 = t.ct * BN;
   const int Km = K[mp];
@@ -259,39 +297,45 @@ __global__ void __launch_bounds__(kThreads) k_analysis_gemm(const Tile* __restri
   const T* A = lam + lam0[mp];
   const T* B = G + (int64_t)mp * npairs * C;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][4] = {};
+  // loaders: A a ring pair's 128 degrees per 32 threads (4 each), B 2 entries a thread
+  const int aq = threadIdx.x >> 5, ar = threadIdx.x & 31;
+  T ra[4], rb[2];
+  auto load = [&](int q0) {
+    const bool qv = q0 + aq < npairs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = ar + 32 * i;
+      ra[i] = qv && k0 + r < KP ? A[(int64_t)(q0 + aq) * KP + k0 + r] : (T)0;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = threadIdx.x + kThreads * i, kk = e >> 6, cc = e & 63;
+      rb[i] = q0 + kk < npairs && c0 + cc < C ? B[(int64_t)(q0 + kk) * C + c0 + cc] : (T)0;
+    }
+  };
+  T acc[8][4] = {};
+  if (t.q0 < npairs) load(t.q0);
   for (int q0 = t.q0; q0 < npairs; q0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
-      const int kk = e >> 6, r = e & 63;
-      As[kk][r] = (q0 + kk < npairs && k0 + r < KP) ? A[(int64_t)(q0 + kk) * KP + k0 + r] : (T)0;
-    }
-    for (int e = threadIdx.x; e < BN * BK; e += kThreads) {
-      const int kk = e >> 6, cc = e & 63;
-      Bs[kk][cc] = (q0 + kk < npairs && c0 + cc < C) ? B[(int64_t)(q0 + kk) * C + c0 + cc] : (T)0;
-    }
-    __syncthreads();
+    __syncthreads();  // the previous step's tiles are consumed
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+    for (int i = 0; i < 4; ++i) As[aq][ar + 32 * i] = ra[i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    for (int i = 0; i < 2; ++i) {
+      const int e = threadIdx.x + kThreads * i;
+      Bs[e >> 6][e & 63] = rb[i];
     }
     __syncthreads();
+    if (q0 + BK < npairs) load(q0 + BK);
+    simt_step<T>(As, Bs, tx, ty, acc);
   }
   T* out = phi + row0[mp] * C;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = k0 + ty + 16 * i;
+  for (int i = 0; i < 8; ++i) {
+    const int r = k0 + 8 * ty + i;
     if (r >= Km) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx + 16 * j;
+      const int c = c0 + 4 * tx + j;
       if (c < C) out[(int64_t)r * C + c] = acc[i][j];
     }
   }
