@@ -715,12 +715,12 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
 
     // ---- SIMT tile lists: synthesis (rows = ring pairs), analysis (rows = degrees)
     std::vector<Tile> ts_syn, ts_ana;
-    const int ctiles = (C + kSimtBN - 1) / kSimtBN;
+    const int ctiles = (C + kSimtBN - 1) / kSimtBN, bm = sh->real_is_double ? kSimtBM64 : kSimtBM;
     for (int mp = 0; mp < nmp; ++mp) {
       if (sh->K[mp] == 0) continue;
-      for (int rt = 0; rt < (np + kSimtBM - 1) / kSimtBM; ++rt)
+      for (int rt = 0; rt < (np + bm - 1) / bm; ++rt)
         for (int ct = 0; ct < ctiles; ++ct) ts_syn.push_back({mp, rt, ct, 0});
-      for (int rt = 0; rt < (sh->K[mp] + kSimtBM - 1) / kSimtBM; ++rt)
+      for (int rt = 0; rt < (sh->K[mp] + bm - 1) / bm; ++rt)
         for (int ct = 0; ct < ctiles; ++ct) ts_ana.push_back({mp, rt, ct, 0});
     }
     sh->n_tiles_syn = (int)ts_syn.size();
@@ -789,16 +789,16 @@ fnl_shells* make_shells_core(const fnl_shell_desc* d_in, int device, bool synth_
       // a k step, and the analysis skips its 16-ring-pair k steps below jmin
       {
         std::vector<Tile> ts, ta;
-        const int ctiles = (C + kSimtBN - 1) / kSimtBN;
+        const int ctiles = (C + kSimtBN - 1) / kSimtBN, bm = sh->real_is_double ? kSimtBM64 : kSimtBM;
         for (int mp = 0; mp < nmp; ++mp) {
           if (sh->K[mp] == 0) continue;
           const int jz = sh->jmin[mp / 2];
           const int kp = (sh->K[mp] + 15) / 16 * 16;
-          for (int rt = 0; rt < (np + kSimtBM - 1) / kSimtBM; ++rt)  // zero tiles still write their
-            for (int ct = 0; ct < ctiles; ++ct)                     // zeros: the adjoint's synthesis
-              ts.push_back({mp, rt, ct, (rt + 1) * kSimtBM <= jz ? kp : 0});  // writes into G
-          for (int rt = 0; rt < (sh->K[mp] + kSimtBM - 1) / kSimtBM; ++rt)
-            for (int ct = 0; ct < ctiles; ++ct) ta.push_back({mp, rt, ct, jz / kSimtBK * kSimtBK});
+          for (int rt = 0; rt < (np + bm - 1) / bm; ++rt)  // zero tiles still write their zeros:
+            for (int ct = 0; ct < ctiles; ++ct)           // the adjoint's synthesis writes into G
+              ts.push_back({mp, rt, ct, (rt + 1) * bm <= jz ? kp : 0});
+          for (int rt = 0; rt < (sh->K[mp] + bm - 1) / bm; ++rt)
+            for (int ct = 0; ct < ctiles; ++ct) ta.push_back({mp, rt, ct, jz / 16 * 16});
         }
         FNL_REQUIRE(ts.size() <= (size_t)sh->n_tiles_syn && ta.size() <= (size_t)sh->n_tiles_ana, "tile lists");
         FNL_CUDA(cudaMemcpy(sh->d_tiles_syn, ts.data(), sizeof(Tile) * ts.size(), cudaMemcpyHostToDevice));

@@ -108,9 +108,9 @@ struct FftPlan {
 };
 
 // Tile of a SIMT grouped GEMM: problem mp, row tile, column tile.
-// Output tiles of the SIMT Legendre GEMMs: kSimtBM rows (ring pairs or degrees) x kSimtBN
-// columns, kSimtBK-deep k steps.
-constexpr int kSimtBM = 128, kSimtBN = 64, kSimtBK = 8;
+// Output tiles of the SIMT Legendre GEMMs: kSimtBM rows (ring pairs or degrees; kSimtBM64 in
+// the FP64 form) x kSimtBN columns, kSimtBK-deep k steps; a tile's first k is a multiple of 16.
+constexpr int kSimtBM = 128, kSimtBM64 = 64, kSimtBN = 64, kSimtBK = 8;
 struct Tile {
   int mp, rt, ct;
   int q0;  // first k of the tile's k loop: the analysis's first ring pair (a multiple of 16), past

@@ -341,6 +341,121 @@ __global__ void __launch_bounds__(kThreads) k_analysis_gemm(const Tile* __restri
   }
 }
 
+// The FP64 form's SIMT GEMMs: 64 x 64 output tiles, 16-deep k slices, 4 x 4 outputs per thread.
+// The FP64 pipe bounds them, and the 128-row tiles' padding (a 385-ring-pair grid fills four
+// of them) cost it more than their reuse saved: 57.5 against 51.9 ms per realisation at l_max
+// 512 in FP64.
+constexpr int BM64 = kSimtBM64, BN64 = 64, BK64 = 16;
+
+// F[mp][jp][c] = sum_k Lambda[mp][jp][k] Phi[mp][k][c]   (rows jp, columns c, depth k)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_synth_gemm64(const Tile* __restrict__ tiles,
+                                                         const int* __restrict__ K,
+                                                         const int64_t* __restrict__ lam0,
+                                                         const int64_t* __restrict__ row0,
+                                                         const T* __restrict__ lam, const T* __restrict__ phi,
+                                                         T* __restrict__ F, int npairs, int C) {
+  __shared__ T As[BK64][BM64 + 1];
+  __shared__ T Bs[BK64][BN64 + 1];
+  const Tile t = tiles[blockIdx.x];
+  const int mp = t.mp, j0 = t.rt * BM64, c0 = t.ct * BN64;
+  const int KP = (K[mp] + 15) / 16 * 16;
+  const T* A = lam + lam0[mp];
+  const T* B = phi + row0[mp] * C;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4] = {};
+  for (int k0 = t.q0; k0 < KP; k0 += BK64) {
+    for (int e = threadIdx.x; e < BM64 * BK64; e += kThreads) {
+      const int r = e >> 4, kk = e & 15;
+      As[kk][r] = (j0 + r < npairs) ? A[(int64_t)(j0 + r) * KP + k0 + kk] : (T)0;
+    }
+    for (int e = threadIdx.x; e < BN64 * BK64; e += kThreads) {
+      const int kk = e >> 6, cc = e & 63;
+      Bs[kk][cc] = (c0 + cc < C) ? B[(int64_t)(k0 + kk) * C + c0 + cc] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK64; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  T* out = F + (int64_t)mp * npairs * C;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = j0 + ty + 16 * i;
+    if (r >= npairs) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx + 16 * j;
+      if (c < C) out[(int64_t)r * C + c] = acc[i][j];
+    }
+  }
+}
+
+// Phi[mp][k][c] = sum_jp Lambda[mp][jp][k] G[mp][jp][c]   (rows k < K[mp], columns c, depth jp)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_analysis_gemm64(const Tile* __restrict__ tiles,
+                                                            const int* __restrict__ K,
+                                                            const int64_t* __restrict__ lam0,
+                                                            const int64_t* __restrict__ row0,
+                                                            const T* __restrict__ lam, const T* __restrict__ G,
+                                                            T* __restrict__ phi, int npairs, int C) {
+  __shared__ T As[BK64][BM64 + 1];
+  __shared__ T Bs[BK64][BN64 + 1];
+  const Tile t = tiles[blockIdx.x];
+  const int mp = t.mp, k0 = t.rt * BM64, c0 = t.ct * BN64;
+  const int Km = K[mp];
+  const int KP = (Km + 15) / 16 * 16;
+  const T* A = lam + lam0[mp];
+  const T* B = G + (int64_t)mp * npairs * C;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4] = {};
+  for (int q0 = t.q0; q0 < npairs; q0 += BK64) {
+    for (int e = threadIdx.x; e < BM64 * BK64; e += kThreads) {
+      const int kk = e >> 6, r = e & 63;
+      As[kk][r] = (q0 + kk < npairs && k0 + r < KP) ? A[(int64_t)(q0 + kk) * KP + k0 + r] : (T)0;
+    }
+    for (int e = threadIdx.x; e < BN64 * BK64; e += kThreads) {
+      const int kk = e >> 6, cc = e & 63;
+      Bs[kk][cc] = (q0 + kk < npairs && c0 + cc < C) ? B[(int64_t)(q0 + kk) * C + c0 + cc] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK64; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  T* out = phi + row0[mp] * C;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = k0 + ty + 16 * i;
+    if (r >= Km) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx + 16 * j;
+      if (c < C) out[(int64_t)r * C + c] = acc[i][j];
+    }
+  }
+}
+
 // (l, m) of triangle entry idx.
 __device__ __forceinline__ void lm_of(int64_t idx, int L, int& l, int& m) {
   // start(m) = m (2L + 1 - m) / 2 is increasing in m; solve and correct by one step.
@@ -496,7 +611,7 @@ void launch_filter(const fnl_shells* sh, uint64_t seed, uint64_t real, const dou
 
 void launch_synth_gemm(const fnl_shells* sh, cudaStream_t st) {
   if (sh->real_is_double)
-    k_synth_gemm<double><<<sh->n_tiles_syn, kThreads, 0, st>>>(sh->d_tiles_syn, sh->d_K, sh->d_lam0, sh->d_row0,
+    k_synth_gemm64<double><<<sh->n_tiles_syn, kThreads, 0, st>>>(sh->d_tiles_syn, sh->d_K, sh->d_lam0, sh->d_row0,
                                                               (const double*)sh->d_lam, (const double*)sh->d_phi,
                                                               (double*)sh->d_F, sh->npairs, sh->C);
   else
@@ -508,7 +623,7 @@ void launch_synth_gemm(const fnl_shells* sh, cudaStream_t st) {
 
 void launch_synth_gemm_to(const fnl_shells* sh, void* out, cudaStream_t st) {
   if (sh->real_is_double)
-    k_synth_gemm<double><<<sh->n_tiles_syn, kThreads, 0, st>>>(sh->d_tiles_syn, sh->d_K, sh->d_lam0, sh->d_row0,
+    k_synth_gemm64<double><<<sh->n_tiles_syn, kThreads, 0, st>>>(sh->d_tiles_syn, sh->d_K, sh->d_lam0, sh->d_row0,
                                                               (const double*)sh->d_lam, (const double*)sh->d_phi,
                                                               (double*)out, sh->npairs, sh->C);
   else
@@ -520,7 +635,7 @@ void launch_synth_gemm_to(const fnl_shells* sh, void* out, cudaStream_t st) {
 
 void launch_analysis_gemm(const fnl_shells* sh, cudaStream_t st) {
   if (sh->real_is_double)
-    k_analysis_gemm<double><<<sh->n_tiles_ana, kThreads, 0, st>>>(
+    k_analysis_gemm64<double><<<sh->n_tiles_ana, kThreads, 0, st>>>(
         sh->d_tiles_ana, sh->d_K, sh->d_lam0, sh->d_row0, (const double*)sh->d_lam, (const double*)sh->d_G,
         (double*)sh->d_phi, sh->npairs, sh->C);
   else
