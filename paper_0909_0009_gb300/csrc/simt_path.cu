@@ -1,7 +1,9 @@
 // SIMT kernels of the FP64 and FP32 forms of the path (real type T = double or float):
 //   k_filter        step (i), Eq. 9: Phi_L = K_l n per (l, m), with a^X_L = v^X_l . n (Eq. 5)
 //   k_synth_gemm    step (ii), Legendre half: per (m, parity) F = Lambda Phi over the northern rings
-//   k_analysis_gemm step (iv), Legendre half: per (m, parity) Phi = Lambda^T G
+//                   (FP32; k_synth_gemm64 for FP64)
+//   k_analysis_gemm step (iv), Legendre half: per (m, parity) Phi = Lambda^T G (FP32;
+//                   k_analysis_gemm64 for FP64)
 //   k_quadrature    step (v), Eq. 5 and Eq. 3, FP64 accumulation
 // plus the layout conversions used by the stage entry points.
 #include <cmath>
