@@ -345,7 +345,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         }
         continue;
       }
-      const int nch = (tl.nsize + 31) / 32;
+      // TC_ANA_STORE takes 32-column chunks; the quadrature takes 16-column half chunks, so that
+      // a 128-degree tile's eight halves spread 3, 3, 2 over a quadrant's three warps (whole
+      // chunks would spread 2, 1, 1)
+      const int cw = MODE == TC_ANA_STORE ? 32 : 16;
+      const int nch = (tl.nsize + cw - 1) / cw;
       const int last = nch - 1 < h ? -1 : h + (nch - 1 - h) / kEpiPerQuad * kEpiPerQuad;  // this warp's last chunk
       if (last < 0) {
         tc_fence_before();
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         if (lane == 0) mbar_arrive(&tempty[acc]);
       }
       for (int ch = h; ch < nch; ch += kEpiPerQuad) {
-        const uint32_t ta = tacc + (uint32_t)(ch * 32);
+        const uint32_t ta = tacc + (uint32_t)(ch * cw);
         if constexpr (MODE == TC_ANA_STORE) {
           float v[32];
           tmem_ld32(ta, v);
@@ -383,28 +387,27 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           continue;
         }
         // radial quadrature (Eq. 5): sum over the shells of this tile of q^X_l[i] Phi_NL,lm(r_i), in
-        // double-float.  The chunk (the warp's 32 columns = 16 shells x (re, im), by 32 degrees) is
-        // turned around through the warp's scratch 8 degrees at a time (element (d, col) at
-        // d 32 + (col ^ 2 d): no bank conflicts either way).  Lane (d, f, b) then sums, for degree d
-        // and field f (T, E), shells 8 b .. 8 b + 7 of the warp's 16, re and im, one after another:
-        // each product exactly as p + e (q = qh + ql: p = v qh rounded, e = its rounding error by
-        // fmaf plus v ql), the p's by error-free two-sums, the e's plainly; the two shell halves
-        // are joined across the lane pair at the end.  The weights of a half chunk (16 degrees)
-        // are requested together, right after its accumulator columns are read.
+        // double-float.  The half chunk (the warp's 32 columns = 16 shells x (re, im), by 16
+        // degrees) is turned around through the warp's scratch 8 degrees at a time (element
+        // (d, col) at d 32 + (col ^ 2 d): no bank conflicts either way).  Lane (d, f, b) then sums,
+        // for degree d and field f (T, E), shells 8 b .. 8 b + 7 of the warp's 16, re and im, one
+        // after another: each product exactly as p + e (q = qh + ql: p = v qh rounded, e = its
+        // rounding error by fmaf plus v ql), the p's by error-free two-sums, the e's plainly; the
+        // two shell halves are joined across the lane pair at the end.  The weights of the 16
+        // degrees are requested together, right after the accumulator columns are read.
         const int s0 = (tl.c0 >> 1) + 16 * q;  // shell of the warp's first column
         const int d = lane >> 2, f = (lane >> 1) & 1, b = lane & 1;
         float* scr = red + (size_t)4 * a.nmax * 8 + (size_t)(warp - 2) * 256;
-#pragma unroll 1
-        for (int hf = 0; hf < 2; ++hf) {
+        {
           float v[16];
-          tmem_ld16(ta + (uint32_t)(16 * hf), v);
+          tmem_ld16(ta, v);
           if (a.split) {
             float w[16];
-            tmem_ld16(ta + (uint32_t)(16 * hf) + (uint32_t)a.cols, w);
+            tmem_ld16(ta + (uint32_t)a.cols, w);
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] += w[j];
           }
-          if (ch == last && hf == 1) {
+          if (ch == last) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
           float4 qq[2][4];  // [sub-block][shell pair]: (qh, ql) of two shells
 #pragma unroll
           for (int sb = 0; sb < 2; ++sb) {
-            const int jj = ch * 32 + hf * 16 + sb * 8 + d;
+            const int jj = ch * 16 + sb * 8 + d;
             const int k = tl.n0 + jj;
             const bool dvalid = jj < tl.nsize && k < tl.kvalid;
             const float4* qrow =
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
               hi = sum;
               li += oli + err;
             }
-            const int jj = ch * 32 + hf * 16 + sb * 8 + d;  // degree column within the tile
+            const int jj = ch * 16 + sb * 8 + d;  // degree column within the tile
             if (jj < tl.nsize) {
               // lane b = 0 writes re, lane b = 1 im: red[q][jj][f][part][hi, lo]
               float* o = red + (size_t)q * (a.nmax * 8) + (size_t)jj * 8 + f * 4 + b * 2;
@@ -473,14 +476,26 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_tc_gemm(const __grid_constant
         for (int n = tid; n < tl.nsize; n += 32 * kEpiWarps) {
           const int k = tl.n0 + n;
           if (k >= tl.kvalid) continue;
-          // the four quadrants' double-float partials, summed in FP64
-          double s[4] = {0.0, 0.0, 0.0, 0.0};  // T re, T im, E re, E im
+          // the four quadrants' double-float partials, summed as double-float (high parts by
+          // error-free two-sums, low parts and rounding errors plainly) and widened to FP64 once
+          // per value: 3 operations of the FP64 pipe per value instead of 16
+          float sh[4], sl[4];  // T re, T im, E re, E im
 #pragma unroll
-          for (int w = 0; w < 4; ++w) {
+          for (int f = 0; f < 4; ++f) sh[f] = red[(size_t)n * 8 + 2 * f], sl[f] = red[(size_t)n * 8 + 2 * f + 1];
+#pragma unroll
+          for (int w = 1; w < 4; ++w) {
             const float* rw = red + (size_t)w * (a.nmax * 8) + (size_t)n * 8;
 #pragma unroll
-            for (int f = 0; f < 4; ++f) s[f] += (double)rw[2 * f] + (double)rw[2 * f + 1];
+            for (int f = 0; f < 4; ++f) {
+              float sum, err;
+              two_sum(sh[f], rw[2 * f], sum, err);
+              sh[f] = sum;
+              sl[f] += err + rw[2 * f + 1];
+            }
           }
+          double s[4];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) s[f] = (double)sh[f] + (double)sl[f];
           const int l = m + p + 2 * k;
           double2* dst = I.part + ((size_t)(tl.c0 >> 7) * I.nalm + alm_idx(l, m, L)) * 2;
           dst[0] = make_double2(s[0], s[1]);
