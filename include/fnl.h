@@ -388,7 +388,7 @@ fnl_status fnl_generate_batch(fnl_batch* b, const uint64_t* seeds, const uint64_
 
 /* Autotuner of the tensor-core forms: times whole realisations (one warm-up and two timed,
  * CUDA events on `stream`) for each candidate tile shape of the two Legendre GEMMs --
- * synthesis tiles of up to 256 or 128 ring pairs, analysis tiles of up to 256 or 128
+ * synthesis tiles of up to 256 or 128 ring pairs, analysis tiles of up to 256, 128 or 96
  * degrees -- and keeps the fastest.  The shape changes no result (every output sums its
  * k blocks in the same order).  *nsyn, *nana (nullable) receive the chosen widths (64 for
  * the SIMT forms, whose tiles are fixed and which this call leaves alone).  Synchronous. */

@@ -478,8 +478,10 @@ fnl_status fnl_shells_autotune(fnl_shells* sh, void* stream, int* nsyn, int* nan
     if (sh->nterms) {
       // candidates: 256-wide tiles (half the MMA instructions, one accumulator set) and
       // 128-wide tiles (two accumulator sets: the epilogue of one tile overlaps the MMAs of
-      // the next), for each GEMM; every candidate timed on whole realisations
-      const int caps[2] = {256, 128};
+      // the next), for each GEMM, and 96-degree analysis tiles (the quadrature epilogue's six
+      // 16-degree half chunks fall two to each of a quadrant's three warps); every candidate
+      // timed on whole realisations
+      const int caps[2] = {256, 128}, acaps[3] = {256, 128, 96};
       cudaEvent_t e0, e1;
       FNL_CUDA(cudaEventCreate(&e0));
       FNL_CUDA(cudaEventCreate(&e1));
@@ -487,7 +489,7 @@ fnl_status fnl_shells_autotune(fnl_shells* sh, void* stream, int* nsyn, int* nan
       int bs = 256, ba = 256;
       try {
         for (int cs : caps)
-          for (int ca : caps) {
+          for (int ca : acaps) {
             FNL_CUDA(cudaStreamSynchronize(st));
             configure_tc(sh, cs, ca);
             run_generate(sh, 0, 0, 1.0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, st, false);

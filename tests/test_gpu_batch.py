@@ -140,11 +140,11 @@ def test_batch_rejects_bad_arguments(F):
 def test_tile_shapes_change_no_result(F, lmax, nr):
     s = make(F, lmax, nr)
     ref = singles([s], [5], [1], [25.0])
-    for syn, ana in ((64, 64), (112, 256), (256, 128), (128, 128)):
+    for syn, ana in ((64, 64), (112, 256), (256, 128), (128, 128), (112, 96)):
         s.set_tiles(syn, ana)
         assert_same([tuple(s.generate(5, 1, 25.0, parts=False)[k] for k in ("aT", "aE"))], ref)
     nsyn, nana = s.autotune()
-    assert 64 <= nsyn <= 256 and nana in (128, 256)
+    assert 64 <= nsyn <= 256 and nana in (96, 128, 256)
     assert_same([tuple(s.generate(5, 1, 25.0, parts=False)[k] for k in ("aT", "aE"))], ref)
     with pytest.raises(F.FnlError):
         s.set_tiles(40, 128)
