@@ -26,8 +26,9 @@
 //               correction products accumulate in two TMEM accumulators (`cols` apart); the
 //               accumulator sets that fit (1 for 256-wide tiles, 2 for 128) rotate over tiles
 //   warps 2-13  epilogue, three warps per TMEM lane quadrant taking turns over the tile's
-//               column chunks (16 columns for the synthesis, 32 for the analysis; more warps
-//               keep more F stores in flight): tcgen05.ld of the accumulator, then per mode:
+//               column chunks (16 columns for the synthesis and the quadrature, 32 for the
+//               per-shell coefficients; more warps keep more F stores in flight): tcgen05.ld
+//               of the accumulator, then per mode:
 //               synthesis -> F (FP32); analysis -> radial quadrature of Eq. 5 reduced over
 //               the shells of the tile (T and E), or the per-shell coefficients.
 // Every mbarrier wait is bounded; on expiry the kernel records an error code and unwinds.
@@ -49,7 +50,7 @@ namespace {
 __constant__ CUtensorMap c_tc_maps[kTcMaxInst * 3];
 
 constexpr int kEpiWarps = 12;                // per TMEM lane quadrant kEpiPerQuad warps take turns
-constexpr int kEpiPerQuad = kEpiWarps / 4;  // over a tile's 32-column chunks
+constexpr int kEpiPerQuad = kEpiWarps / 4;  // over a tile's column chunks
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, A MN-major, B K-major, M = 128.
