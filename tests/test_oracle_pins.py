@@ -354,6 +354,46 @@ def _small_setup(L=12, nr=6, seed=3):
     return r, w, aT, aE, K, O.Grid(L, nt, nph)
 
 
+def _radial_integral_errors(nr: int = 128, L: int = 7) -> tuple[float, float]:
+    """Step (v) against the radial integral a_lm = int dr r^2 Phi_lm(r) alpha_l(r) (Eq. 5 of
+    Sect. 2) in closed form, on the workload's midpoint rule over [R_MIN, R_MAX]:
+    - Phi_lm(r) = 1 + i and alpha_l(r) = c_l (a different constant per degree): the integral is
+      c_l (1 + i) (R_MAX^3 - R_MIN^3) / 3, which the midpoint rule misses by the known amount
+      -(R_MAX - R_MIN) h^2 / 12 per unit c_l (the error term of a quadratic);
+    - alpha_l(r) = c_l / r^2: the integral c_l (1 + i) (R_MAX - R_MIN), exact for the rule.
+    Returns the two largest relative errors over all (l, m)."""
+    r, w = W.radial_grid(nr)
+    h = (W.R_MAX - W.R_MIN) / nr
+    c = 1.0 + 0.37 * np.arange(L + 1)
+    l, _ = W.alm_lm(L)
+    phi = np.full((W.n_alm(L), nr), 1.0 + 1.0j)
+    a1 = O.radial_quadrature(phi, O.quadrature_weights(r, w, c[:, None] * np.ones((1, nr))))
+    i1 = c[l] * (1.0 + 1.0j) * ((W.R_MAX ** 3 - W.R_MIN ** 3) / 3.0 - (W.R_MAX - W.R_MIN) * h * h / 12.0)
+    a2 = O.radial_quadrature(phi, O.quadrature_weights(r, w, c[:, None] / (r * r)[None, :]))
+    i2 = c[l] * (1.0 + 1.0j) * (W.R_MAX - W.R_MIN)
+    return float(np.max(np.abs(a1 - i1) / np.abs(i1))), float(np.max(np.abs(a2 - i2) / np.abs(i2)))
+
+
+def test_radial_quadrature_integrates_the_r2_measure():
+    e1, e2 = _radial_integral_errors()
+    assert e1 < 1e-13 and e2 < 1e-13
+
+
+def test_planted_radial_quadrature_mistakes_are_caught(monkeypatch):
+    mod = O.fnl_oracle
+    orig_q, orig_rq = mod.quadrature_weights, mod.radial_quadrature
+    # the r^2 of the measure dropped
+    monkeypatch.setattr(mod, "quadrature_weights", lambda r, w, alpha: orig_q(r, w, alpha) / np.asarray(r) ** 2)
+    monkeypatch.setattr(O, "quadrature_weights", mod.quadrature_weights)
+    assert min(_radial_integral_errors()) > 1e-3
+    monkeypatch.undo()
+    # the weights of degree l applied to the coefficients of degree l + 1
+    monkeypatch.setattr(mod, "radial_quadrature", lambda phi, q: orig_rq(phi, np.roll(q, 1, axis=0)))
+    monkeypatch.setattr(O, "radial_quadrature", mod.radial_quadrature)
+    assert min(_radial_integral_errors()) > 1e-3
+    monkeypatch.undo()
+
+
 def test_linearity_in_fnl():
     r, w, aT, aE, K, g = _small_setup()
     n = O.philox_noise(12, 6, seed=1, realisation=0)
