@@ -448,6 +448,27 @@ def test_fnl0_linear_part_is_the_filtered_noise_projection():
     assert np.max(np.abs(out["aLT"] - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
+def test_planted_filter_mistakes_are_caught(monkeypatch):
+    """Step (i) with K_l transposed (Phi_L(r_i) = sum_j K_l[j, i] n(r_j)), or with the noise
+    of degree l filtered by K of degree l + 1, fails the f_NL = 0 projection pin above."""
+    def projection_pin_fails():
+        try:
+            test_fnl0_linear_part_is_the_filtered_noise_projection()
+        except AssertionError:
+            return True
+        return False
+
+    assert not projection_pin_fails()
+    mod = O.fnl_oracle
+    orig = mod.phi_linear
+    monkeypatch.setattr(mod, "phi_linear", lambda K, n: orig(np.transpose(K, (0, 2, 1)), n))
+    assert projection_pin_fails()
+    monkeypatch.undo()
+    monkeypatch.setattr(mod, "phi_linear", lambda K, n: orig(np.roll(K, 1, axis=0), n))
+    assert projection_pin_fails()
+    monkeypatch.undo()
+
+
 @pytest.mark.parametrize("parts", [[(0, 6)], [(0, 3), (3, 6)], [(0, 1), (1, 4), (4, 5), (5, 6)]])
 def test_shell_shards_sum_to_the_whole_recipe(parts):
     # Eq. 5 and Eq. 3 sum per-shell terms: shards partitioning the shells add up to the recipe
